@@ -1,0 +1,180 @@
+/*
+ * nb.h -- C ABI of libnb, a direct N-body block-step Hermite integrator whose
+ * hot path runs as hand-written CUDA kernels on one B300 (sm_103a).
+ *
+ * The method is the one the paper benchmarks (Berczik, Spurzem et al., "Up to
+ * 700k GPU cores, Kepler, and the Exascale future for simulations of star
+ * clusters around black holes"): direct summation of the Newtonian forces
+ * between all particles, individual hierarchical block time-steps, and Hermite
+ * integration of 4th, 6th and 8th order (abstract; "Codes description"), with
+ * the force evaluated either all in FP64 or in mixed FP32 + FP64 precision
+ * (captions of the speed figures for the K20 and C2050 cards).
+ *
+ * Units: G = 1.  Pair softening: eps_ij^2 = max(eps_i^2, eps_j^2).
+ *
+ * Conventions for every call:
+ *   - returns NB_OK (0) or a negative NB_ERR_* code; no C++ exception crosses
+ *     the ABI; nb_last_error(ctx) describes the last failure on that context;
+ *   - host arrays are float64, row-major [n][3] for vectors; they are copied,
+ *     never retained: the caller keeps ownership;
+ *   - device work is ordered on the context's stream (nb_set_stream); calls
+ *     that return values to the host synchronise that stream;
+ *   - a context belongs to the device that was current at nb_create and is
+ *     not thread safe: use one context per host thread.
+ */
+#ifndef NB_H
+#define NB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ codes */
+#define NB_OK 0
+#define NB_ERR_ARG (-1)          /* invalid argument or call order                 */
+#define NB_ERR_CUDA (-2)         /* a CUDA runtime call or kernel launch failed    */
+#define NB_ERR_NOT_SYNC (-3)     /* nb_energy with particles at different times    */
+#define NB_ERR_DT_UNDERFLOW (-4) /* a particle's time step fell below dt_min       */
+#define NB_ERR_TIMEOUT (-5)      /* a bounded device-side wait ran out             */
+#define NB_ERR_NAN (-6)          /* non-finite input or state                      */
+#define NB_ERR_NOMEM (-7)        /* device allocation failed                       */
+
+#define NB_FP64 0  /* every force operation in FP64                              */
+#define NB_MIXED 1 /* positions as double-single pairs, FP32 force chain,        */
+                   /* compensated (double-single) accumulation, FP64 outside    */
+
+typedef struct nb_ctx nb_ctx;
+
+/* -------------------------------------------------------------- lifetime */
+
+/* Route every device allocation of contexts created afterwards through
+ * alloc/free_ (for example a framework's caching allocator).  alloc must return
+ * device memory aligned to at least 256 bytes, or NULL on failure; free_ is
+ * called with the pointers alloc returned.  Pass NULL, NULL to restore
+ * cudaMalloc/cudaFree.  Process-wide; call before nb_create.                */
+int nb_set_allocator(void* (*alloc)(size_t bytes, void* user), void (*free_)(void* ptr, void* user),
+                     void* user);
+
+/* Create a context for n >= 1 particles integrated with the Hermite scheme of
+ * the given order (4, 6 or 8; abstract), uniform Plummer softening eps >= 0.
+ * Allocates the structure-of-arrays state in device memory.  Defaults:
+ * NB_MIXED, eta = 0.2, eta_s = 0.01, dt_max = 1/16, dt_min = 2^-40.       */
+int nb_create(nb_ctx** out, int64_t n, int order, double eps);
+
+/* Free every device and host resource of ctx.  NULL is ignored.            */
+void nb_destroy(nb_ctx* ctx);
+
+/* Message for the last failed call on ctx (or on nb_create when ctx is NULL). */
+const char* nb_last_error(const nb_ctx* ctx);
+
+/* Order later device work on this CUDA stream (a cudaStream_t); NULL = the
+ * legacy default stream.                                                   */
+int nb_set_stream(nb_ctx* ctx, void* cuda_stream);
+
+/* ------------------------------------------------------------ parameters */
+
+/* NB_FP64 or NB_MIXED (mixed fp32 + fp64 force, captions of the paper's speed
+ * figures).  Takes effect at the next nb_predict.                          */
+int nb_set_precision(nb_ctx* ctx, int mode);
+
+/* Per-particle softening eps_i (host [n], each >= 0) or NULL for the uniform
+ * eps of nb_create.  Pairs use max(eps_i^2, eps_j^2).  Call before
+ * nb_set_particles.                                                        */
+int nb_set_softening(nb_ctx* ctx, const double* eps_i);
+
+/* Time-step parameters: accuracy eta > 0, start-up eta_s > 0, maximum step
+ * dt_max (a power of two), minimum dt_min > 0 (smaller steps fail with
+ * NB_ERR_DT_UNDERFLOW).  Individual block steps are powers of two
+ * (abstract: "individual hierarchically block time-steps").               */
+int nb_set_params(nb_ctx* ctx, double eta, double eta_s, double dt_max, double dt_min);
+
+/* ------------------------------------------------------------- the method */
+
+/* Load masses m [n] (>= 0), positions x [n][3] and velocities v [n][3] (host)
+ * at t = 0, then start the integration: force with every particle active
+ * (acc, jerk, snap and, for order 8, crackle), start-up step
+ * eta_s |a| / |jerk| quantised to a power of two <= dt_max.               */
+int nb_set_particles(nb_ctx* ctx, const double* m, const double* x, const double* v);
+
+/* Block scheduler (abstract: individual hierarchical block time-steps).
+ * t_blk = min_i (t_i + dt_i); the active set is every i with
+ * t_i + dt_i == t_blk, in ascending index order, kept on the device for the
+ * next nb_force.  Writes *t_blk, *n_act and, if idx_out != NULL, the indices
+ * to idx_out (host, capacity n).                                          */
+int nb_next_block(nb_ctx* ctx, double* t_blk, int32_t* idx_out, int64_t* n_act);
+
+/* Predictor: advance every particle's position and velocity (and, for orders
+ * 6 and 8, acceleration; for 8, jerk) from its own time t_i to t by the
+ * Taylor series in the derivatives it holds, and write the j-particle store
+ * the force kernel reads.  t must be >= every t_i.                        */
+int nb_predict(nb_ctx* ctx, double t);
+
+/* Force: for each listed particle i, sum over all j != i of the Plummer-
+ * softened Newtonian acceleration and its time derivatives up to the order's
+ * needs, plus the potential ("Codes description": the GPUs compute the
+ * gravitational forces between particles).  active_idx: n_act distinct
+ * indices in [0, n), host or device memory (detected), or NULL to use the
+ * list of the last nb_next_block.  Must follow nb_predict.                 */
+int nb_force(nb_ctx* ctx, const int32_t* active_idx, int64_t n_act);
+
+/* Corrector and time step for the particles of the last nb_force: Hermite
+ * correction of order p, Hermite interpolation of the higher derivatives,
+ * new step by the generalised Aarseth criterion quantised to a power of two
+ * commensurate with the block time (abstract: 4th/6th/8th-order Hermite with
+ * hierarchical block steps).  Sets t_i to the predicted time.              */
+int nb_correct(nb_ctx* ctx);
+
+/* One block step: nb_next_block, nb_predict(t_blk), nb_force(NULL),
+ * nb_correct.  Optional outputs (NULL to skip).                           */
+int nb_block_step(nb_ctx* ctx, double* t_blk, int64_t* n_act);
+
+/* Block steps until the next block time would exceed t_end.  Optional
+ * outputs: blocks taken and pairwise interactions evaluated (n_act * n per
+ * block).                                                                  */
+int nb_step_until(nb_ctx* ctx, double t_end, int64_t* n_blocks, int64_t* n_interactions);
+
+/* Kinetic and potential energy, E = sum m v^2 / 2 - sum_{i<j} m_i m_j / R_ij,
+ * evaluated on the device in the context's precision.  Every particle must
+ * be at the same time (a synchronised block), else NB_ERR_NOT_SYNC.        */
+int nb_energy(nb_ctx* ctx, double* ekin, double* epot);
+
+/* -------------------------------------------------------- state exchange */
+
+/* Copy the state to host arrays (any may be NULL): x, v [n][3];
+ * d [n][6][3] = acc, jerk, snap, crackle, a^(4), a^(5) (unused ones zero);
+ * t, dt [n].  Synchronises.                                                */
+int nb_get_state(nb_ctx* ctx, double* x, double* v, double* d, double* t, double* dt);
+
+/* Replace the state from host arrays with the nb_get_state layout (all
+ * required; masses and softening are kept).  For checkpoint/restart.      */
+int nb_set_state(nb_ctx* ctx, const double* x, const double* v, const double* d, const double* t,
+                 const double* dt);
+
+/* Result of the last nb_force for its n_act particles, in list order (any
+ * output may be NULL): acc, jerk, snap, crackle [n_act][3], pot [n_act].
+ * Unused derivatives are zero.  Synchronises.                              */
+int nb_get_force(nb_ctx* ctx, double* acc, double* jerk, double* snap, double* crackle, double* pot);
+
+/* The predicted j-particle store of the last nb_predict, converted to double
+ * exactly as the force kernel sees it (mixed: hi + lo positions, FP32
+ * velocity/acc/jerk): xp, vp, ap, jp [n][3] (NULL to skip).  Synchronises. */
+int nb_get_predicted(nb_ctx* ctx, double* xp, double* vp, double* ap, double* jp);
+
+/* Kernel launch shape of the last nb_force: CTAs along i, j-splits, threads
+ * per CTA (any output may be NULL).                                       */
+int nb_get_launch(nb_ctx* ctx, int* i_tiles, int* j_splits, int* threads);
+
+/* Force the j-split count of later nb_force calls (0 = automatic).         */
+int nb_set_jsplit(nb_ctx* ctx, int j_splits);
+
+/* Library version string.                                                  */
+const char* nb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NB_H */

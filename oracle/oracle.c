@@ -319,25 +319,27 @@ int orc_interp(int mm, double h, const double* D0, const double* D1, double* out
 /*                       (sqrt(|a(p-3)||a(p-1)|) + |a(p-2)|)]^(1/(p-3))        */
 /* A zero denominator gives an unbounded step (limited by the quantiser).      */
 /* ------------------------------------------------------------------------- */
-static ld norm3(const double* p)
+/* The step decides an integer (a power of two), so it is taken in double, the
+   precision of the device path; the acc derivatives it reads are doubles. */
+static double norm3d(const double* p)
 {
-    return sqrtl((ld)p[0] * p[0] + (ld)p[1] * p[1] + (ld)p[2] * p[2]);
+    return sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
 }
 
 double orc_dt_criterion(int order, double eta, const double* D)
 {
-    ld n0 = norm3(D), n1 = norm3(D + 3), n2 = norm3(D + 6);
+    double n0 = norm3d(D), n1 = norm3d(D + 3), n2 = norm3d(D + 6);
     if (order == 4) {
-        ld n3 = norm3(D + 9);
-        ld num = n0 * n2 + n1 * n1, den = n1 * n3 + n2 * n2;
+        double n3 = norm3d(D + 9);
+        double num = n0 * n2 + n1 * n1, den = n1 * n3 + n2 * n2;
         if (!(den > 0)) return INFINITY;
-        return (double)sqrtl((ld)eta * num / den);
+        return sqrt(eta * num / den);
     }
     int p = order;
-    ld nlo = norm3(D + 3 * (p - 3)), nmid = norm3(D + 3 * (p - 2)), nhi = norm3(D + 3 * (p - 1));
-    ld num = sqrtl(n0 * n2) + n1, den = sqrtl(nlo * nhi) + nmid;
+    double nlo = norm3d(D + 3 * (p - 3)), nmid = norm3d(D + 3 * (p - 2)), nhi = norm3d(D + 3 * (p - 1));
+    double num = sqrt(n0 * n2) + n1, den = sqrt(nlo * nhi) + nmid;
     if (!(den > 0)) return INFINITY;
-    return (double)((ld)eta * powl(num / den, 1.0L / (p - 3)));
+    return eta * pow(num / den, 1.0 / (p - 3));
 }
 
 /* Largest power-of-two fraction of dt_max that is <= lim, then halved until   */
@@ -355,9 +357,9 @@ int orc_dt_quantise(double lim, double t1, double dt_max, double dt_min, double*
 /* Startup step at t = 0 (no history): eta_s |a| / |j|.                        */
 double orc_dt_startup(double eta_s, const double* a, const double* j)
 {
-    ld na = norm3(a), nj = norm3(j);
+    double na = norm3d(a), nj = norm3d(j);
     if (!(nj > 0)) return INFINITY;
-    return (double)((ld)eta_s * na / nj);
+    return eta_s * na / nj;
 }
 
 /* ------------------------------------------------------------------------- */
