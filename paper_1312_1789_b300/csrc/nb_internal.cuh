@@ -1,0 +1,202 @@
+// nb_internal.cuh -- shared definitions of libnb's CUDA sources (sm_103a).
+//
+// Device state is structure-of-arrays FP64 in HBM, padded to np = a multiple of
+// the force kernel's j tile:
+//   m[np], eps2[np]                 mass and squared softening
+//   x[3][np], v[3][np]              position, velocity   (component-major)
+//   d[6][3][np]                     acc, jerk, snap, crackle, a^(4), a^(5)
+//   t[np], dt[np]                   particle time and block step
+//   pot[np]                         potential of the last force
+// The predictor writes the j-particle store read by the force kernel, one
+// fixed-size record per particle (see the record layouts below).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nb.h"
+
+namespace nb {
+
+// j tile of the force kernel: records staged per bulk copy.
+constexpr int JT = 128;
+// threads (= i-particles) per force CTA.
+constexpr int FORCE_NT = 128;
+// stages of the force kernel's shared-memory ring.
+constexpr int NSTAGE = 3;
+// spin limit of a bounded mbarrier wait, in SM clock cycles (~2 s at 2 GHz).
+constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;
+
+// Record sizes in 16-byte words.
+// Mixed record (float4 words), 48 / 64 / 80 bytes for orders 4 / 6 / 8:
+//   w0 = (x_hi.xyz, m)   w1 = (x_lo.xyz, eps2)   w2 = (v.xyz, 0)
+//   w3 = (a.xyz, 0)      [order >= 6]            w4 = (jerk.xyz, 0) [order 8]
+// FP64 record (double2 words), 64 / 96 / 128 bytes:
+//   w0 = (x.x, x.y)  w1 = (x.z, m)  w2 = (v.x, v.y)  w3 = (v.z, eps2)
+//   w4 = (a.x, a.y)  w5 = (a.z, 0)  [order >= 6]
+//   w6 = (j.x, j.y)  w7 = (j.z, 0)  [order 8]
+__host__ __device__ constexpr int mixed_rw(int order) { return order == 4 ? 3 : order == 6 ? 4 : 5; }
+__host__ __device__ constexpr int fp64_rw(int order) { return order == 4 ? 4 : order == 6 ? 6 : 8; }
+// components of a force result: acc, jerk[, snap[, crackle]] x 3, then pot.
+__host__ __device__ constexpr int ncomp(int order) { return order == 0 ? 1 : 3 * (order / 2) + 1; }
+
+// Scalars shared between the scheduler, the kernels and the host.
+struct DevScalars {
+    long long n_act;  // size of the active list
+    double t_blk;     // block time
+    int status;       // first error raised by a kernel (NB_OK if none)
+    int pad;
+};
+
+__device__ __forceinline__ void raise_status(DevScalars* sc, int code)
+{
+    atomicCAS(&sc->status, NB_OK, code);
+}
+
+// ------------------------------------------------------------ bulk copies
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// One-dimensional TMA bulk copy global -> shared; completion is signalled on bar.
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of bar to complete, giving up after WAIT_LIMIT_CYCLES.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > WAIT_LIMIT_CYCLES) return false;
+    }
+    return true;
+}
+
+// ------------------------------------------------------ double-single sums
+// Error-free sum (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// (hi, lo) += x, compensated.
+__device__ __forceinline__ void ds_add(float& hi, float& lo, float x)
+{
+    float s, e;
+    two_sum(hi, x, s, e);
+    hi = s;
+    lo += e;
+}
+
+}  // namespace nb
+
+// ------------------------------------------------------------ the context
+struct nb_ctx {
+    int dev = 0;
+    int64_t n = 0;   // particles
+    int64_t np = 0;  // padded to a multiple of nb::JT
+    int order = 6;
+    int prec = NB_MIXED;
+    int pred_prec = -1;  // precision of the store written by the last predict
+    double eps = 0.0;
+    int pair_eps = 0;  // per-particle softening in use
+    double eta = 0.2, eta_s = 0.01, dt_max = 1.0 / 16, dt_min = 0x1p-40;
+    cudaStream_t stream = nullptr;
+    int jsplit_force = 0;
+    int sm_count = 148;
+
+    // state (FP64 SoA)
+    double *m = nullptr, *eps2 = nullptr, *x = nullptr, *v = nullptr, *d = nullptr;
+    double *t = nullptr, *dt = nullptr, *pot = nullptr;
+    // j-particle store
+    void* jstore = nullptr;
+    // scheduler
+    int32_t* act_idx = nullptr;   // [n] active list
+    int32_t* all_idx = nullptr;   // [n] 0..n-1
+    int32_t* chunk_cnt = nullptr; // per-chunk counts
+    int n_chunks = 0;
+    nb::DevScalars* sc = nullptr;
+    nb::DevScalars* h_sc = nullptr;  // pinned
+    double* red = nullptr;           // reduction scratch [red_len]
+    int red_len = 0;
+    double* h_red = nullptr;         // pinned, 4 doubles (energy sums, time range)
+    // force
+    int32_t* f_idx = nullptr;  // [n] list of the last force
+    int64_t f_n = 0;
+    double f_t = 0.0;
+    int f_order = 0;
+    double* partial = nullptr;  // j-split partial sums
+    size_t partial_cap = 0;     // doubles
+    double* F = nullptr;        // [ncomp][n] reduced force, list order
+    int have_particles = 0, have_pred = 0, have_force = 0;
+    double t_pred = 0.0;
+    int F_order = -1;           // order of the result held in F (-1: none)
+    int64_t F_n = 0;            // its list length
+    int64_t sched_n = 0;        // result of the last scheduler pass
+    double sched_t = 0.0;
+    int have_sched = 0;
+    int last_itiles = 0, last_jsplit = 0, last_threads = 0;
+    // allocator captured at creation
+    void* (*alloc_fn)(size_t, void*) = nullptr;
+    void (*free_fn)(void*, void*) = nullptr;
+    void* alloc_user = nullptr;
+    char err[512] = {0};
+};
+
+namespace nb {
+
+// Launchers (k_*.cu); each returns cudaGetLastError() of its launches.
+cudaError_t launch_sched(nb_ctx* c);
+cudaError_t launch_predict(nb_ctx* c, double t);
+cudaError_t launch_force(nb_ctx* c, int order, const int32_t* idx, int64_t n_act, int jsplit, int itiles);
+cudaError_t launch_force_reduce(nb_ctx* c, int order, const int32_t* idx, int64_t n_act, int jsplit);
+cudaError_t launch_correct(nb_ctx* c);
+cudaError_t launch_startup_store(nb_ctx* c, int order);
+cudaError_t launch_startup_dt(nb_ctx* c);
+cudaError_t launch_energy_sums(nb_ctx* c, int with_pot);
+int force_occupancy(nb_ctx* c, int order);
+int sched_grid(const nb_ctx* c);
+int sched_chunks(int64_t n);
+int energy_grid(const nb_ctx* c);
+
+}  // namespace nb
