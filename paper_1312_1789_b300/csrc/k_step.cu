@@ -1,0 +1,565 @@
+// k_step.cu -- the kernels around the force: block scheduler (K5), predictor
+// (K1), Hermite corrector + time step (K4), start-up and energy support.
+//
+// All of them read and write the FP64 structure-of-arrays state and are bound
+// by HBM bandwidth or by the (slow on this part) FP64 pipe, not by the FP32
+// pipe the force kernel saturates.
+#include <cmath>
+
+#include "nb_internal.cuh"
+
+namespace nb {
+
+// ===================================================================== K5
+// Block scheduler (abstract: individual hierarchical block time-steps):
+// t_blk = min_i (t_i + dt_i), active = {i : t_i + dt_i == t_blk} ascending.
+// Three passes, no atomics, deterministic:
+//   1. per-CTA minima -> red[]
+//   2. every chunk CTA reduces red[] to t_blk and counts its matches
+//   3. every chunk CTA adds the counts of the chunks before it and scatters
+//      its matches in index order using warp ballots and prefix sums.
+constexpr int SCHED_NT = 256;
+constexpr int SCHED_PER = 8;
+constexpr int SCHED_CHUNK = SCHED_NT * SCHED_PER;
+
+__device__ __forceinline__ double warp_min(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int warp_isum(int v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(SCHED_NT) k_sched_min(const double* __restrict__ t, const double* __restrict__ dt,
+                                                        int64_t n, double* __restrict__ red, DevScalars* sc)
+{
+    __shared__ double ws[SCHED_NT / 32];
+    double mn = INFINITY;
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * SCHED_NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * SCHED_NT) {
+        const double tn = t[i] + dt[i];
+        bad |= !(tn == tn);
+        mn = fmin(mn, tn);
+    }
+    if (bad) raise_status(sc, NB_ERR_NAN);
+    mn = warp_min(mn);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = mn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = ws[0];
+        for (int w = 1; w < SCHED_NT / 32; ++w) b = fmin(b, ws[w]);
+        red[blockIdx.x] = b;
+    }
+}
+
+__device__ double block_min_of(const double* red, int nred)
+{
+    __shared__ double ws[SCHED_NT / 32];
+    __shared__ double res;
+    double mn = INFINITY;
+    for (int k = threadIdx.x; k < nred; k += SCHED_NT) mn = fmin(mn, red[k]);
+    mn = warp_min(mn);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = mn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = ws[0];
+        for (int w = 1; w < SCHED_NT / 32; ++w) b = fmin(b, ws[w]);
+        res = b;
+    }
+    __syncthreads();
+    return res;
+}
+
+__global__ void __launch_bounds__(SCHED_NT) k_sched_count(const double* __restrict__ t, const double* __restrict__ dt,
+                                                          int64_t n, const double* __restrict__ red, int nred,
+                                                          int32_t* __restrict__ cnt, DevScalars* sc)
+{
+    __shared__ int wc[SCHED_NT / 32];
+    const double tb = block_min_of(red, nred);
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc->t_blk = tb;
+    const int64_t base = (int64_t)blockIdx.x * SCHED_CHUNK;
+    int c = 0;
+    for (int it = 0; it < SCHED_PER; ++it) {
+        const int64_t i = base + it * SCHED_NT + threadIdx.x;
+        if (i < n && t[i] + dt[i] == tb) ++c;
+    }
+    c = warp_isum(c);
+    if ((threadIdx.x & 31) == 0) wc[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int w = 0; w < SCHED_NT / 32; ++w) s += wc[w];
+        cnt[blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(SCHED_NT) k_sched_scatter(const double* __restrict__ t, const double* __restrict__ dt,
+                                                            int64_t n, const int32_t* __restrict__ cnt, int nchunks,
+                                                            int32_t* __restrict__ idx, DevScalars* sc)
+{
+    __shared__ int wtot[SCHED_NT / 32];
+    __shared__ int s_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // offset of this chunk = sum of the counts before it
+    int o = 0;
+    for (int k = threadIdx.x; k < (int)blockIdx.x; k += SCHED_NT) o += cnt[k];
+    o = warp_isum(o);
+    if (lane == 0) wtot[warp] = o;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int w = 0; w < SCHED_NT / 32; ++w) s += wtot[w];
+        s_base = s;
+    }
+    __syncthreads();
+    int base = s_base;
+    const double tb = sc->t_blk;
+    const int64_t c0 = (int64_t)blockIdx.x * SCHED_CHUNK;
+    for (int it = 0; it < SCHED_PER; ++it) {
+        __syncthreads();  // wtot reuse
+        const int64_t i = c0 + it * SCHED_NT + threadIdx.x;
+        const bool f = i < n && t[i] + dt[i] == tb;
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) wtot[warp] = __popc(bal);
+        __syncthreads();
+        int woff = 0, tot = 0;
+        for (int w = 0; w < SCHED_NT / 32; ++w) {
+            const int x = wtot[w];
+            if (w < warp) woff += x;
+            tot += x;
+        }
+        if (f) idx[base + woff + __popc(bal & ((1u << lane) - 1u))] = (int32_t)i;
+        base += tot;
+    }
+    if (blockIdx.x == nchunks - 1 && threadIdx.x == 0) sc->n_act = base;
+}
+
+int sched_grid(const nb_ctx* c)
+{
+    int g = c->sm_count * 2;
+    const int64_t need = (c->n + SCHED_NT - 1) / SCHED_NT;
+    if (need < g) g = (int)need;
+    return g < 1 ? 1 : g;
+}
+
+int sched_chunks(int64_t n) { return (int)((n + SCHED_CHUNK - 1) / SCHED_CHUNK); }
+
+cudaError_t launch_sched(nb_ctx* c)
+{
+    const int g = sched_grid(c);
+    const int nch = sched_chunks(c->n);
+    k_sched_min<<<g, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, c->red, c->sc);
+    k_sched_count<<<nch, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, c->red, g, c->chunk_cnt, c->sc);
+    k_sched_scatter<<<nch, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, c->chunk_cnt, nch, c->act_idx, c->sc);
+    return cudaGetLastError();
+}
+
+// ===================================================================== K1
+// Predictor: Taylor series of every particle from t_i to tp.
+//   orders 4, 6: x to the crackle term (dt^5), v to dt^4; order 6 also a to dt^3
+//   order 8: x to a^(5) (dt^7), v to dt^6, a to dt^5, jerk to dt^4
+// Writes the j-particle store in the requested precision; padding records
+// (i >= n) get m = 0 and eps2 = 1 so they contribute exactly zero.
+template <int ORDER, bool MIXED>
+__global__ void __launch_bounds__(256) k_predict(const double* __restrict__ m, const double* __restrict__ eps2,
+                                                 const double* __restrict__ x, const double* __restrict__ v,
+                                                 const double* __restrict__ d, const double* __restrict__ t,
+                                                 int64_t n, int64_t np, double tp, void* __restrict__ jstore)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    constexpr int RW = MIXED ? mixed_rw(ORDER) : fp64_rw(ORDER);
+    double xp[3] = {0, 0, 0}, vp[3] = {0, 0, 0}, ap[3] = {0, 0, 0}, jp[3] = {0, 0, 0};
+    double mi = 0.0, ei = 1.0;
+    if (i < n) {
+        mi = m[i];
+        ei = eps2[i];
+        const double h = tp - t[i];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double a0 = d[(0 * 3 + c) * np + i], j0 = d[(1 * 3 + c) * np + i];
+            const double s0 = d[(2 * 3 + c) * np + i], c0 = d[(3 * 3 + c) * np + i];
+            const double x0 = x[c * np + i], v0 = v[c * np + i];
+            if (ORDER == 8) {
+                const double d4 = d[(4 * 3 + c) * np + i], d5 = d[(5 * 3 + c) * np + i];
+                xp[c] = x0 + h * (v0 + h * (a0 * (1.0 / 2) + h * (j0 * (1.0 / 6) + h * (s0 * (1.0 / 24) +
+                        h * (c0 * (1.0 / 120) + h * (d4 * (1.0 / 720) + h * d5 * (1.0 / 5040)))))));
+                vp[c] = v0 + h * (a0 + h * (j0 * (1.0 / 2) + h * (s0 * (1.0 / 6) + h * (c0 * (1.0 / 24) +
+                        h * (d4 * (1.0 / 120) + h * d5 * (1.0 / 720))))));
+                ap[c] = a0 + h * (j0 + h * (s0 * (1.0 / 2) + h * (c0 * (1.0 / 6) + h * (d4 * (1.0 / 24) +
+                        h * d5 * (1.0 / 120)))));
+                jp[c] = j0 + h * (s0 + h * (c0 * (1.0 / 2) + h * (d4 * (1.0 / 6) + h * d5 * (1.0 / 24))));
+            } else {
+                xp[c] = x0 + h * (v0 + h * (a0 * (1.0 / 2) + h * (j0 * (1.0 / 6) + h * (s0 * (1.0 / 24) +
+                        h * c0 * (1.0 / 120)))));
+                vp[c] = v0 + h * (a0 + h * (j0 * (1.0 / 2) + h * (s0 * (1.0 / 6) + h * c0 * (1.0 / 24))));
+                ap[c] = a0 + h * (j0 + h * (s0 * (1.0 / 2) + h * c0 * (1.0 / 6)));
+            }
+        }
+    }
+    if (MIXED) {
+        float4* r = reinterpret_cast<float4*>(jstore) + (size_t)i * RW;
+        float hx[3], lx[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            hx[c] = __double2float_rn(xp[c]);
+            lx[c] = __double2float_rn(xp[c] - (double)hx[c]);
+        }
+        r[0] = make_float4(hx[0], hx[1], hx[2], (float)mi);
+        r[1] = make_float4(lx[0], lx[1], lx[2], (float)ei);
+        r[2] = make_float4((float)vp[0], (float)vp[1], (float)vp[2], 0.f);
+        if (ORDER >= 6) r[3] = make_float4((float)ap[0], (float)ap[1], (float)ap[2], 0.f);
+        if (ORDER >= 8) r[4] = make_float4((float)jp[0], (float)jp[1], (float)jp[2], 0.f);
+    } else {
+        double2* r = reinterpret_cast<double2*>(jstore) + (size_t)i * RW;
+        r[0] = make_double2(xp[0], xp[1]);
+        r[1] = make_double2(xp[2], mi);
+        r[2] = make_double2(vp[0], vp[1]);
+        r[3] = make_double2(vp[2], ei);
+        if (ORDER >= 6) {
+            r[4] = make_double2(ap[0], ap[1]);
+            r[5] = make_double2(ap[2], 0.0);
+        }
+        if (ORDER >= 8) {
+            r[6] = make_double2(jp[0], jp[1]);
+            r[7] = make_double2(jp[2], 0.0);
+        }
+    }
+}
+
+cudaError_t launch_predict(nb_ctx* c, double t)
+{
+    const int nt = 256;
+    const int nb = (int)((c->np + nt - 1) / nt);
+    const bool mixed = c->prec == NB_MIXED;
+#define NB_PRED(O)                                                                                       \
+    if (mixed)                                                                                           \
+        k_predict<O, true><<<nb, nt, 0, c->stream>>>(c->m, c->eps2, c->x, c->v, c->d, c->t, c->n, c->np, \
+                                                     t, c->jstore);                                      \
+    else                                                                                                 \
+        k_predict<O, false><<<nb, nt, 0, c->stream>>>(c->m, c->eps2, c->x, c->v, c->d, c->t, c->n,      \
+                                                      c->np, t, c->jstore);
+    if (c->order == 4) {
+        NB_PRED(4)
+    } else if (c->order == 6) {
+        NB_PRED(6)
+    } else {
+        NB_PRED(8)
+    }
+#undef NB_PRED
+    return cudaGetLastError();
+}
+
+// ===================================================================== K4
+// Quantised block step: the largest power of two <= min(lim, dt_max) that
+// divides t1 (all block times are dyadic, so the divisibility test is exact).
+__device__ double quantise_dt(double lim, double t1, double dt_max, double dt_min, DevScalars* sc)
+{
+    if (!(lim == lim)) {
+        raise_status(sc, NB_ERR_NAN);
+        return dt_max;
+    }
+    double dt;
+    if (lim >= dt_max) {
+        dt = dt_max;
+    } else if (lim < dt_min) {
+        raise_status(sc, NB_ERR_DT_UNDERFLOW);
+        return dt_min;
+    } else {
+        // clear the mantissa: 2^floor(log2(lim)) for a positive normal double
+        dt = __longlong_as_double(__double_as_longlong(lim) & 0xFFF0000000000000LL);
+    }
+    while (dt >= dt_min) {
+        const double q = t1 / dt;
+        if (q == floor(q)) break;
+        dt *= 0.5;
+    }
+    if (dt < dt_min) {
+        raise_status(sc, NB_ERR_DT_UNDERFLOW);
+        return dt_min;
+    }
+    return dt;
+}
+
+__device__ __forceinline__ double norm3(const double* p) { return sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]); }
+
+// Generalised Aarseth criterion from acc derivatives H[0..p-1] at t1:
+//   p = 4: sqrt(eta (|a||a2| + |a1|^2) / (|a1||a3| + |a2|^2))
+//   p = 6, 8: eta ((sqrt(|a||a2|) + |a1|) / (sqrt(|a(p-3)||a(p-1)|) + |a(p-2)|))^(1/(p-3))
+template <int ORDER>
+__device__ double dt_criterion(double eta, const double (*H)[3])
+{
+    const double n0 = norm3(H[0]), n1 = norm3(H[1]), n2 = norm3(H[2]);
+    if (ORDER == 4) {
+        const double n3 = norm3(H[3]);
+        const double num = n0 * n2 + n1 * n1, den = n1 * n3 + n2 * n2;
+        if (!(den > 0.0)) return INFINITY;
+        return sqrt(eta * num / den);
+    }
+    const double nlo = norm3(H[ORDER - 3]), nmid = norm3(H[ORDER - 2]), nhi = norm3(H[ORDER - 1]);
+    const double num = sqrt(n0 * n2) + n1, den = sqrt(nlo * nhi) + nmid;
+    if (!(den > 0.0)) return INFINITY;
+    return ORDER == 6 ? eta * cbrt(num / den) : eta * pow(num / den, 0.2);
+}
+
+// Corrector, interpolation and new step for the particles of the last force.
+// L = acc derivatives at t0 (held), R = new ones at t1 = tf (force); the
+// Hermite interpolant through L[0..mm-1], R[0..mm-1] (mm = p/2) gives the
+// higher derivatives at t1 in closed form (derived symbolically).
+template <int ORDER>
+__global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fidx, int fn, double tf,
+                                                 const double* __restrict__ F, int64_t n, int64_t np,
+                                                 double* __restrict__ x, double* __restrict__ v,
+                                                 double* __restrict__ d, double* __restrict__ t,
+                                                 double* __restrict__ dtv, double* __restrict__ pot, double eta,
+                                                 double dt_max, double dt_min, DevScalars* sc)
+{
+    constexpr int MM = ORDER / 2;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= fn) return;
+    const int i = fidx[p];
+    if ((unsigned)i >= (unsigned)n) {
+        raise_status(sc, NB_ERR_ARG);
+        return;
+    }
+    const double h = tf - t[i];
+    if (!(h > 0.0)) {
+        raise_status(sc, NB_ERR_ARG);
+        return;
+    }
+    double L[4][3], H[8][3];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) L[k][c] = d[(k * 3 + c) * np + i];
+#pragma unroll
+    for (int k = 0; k < MM; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) H[k][c] = F[(size_t)(3 * k + c) * fn + p];
+    const double potn = F[(size_t)(3 * MM) * fn + p];
+
+    const double ih = 1.0 / h;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double L0 = L[0][c], L1 = L[1][c], L2 = L[2][c], L3 = L[3][c];
+        const double R0 = H[0][c], R1 = H[1][c];
+        if (ORDER == 4) {
+            H[2][c] = 2.0 * (3.0 * (L0 - R0) + h * (L1 + 2.0 * R1)) * ih * ih;
+            H[3][c] = 6.0 * (2.0 * (L0 - R0) + h * (L1 + R1)) * ih * ih * ih;
+        } else if (ORDER == 6) {
+            const double R2 = H[2][c];
+            const double h2 = h * h;
+            H[3][c] = 3.0 * (20.0 * (R0 - L0) + h2 * (3.0 * R2 - L2) - 4.0 * h * (2.0 * L1 + 3.0 * R1)) * ih * ih * ih;
+            H[4][c] = 12.0 * (30.0 * (R0 - L0) + h2 * (3.0 * R2 - 2.0 * L2) - 2.0 * h * (7.0 * L1 + 8.0 * R1)) *
+                      (ih * ih) * (ih * ih);
+            H[5][c] = 60.0 * (12.0 * (R0 - L0) + h2 * (R2 - L2) - 6.0 * h * (L1 + R1)) * (ih * ih) * (ih * ih) * ih;
+        } else {
+            const double R2 = H[2][c], R3 = H[3][c];
+            const double h2 = h * h, h3 = h2 * h;
+            const double ih2 = ih * ih, ih4 = ih2 * ih2;
+            H[4][c] = 4.0 * (210.0 * (L0 - R0) + h3 * (L3 + 4.0 * R3) + 15.0 * h2 * (L2 - 2.0 * R2) +
+                             30.0 * h * (3.0 * L1 + 4.0 * R1)) * ih4;
+            H[5][c] = 60.0 * (168.0 * (L0 - R0) + h3 * (L3 + 2.0 * R3) + 2.0 * h2 * (7.0 * L2 - 10.0 * R2) +
+                              6.0 * h * (13.0 * L1 + 15.0 * R1)) * ih4 * ih;
+            H[6][c] = 120.0 * (420.0 * (L0 - R0) + h3 * (3.0 * L3 + 4.0 * R3) + 3.0 * h2 * (13.0 * L2 - 15.0 * R2) +
+                               12.0 * h * (17.0 * L1 + 18.0 * R1)) * ih4 * ih2;
+            H[7][c] = 840.0 * (120.0 * (L0 - R0) + h3 * (L3 + R3) + 12.0 * h2 * (L2 - R2) + 60.0 * h * (L1 + R1)) *
+                      ih4 * ih2 * ih;
+        }
+    }
+
+    // two-point Hermite corrector of order p for v' = a, then x' = v
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double v0 = v[c * np + i], x0 = x[c * np + i];
+        double v1, x1;
+        if (ORDER == 4) {
+            v1 = v0 + h * 0.5 * (L[0][c] + H[0][c]) - h * h * (1.0 / 12) * (H[1][c] - L[1][c]);
+            x1 = x0 + h * 0.5 * (v0 + v1) - h * h * (1.0 / 12) * (H[0][c] - L[0][c]);
+        } else if (ORDER == 6) {
+            v1 = v0 + h * 0.5 * (L[0][c] + H[0][c]) - h * h * 0.1 * (H[1][c] - L[1][c]) +
+                 h * h * h * (1.0 / 120) * (L[2][c] + H[2][c]);
+            x1 = x0 + h * 0.5 * (v0 + v1) - h * h * 0.1 * (H[0][c] - L[0][c]) +
+                 h * h * h * (1.0 / 120) * (L[1][c] + H[1][c]);
+        } else {
+            v1 = v0 + h * 0.5 * (L[0][c] + H[0][c]) - h * h * (3.0 / 28) * (H[1][c] - L[1][c]) +
+                 h * h * h * (1.0 / 84) * (L[2][c] + H[2][c]) - h * h * h * h * (1.0 / 1680) * (H[3][c] - L[3][c]);
+            x1 = x0 + h * 0.5 * (v0 + v1) - h * h * (3.0 / 28) * (H[0][c] - L[0][c]) +
+                 h * h * h * (1.0 / 84) * (L[1][c] + H[1][c]) - h * h * h * h * (1.0 / 1680) * (H[2][c] - L[2][c]);
+        }
+        v[c * np + i] = v1;
+        x[c * np + i] = x1;
+    }
+
+    double lim = dt_criterion<ORDER>(eta, H);
+    if (2.0 * h < lim) lim = 2.0 * h;
+    const double dtn = quantise_dt(lim, tf, dt_max, dt_min, sc);
+
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) d[(k * 3 + c) * np + i] = (k < 2 * MM) ? H[k][c] : 0.0;
+    t[i] = tf;
+    dtv[i] = dtn;
+    pot[i] = potn;
+}
+
+cudaError_t launch_correct(nb_ctx* c)
+{
+    const int nt = 128;
+    const int nb = (int)((c->f_n + nt - 1) / nt);
+#define NB_CORR(O)                                                                                          \
+    k_correct<O><<<nb, nt, 0, c->stream>>>(c->f_idx, (int)c->f_n, c->f_t, c->F, c->n, c->np, c->x, c->v,   \
+                                           c->d, c->t, c->dt, c->pot, c->eta, c->dt_max, c->dt_min, c->sc);
+    if (c->order == 4) {
+        NB_CORR(4)
+    } else if (c->order == 6) {
+        NB_CORR(6)
+    } else {
+        NB_CORR(8)
+    }
+#undef NB_CORR
+    return cudaGetLastError();
+}
+
+// ============================================================== start-up
+// Copy the start-up force (every particle active, list = identity) into the
+// held derivatives: acc, jerk from the order-4 pass, snap from the order-6
+// pass, crackle from the order-8 pass.
+template <int PASS>
+__global__ void k_startup_store(const double* __restrict__ F, int64_t n, int64_t np, double* __restrict__ d,
+                                double* __restrict__ pot)
+{
+    constexpr int MM = PASS / 2;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int k = 0; k < MM; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) d[(k * 3 + c) * np + i] = F[(size_t)(3 * k + c) * n + i];
+    pot[i] = F[(size_t)(3 * MM) * n + i];
+}
+
+cudaError_t launch_startup_store(nb_ctx* c, int order)
+{
+    const int nt = 256;
+    const int nb = (int)((c->n + nt - 1) / nt);
+    if (order == 4) k_startup_store<4><<<nb, nt, 0, c->stream>>>(c->F, c->n, c->np, c->d, c->pot);
+    else if (order == 6) k_startup_store<6><<<nb, nt, 0, c->stream>>>(c->F, c->n, c->np, c->d, c->pot);
+    else k_startup_store<8><<<nb, nt, 0, c->stream>>>(c->F, c->n, c->np, c->d, c->pot);
+    return cudaGetLastError();
+}
+
+// Start-up step eta_s |a| / |jerk|, quantised at t = 0; t_i = 0.
+__global__ void k_startup_dt(const double* __restrict__ d, int64_t n, int64_t np, double* __restrict__ t,
+                             double* __restrict__ dtv, double eta_s, double dt_max, double dt_min, DevScalars* sc)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double a[3], j[3];
+    for (int c = 0; c < 3; ++c) {
+        a[c] = d[(0 * 3 + c) * np + i];
+        j[c] = d[(1 * 3 + c) * np + i];
+    }
+    const double na = norm3(a), nj = norm3(j);
+    const double lim = nj > 0.0 ? eta_s * na / nj : INFINITY;
+    t[i] = 0.0;
+    dtv[i] = quantise_dt(lim, 0.0, dt_max, dt_min, sc);
+}
+
+cudaError_t launch_startup_dt(nb_ctx* c)
+{
+    const int nt = 256;
+    const int nb = (int)((c->n + nt - 1) / nt);
+    k_startup_dt<<<nb, nt, 0, c->stream>>>(c->d, c->n, c->np, c->t, c->dt, c->eta_s, c->dt_max, c->dt_min, c->sc);
+    return cudaGetLastError();
+}
+
+// ================================================================ energy
+// Deterministic two-level sums: kinetic sum m v^2 / 2 and potential
+// sum m_i pot_i / 2 (pot from an order-0 force pass, list = identity), and the
+// time range min t_i, max t_i for the synchronisation check.
+__global__ void __launch_bounds__(256) k_energy_part(const double* __restrict__ m, const double* __restrict__ v,
+                                                     const double* __restrict__ F, const double* __restrict__ t,
+                                                     int64_t n, int64_t np, double* __restrict__ red)
+{
+    __shared__ double sk[8], sp[8], smn[8], smx[8];
+    double k = 0.0, w = 0.0, tmn = INFINITY, tmx = -INFINITY;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double vx = v[i], vy = v[np + i], vz = v[2 * np + i];
+        k += 0.5 * m[i] * (vx * vx + vy * vy + vz * vz);
+        if (F) w += 0.5 * m[i] * F[i];
+        tmn = fmin(tmn, t[i]);
+        tmx = fmax(tmx, t[i]);
+    }
+    k = warp_sum(k);
+    w = warp_sum(w);
+    tmn = warp_min(tmn);
+    for (int o = 16; o > 0; o >>= 1) tmx = fmax(tmx, __shfl_xor_sync(0xffffffffu, tmx, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        sk[warp] = k;
+        sp[warp] = w;
+        smn[warp] = tmn;
+        smx[warp] = tmx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0, mn = INFINITY, mx = -INFINITY;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+            a += sk[q];
+            b += sp[q];
+            mn = fmin(mn, smn[q]);
+            mx = fmax(mx, smx[q]);
+        }
+        red[4 * blockIdx.x + 0] = a;
+        red[4 * blockIdx.x + 1] = b;
+        red[4 * blockIdx.x + 2] = mn;
+        red[4 * blockIdx.x + 3] = mx;
+    }
+}
+
+__global__ void k_energy_final(const double* __restrict__ red, int nb, double* __restrict__ out)
+{
+    if (threadIdx.x != 0) return;
+    double a = 0, b = 0, mn = INFINITY, mx = -INFINITY;
+    for (int q = 0; q < nb; ++q) {
+        a += red[4 * q + 0];
+        b += red[4 * q + 1];
+        mn = fmin(mn, red[4 * q + 2]);
+        mx = fmax(mx, red[4 * q + 3]);
+    }
+    out[0] = a;
+    out[1] = b;
+    out[2] = mn;
+    out[3] = mx;
+}
+
+int energy_grid(const nb_ctx* c)
+{
+    int g = c->sm_count;
+    const int64_t need = (c->n + 255) / 256;
+    if (need < g) g = (int)need;
+    return g < 1 ? 1 : g;
+}
+
+// with_pot = 0: only the time range and kinetic energy (F unused).
+cudaError_t launch_energy_sums(nb_ctx* c, int with_pot)
+{
+    const int g = energy_grid(c);
+    k_energy_part<<<g, 256, 0, c->stream>>>(c->m, c->v, with_pot ? c->F : nullptr, c->t, c->n, c->np, c->red);
+    k_energy_final<<<1, 32, 0, c->stream>>>(c->red, g, c->red + 4 * g);
+    return cudaGetLastError();
+}
+
+}  // namespace nb
