@@ -63,11 +63,19 @@ typedef long double ld;
 /*   phi = -m_j / R                                                            */
 /* Order 4 uses A, J; order 6 adds S; order 8 adds C.                          */
 /* ------------------------------------------------------------------------- */
+static ld norm3l(const ld* p)
+{
+    return sqrtl(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+}
+
+/* absum receives sum_j |A_ij|, |J_ij|, |S_ij|, |C_ij|, |phi_ij|: the size of
+   the terms each total is made of, i.e. its condition scale. */
 static void force_one(int64_t n, const double* m, const double* eps2,
                       const double* x, const double* v, const double* a, const double* jk,
-                      int order, int64_t i, ld A[3], ld J[3], ld S[3], ld C[3], ld* phi)
+                      int order, int64_t i, ld A[3], ld J[3], ld S[3], ld C[3], ld* phi, ld absum[5])
 {
     for (int k = 0; k < 3; k++) { A[k] = 0; J[k] = 0; S[k] = 0; C[k] = 0; }
+    for (int k = 0; k < 5; k++) absum[k] = 0;
     *phi = 0;
     for (int64_t j = 0; j < n; j++) {
         if (j == i) continue;
@@ -103,6 +111,11 @@ static void force_one(int64_t n, const double* m, const double* eps2,
             C[k] += pC[k];
         }
         *phi -= (ld)m[j] / R;
+        absum[0] += norm3l(pA);
+        absum[1] += norm3l(pJ);
+        absum[2] += norm3l(pS);
+        absum[3] += norm3l(pC);
+        absum[4] += (ld)m[j] / R;
     }
 }
 
@@ -110,7 +123,7 @@ int orc_force(int64_t n, const double* m, const double* eps2,
               const double* x, const double* v, const double* a, const double* jk,
               int order, int64_t n_act, const int32_t* idx,
               double* acc, double* jerk, double* snap, double* crackle, double* pot,
-              int nthreads)
+              double* absum, int nthreads)
 {
     if (n < 0 || n_act < 0 || !(order == 4 || order == 6 || order == 8)) return ORC_ERR_ARG;
     if (order >= 6 && !a) return ORC_ERR_ARG;
@@ -122,8 +135,10 @@ int orc_force(int64_t n, const double* m, const double* eps2,
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
 #endif
     for (int64_t p = 0; p < n_act; p++) {
-        ld A[3], J[3], S[3], C[3], phi;
-        force_one(n, m, eps2, x, v, a, jk, order, idx[p], A, J, S, C, &phi);
+        ld A[3], J[3], S[3], C[3], phi, ab[5];
+        force_one(n, m, eps2, x, v, a, jk, order, idx[p], A, J, S, C, &phi, ab);
+        if (absum)
+            for (int k = 0; k < 5; k++) absum[5 * p + k] = (double)ab[k];
         for (int k = 0; k < 3; k++) {
             if (acc) acc[3 * p + k] = (double)A[k];
             if (jerk) jerk[3 * p + k] = (double)J[k];
@@ -434,7 +449,7 @@ int orc_integrate(int64_t n, const double* m, const double* eps2,
                     ap[3 * i + c] = d[18 * i + c];
                     jp[3 * i + c] = d[18 * i + 3 + c];
                 }
-            rc = orc_force(n, m, eps2, x, v, ap, jp, po, n, idx, F, F + 3 * n, F + 6 * n, F + 9 * n, ph,
+            rc = orc_force(n, m, eps2, x, v, ap, jp, po, n, idx, F, F + 3 * n, F + 6 * n, F + 9 * n, ph, NULL,
                            P->nthreads);
             if (rc) goto done;
             for (int64_t i = 0; i < n; i++)
@@ -477,7 +492,7 @@ int orc_integrate(int64_t n, const double* m, const double* eps2,
         nb++;
         rc = orc_predict(n, order, tb, t, x, v, d, xp, vp, ap, jp);
         if (rc) goto done;
-        rc = orc_force(n, m, eps2, xp, vp, ap, jp, order, na, idx, F, F + 3 * n, F + 6 * n, F + 9 * n, ph,
+        rc = orc_force(n, m, eps2, xp, vp, ap, jp, order, na, idx, F, F + 3 * n, F + 6 * n, F + 9 * n, ph, NULL,
                        P->nthreads);
         if (rc) goto done;
         for (int64_t p = 0; p < na; p++) {

@@ -36,7 +36,7 @@ def lib():
         path = build()
         L = C.CDLL(path)
         d, i64, i32 = C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_int32)
-        L.orc_force.argtypes = [i64, d, d, d, d, d, d, C.c_int, i64, i32, d, d, d, d, d, C.c_int]
+        L.orc_force.argtypes = [i64, d, d, d, d, d, d, C.c_int, i64, i32, d, d, d, d, d, d, C.c_int]
         L.orc_energy.argtypes = [i64, d, d, d, d, d, d, C.c_int]
         L.orc_predict.argtypes = [i64, C.c_int, C.c_double, d, d, d, d, d, d, d, d]
         L.orc_correct.argtypes = [C.c_int, C.c_double, d, d, d, d, d, d]
@@ -83,7 +83,11 @@ def num_threads() -> int:
 
 
 def force(m, eps2, x, v, a=None, jk=None, order=6, idx=None, nthreads=1):
-    """Direct-sum acc, jerk, snap, crackle and potential on particles idx."""
+    """Direct-sum acc, jerk, snap, crackle and potential on particles idx.
+
+    Also returns "absum" [n_act][5]: sum over j of |A_ij|, |J_ij|, |S_ij|,
+    |C_ij| and m_j/R_ij, the magnitude of the terms behind each total.
+    """
     m = _f64(m)
     n = m.shape[0]
     eps2 = _f64(np.broadcast_to(eps2, (n,)))
@@ -95,9 +99,10 @@ def force(m, eps2, x, v, a=None, jk=None, order=6, idx=None, nthreads=1):
     na = idx.shape[0]
     out = {k: np.zeros((na, 3)) for k in ("acc", "jerk", "snap", "crackle")}
     out["pot"] = np.zeros(na)
+    out["absum"] = np.zeros((na, 5))
     rc = lib().orc_force(n, _p(m), _p(eps2), _p(x), _p(v), _p(a), _p(jk), order, na, _p(idx),
                          _p(out["acc"]), _p(out["jerk"]), _p(out["snap"]), _p(out["crackle"]),
-                         _p(out["pot"]), int(nthreads))
+                         _p(out["pot"]), _p(out["absum"]), int(nthreads))
     _check(rc, "orc_force")
     return out
 

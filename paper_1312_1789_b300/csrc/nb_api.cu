@@ -1,0 +1,621 @@
+// nb_api.cu -- host side of libnb: the C ABI declared in include/nb.h.
+//
+// Owns the device state, sequences the kernels of one block step on the
+// context's stream, validates arguments on the host and turns the status word
+// the kernels raise into NB_ERR_* codes at every synchronisation point.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "nb_internal.cuh"
+
+using namespace nb;
+
+namespace {
+
+void* (*g_alloc)(size_t, void*) = nullptr;
+void (*g_free)(void*, void*) = nullptr;
+void* g_user = nullptr;
+char g_err[512] = "";
+
+int set_err(nb_ctx* c, int code, const char* fmt, ...)
+{
+    char* dst = c ? c->err : g_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+const char* code_name(int code)
+{
+    switch (code) {
+    case NB_OK: return "ok";
+    case NB_ERR_ARG: return "invalid argument";
+    case NB_ERR_CUDA: return "CUDA error";
+    case NB_ERR_NOT_SYNC: return "particles not synchronised";
+    case NB_ERR_DT_UNDERFLOW: return "time step below dt_min";
+    case NB_ERR_TIMEOUT: return "device wait timed out";
+    case NB_ERR_NAN: return "non-finite value";
+    case NB_ERR_NOMEM: return "out of device memory";
+    default: return "unknown";
+    }
+}
+
+#define NB_CUDA(c, call)                                                                                       \
+    do {                                                                                                       \
+        cudaError_t e_ = (call);                                                                               \
+        if (e_ != cudaSuccess)                                                                                 \
+            return set_err((c), NB_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                           __LINE__);                                                                          \
+    } while (0)
+
+#define NB_TRY(expr)                \
+    do {                            \
+        int r_ = (expr);            \
+        if (r_ != NB_OK) return r_; \
+    } while (0)
+
+template <typename T>
+int dalloc(nb_ctx* c, T** p, size_t count)
+{
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 256;
+    void* q = nullptr;
+    if (c->alloc_fn) {
+        q = c->alloc_fn(bytes, c->alloc_user);
+        if (!q) return set_err(c, NB_ERR_NOMEM, "allocator returned NULL for %zu bytes", bytes);
+    } else {
+        cudaError_t e = cudaMalloc(&q, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(c, NB_ERR_NOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        }
+    }
+    *p = static_cast<T*>(q);
+    return NB_OK;
+}
+
+void dfree(nb_ctx* c, void* p)
+{
+    if (!p) return;
+    if (c->free_fn) c->free_fn(p, c->alloc_user);
+    else cudaFree(p);
+}
+
+bool finite_all(const double* a, size_t n)
+{
+    for (size_t k = 0; k < n; ++k)
+        if (!std::isfinite(a[k])) return false;
+    return true;
+}
+
+bool is_pow2(double x)
+{
+    if (!(x > 0.0) || !std::isfinite(x)) return false;
+    int e;
+    return std::frexp(x, &e) == 0.5;
+}
+
+// Read the device scalars (waits for the stream) and turn a raised status into
+// an error code; the status word is cleared for the next call.
+int sync_scalars(nb_ctx* c)
+{
+    NB_CUDA(c, cudaMemcpyAsync(c->h_sc, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    const int st = c->h_sc->status;
+    if (st != NB_OK) {
+        NB_CUDA(c, cudaMemsetAsync(&c->sc->status, 0, sizeof(int), c->stream));
+        NB_CUDA(c, cudaStreamSynchronize(c->stream));
+        return set_err(c, st, "device kernel reported: %s", code_name(st));
+    }
+    return NB_OK;
+}
+
+// Launch shape of the force: FORCE_NT i-particles per CTA; the j range is
+// split so that small active sets still fill every SM (j-split), capped by the
+// partial-sum buffer.
+void choose_shape(nb_ctx* c, int order, int64_t n_act, int* itiles, int* jsplit)
+{
+    const int it = (int)((n_act + FORCE_NT - 1) / FORCE_NT);
+    const int ntiles = (int)(c->np / JT);
+    int js;
+    if (c->jsplit_force > 0) {
+        js = c->jsplit_force;
+    } else {
+        const int target = c->sm_count * force_occupancy(c, order);
+        js = it >= target ? 1 : (target + it - 1) / it;
+    }
+    if (js > ntiles) js = ntiles;
+    if (js < 1) js = 1;
+    while (js > 1 && (size_t)js * ncomp(order) * (size_t)n_act > c->partial_cap) --js;
+    *itiles = it;
+    *jsplit = js;
+}
+
+int run_force(nb_ctx* c, int order, const int32_t* idx_dev, int64_t n_act)
+{
+    int it, js;
+    choose_shape(c, order, n_act, &it, &js);
+    NB_CUDA(c, launch_force(c, order, idx_dev, n_act, js, it));
+    NB_CUDA(c, launch_force_reduce(c, order, idx_dev, n_act, js));
+    c->last_itiles = it;
+    c->last_jsplit = js;
+    c->last_threads = FORCE_NT;
+    c->F_order = order;
+    c->F_n = n_act;
+    return NB_OK;
+}
+
+int do_predict(nb_ctx* c, double t)
+{
+    NB_CUDA(c, launch_predict(c, t));
+    c->pred_prec = c->prec;
+    c->have_pred = 1;
+    c->t_pred = t;
+    return NB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* nb_version(void) { return "libnb 0.1 (sm_103a)"; }
+
+const char* nb_last_error(const nb_ctx* c) { return c ? c->err : g_err; }
+
+int nb_set_allocator(void* (*alloc)(size_t, void*), void (*free_)(void*, void*), void* user)
+{
+    if ((alloc == nullptr) != (free_ == nullptr)) return set_err(nullptr, NB_ERR_ARG, "alloc and free must be set together");
+    g_alloc = alloc;
+    g_free = free_;
+    g_user = user;
+    return NB_OK;
+}
+
+void nb_destroy(nb_ctx* c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    void* ptrs[] = {c->m, c->eps2, c->x, c->v, c->d, c->t, c->dt, c->pot, c->jstore, c->act_idx, c->all_idx,
+                    c->chunk_cnt, c->sc, c->red, c->f_idx, c->partial, c->F};
+    for (void* p : ptrs) dfree(c, p);
+    if (c->h_sc) cudaFreeHost(c->h_sc);
+    if (c->h_red) cudaFreeHost(c->h_red);
+    delete c;
+}
+
+int nb_create(nb_ctx** out, int64_t n, int order, double eps)
+{
+    if (!out) return set_err(nullptr, NB_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > (1LL << 28)) return set_err(nullptr, NB_ERR_ARG, "n = %lld outside [1, 2^28]", (long long)n);
+    if (!(order == 4 || order == 6 || order == 8)) return set_err(nullptr, NB_ERR_ARG, "order %d not 4, 6 or 8", order);
+    if (!(eps >= 0.0) || !std::isfinite(eps)) return set_err(nullptr, NB_ERR_ARG, "eps must be finite and >= 0");
+    nb_ctx* c = new (std::nothrow) nb_ctx();
+    if (!c) return set_err(nullptr, NB_ERR_NOMEM, "host allocation failed");
+    c->alloc_fn = g_alloc;
+    c->free_fn = g_free;
+    c->alloc_user = g_user;
+    c->n = n;
+    c->np = (n + JT - 1) / JT * JT;
+    c->order = order;
+    c->eps = eps;
+    int rc = NB_OK;
+    auto fail = [&](int code) {
+        snprintf(g_err, sizeof g_err, "%s", c->err);
+        nb_destroy(c);
+        return code;
+    };
+    if (cudaGetDevice(&c->dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess) {
+        cudaGetLastError();
+        set_err(c, NB_ERR_CUDA, "no usable CUDA device");
+        return fail(NB_ERR_CUDA);
+    }
+    const size_t np = (size_t)c->np;
+    const int nc = ncomp(order);
+    const size_t rec = (size_t)(fp64_rw(order) > mixed_rw(order) ? fp64_rw(order) : mixed_rw(order)) * 16;
+    c->n_chunks = sched_chunks(n);
+    c->red_len = 4 * c->sm_count + 8;
+    if (c->red_len < 2 * c->sm_count) c->red_len = 2 * c->sm_count;
+    const size_t span = (size_t)2 * 16 * c->sm_count * FORCE_NT;
+    c->partial_cap = (size_t)nc * ((size_t)n > span ? (size_t)n : span);
+    if ((rc = dalloc(c, &c->m, np)) || (rc = dalloc(c, &c->eps2, np)) || (rc = dalloc(c, &c->x, 3 * np)) ||
+        (rc = dalloc(c, &c->v, 3 * np)) || (rc = dalloc(c, &c->d, 18 * np)) || (rc = dalloc(c, &c->t, np)) ||
+        (rc = dalloc(c, &c->dt, np)) || (rc = dalloc(c, &c->pot, np)) ||
+        (rc = dalloc(c, reinterpret_cast<unsigned char**>(&c->jstore), np * rec)) ||
+        (rc = dalloc(c, &c->act_idx, (size_t)n)) || (rc = dalloc(c, &c->all_idx, (size_t)n)) ||
+        (rc = dalloc(c, &c->f_idx, (size_t)n)) || (rc = dalloc(c, &c->chunk_cnt, (size_t)c->n_chunks)) ||
+        (rc = dalloc(c, &c->sc, 1)) || (rc = dalloc(c, &c->red, (size_t)c->red_len)) ||
+        (rc = dalloc(c, &c->partial, c->partial_cap)) || (rc = dalloc(c, &c->F, (size_t)nc * (size_t)n)))
+        return fail(rc);
+    if (cudaMallocHost(&c->h_sc, sizeof(DevScalars)) != cudaSuccess ||
+        cudaMallocHost(&c->h_red, 4 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        set_err(c, NB_ERR_NOMEM, "pinned host allocation failed");
+        return fail(NB_ERR_NOMEM);
+    }
+    std::vector<int32_t> iota((size_t)n);
+    for (int64_t k = 0; k < n; ++k) iota[(size_t)k] = (int32_t)k;
+    if (cudaMemcpy(c->all_idx, iota.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(c->sc, 0, sizeof(DevScalars)) != cudaSuccess || cudaMemset(c->m, 0, np * 8) != cudaSuccess ||
+        cudaMemset(c->x, 0, 3 * np * 8) != cudaSuccess || cudaMemset(c->v, 0, 3 * np * 8) != cudaSuccess ||
+        cudaMemset(c->d, 0, 18 * np * 8) != cudaSuccess || cudaMemset(c->t, 0, np * 8) != cudaSuccess ||
+        cudaMemset(c->dt, 0, np * 8) != cudaSuccess || cudaMemset(c->pot, 0, np * 8) != cudaSuccess) {
+        cudaGetLastError();
+        set_err(c, NB_ERR_CUDA, "device initialisation failed");
+        return fail(NB_ERR_CUDA);
+    }
+    std::vector<double> e2(np, eps * eps);
+    if (cudaMemcpy(c->eps2, e2.data(), np * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        set_err(c, NB_ERR_CUDA, "device initialisation failed");
+        return fail(NB_ERR_CUDA);
+    }
+    *out = c;
+    return NB_OK;
+}
+
+int nb_set_stream(nb_ctx* c, void* stream)
+{
+    if (!c) return NB_ERR_ARG;
+    c->stream = static_cast<cudaStream_t>(stream);
+    return NB_OK;
+}
+
+int nb_set_precision(nb_ctx* c, int mode)
+{
+    if (!c) return NB_ERR_ARG;
+    if (mode != NB_FP64 && mode != NB_MIXED) return set_err(c, NB_ERR_ARG, "precision %d not NB_FP64 or NB_MIXED", mode);
+    c->prec = mode;
+    return NB_OK;
+}
+
+int nb_set_softening(nb_ctx* c, const double* eps_i)
+{
+    if (!c) return NB_ERR_ARG;
+    std::vector<double> e2((size_t)c->np, c->eps * c->eps);
+    if (eps_i) {
+        for (int64_t k = 0; k < c->n; ++k) {
+            if (!(eps_i[k] >= 0.0) || !std::isfinite(eps_i[k]))
+                return set_err(c, NB_ERR_ARG, "eps_i[%lld] must be finite and >= 0", (long long)k);
+            e2[(size_t)k] = eps_i[k] * eps_i[k];
+        }
+    }
+    NB_CUDA(c, cudaMemcpyAsync(c->eps2, e2.data(), e2.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->pair_eps = eps_i != nullptr;
+    c->have_pred = 0;
+    return NB_OK;
+}
+
+int nb_set_params(nb_ctx* c, double eta, double eta_s, double dt_max, double dt_min)
+{
+    if (!c) return NB_ERR_ARG;
+    if (!(eta > 0.0) || !std::isfinite(eta) || !(eta_s > 0.0) || !std::isfinite(eta_s))
+        return set_err(c, NB_ERR_ARG, "eta and eta_s must be positive and finite");
+    if (!is_pow2(dt_max)) return set_err(c, NB_ERR_ARG, "dt_max must be a power of two");
+    if (!(dt_min > 0.0) || !(dt_min <= dt_max)) return set_err(c, NB_ERR_ARG, "need 0 < dt_min <= dt_max");
+    c->eta = eta;
+    c->eta_s = eta_s;
+    c->dt_max = dt_max;
+    c->dt_min = dt_min;
+    return NB_OK;
+}
+
+int nb_set_jsplit(nb_ctx* c, int js)
+{
+    if (!c) return NB_ERR_ARG;
+    if (js < 0) return set_err(c, NB_ERR_ARG, "j_splits must be >= 0");
+    c->jsplit_force = js;
+    return NB_OK;
+}
+
+int nb_get_launch(nb_ctx* c, int* it, int* js, int* nt)
+{
+    if (!c) return NB_ERR_ARG;
+    if (it) *it = c->last_itiles;
+    if (js) *js = c->last_jsplit;
+    if (nt) *nt = c->last_threads;
+    return NB_OK;
+}
+
+// Host [n][3] -> device [3][np]
+static int upload_vec(nb_ctx* c, double* dst, const double* src)
+{
+    std::vector<double> tmp((size_t)3 * c->np, 0.0);
+    for (int64_t i = 0; i < c->n; ++i)
+        for (int k = 0; k < 3; ++k) tmp[(size_t)k * c->np + i] = src[3 * i + k];
+    NB_CUDA(c, cudaMemcpyAsync(dst, tmp.data(), tmp.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    return NB_OK;
+}
+
+static int download_vec(nb_ctx* c, double* dst, const double* src)
+{
+    std::vector<double> tmp((size_t)3 * c->np);
+    NB_CUDA(c, cudaMemcpyAsync(tmp.data(), src, tmp.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int64_t i = 0; i < c->n; ++i)
+        for (int k = 0; k < 3; ++k) dst[3 * i + k] = tmp[(size_t)k * c->np + i];
+    return NB_OK;
+}
+
+int nb_set_particles(nb_ctx* c, const double* m, const double* x, const double* v)
+{
+    if (!c || !m || !x || !v) return c ? set_err(c, NB_ERR_ARG, "m, x and v are required") : NB_ERR_ARG;
+    const size_t n = (size_t)c->n, np = (size_t)c->np;
+    for (size_t k = 0; k < n; ++k)
+        if (!(m[k] >= 0.0) || !std::isfinite(m[k])) return set_err(c, NB_ERR_ARG, "masses must be finite and >= 0");
+    if (!finite_all(x, 3 * n) || !finite_all(v, 3 * n)) return set_err(c, NB_ERR_NAN, "non-finite position or velocity");
+    std::vector<double> mm(np, 0.0);
+    for (size_t k = 0; k < n; ++k) mm[k] = m[k];
+    NB_CUDA(c, cudaMemcpyAsync(c->m, mm.data(), np * 8, cudaMemcpyHostToDevice, c->stream));
+    NB_TRY(upload_vec(c, c->x, x));
+    NB_TRY(upload_vec(c, c->v, v));
+    NB_CUDA(c, cudaMemsetAsync(c->d, 0, 18 * np * 8, c->stream));
+    NB_CUDA(c, cudaMemsetAsync(c->t, 0, np * 8, c->stream));
+    NB_CUDA(c, cudaMemsetAsync(c->dt, 0, np * 8, c->stream));
+    NB_CUDA(c, cudaMemsetAsync(c->pot, 0, np * 8, c->stream));
+    NB_CUDA(c, cudaMemsetAsync(&c->sc->status, 0, sizeof(int), c->stream));
+    c->have_particles = 1;
+    c->have_force = 0;
+    c->have_sched = 0;
+    // Start-up: at t = 0 only positions and velocities are known.  The order-4
+    // pass gives acc and jerk; with those as the predicted acc the order-6 pass
+    // gives snap; with acc and jerk the order-8 pass gives crackle.
+    for (int pass = 4; pass <= c->order; pass += 2) {
+        NB_TRY(do_predict(c, 0.0));
+        NB_TRY(run_force(c, pass, c->all_idx, c->n));
+        NB_CUDA(c, launch_startup_store(c, pass));
+    }
+    NB_CUDA(c, launch_startup_dt(c));
+    c->have_pred = 0;
+    c->F_order = -1;
+    return sync_scalars(c);
+}
+
+int nb_next_block(nb_ctx* c, double* t_blk, int32_t* idx_out, int64_t* n_act)
+{
+    if (!c) return NB_ERR_ARG;
+    if (!c->have_particles) return set_err(c, NB_ERR_ARG, "nb_next_block before nb_set_particles");
+    NB_CUDA(c, launch_sched(c));
+    NB_TRY(sync_scalars(c));
+    c->sched_t = c->h_sc->t_blk;
+    c->sched_n = c->h_sc->n_act;
+    c->have_sched = 1;
+    if (t_blk) *t_blk = c->sched_t;
+    if (n_act) *n_act = c->sched_n;
+    if (idx_out) {
+        NB_CUDA(c, cudaMemcpyAsync(idx_out, c->act_idx, sizeof(int32_t) * (size_t)c->sched_n, cudaMemcpyDeviceToHost,
+                                   c->stream));
+        NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return NB_OK;
+}
+
+int nb_predict(nb_ctx* c, double t)
+{
+    if (!c) return NB_ERR_ARG;
+    if (!c->have_particles) return set_err(c, NB_ERR_ARG, "nb_predict before nb_set_particles");
+    if (!std::isfinite(t)) return set_err(c, NB_ERR_ARG, "t must be finite");
+    c->have_force = 0;
+    return do_predict(c, t);
+}
+
+int nb_force(nb_ctx* c, const int32_t* idx, int64_t n_act)
+{
+    if (!c) return NB_ERR_ARG;
+    if (!c->have_pred) return set_err(c, NB_ERR_ARG, "nb_force needs a preceding nb_predict");
+    if (!idx) {
+        if (!c->have_sched) return set_err(c, NB_ERR_ARG, "nb_force(NULL) needs a preceding nb_next_block");
+        if (n_act <= 0) n_act = c->sched_n;
+        if (n_act != c->sched_n)
+            return set_err(c, NB_ERR_ARG, "n_act %lld differs from the scheduled %lld", (long long)n_act,
+                           (long long)c->sched_n);
+        NB_CUDA(c, cudaMemcpyAsync(c->f_idx, c->act_idx, sizeof(int32_t) * (size_t)n_act, cudaMemcpyDeviceToDevice,
+                                   c->stream));
+    } else {
+        if (n_act < 1 || n_act > c->n) return set_err(c, NB_ERR_ARG, "n_act = %lld outside [1, n]", (long long)n_act);
+        cudaPointerAttributes pa;
+        bool on_device = false;
+        if (cudaPointerGetAttributes(&pa, idx) == cudaSuccess)
+            on_device = pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged;
+        else
+            cudaGetLastError();
+        if (on_device) {
+            NB_CUDA(c, cudaMemcpyAsync(c->f_idx, idx, sizeof(int32_t) * (size_t)n_act, cudaMemcpyDeviceToDevice,
+                                       c->stream));
+        } else {
+            for (int64_t k = 0; k < n_act; ++k)
+                if (idx[k] < 0 || idx[k] >= c->n)
+                    return set_err(c, NB_ERR_ARG, "active_idx[%lld] = %d out of range", (long long)k, idx[k]);
+            NB_CUDA(c, cudaMemcpyAsync(c->f_idx, idx, sizeof(int32_t) * (size_t)n_act, cudaMemcpyHostToDevice,
+                                       c->stream));
+        }
+    }
+    NB_TRY(run_force(c, c->order, c->f_idx, n_act));
+    c->f_n = n_act;
+    c->f_t = c->t_pred;
+    c->f_order = c->order;
+    c->have_force = 1;
+    return NB_OK;
+}
+
+int nb_correct(nb_ctx* c)
+{
+    if (!c) return NB_ERR_ARG;
+    if (!c->have_force || c->F_order != c->order)
+        return set_err(c, NB_ERR_ARG, "nb_correct needs a preceding nb_force");
+    NB_CUDA(c, launch_correct(c));
+    c->have_force = 0;
+    c->have_pred = 0;
+    c->have_sched = 0;
+    c->F_order = -1;
+    return NB_OK;
+}
+
+int nb_block_step(nb_ctx* c, double* t_blk, int64_t* n_act)
+{
+    double tb;
+    int64_t na;
+    NB_TRY(nb_next_block(c, &tb, nullptr, &na));
+    NB_TRY(nb_predict(c, tb));
+    NB_TRY(nb_force(c, nullptr, na));
+    NB_TRY(nb_correct(c));
+    if (t_blk) *t_blk = tb;
+    if (n_act) *n_act = na;
+    return NB_OK;
+}
+
+int nb_step_until(nb_ctx* c, double t_end, int64_t* n_blocks, int64_t* n_inter)
+{
+    if (!c) return NB_ERR_ARG;
+    if (!std::isfinite(t_end)) return set_err(c, NB_ERR_ARG, "t_end must be finite");
+    int64_t nb = 0, ni = 0;
+    for (;;) {
+        double tb;
+        int64_t na;
+        NB_TRY(nb_next_block(c, &tb, nullptr, &na));
+        if (tb > t_end) break;
+        NB_TRY(nb_predict(c, tb));
+        NB_TRY(nb_force(c, nullptr, na));
+        NB_TRY(nb_correct(c));
+        ++nb;
+        ni += na * c->n;
+    }
+    if (n_blocks) *n_blocks = nb;
+    if (n_inter) *n_inter = ni;
+    return sync_scalars(c);
+}
+
+int nb_energy(nb_ctx* c, double* ekin, double* epot)
+{
+    if (!c) return NB_ERR_ARG;
+    if (!c->have_particles) return set_err(c, NB_ERR_ARG, "nb_energy before nb_set_particles");
+    const int g = energy_grid(c);
+    NB_CUDA(c, launch_energy_sums(c, 0));
+    NB_CUDA(c, cudaMemcpyAsync(c->h_red, c->red + 4 * g, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    NB_TRY(sync_scalars(c));
+    const double tmin = c->h_red[2], tmax = c->h_red[3];
+    if (tmin != tmax)
+        return set_err(c, NB_ERR_NOT_SYNC, "particles at different times (%.17g .. %.17g)", tmin, tmax);
+    // potential from the positions at the common time (prediction by 0)
+    c->have_force = 0;
+    NB_TRY(do_predict(c, tmin));
+    NB_TRY(run_force(c, 0, c->all_idx, c->n));
+    NB_CUDA(c, launch_energy_sums(c, 1));
+    NB_CUDA(c, cudaMemcpyAsync(c->h_red, c->red + 4 * g, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    NB_TRY(sync_scalars(c));
+    if (ekin) *ekin = c->h_red[0];
+    if (epot) *epot = c->h_red[1];
+    return NB_OK;
+}
+
+int nb_get_state(nb_ctx* c, double* x, double* v, double* d, double* t, double* dt)
+{
+    if (!c) return NB_ERR_ARG;
+    NB_TRY(sync_scalars(c));
+    const size_t n = (size_t)c->n, np = (size_t)c->np;
+    if (x) NB_TRY(download_vec(c, x, c->x));
+    if (v) NB_TRY(download_vec(c, v, c->v));
+    if (d) {
+        std::vector<double> tmp(18 * np);
+        NB_CUDA(c, cudaMemcpyAsync(tmp.data(), c->d, tmp.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+        NB_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (size_t i = 0; i < n; ++i)
+            for (int q = 0; q < 18; ++q) d[18 * i + q] = tmp[(size_t)q * np + i];
+    }
+    if (t) NB_CUDA(c, cudaMemcpyAsync(t, c->t, n * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (dt) NB_CUDA(c, cudaMemcpyAsync(dt, c->dt, n * 8, cudaMemcpyDeviceToHost, c->stream));
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    return NB_OK;
+}
+
+int nb_set_state(nb_ctx* c, const double* x, const double* v, const double* d, const double* t, const double* dt)
+{
+    if (!c) return NB_ERR_ARG;
+    if (!x || !v || !d || !t || !dt) return set_err(c, NB_ERR_ARG, "x, v, d, t and dt are required");
+    const size_t n = (size_t)c->n, np = (size_t)c->np;
+    if (!finite_all(x, 3 * n) || !finite_all(v, 3 * n) || !finite_all(d, 18 * n) || !finite_all(t, n) ||
+        !finite_all(dt, n))
+        return set_err(c, NB_ERR_NAN, "non-finite state");
+    for (size_t i = 0; i < n; ++i)
+        if (!(dt[i] > 0.0)) return set_err(c, NB_ERR_ARG, "dt[%zu] must be > 0", i);
+    NB_TRY(upload_vec(c, c->x, x));
+    NB_TRY(upload_vec(c, c->v, v));
+    std::vector<double> tmp(18 * np, 0.0);
+    for (size_t i = 0; i < n; ++i)
+        for (int q = 0; q < 18; ++q) tmp[(size_t)q * np + i] = d[18 * i + q];
+    NB_CUDA(c, cudaMemcpyAsync(c->d, tmp.data(), tmp.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    NB_CUDA(c, cudaMemcpyAsync(c->t, t, n * 8, cudaMemcpyHostToDevice, c->stream));
+    NB_CUDA(c, cudaMemcpyAsync(c->dt, dt, n * 8, cudaMemcpyHostToDevice, c->stream));
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->have_particles = 1;
+    c->have_pred = c->have_force = c->have_sched = 0;
+    c->F_order = -1;
+    return NB_OK;
+}
+
+int nb_get_force(nb_ctx* c, double* acc, double* jerk, double* snap, double* crackle, double* pot)
+{
+    if (!c) return NB_ERR_ARG;
+    if (c->F_order < 4) return set_err(c, NB_ERR_ARG, "no force result held (call nb_force first)");
+    NB_TRY(sync_scalars(c));
+    const int o = c->F_order, nc = ncomp(o);
+    const size_t fn = (size_t)c->F_n;
+    std::vector<double> tmp((size_t)nc * fn);
+    NB_CUDA(c, cudaMemcpyAsync(tmp.data(), c->F, tmp.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    double* outs[4] = {acc, jerk, snap, crackle};
+    for (int q = 0; q < 4; ++q) {
+        if (!outs[q]) continue;
+        for (size_t p = 0; p < fn; ++p)
+            for (int k = 0; k < 3; ++k) outs[q][3 * p + k] = (q < o / 2) ? tmp[(size_t)(3 * q + k) * fn + p] : 0.0;
+    }
+    if (pot)
+        for (size_t p = 0; p < fn; ++p) pot[p] = tmp[(size_t)(nc - 1) * fn + p];
+    return NB_OK;
+}
+
+int nb_get_predicted(nb_ctx* c, double* xp, double* vp, double* ap, double* jp)
+{
+    if (!c) return NB_ERR_ARG;
+    if (!c->have_pred) return set_err(c, NB_ERR_ARG, "no predicted store (call nb_predict first)");
+    NB_TRY(sync_scalars(c));
+    const size_t n = (size_t)c->n;
+    const bool mixed = c->pred_prec == NB_MIXED;
+    const int rw = mixed ? mixed_rw(c->order) : fp64_rw(c->order);
+    std::vector<unsigned char> raw(n * rw * 16);
+    NB_CUDA(c, cudaMemcpyAsync(raw.data(), c->jstore, raw.size(), cudaMemcpyDeviceToHost, c->stream));
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (size_t i = 0; i < n; ++i) {
+        const unsigned char* r = raw.data() + i * rw * 16;
+        if (mixed) {
+            const float* f = reinterpret_cast<const float*>(r);
+            for (int k = 0; k < 3; ++k) {
+                if (xp) xp[3 * i + k] = (double)f[k] + (double)f[4 + k];
+                if (vp) vp[3 * i + k] = f[8 + k];
+                if (ap) ap[3 * i + k] = c->order >= 6 ? f[12 + k] : 0.0;
+                if (jp) jp[3 * i + k] = c->order >= 8 ? f[16 + k] : 0.0;
+            }
+        } else {
+            const double* q = reinterpret_cast<const double*>(r);
+            for (int k = 0; k < 3; ++k) {
+                if (xp) xp[3 * i + k] = q[k];
+                if (vp) vp[3 * i + k] = q[4 + k];
+                if (ap) ap[3 * i + k] = c->order >= 6 ? q[8 + k] : 0.0;
+                if (jp) jp[3 * i + k] = c->order >= 8 ? q[12 + k] : 0.0;
+            }
+        }
+    }
+    return NB_OK;
+}
+
+}  // extern "C"

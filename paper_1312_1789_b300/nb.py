@@ -1,0 +1,276 @@
+"""ctypes binding of libnb (include/nb.h): argument marshalling only.
+
+Every step of the method runs inside libnb.so's CUDA kernels; this module
+converts numpy arrays (host) or torch tensors (device pointers) into the C
+ABI's plain pointers and raises NBError on a negative return code.  There is
+no CPU fallback: if libnb.so is missing or cannot be loaded, `lib()` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnb.so")
+
+NB_OK = 0
+NB_ERR_ARG = -1
+NB_ERR_CUDA = -2
+NB_ERR_NOT_SYNC = -3
+NB_ERR_DT_UNDERFLOW = -4
+NB_ERR_TIMEOUT = -5
+NB_ERR_NAN = -6
+NB_ERR_NOMEM = -7
+NB_FP64 = 0
+NB_MIXED = 1
+
+# Every function the header declares, with its C signature.
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_I32 = C.POINTER(C.c_int32)
+_I64 = C.POINTER(C.c_int64)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+SIGNATURES = {
+    "nb_set_allocator": (C.c_int, [ALLOC_FN, FREE_FN, _P]),
+    "nb_create": (C.c_int, [C.POINTER(_P), C.c_int64, C.c_int, C.c_double]),
+    "nb_destroy": (None, [_P]),
+    "nb_last_error": (C.c_char_p, [_P]),
+    "nb_set_stream": (C.c_int, [_P, _P]),
+    "nb_set_precision": (C.c_int, [_P, C.c_int]),
+    "nb_set_softening": (C.c_int, [_P, _D]),
+    "nb_set_params": (C.c_int, [_P, C.c_double, C.c_double, C.c_double, C.c_double]),
+    "nb_set_particles": (C.c_int, [_P, _D, _D, _D]),
+    "nb_next_block": (C.c_int, [_P, _D, _I32, _I64]),
+    "nb_predict": (C.c_int, [_P, C.c_double]),
+    "nb_force": (C.c_int, [_P, _P, C.c_int64]),
+    "nb_correct": (C.c_int, [_P]),
+    "nb_block_step": (C.c_int, [_P, _D, _I64]),
+    "nb_step_until": (C.c_int, [_P, C.c_double, _I64, _I64]),
+    "nb_energy": (C.c_int, [_P, _D, _D]),
+    "nb_get_state": (C.c_int, [_P, _D, _D, _D, _D, _D]),
+    "nb_set_state": (C.c_int, [_P, _D, _D, _D, _D, _D]),
+    "nb_get_force": (C.c_int, [_P, _D, _D, _D, _D, _D]),
+    "nb_get_predicted": (C.c_int, [_P, _D, _D, _D, _D]),
+    "nb_get_launch": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "nb_set_jsplit": (C.c_int, [_P, C.c_int]),
+    "nb_version": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+class NBError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libnb error {code}: {msg}")
+        self.code = code
+
+
+def lib(path: str = LIB_PATH):
+    """Load libnb.so (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"libnb.so not found at {path}; run `python -m paper_1312_1789_b300.build`")
+        L = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def version() -> str:
+    return lib().nb_version().decode()
+
+
+def _d(a):
+    return None if a is None else a.ctypes.data_as(_D)
+
+
+def _vec(a, n):
+    return np.ascontiguousarray(a, dtype=np.float64).reshape(n, 3)
+
+
+class NBody:
+    """One libnb context: n particles, Hermite order 4/6/8, softening eps.
+
+    Host arrays are numpy float64 ([n][3] for vectors).  Device index arrays
+    may be passed as torch int32 CUDA tensors.
+    """
+
+    def __init__(self, n: int, order: int = 6, eps: float = 0.0, precision: int = NB_MIXED):
+        self._L = lib()
+        self._h = _P()
+        rc = self._L.nb_create(C.byref(self._h), int(n), int(order), float(eps))
+        if rc != NB_OK:
+            raise NBError(rc, self._L.nb_last_error(None).decode())
+        self.n = int(n)
+        self.order = int(order)
+        self.set_precision(precision)
+
+    # -------------------------------------------------------------- plumbing
+    def _check(self, rc):
+        if rc != NB_OK:
+            raise NBError(rc, self._L.nb_last_error(self._h).decode())
+        return rc
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            self._L.nb_destroy(self._h)
+            self._h = _P()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ parameters
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+        handle = getattr(stream, "cuda_stream", stream)
+        self._check(self._L.nb_set_stream(self._h, _P(handle or 0)))
+
+    def set_precision(self, mode: int):
+        self._check(self._L.nb_set_precision(self._h, int(mode)))
+
+    def set_softening(self, eps_i=None):
+        e = None if eps_i is None else np.ascontiguousarray(eps_i, dtype=np.float64)
+        self._check(self._L.nb_set_softening(self._h, _d(e)))
+
+    def set_params(self, eta=0.2, eta_s=0.01, dt_max=1.0 / 16, dt_min=2.0 ** -40):
+        self._check(self._L.nb_set_params(self._h, eta, eta_s, dt_max, dt_min))
+
+    def set_jsplit(self, js: int):
+        self._check(self._L.nb_set_jsplit(self._h, int(js)))
+
+    # ------------------------------------------------------------- the method
+    def set_particles(self, m, x, v):
+        m = np.ascontiguousarray(m, dtype=np.float64)
+        self._check(self._L.nb_set_particles(self._h, _d(m), _d(_vec(x, self.n)), _d(_vec(v, self.n))))
+
+    def next_block(self, want_idx: bool = False):
+        tb = C.c_double()
+        na = C.c_int64()
+        idx = np.zeros(self.n, dtype=np.int32) if want_idx else None
+        self._check(self._L.nb_next_block(self._h, C.byref(tb), None if idx is None else idx.ctypes.data_as(_I32),
+                                          C.byref(na)))
+        if want_idx:
+            return tb.value, idx[: na.value].copy()
+        return tb.value, na.value
+
+    def predict(self, t: float):
+        self._check(self._L.nb_predict(self._h, float(t)))
+
+    def force(self, idx=None, n_act: int = 0):
+        """idx: None (scheduler's list), a numpy int array, or a CUDA int32 tensor."""
+        if idx is None:
+            self._check(self._L.nb_force(self._h, None, int(n_act)))
+            return
+        if hasattr(idx, "data_ptr"):
+            self._check(self._L.nb_force(self._h, _P(idx.data_ptr()), int(idx.numel())))
+            return
+        a = np.ascontiguousarray(idx, dtype=np.int32)
+        self._check(self._L.nb_force(self._h, a.ctypes.data_as(_P), int(a.shape[0])))
+
+    def correct(self):
+        self._check(self._L.nb_correct(self._h))
+
+    def block_step(self):
+        tb = C.c_double()
+        na = C.c_int64()
+        self._check(self._L.nb_block_step(self._h, C.byref(tb), C.byref(na)))
+        return tb.value, na.value
+
+    def step_until(self, t_end: float):
+        nb_ = C.c_int64()
+        ni = C.c_int64()
+        self._check(self._L.nb_step_until(self._h, float(t_end), C.byref(nb_), C.byref(ni)))
+        return nb_.value, ni.value
+
+    def energy(self):
+        ek = C.c_double()
+        ep = C.c_double()
+        self._check(self._L.nb_energy(self._h, C.byref(ek), C.byref(ep)))
+        return ek.value, ep.value
+
+    # --------------------------------------------------------- state exchange
+    def get_state(self):
+        n = self.n
+        x, v = np.zeros((n, 3)), np.zeros((n, 3))
+        d = np.zeros((n, 6, 3))
+        t, dt = np.zeros(n), np.zeros(n)
+        self._check(self._L.nb_get_state(self._h, _d(x), _d(v), _d(d), _d(t), _d(dt)))
+        return {"x": x, "v": v, "d": d, "t": t, "dt": dt}
+
+    def set_state(self, x, v, d, t, dt):
+        n = self.n
+        self._check(self._L.nb_set_state(self._h, _d(_vec(x, n)), _d(_vec(v, n)),
+                                         _d(np.ascontiguousarray(d, dtype=np.float64).reshape(n, 6, 3)),
+                                         _d(np.ascontiguousarray(t, dtype=np.float64)),
+                                         _d(np.ascontiguousarray(dt, dtype=np.float64))))
+
+    def get_force(self, n_act: int):
+        out = {k: np.zeros((n_act, 3)) for k in ("acc", "jerk", "snap", "crackle")}
+        out["pot"] = np.zeros(n_act)
+        self._check(self._L.nb_get_force(self._h, _d(out["acc"]), _d(out["jerk"]), _d(out["snap"]),
+                                         _d(out["crackle"]), _d(out["pot"])))
+        return out
+
+    def get_predicted(self):
+        n = self.n
+        xp, vp, ap, jp = (np.zeros((n, 3)) for _ in range(4))
+        self._check(self._L.nb_get_predicted(self._h, _d(xp), _d(vp), _d(ap), _d(jp)))
+        return xp, vp, ap, jp
+
+    def get_launch(self):
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        self._check(self._L.nb_get_launch(self._h, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
+
+
+class TorchAllocator:
+    """Routes libnb's device allocations through torch's caching allocator.
+
+    Keep the instance alive while contexts created under it exist.
+    """
+
+    def __init__(self, device=None):
+        import torch
+        self._torch = torch
+        self._device = torch.cuda.current_device() if device is None else device
+        self._alloc = ALLOC_FN(self._do_alloc)
+        self._free = FREE_FN(self._do_free)
+
+    def _do_alloc(self, nbytes, _user):
+        try:
+            return int(self._torch.cuda.caching_allocator_alloc(int(nbytes), self._device))
+        except Exception:
+            return None
+
+    def _do_free(self, ptr, _user):
+        self._torch.cuda.caching_allocator_delete(ptr)
+
+    def install(self):
+        rc = lib().nb_set_allocator(self._alloc, self._free, None)
+        if rc != NB_OK:
+            raise NBError(rc, lib().nb_last_error(None).decode())
+        return self
+
+    @staticmethod
+    def uninstall():
+        lib().nb_set_allocator(ALLOC_FN(), FREE_FN(), None)

@@ -1,0 +1,70 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+include/nb.h declares.  No compute call runs here: these tests need no GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "nb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(nb_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libnb():
+    from paper_1312_1789_b300 import build, nb
+    build.build()
+    return nb.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("nb_create", "nb_set_particles", "nb_predict", "nb_force", "nb_correct", "nb_next_block",
+                     "nb_energy", "nb_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(libnb):
+    missing = [n for n in _declared() if not hasattr(libnb, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_1312_1789_b300 import nb
+    assert sorted(nb.SIGNATURES) == _declared()
+
+
+def test_version_string(libnb):
+    assert b"sm_103a" in libnb.nb_version()
+
+
+def test_create_rejects_bad_arguments_before_touching_the_device(libnb):
+    h = C.c_void_p()
+    assert libnb.nb_create(C.byref(h), 0, 6, 1e-4) == -1
+    assert libnb.nb_create(C.byref(h), 16, 5, 1e-4) == -1
+    assert libnb.nb_create(C.byref(h), 16, 6, -1.0) == -1
+    assert libnb.nb_create(C.byref(h), 16, 6, float("nan")) == -1
+    assert b"eps" in libnb.nb_last_error(None)
+    assert not h.value
+
+
+def test_null_context_is_rejected(libnb):
+    assert libnb.nb_predict(None, 0.0) == -1
+    assert libnb.nb_correct(None) == -1
+    libnb.nb_destroy(None)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_1312_1789_b300 import nb
+    saved = nb._lib
+    nb._lib = None
+    try:
+        with pytest.raises(ImportError):
+            nb.lib(str(tmp_path / "libnb.so"))
+    finally:
+        nb._lib = saved
