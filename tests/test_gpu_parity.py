@@ -1,0 +1,407 @@
+"""GPU parity: every kernel of the hot path, called through the C ABI, against
+the CPU oracle on the same seeded inputs (tolerances: tests/gpu_common.py).
+
+Sizes span several 128-particle j tiles and a ragged tail; the large-N test
+runs the 2^20 + 2 nucleus workload in the launch shape the benchmark times and
+checks sampled particles one by one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as orc
+from gpu_common import assert_force_close, make_ctx, oracle_force_on_predicted
+from paper_1312_1789_b300 import ics, nb
+
+pytestmark = pytest.mark.gpu
+
+PRECS = [nb.NB_FP64, nb.NB_MIXED]
+PNAME = {nb.NB_FP64: "fp64", nb.NB_MIXED: "mixed"}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1312_1789_b300 import build
+    build.build()
+    nb.lib()
+
+
+def _system(n, seed, kind):
+    """Plummer sphere (uniform eps 1e-4) or stars + two unsoftened holes."""
+    if kind == "plummer":
+        m, x, v = ics.plummer(n, seed)
+        return m, x, v, np.full(n, 1e-8)
+    m, x, v = ics.plummer(n - 2, seed)
+    mb, xb, vb = ics.bh_circular_pair(0.005, 0.1)
+    eps2 = np.concatenate([np.full(n - 2, 1e-8), np.zeros(2)])
+    return np.concatenate([m, mb]), np.concatenate([x, xb]), np.concatenate([v, vb]), eps2
+
+
+def _idx(kind, n, rng):
+    if kind == "all":
+        return np.arange(n, dtype=np.int32)
+    if kind == "subset":
+        return np.sort(rng.choice(n, 37, replace=False)).astype(np.int32)
+    return np.array([n // 2], dtype=np.int32)
+
+
+# ------------------------------------------------------------------ force K2+K3
+@pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
+@pytest.mark.parametrize("order", [4, 6, 8])
+@pytest.mark.parametrize("kind", ["plummer", "holes"])
+def test_force_parity(prec, order, kind):
+    n = 3 * 128 + 37
+    m, x, v, eps2 = _system(n, 7 + order, kind)
+    ctx = make_ctx(m, x, v, eps2, order, prec, pair=(kind == "holes"))
+    ctx.step_until(1.0 / 128)  # non-trivial held derivatives and times
+    tb, _ = ctx.next_block()
+    ctx.predict(tb)
+    rng = np.random.default_rng(order)
+    for which in ("all", "subset", "one"):
+        idx = _idx(which, n, rng)
+        O = oracle_force_on_predicted(ctx, m, eps2, idx, order)
+        for js in (0, 1, 3, 7):
+            ctx.set_jsplit(js)
+            ctx.force(idx)
+            G = ctx.get_force(len(idx))
+            assert_force_close(G, O, order, prec, f"{PNAME[prec]} order {order} {kind} {which} jsplit {js}")
+    ctx.close()
+
+
+def test_force_jsplit_changes_only_rounding():
+    # FP64 results of different split counts agree to rounding; a given
+    # launch shape is bitwise reproducible.
+    n = 1000
+    m, x, v, eps2 = _system(n, 3, "plummer")
+    ctx = make_ctx(m, x, v, eps2, 6, nb.NB_FP64)
+    ctx.predict(1.0 / 256)
+    idx = np.arange(n, dtype=np.int32)
+    ctx.set_jsplit(5)
+    ctx.force(idx)
+    a = ctx.get_force(n)["acc"]
+    ctx.force(idx)
+    b = ctx.get_force(n)["acc"]
+    assert np.array_equal(a, b)
+    ctx.set_jsplit(1)
+    ctx.force(idx)
+    c = ctx.get_force(n)["acc"]
+    assert np.allclose(a, c, rtol=1e-13, atol=0)
+
+
+# -------------------------------------------------------------------- predictor
+@pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
+@pytest.mark.parametrize("order", [4, 6, 8])
+def test_predictor_parity(prec, order):
+    n = 2 * 128 + 5
+    m, x, v, eps2 = _system(n, 21, "plummer")
+    ctx = make_ctx(m, x, v, eps2, order, prec)
+    ctx.step_until(1.0 / 64)
+    tb, _ = ctx.next_block()
+    ctx.predict(tb)
+    S = ctx.get_state()
+    assert np.any(S["t"] != S["t"][0]), "want particles at different times"
+    xo, vo, ao, jo = orc.predict(order, tb, S["t"], S["x"], S["v"], S["d"])
+    xg, vg, ag, jg = ctx.get_predicted()
+    if prec == nb.NB_FP64:
+        assert np.all(np.abs(xg - xo) <= 2e-15 * np.maximum(np.abs(xo), 1.0))
+        assert np.all(np.abs(vg - vo) <= 2e-15 * np.maximum(np.abs(vo), 1.0))
+        if order >= 6:
+            assert np.all(np.abs(ag - ao) <= 1e-14 * np.maximum(np.abs(ao), 1.0))
+        if order >= 8:
+            assert np.all(np.abs(jg - jo) <= 1e-13 * np.maximum(np.abs(jo), 1.0))
+    else:
+        # double-single position: |hi + lo - x| <= 2^-48 |x|; the rest is one float rounding
+        assert np.all(np.abs(xg - xo) <= 2e-14 * np.maximum(np.abs(xo), 1e-3))
+        assert np.all(np.abs(vg - vo) <= 1.2e-7 * np.abs(vo) + 1e-15)
+        if order >= 6:
+            assert np.all(np.abs(ag - ao) <= 1.2e-7 * np.abs(ao) + 1e-14)
+        if order >= 8:
+            assert np.all(np.abs(jg - jo) <= 1.2e-7 * np.abs(jo) + 1e-13)
+
+
+# -------------------------------------------------------------------- scheduler
+def test_scheduler_parity():
+    n = 2048 + 300  # more than one scheduler chunk, ragged
+    m, x, v, eps2 = _system(n, 5, "plummer")
+    ctx = make_ctx(m, x, v, eps2, 6, nb.NB_MIXED)
+    for t_stop in (0.0, 1.0 / 512, 1.0 / 128, 1.0 / 32):
+        if t_stop > 0:
+            ctx.step_until(t_stop)
+        S = ctx.get_state()
+        tb_o, idx_o = orc.next_block(S["t"], S["dt"])
+        tb_g, idx_g = ctx.next_block(want_idx=True)
+        assert tb_g == tb_o
+        assert np.array_equal(idx_g, idx_o)
+
+
+# -------------------------------------------------------------------- corrector
+@pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
+@pytest.mark.parametrize("order", [4, 6, 8])
+def test_corrector_parity(prec, order):
+    n = 3 * 128 + 11
+    m, x, v, eps2 = _system(n, 40 + order, "plummer")
+    eta = 0.2 if order != 4 else 0.02
+    ctx = make_ctx(m, x, v, eps2, order, prec, eta=eta)
+    ctx.step_until(1.0 / 64)
+    tb, idx = ctx.next_block(want_idx=True)
+    ctx.predict(tb)
+    ctx.force()
+    S0 = ctx.get_state()
+    F = ctx.get_force(len(idx))
+    ctx.correct()
+    S1 = ctx.get_state()
+    mm = order // 2
+    newd = np.stack([F["acc"], F["jerk"], F["snap"], F["crackle"]], axis=1)  # [n_act][4][3]
+    for p, i in enumerate(idx):
+        h = tb - S0["t"][i]
+        D0 = S0["d"][i, :4]
+        D1 = newd[p, :mm]
+        hi = orc.interp(mm, h, D0[:mm], D1)
+        Dfull = np.vstack([D1, hi])
+        x1, v1 = orc.correct(order, h, S0["x"][i], S0["v"][i], D0, Dfull[:4])
+        lim = min(orc.dt_criterion(order, eta, Dfull), 2 * h)
+        dt_o = orc.dt_quantise(lim, tb, 1.0 / 16, 2.0 ** -40)
+        assert S1["t"][i] == tb
+        assert S1["dt"][i] == dt_o, (i, S1["dt"][i], dt_o)
+        assert np.all(np.abs(S1["x"][i] - x1) <= 2e-15 * max(1.0, np.abs(x1).max()))
+        assert np.all(np.abs(S1["v"][i] - v1) <= 2e-15 * max(1.0, np.abs(v1).max()))
+        assert np.array_equal(S1["d"][i, :mm], D1)
+        for k in range(mm, min(2 * mm, 6)):
+            scale = sum((np.linalg.norm(D0[q]) + np.linalg.norm(D1[q])) * h ** (q - k) for q in range(mm))
+            assert np.linalg.norm(S1["d"][i, k] - hi[k - mm]) <= 1e-11 * scale, (i, k)
+
+
+# ---------------------------------------------------------- whole integration
+def test_block_sequence_plummer_1k_exact():
+    # Plummer N = 1024, order 6, eps 1e-4, eta 0.2, dt_max 1/16 to t = 0.125:
+    # FP64 path and oracle take the identical sequence of (t_blk, active set).
+    wl = ics.standard_workload(0)
+    st = orc.State(wl.m, wl.eps2, wl.x, wl.v)
+    log = orc.integrate(st, order=6, t_end=wl.t_end, eta=wl.eta, nthreads=16, log=True)
+    ctx = make_ctx(wl.m, wl.x, wl.v, wl.eps2, 6, nb.NB_FP64)
+    k = 0
+    while True:
+        tb, idx = ctx.next_block(want_idx=True)
+        if tb > wl.t_end:
+            break
+        assert k < len(log), "device took more blocks"
+        assert tb == log[k][0], f"block {k}: t {tb} vs {log[k][0]}"
+        assert np.array_equal(idx, log[k][1]), f"block {k}: active sets differ"
+        ctx.predict(tb)
+        ctx.force()
+        ctx.correct()
+        k += 1
+    assert k == len(log)
+    S = ctx.get_state()
+    assert np.all(S["t"] == wl.t_end)
+    assert np.max(np.abs(S["x"] - st.x)) < 1e-11
+    assert np.max(np.abs(S["v"] - st.v)) < 1e-10
+    assert np.array_equal(S["dt"], st.dt)
+
+
+def test_mixed_energy_error_close_to_fp64():
+    # Same system on both paths to t = 0.125; energies measured in FP64.
+    wl = ics.standard_workload(0)
+    out = {}
+    for prec in PRECS:
+        ctx = make_ctx(wl.m, wl.x, wl.v, wl.eps2, 6, prec)
+        ctx.set_precision(nb.NB_FP64)
+        e0 = sum(ctx.energy())
+        ctx.set_precision(prec)
+        ctx.step_until(wl.t_end)
+        ctx.set_precision(nb.NB_FP64)
+        e1 = sum(ctx.energy())
+        out[prec] = (e1 - e0) / e0
+    print("dE/E fp64 %.3e mixed %.3e" % (out[nb.NB_FP64], out[nb.NB_MIXED]))
+    assert abs(out[nb.NB_FP64]) < 1e-9
+    assert abs(out[nb.NB_MIXED]) < 1e-8
+
+
+# ----------------------------------------------------------------------- energy
+@pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
+def test_energy_parity(prec):
+    n = 3 * 128 + 7
+    m, x, v, eps2 = _system(n, 9, "holes")
+    ctx = make_ctx(m, x, v, eps2, 6, prec, pair=True)
+    ek, ep = ctx.energy()
+    ek_o, ep_o = orc.energy(m, eps2, x, v)
+    tol = 1e-13 if prec == nb.NB_FP64 else 1e-6
+    assert ek == pytest.approx(ek_o, rel=1e-14)
+    assert ep == pytest.approx(ep_o, rel=tol)
+    ctx.step_until(1.0 / 16)
+    S = ctx.get_state()
+    assert np.all(S["t"] == 1.0 / 16)
+    ek, ep = ctx.energy()
+    ek_o, ep_o = orc.energy(m, eps2, S["x"], S["v"])
+    assert ek == pytest.approx(ek_o, rel=1e-14)
+    assert ep == pytest.approx(ep_o, rel=tol)
+
+
+# ------------------------------------------------------------ full-size sample
+def test_nucleus_2pow20_sampled_parity():
+    # 2^20 stars + two holes, every particle active (the benchmarked block),
+    # mixed path; sampled particles (both holes among them) against the oracle
+    # one by one.  Then the FP64 path on a 64-particle block of the same system.
+    wl = ics.standard_workload(2)
+    n = wl.n
+    ctx = make_ctx(wl.m, wl.x, wl.v, wl.eps2, 6, nb.NB_MIXED, pair=True)
+    ctx.predict(2.0 ** -12)
+    ctx.force(np.arange(n, dtype=np.int32))
+    it, js, nt = ctx.get_launch()
+    assert it * nt >= n and js >= 1
+    G = ctx.get_force(n)
+    rng = np.random.default_rng(0)
+    sample = np.concatenate([rng.choice(n - 2, 22, replace=False), [n - 2, n - 1]]).astype(np.int32)
+    O = oracle_force_on_predicted(ctx, wl.m, wl.eps2, sample, 6)
+    Gs = {k: G[k][sample] for k in G}
+    assert_force_close(Gs, O, 6, nb.NB_MIXED, "nucleus 2^20 mixed, sampled")
+    ctx.set_precision(nb.NB_FP64)
+    ctx.predict(2.0 ** -12)
+    blk = np.sort(rng.choice(n, 64, replace=False)).astype(np.int32)
+    ctx.force(blk)
+    G = ctx.get_force(len(blk))
+    O = oracle_force_on_predicted(ctx, wl.m, wl.eps2, blk, 6)
+    assert_force_close(G, O, 6, nb.NB_FP64, "nucleus 2^20 fp64, 64-particle block")
+    ctx.close()
+
+
+# --------------------------------------------------------- checkpoint / restart
+@pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
+def test_checkpoint_restart_is_bitwise(prec):
+    n = 700
+    m, x, v, eps2 = _system(n, 12, "plummer")
+    a = make_ctx(m, x, v, eps2, 6, prec)
+    a.step_until(1.0 / 64)
+    S = a.get_state()
+    b = make_ctx(m, x, v, eps2, 6, prec)
+    b.set_state(S["x"], S["v"], S["d"], S["t"], S["dt"])
+    a.step_until(1.0 / 16)
+    b.step_until(1.0 / 16)
+    Sa, Sb = a.get_state(), b.get_state()
+    for k in Sa:
+        assert np.array_equal(Sa[k], Sb[k]), k
+
+
+# ------------------------------------------------------------------ edge cases
+def test_single_particle_moves_in_a_straight_line():
+    ctx = nb.NBody(1, 6, 1e-4, nb.NB_FP64)
+    ctx.set_particles([1.0], [[0.5, -0.25, 2.0]], [[0.125, 0.5, -1.0]])
+    nbk, ni = ctx.step_until(0.5)
+    assert nbk == 8 and ni == 8
+    S = ctx.get_state()
+    assert np.allclose(S["x"][0], [0.5 + 0.0625, -0.25 + 0.25, 2.0 - 0.5], rtol=0, atol=1e-15)
+    assert np.all(S["d"] == 0) and S["dt"][0] == 1.0 / 16
+
+
+@pytest.mark.parametrize("order", [4, 6, 8])
+def test_unsoftened_kepler_pair_matches_oracle(order):
+    m = np.array([0.5, 0.5])
+    e = 0.5
+    r = 1 + e
+    vrel = math.sqrt((1 - e) / (1 + e))
+    x = np.array([[0.5 * r, 0, 0], [-0.5 * r, 0, 0]])
+    v = np.array([[0, 0.5 * vrel, 0], [0, -0.5 * vrel, 0]])
+    eta = 0.02 if order == 4 else 0.1
+    ctx = make_ctx(m, x, v, np.zeros(2), order, nb.NB_FP64, eta=eta, pair=True)
+    ctx.step_until(2.0)
+    st = orc.State(m, 0.0, x, v)
+    orc.integrate(st, order=order, t_end=2.0, eta=eta)
+    S = ctx.get_state()
+    assert np.max(np.abs(S["x"] - st.x)) < 1e-11
+    assert np.array_equal(S["dt"], st.dt)
+
+
+def test_ragged_sizes_force():
+    for n in (1, 2, 127, 128, 129, 255):
+        m, x, v, eps2 = _system(max(n, 3), 77, "plummer")
+        m, x, v, eps2 = m[:n], x[:n], v[:n], eps2[:n]
+        ctx = make_ctx(m, x, v, eps2, 6, nb.NB_FP64)
+        ctx.predict(1.0 / 1024)
+        idx = np.arange(n, dtype=np.int32)
+        ctx.force(idx)
+        G = ctx.get_force(n)
+        O = oracle_force_on_predicted(ctx, m, eps2, idx, 6)
+        if n == 1:
+            assert np.all(G["acc"] == 0) and G["pot"][0] == 0.0
+        else:
+            assert_force_close(G, O, 6, nb.NB_FP64, f"n={n}")
+
+
+# --------------------------------------------------------------- error paths
+def test_errors_are_reported_not_faulted():
+    n = 300
+    m, x, v, eps2 = _system(n, 1, "plummer")
+    ctx = make_ctx(m, x, v, eps2, 6, nb.NB_MIXED)
+    with pytest.raises(nb.NBError) as e:
+        ctx.correct()
+    assert e.value.code == nb.NB_ERR_ARG
+    ctx.predict(1.0 / 64)
+    with pytest.raises(nb.NBError) as e:
+        ctx.force(np.array([0, n + 3], dtype=np.int32))
+    assert e.value.code == nb.NB_ERR_ARG
+    ctx.step_until(1.0 / 256)
+    S = ctx.get_state()
+    if np.all(S["t"] == S["t"][0]):
+        ctx.block_step()
+    with pytest.raises(nb.NBError) as e:
+        ctx.energy()
+    assert e.value.code == nb.NB_ERR_NOT_SYNC
+    bad = x.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(nb.NBError) as e:
+        ctx.set_particles(m, bad, v)
+    assert e.value.code == nb.NB_ERR_NAN
+    # a minimum step larger than what the start-up criterion asks for
+    c2 = nb.NBody(n, 6, 1e-4, nb.NB_FP64)
+    c2.set_params(0.2, 0.01, 1.0 / 16, 1.0 / 32)
+    with pytest.raises(nb.NBError) as e:
+        c2.set_particles(m, x, v)
+    assert e.value.code == nb.NB_ERR_DT_UNDERFLOW
+
+
+def test_device_index_out_of_range_is_reported():
+    torch = pytest.importorskip("torch")
+    n = 300
+    m, x, v, eps2 = _system(n, 2, "plummer")
+    ctx = make_ctx(m, x, v, eps2, 6, nb.NB_FP64)
+    ctx.predict(1.0 / 64)
+    idx = torch.tensor([1, 2, n + 10], dtype=torch.int32, device="cuda")
+    ctx.force(idx)
+    with pytest.raises(nb.NBError) as e:
+        ctx.get_force(3)
+    assert e.value.code == nb.NB_ERR_ARG
+    # the context stays usable
+    ctx.force(np.array([1, 2], dtype=np.int32))
+    assert ctx.get_force(2)["acc"].shape == (2, 3)
+
+
+# ----------------------------------------------------------- torch plumbing
+def test_torch_allocator_stream_and_device_indices():
+    torch = pytest.importorskip("torch")
+    n = 600
+    m, x, v, eps2 = _system(n, 8, "plummer")
+    ref = make_ctx(m, x, v, eps2, 6, nb.NB_MIXED)
+    ref.step_until(1.0 / 64)
+    alloc = nb.TorchAllocator().install()
+    try:
+        ctx = nb.NBody(n, 6, 1e-4, nb.NB_MIXED)
+        s = torch.cuda.Stream()
+        ctx.set_stream(s)
+        ctx.set_particles(m, x, v)
+        ctx.step_until(1.0 / 64)
+        A, B = ref.get_state(), ctx.get_state()
+        for k in A:
+            assert np.array_equal(A[k], B[k]), k
+        tb, idx = ctx.next_block(want_idx=True)
+        ctx.predict(tb)
+        ctx.force(torch.from_numpy(idx).cuda())
+        G = ctx.get_force(len(idx))
+        ref.next_block()
+        ref.predict(tb)
+        ref.force(idx)
+        assert np.array_equal(G["acc"], ref.get_force(len(idx))["acc"])
+        ctx.close()
+    finally:
+        nb.TorchAllocator.uninstall()
+    del alloc
