@@ -59,6 +59,71 @@ __device__ void drain_after_timeout(uint64_t* bars, int k, int nt)
     for (int kk = k; kk < nt && kk < k + NSTAGE; ++kk) mbar_wait_bounded(&bars[kk % NSTAGE], (kk / NSTAGE) & 1);
 }
 
+// One j tile for one i-particle: accumulates the pair terms into acc.  SELF:
+// the tile may contain the i-particle itself (at position self_rel), whose
+// pair is skipped by zeroing its inverse distance (every term carries it).
+template <int ORDER, int RW, bool PAIR, bool SELF>
+__device__ __forceinline__ void tile_mixed(const float4* __restrict__ b, const float4 i0, const float4 i1,
+                                           const float4 i2, const float4 i3, const float4 i4, const float ei2,
+                                           const float eps2u, const int self_rel, float (&acc)[ncomp(ORDER)])
+{
+    constexpr int NC = ncomp(ORDER);
+#pragma unroll 2
+    for (int jj = 0; jj < JT; ++jj) {
+        const float4 w0 = b[jj * RW + 0];
+        const float4 w1 = b[jj * RW + 1];
+        const float dx = (w0.x - i0.x) + (w1.x - i1.x);
+        const float dy = (w0.y - i0.y) + (w1.y - i1.y);
+        const float dz = (w0.z - i0.z) + (w1.z - i1.z);
+        const float e2 = PAIR ? fmaxf(w1.w, ei2) : eps2u;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, e2)));
+        float rinv = guard_rinv<PAIR>(r2);
+        if (SELF) rinv = (jj == self_rel) ? 0.0f : rinv;
+        const float mr = w0.w * rinv;
+        if (ORDER == 0) {
+            acc[0] += mr;
+            continue;
+        }
+        const float rinv2 = rinv * rinv;
+        const float q = mr * rinv2;
+        const float4 w2 = b[jj * RW + 2];
+        const float dvx = w2.x - i2.x, dvy = w2.y - i2.y, dvz = w2.z - i2.z;
+        acc[0] = fmaf(q, dx, acc[0]);
+        acc[1] = fmaf(q, dy, acc[1]);
+        acc[2] = fmaf(q, dz, acc[2]);
+        const float al = fmaf(dx, dvx, fmaf(dy, dvy, dz * dvz)) * rinv2;
+        const float c1 = -3.0f * al;
+        acc[3] = fmaf(q, fmaf(c1, dx, dvx), acc[3]);
+        acc[4] = fmaf(q, fmaf(c1, dy, dvy), acc[4]);
+        acc[5] = fmaf(q, fmaf(c1, dz, dvz), acc[5]);
+        if (ORDER >= 6) {
+            const float4 w3 = b[jj * RW + 3];
+            const float dax = w3.x - i3.x, day = w3.y - i3.y, daz = w3.z - i3.z;
+            const float w =
+                fmaf(dvx, dvx, fmaf(dvy, dvy, fmaf(dvz, dvz, fmaf(dx, dax, fmaf(dy, day, dz * daz))))) * rinv2;
+            const float c2 = -6.0f * al;
+            const float c3 = fmaf(15.0f * al, al, -3.0f * w);
+            acc[6] = fmaf(q, fmaf(c3, dx, fmaf(c2, dvx, dax)), acc[6]);
+            acc[7] = fmaf(q, fmaf(c3, dy, fmaf(c2, dvy, day)), acc[7]);
+            acc[8] = fmaf(q, fmaf(c3, dz, fmaf(c2, dvz, daz)), acc[8]);
+            if (ORDER >= 8) {
+                const float4 w4 = b[jj * RW + 4];
+                const float dkx = w4.x - i4.x, dky = w4.y - i4.y, dkz = w4.z - i4.z;
+                const float u =
+                    fmaf(3.0f, fmaf(dvx, dax, fmaf(dvy, day, dvz * daz)), fmaf(dx, dkx, fmaf(dy, dky, dz * dkz))) *
+                    rinv2;
+                const float c4 = -9.0f * al;
+                const float c5 = fmaf(45.0f * al, al, -9.0f * w);
+                const float c6 = fmaf(al, fmaf(-105.0f * al, al, 45.0f * w), -3.0f * u);
+                acc[9] = fmaf(q, fmaf(c6, dx, fmaf(c5, dvx, fmaf(c4, dax, dkx))), acc[9]);
+                acc[10] = fmaf(q, fmaf(c6, dy, fmaf(c5, dvy, fmaf(c4, day, dky))), acc[10]);
+                acc[11] = fmaf(q, fmaf(c6, dz, fmaf(c5, dvz, fmaf(c4, daz, dkz))), acc[11]);
+            }
+        }
+        acc[NC - 1] += mr;
+    }
+}
+
 // ----------------------------------------------------------------- mixed
 template <int ORDER, int RW, bool PAIR>
 __global__ void __launch_bounds__(FORCE_NT) k_force_mixed(const float4* __restrict__ js, const int32_t* __restrict__ idx,
@@ -124,60 +189,12 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_mixed(const float4* __restri
         float acc[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) acc[c] = 0.f;
-
-#pragma unroll 2
-        for (int jj = 0; jj < JT; ++jj) {
-            const float4 w0 = b[jj * RW + 0];
-            const float4 w1 = b[jj * RW + 1];
-            const float dx = (w0.x - i0.x) + (w1.x - i1.x);
-            const float dy = (w0.y - i0.y) + (w1.y - i1.y);
-            const float dz = (w0.z - i0.z) + (w1.z - i1.z);
-            const float e2 = PAIR ? fmaxf(w1.w, ei2) : eps2u;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, e2)));
-            const float rinv = guard_rinv<PAIR>(r2);
-            const float mr = w0.w * rinv;
-            if (ORDER == 0) {
-                acc[0] += mr;
-                continue;
-            }
-            const float rinv2 = rinv * rinv;
-            const float q = mr * rinv2;
-            const float4 w2 = b[jj * RW + 2];
-            const float dvx = w2.x - i2.x, dvy = w2.y - i2.y, dvz = w2.z - i2.z;
-            acc[0] = fmaf(q, dx, acc[0]);
-            acc[1] = fmaf(q, dy, acc[1]);
-            acc[2] = fmaf(q, dz, acc[2]);
-            const float al = fmaf(dx, dvx, fmaf(dy, dvy, dz * dvz)) * rinv2;
-            const float c1 = -3.0f * al;
-            acc[3] = fmaf(q, fmaf(c1, dx, dvx), acc[3]);
-            acc[4] = fmaf(q, fmaf(c1, dy, dvy), acc[4]);
-            acc[5] = fmaf(q, fmaf(c1, dz, dvz), acc[5]);
-            if (ORDER >= 6) {
-                const float4 w3 = b[jj * RW + 3];
-                const float dax = w3.x - i3.x, day = w3.y - i3.y, daz = w3.z - i3.z;
-                const float w = fmaf(dvx, dvx, fmaf(dvy, dvy, fmaf(dvz, dvz, fmaf(dx, dax, fmaf(dy, day, dz * daz))))) *
-                                rinv2;
-                const float c2 = -6.0f * al;
-                const float c3 = fmaf(15.0f * al, al, -3.0f * w);
-                acc[6] = fmaf(q, fmaf(c3, dx, fmaf(c2, dvx, dax)), acc[6]);
-                acc[7] = fmaf(q, fmaf(c3, dy, fmaf(c2, dvy, day)), acc[7]);
-                acc[8] = fmaf(q, fmaf(c3, dz, fmaf(c2, dvz, daz)), acc[8]);
-                if (ORDER >= 8) {
-                    const float4 w4 = b[jj * RW + 4];
-                    const float dkx = w4.x - i4.x, dky = w4.y - i4.y, dkz = w4.z - i4.z;
-                    const float u =
-                        fmaf(3.0f, fmaf(dvx, dax, fmaf(dvy, day, dvz * daz)), fmaf(dx, dkx, fmaf(dy, dky, dz * dkz))) *
-                        rinv2;
-                    const float c4 = -9.0f * al;
-                    const float c5 = fmaf(45.0f * al, al, -9.0f * w);
-                    const float c6 = fmaf(al, fmaf(-105.0f * al, al, 45.0f * w), -3.0f * u);
-                    acc[9] = fmaf(q, fmaf(c6, dx, fmaf(c5, dvx, fmaf(c4, dax, dkx))), acc[9]);
-                    acc[10] = fmaf(q, fmaf(c6, dy, fmaf(c5, dvy, fmaf(c4, day, dky))), acc[10]);
-                    acc[11] = fmaf(q, fmaf(c6, dz, fmaf(c5, dvz, fmaf(c4, daz, dkz))), acc[11]);
-                }
-            }
-            acc[NC - 1] += mr;
-        }
+        // the tile holding a lane's own particle takes the masked variant
+        const int self_rel = gi - (t0 + k) * JT;
+        if (__any_sync(0xffffffffu, (unsigned)self_rel < (unsigned)JT))
+            tile_mixed<ORDER, RW, PAIR, true>(b, i0, i1, i2, i3, i4, ei2, eps2u, self_rel, acc);
+        else
+            tile_mixed<ORDER, RW, PAIR, false>(b, i0, i1, i2, i3, i4, ei2, eps2u, -1, acc);
 #pragma unroll
         for (int c = 0; c < NC; ++c) ds_add(hi[c], lo[c], acc[c]);
 
@@ -192,6 +209,64 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_mixed(const float4* __restri
 #pragma unroll
         for (int c = 0; c < NC; ++c)
             partial[((size_t)split * NC + c) * n_act + p] = (double)hi[c] + (double)lo[c];
+    }
+}
+
+template <int ORDER, int RW, bool PAIR, bool SELF>
+__device__ __forceinline__ void tile_fp64(const double2* __restrict__ b, const double2 i0, const double2 i1,
+                                          const double2 i2, const double2 i3, const double2 i4, const double2 i5,
+                                          const double2 i6, const double2 i7, const double ei2, const double eps2u,
+                                          const int self_rel, double (&acc)[ncomp(ORDER)])
+{
+    constexpr int NC = ncomp(ORDER);
+    for (int jj = 0; jj < JT; ++jj) {
+        const double2 w0 = b[jj * RW + 0], w1 = b[jj * RW + 1];
+        const double dx = w0.x - i0.x, dy = w0.y - i0.y, dz = w1.x - i1.x;
+        const double2 w3 = b[jj * RW + 3];
+        const double e2 = PAIR ? fmax(w3.y, ei2) : eps2u;
+        const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, e2)));
+        double rinv = guard_rinv_d<PAIR>(r2);
+        if (SELF) rinv = (jj == self_rel) ? 0.0 : rinv;
+        const double mr = w1.y * rinv;
+        if (ORDER == 0) {
+            acc[0] += mr;
+            continue;
+        }
+        const double rinv2 = rinv * rinv;
+        const double q = mr * rinv2;
+        const double2 w2 = b[jj * RW + 2];
+        const double dvx = w2.x - i2.x, dvy = w2.y - i2.y, dvz = w3.x - i3.x;
+        acc[0] = fma(q, dx, acc[0]);
+        acc[1] = fma(q, dy, acc[1]);
+        acc[2] = fma(q, dz, acc[2]);
+        const double al = fma(dx, dvx, fma(dy, dvy, dz * dvz)) * rinv2;
+        const double c1 = -3.0 * al;
+        acc[3] = fma(q, fma(c1, dx, dvx), acc[3]);
+        acc[4] = fma(q, fma(c1, dy, dvy), acc[4]);
+        acc[5] = fma(q, fma(c1, dz, dvz), acc[5]);
+        if (ORDER >= 6) {
+            const double2 w4 = b[jj * RW + 4], w5 = b[jj * RW + 5];
+            const double dax = w4.x - i4.x, day = w4.y - i4.y, daz = w5.x - i5.x;
+            const double w = fma(dvx, dvx, fma(dvy, dvy, fma(dvz, dvz, fma(dx, dax, fma(dy, day, dz * daz))))) * rinv2;
+            const double c2 = -6.0 * al;
+            const double c3 = fma(15.0 * al, al, -3.0 * w);
+            acc[6] = fma(q, fma(c3, dx, fma(c2, dvx, dax)), acc[6]);
+            acc[7] = fma(q, fma(c3, dy, fma(c2, dvy, day)), acc[7]);
+            acc[8] = fma(q, fma(c3, dz, fma(c2, dvz, daz)), acc[8]);
+            if (ORDER >= 8) {
+                const double2 w6 = b[jj * RW + 6], w7 = b[jj * RW + 7];
+                const double dkx = w6.x - i6.x, dky = w6.y - i6.y, dkz = w7.x - i7.x;
+                const double u =
+                    fma(3.0, fma(dvx, dax, fma(dvy, day, dvz * daz)), fma(dx, dkx, fma(dy, dky, dz * dkz))) * rinv2;
+                const double c4 = -9.0 * al;
+                const double c5 = fma(45.0 * al, al, -9.0 * w);
+                const double c6 = fma(al, fma(-105.0 * al, al, 45.0 * w), -3.0 * u);
+                acc[9] = fma(q, fma(c6, dx, fma(c5, dvx, fma(c4, dax, dkx))), acc[9]);
+                acc[10] = fma(q, fma(c6, dy, fma(c5, dvy, fma(c4, day, dky))), acc[10]);
+                acc[11] = fma(q, fma(c6, dz, fma(c5, dvz, fma(c4, daz, dkz))), acc[11]);
+            }
+        }
+        acc[NC - 1] += mr;
     }
 }
 
@@ -265,56 +340,11 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_fp64(const double2* __restri
         double acc[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) acc[c] = 0.0;
-
-        for (int jj = 0; jj < JT; ++jj) {
-            const double2 w0 = b[jj * RW + 0], w1 = b[jj * RW + 1];
-            const double dx = w0.x - i0.x, dy = w0.y - i0.y, dz = w1.x - i1.x;
-            const double2 w3 = b[jj * RW + 3];
-            const double e2 = PAIR ? fmax(w3.y, ei2) : eps2u;
-            const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, e2)));
-            const double rinv = guard_rinv_d<PAIR>(r2);
-            const double mr = w1.y * rinv;
-            if (ORDER == 0) {
-                acc[0] += mr;
-                continue;
-            }
-            const double rinv2 = rinv * rinv;
-            const double q = mr * rinv2;
-            const double2 w2 = b[jj * RW + 2];
-            const double dvx = w2.x - i2.x, dvy = w2.y - i2.y, dvz = w3.x - i3.x;
-            acc[0] = fma(q, dx, acc[0]);
-            acc[1] = fma(q, dy, acc[1]);
-            acc[2] = fma(q, dz, acc[2]);
-            const double al = fma(dx, dvx, fma(dy, dvy, dz * dvz)) * rinv2;
-            const double c1 = -3.0 * al;
-            acc[3] = fma(q, fma(c1, dx, dvx), acc[3]);
-            acc[4] = fma(q, fma(c1, dy, dvy), acc[4]);
-            acc[5] = fma(q, fma(c1, dz, dvz), acc[5]);
-            if (ORDER >= 6) {
-                const double2 w4 = b[jj * RW + 4], w5 = b[jj * RW + 5];
-                const double dax = w4.x - i4.x, day = w4.y - i4.y, daz = w5.x - i5.x;
-                const double w =
-                    fma(dvx, dvx, fma(dvy, dvy, fma(dvz, dvz, fma(dx, dax, fma(dy, day, dz * daz))))) * rinv2;
-                const double c2 = -6.0 * al;
-                const double c3 = fma(15.0 * al, al, -3.0 * w);
-                acc[6] = fma(q, fma(c3, dx, fma(c2, dvx, dax)), acc[6]);
-                acc[7] = fma(q, fma(c3, dy, fma(c2, dvy, day)), acc[7]);
-                acc[8] = fma(q, fma(c3, dz, fma(c2, dvz, daz)), acc[8]);
-                if (ORDER >= 8) {
-                    const double2 w6 = b[jj * RW + 6], w7 = b[jj * RW + 7];
-                    const double dkx = w6.x - i6.x, dky = w6.y - i6.y, dkz = w7.x - i7.x;
-                    const double u =
-                        fma(3.0, fma(dvx, dax, fma(dvy, day, dvz * daz)), fma(dx, dkx, fma(dy, dky, dz * dkz))) * rinv2;
-                    const double c4 = -9.0 * al;
-                    const double c5 = fma(45.0 * al, al, -9.0 * w);
-                    const double c6 = fma(al, fma(-105.0 * al, al, 45.0 * w), -3.0 * u);
-                    acc[9] = fma(q, fma(c6, dx, fma(c5, dvx, fma(c4, dax, dkx))), acc[9]);
-                    acc[10] = fma(q, fma(c6, dy, fma(c5, dvy, fma(c4, day, dky))), acc[10]);
-                    acc[11] = fma(q, fma(c6, dz, fma(c5, dvz, fma(c4, daz, dkz))), acc[11]);
-                }
-            }
-            acc[NC - 1] += mr;
-        }
+        const int self_rel = gi - (t0 + k) * JT;
+        if (__any_sync(0xffffffffu, (unsigned)self_rel < (unsigned)JT))
+            tile_fp64<ORDER, RW, PAIR, true>(b, i0, i1, i2, i3, i4, i5, i6, i7, ei2, eps2u, self_rel, acc);
+        else
+            tile_fp64<ORDER, RW, PAIR, false>(b, i0, i1, i2, i3, i4, i5, i6, i7, ei2, eps2u, -1, acc);
 #pragma unroll
         for (int c = 0; c < NC; ++c) sum[c] += acc[c];
 
@@ -332,9 +362,7 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_fp64(const double2* __restri
 }
 
 // -------------------------------------------------------------------- K3
-// F[c][p] = sum over splits in fixed order; the potential becomes
-// -(sum_j m_j / R_ij - m_i / eps_i), removing the self pair the kernel included
-// (the self pair contributes to no derivative: its difference vectors are 0).
+// F[c][p] = sum over splits in fixed order; the potential sum is negated.
 template <int NC>
 __global__ void k_force_reduce(const double* __restrict__ partial, int jsplit, int n_act,
                                const int32_t* __restrict__ idx, const double* __restrict__ m,
@@ -342,17 +370,11 @@ __global__ void k_force_reduce(const double* __restrict__ partial, int jsplit, i
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_act) return;
-    int gi = idx[p];
-    if ((unsigned)gi >= (unsigned)n) gi = 0;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         double s = 0.0;
         for (int sp = 0; sp < jsplit; ++sp) s += partial[((size_t)sp * NC + c) * n_act + p];
-        if (c == NC - 1) {
-            const double e2 = eps2[gi];
-            const double self = e2 > 0.0 ? m[gi] / sqrt(e2) : 0.0;
-            s = -(s - self);
-        }
+        if (c == NC - 1) s = -s;
         F[(size_t)c * n_act + p] = s;
     }
 }
