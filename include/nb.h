@@ -170,6 +170,35 @@ int nb_get_launch(nb_ctx* ctx, int* i_tiles, int* j_splits, int* threads);
 /* Force the j-split count of later nb_force calls (0 = automatic).         */
 int nb_set_jsplit(nb_ctx* ctx, int j_splits);
 
+/* Give every particle the step dt, so that the next block is the whole
+ * system -- the synchronised block that occurs at every multiple of dt_max of
+ * a hierarchical block-step run (abstract).  All particles must be at one
+ * common time t divisible by dt, and dt must be a power of two <= dt_max;
+ * violations raise NB_ERR_NOT_SYNC / NB_ERR_ARG at the next synchronising
+ * call.  Device-side, no synchronisation.                                  */
+int nb_set_block_step(nb_ctx* ctx, double dt);
+
+/* ------------------------------------------------------------- profiling */
+
+/* Phases of the per-phase timers: scheduler, predictor, force kernel, j-split
+ * reduction, corrector, everything else (start-up, energy, step reset).     */
+#define NB_NPHASES 6
+#define NB_PHASE_SCHED 0
+#define NB_PHASE_PREDICT 1
+#define NB_PHASE_FORCE 2
+#define NB_PHASE_REDUCE 3
+#define NB_PHASE_CORRECT 4
+#define NB_PHASE_OTHER 5
+
+/* enable != 0: reset the totals and time every later kernel launch with CUDA
+ * events recorded on the context's stream around it; 0: stop timing.       */
+int nb_set_profiling(nb_ctx* ctx, int enable);
+
+/* Device milliseconds and kernel launches per phase since profiling was
+ * enabled (arrays of NB_NPHASES; either may be NULL), and the number of
+ * kernel launches since nb_create (NULL to skip).  Synchronises.           */
+int nb_get_profile(nb_ctx* ctx, double* ms, int64_t* launches, int64_t* total_launches);
+
 /* Library version string.                                                  */
 const char* nb_version(void);
 

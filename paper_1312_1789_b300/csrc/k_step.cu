@@ -485,6 +485,32 @@ cudaError_t launch_startup_dt(nb_ctx* c)
     return cudaGetLastError();
 }
 
+// ======================================================== shared step
+// Every particle gets the step dtval; all must share t_0 = t[0], divisible by
+// dtval (checked here, reported through the status word).
+__global__ void k_set_dt(const double* __restrict__ t, double* __restrict__ dtv, int64_t n, double dtval,
+                         DevScalars* sc)
+{
+    const double t0 = t[0];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (t[i] != t0) raise_status(sc, NB_ERR_NOT_SYNC);
+        dtv[i] = dtval;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const double q = t0 / dtval;
+        if (q != floor(q)) raise_status(sc, NB_ERR_ARG);
+    }
+}
+
+cudaError_t launch_set_dt(nb_ctx* c, double dt)
+{
+    int g = c->sm_count * 2;
+    const int64_t need = (c->n + 255) / 256;
+    if (need < g) g = (int)need;
+    k_set_dt<<<g < 1 ? 1 : g, 256, 0, c->stream>>>(c->t, c->dt, c->n, dt, c->sc);
+    return cudaGetLastError();
+}
+
 // ================================================================ energy
 // Deterministic two-level sums: kinetic sum m v^2 / 2 and potential
 // sum m_i pot_i / 2 (pot from an order-0 force pass, list = identity), and the

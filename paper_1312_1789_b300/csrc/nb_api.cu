@@ -101,12 +101,58 @@ bool is_pow2(double x)
     return std::frexp(x, &e) == 0.5;
 }
 
+// ------------------------------------------------------------- profiling
+cudaEvent_t prof_event(nb_ctx* c)
+{
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Fold completed event pairs into the per-phase totals (stream synchronised).
+void prof_fold(nb_ctx* c)
+{
+    for (auto& r : c->prof_recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) c->prof_ms[r.phase] += ms;
+        else cudaGetLastError();
+        c->ev_pool.push_back(r.a);
+        c->ev_pool.push_back(r.b);
+    }
+    c->prof_recs.clear();
+}
+
+// Run one launcher (nk kernels) as phase `phase`, counting and, when profiling
+// is on, bracketing it with events on the context's stream.
+template <typename F>
+cudaError_t timed(nb_ctx* c, int phase, int nk, F&& launch)
+{
+    c->n_launch += nk;
+    if (!c->prof_on) return launch();
+    cudaEvent_t a = prof_event(c), b = prof_event(c);
+    if (a) cudaEventRecord(a, c->stream);
+    const cudaError_t e = launch();
+    if (b) cudaEventRecord(b, c->stream);
+    if (a && b) c->prof_recs.push_back({a, b, phase});
+    c->prof_n[phase] += nk;
+    return e;
+}
+
 // Read the device scalars (waits for the stream) and turn a raised status into
 // an error code; the status word is cleared for the next call.
 int sync_scalars(nb_ctx* c)
 {
     NB_CUDA(c, cudaMemcpyAsync(c->h_sc, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
     NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (!c->prof_recs.empty()) prof_fold(c);
     const int st = c->h_sc->status;
     if (st != NB_OK) {
         NB_CUDA(c, cudaMemsetAsync(&c->sc->status, 0, sizeof(int), c->stream));
@@ -141,8 +187,8 @@ int run_force(nb_ctx* c, int order, const int32_t* idx_dev, int64_t n_act)
 {
     int it, js;
     choose_shape(c, order, n_act, &it, &js);
-    NB_CUDA(c, launch_force(c, order, idx_dev, n_act, js, it));
-    NB_CUDA(c, launch_force_reduce(c, order, idx_dev, n_act, js));
+    NB_CUDA(c, timed(c, NB_PHASE_FORCE, 1, [&] { return launch_force(c, order, idx_dev, n_act, js, it); }));
+    NB_CUDA(c, timed(c, NB_PHASE_REDUCE, 1, [&] { return launch_force_reduce(c, order, idx_dev, n_act, js); }));
     c->last_itiles = it;
     c->last_jsplit = js;
     c->last_threads = FORCE_NT;
@@ -153,7 +199,7 @@ int run_force(nb_ctx* c, int order, const int32_t* idx_dev, int64_t n_act)
 
 int do_predict(nb_ctx* c, double t)
 {
-    NB_CUDA(c, launch_predict(c, t));
+    NB_CUDA(c, timed(c, NB_PHASE_PREDICT, 1, [&] { return launch_predict(c, t); }));
     c->pred_prec = c->prec;
     c->have_pred = 1;
     c->t_pred = t;
@@ -186,6 +232,11 @@ void nb_destroy(nb_ctx* c)
     for (void* p : ptrs) dfree(c, p);
     if (c->h_sc) cudaFreeHost(c->h_sc);
     if (c->h_red) cudaFreeHost(c->h_red);
+    for (auto& r : c->prof_recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
 }
 
@@ -372,9 +423,9 @@ int nb_set_particles(nb_ctx* c, const double* m, const double* x, const double* 
     for (int pass = 4; pass <= c->order; pass += 2) {
         NB_TRY(do_predict(c, 0.0));
         NB_TRY(run_force(c, pass, c->all_idx, c->n));
-        NB_CUDA(c, launch_startup_store(c, pass));
+        NB_CUDA(c, timed(c, NB_PHASE_OTHER, 1, [&] { return launch_startup_store(c, pass); }));
     }
-    NB_CUDA(c, launch_startup_dt(c));
+    NB_CUDA(c, timed(c, NB_PHASE_OTHER, 1, [&] { return launch_startup_dt(c); }));
     c->have_pred = 0;
     c->F_order = -1;
     return sync_scalars(c);
@@ -384,7 +435,7 @@ int nb_next_block(nb_ctx* c, double* t_blk, int32_t* idx_out, int64_t* n_act)
 {
     if (!c) return NB_ERR_ARG;
     if (!c->have_particles) return set_err(c, NB_ERR_ARG, "nb_next_block before nb_set_particles");
-    NB_CUDA(c, launch_sched(c));
+    NB_CUDA(c, timed(c, NB_PHASE_SCHED, 3, [&] { return launch_sched(c); }));
     NB_TRY(sync_scalars(c));
     c->sched_t = c->h_sc->t_blk;
     c->sched_n = c->h_sc->n_act;
@@ -452,7 +503,7 @@ int nb_correct(nb_ctx* c)
     if (!c) return NB_ERR_ARG;
     if (!c->have_force || c->F_order != c->order)
         return set_err(c, NB_ERR_ARG, "nb_correct needs a preceding nb_force");
-    NB_CUDA(c, launch_correct(c));
+    NB_CUDA(c, timed(c, NB_PHASE_CORRECT, 1, [&] { return launch_correct(c); }));
     c->have_force = 0;
     c->have_pred = 0;
     c->have_sched = 0;
@@ -499,7 +550,7 @@ int nb_energy(nb_ctx* c, double* ekin, double* epot)
     if (!c) return NB_ERR_ARG;
     if (!c->have_particles) return set_err(c, NB_ERR_ARG, "nb_energy before nb_set_particles");
     const int g = energy_grid(c);
-    NB_CUDA(c, launch_energy_sums(c, 0));
+    NB_CUDA(c, timed(c, NB_PHASE_OTHER, 2, [&] { return launch_energy_sums(c, 0); }));
     NB_CUDA(c, cudaMemcpyAsync(c->h_red, c->red + 4 * g, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     NB_TRY(sync_scalars(c));
     const double tmin = c->h_red[2], tmax = c->h_red[3];
@@ -509,7 +560,7 @@ int nb_energy(nb_ctx* c, double* ekin, double* epot)
     c->have_force = 0;
     NB_TRY(do_predict(c, tmin));
     NB_TRY(run_force(c, 0, c->all_idx, c->n));
-    NB_CUDA(c, launch_energy_sums(c, 1));
+    NB_CUDA(c, timed(c, NB_PHASE_OTHER, 2, [&] { return launch_energy_sums(c, 1); }));
     NB_CUDA(c, cudaMemcpyAsync(c->h_red, c->red + 4 * g, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     NB_TRY(sync_scalars(c));
     if (ekin) *ekin = c->h_red[0];
@@ -615,6 +666,42 @@ int nb_get_predicted(nb_ctx* c, double* xp, double* vp, double* ap, double* jp)
             }
         }
     }
+    return NB_OK;
+}
+
+int nb_set_block_step(nb_ctx* c, double dt)
+{
+    if (!c) return NB_ERR_ARG;
+    if (!c->have_particles) return set_err(c, NB_ERR_ARG, "nb_set_block_step before nb_set_particles");
+    if (!is_pow2(dt) || dt > c->dt_max) return set_err(c, NB_ERR_ARG, "dt must be a power of two <= dt_max");
+    NB_CUDA(c, timed(c, NB_PHASE_OTHER, 1, [&] { return launch_set_dt(c, dt); }));
+    c->have_sched = 0;
+    return NB_OK;
+}
+
+int nb_set_profiling(nb_ctx* c, int enable)
+{
+    if (!c) return NB_ERR_ARG;
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    prof_fold(c);
+    for (int k = 0; k < NB_NPHASES; ++k) {
+        c->prof_ms[k] = 0.0;
+        c->prof_n[k] = 0;
+    }
+    c->prof_on = enable != 0;
+    return NB_OK;
+}
+
+int nb_get_profile(nb_ctx* c, double* ms, int64_t* launches, int64_t* total)
+{
+    if (!c) return NB_ERR_ARG;
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    prof_fold(c);
+    for (int k = 0; k < NB_NPHASES; ++k) {
+        if (ms) ms[k] = c->prof_ms[k];
+        if (launches) launches[k] = c->prof_n[k];
+    }
+    if (total) *total = c->n_launch;
     return NB_OK;
 }
 

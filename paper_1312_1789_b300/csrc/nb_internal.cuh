@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "nb.h"
 
 namespace nb {
@@ -176,6 +178,17 @@ struct nb_ctx {
     double sched_t = 0.0;
     int have_sched = 0;
     int last_itiles = 0, last_jsplit = 0, last_threads = 0;
+    // profiling: event pairs around launches, folded into totals at syncs
+    struct ProfRec {
+        cudaEvent_t a, b;
+        int phase;
+    };
+    int prof_on = 0;
+    std::vector<ProfRec> prof_recs;
+    std::vector<cudaEvent_t> ev_pool;
+    double prof_ms[NB_NPHASES] = {0};
+    int64_t prof_n[NB_NPHASES] = {0};
+    int64_t n_launch = 0;  // kernel launches since creation
     // allocator captured at creation
     void* (*alloc_fn)(size_t, void*) = nullptr;
     void (*free_fn)(void*, void*) = nullptr;
@@ -194,6 +207,7 @@ cudaError_t launch_correct(nb_ctx* c);
 cudaError_t launch_startup_store(nb_ctx* c, int order);
 cudaError_t launch_startup_dt(nb_ctx* c);
 cudaError_t launch_energy_sums(nb_ctx* c, int with_pot);
+cudaError_t launch_set_dt(nb_ctx* c, double dt);
 int force_occupancy(nb_ctx* c, int order);
 int sched_grid(const nb_ctx* c);
 int sched_chunks(int64_t n);

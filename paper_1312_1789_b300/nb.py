@@ -57,7 +57,12 @@ SIGNATURES = {
     "nb_get_launch": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "nb_set_jsplit": (C.c_int, [_P, C.c_int]),
     "nb_version": (C.c_char_p, []),
+    "nb_set_block_step": (C.c_int, [_P, C.c_double]),
+    "nb_set_profiling": (C.c_int, [_P, C.c_int]),
+    "nb_get_profile": (C.c_int, [_P, _D, _I64, _I64]),
 }
+NB_NPHASES = 6
+PHASES = ("sched", "predict", "force", "reduce", "correct", "other")
 
 _lib = None
 
@@ -236,6 +241,20 @@ class NBody:
         xp, vp, ap, jp = (np.zeros((n, 3)) for _ in range(4))
         self._check(self._L.nb_get_predicted(self._h, _d(xp), _d(vp), _d(ap), _d(jp)))
         return xp, vp, ap, jp
+
+    def set_block_step(self, dt: float):
+        self._check(self._L.nb_set_block_step(self._h, float(dt)))
+
+    def set_profiling(self, enable: bool):
+        self._check(self._L.nb_set_profiling(self._h, 1 if enable else 0))
+
+    def get_profile(self):
+        """{phase: (ms, launches)} since profiling was enabled, and total launches."""
+        ms = np.zeros(NB_NPHASES)
+        nl = np.zeros(NB_NPHASES, dtype=np.int64)
+        tot = C.c_int64()
+        self._check(self._L.nb_get_profile(self._h, _d(ms), nl.ctypes.data_as(_I64), C.byref(tot)))
+        return {p: (float(ms[k]), int(nl[k])) for k, p in enumerate(PHASES)}, tot.value
 
     def get_launch(self):
         a, b, c = C.c_int(), C.c_int(), C.c_int()

