@@ -341,20 +341,66 @@ static double norm3d(const double* p)
     return sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
 }
 
-double orc_dt_criterion(int order, double eta, const double* D)
+static double criterion_from_norms(int order, double eta, const double* n)
 {
-    double n0 = norm3d(D), n1 = norm3d(D + 3), n2 = norm3d(D + 6);
     if (order == 4) {
-        double n3 = norm3d(D + 9);
-        double num = n0 * n2 + n1 * n1, den = n1 * n3 + n2 * n2;
+        double num = n[0] * n[2] + n[1] * n[1], den = n[1] * n[3] + n[2] * n[2];
         if (!(den > 0)) return INFINITY;
         return sqrt(eta * num / den);
     }
     int p = order;
-    double nlo = norm3d(D + 3 * (p - 3)), nmid = norm3d(D + 3 * (p - 2)), nhi = norm3d(D + 3 * (p - 1));
-    double num = sqrt(n0 * n2) + n1, den = sqrt(nlo * nhi) + nmid;
+    double num = sqrt(n[0] * n[2]) + n[1], den = sqrt(n[p - 3] * n[p - 1]) + n[p - 2];
     if (!(den > 0)) return INFINITY;
     return eta * pow(num / den, 1.0 / (p - 3));
+}
+
+double orc_dt_criterion(int order, double eta, const double* D)
+{
+    double n[8];
+    for (int k = 0; k < order; k++) n[k] = norm3d(D + 3 * k);
+    return criterion_from_norms(order, eta, n);
+}
+
+/* Noise floor of the interpolated derivatives (reading for reduced-precision
+   forces): the new derivatives mm..2mm-1 are linear in the inputs L_r (held,
+   at t0) and R_r (new force, at t1), r < mm.  If each input carries relative
+   rounding eps[r], derivative k carries at most
+       N_k = sum_r |dd_k/dL_r| eps[r] |L_r| + |dd_k/dR_r| eps[r] |R_r| ,
+   the partial derivatives read off this oracle's own interpolant by feeding
+   it unit inputs.  N[q] is the floor of derivative mm + q. */
+int orc_noise_floor(int mm, double h, const double* D0, const double* D1, const double* eps, double* N)
+{
+    if (mm < 1 || mm > 4 || !(h > 0)) return ORC_ERR_ARG;
+    for (int q = 0; q < mm; q++) N[q] = 0;
+    for (int r = 0; r < mm; r++) {
+        for (int side = 0; side < 2; side++) {
+            double U0[12] = {0}, U1[12] = {0}, out[12];
+            (side == 0 ? U0 : U1)[3 * r] = 1.0;
+            int rc = orc_interp(mm, h, U0, U1, out);
+            if (rc) return rc;
+            double mag = norm3d((side == 0 ? D0 : D1) + 3 * r);
+            for (int q = 0; q < mm; q++) N[q] += fabs(out[3 * q]) * eps[r] * mag;
+        }
+    }
+    return ORC_OK;
+}
+
+/* Step criterion after a step of length h: D0 = held derivatives at t0 (rows
+   0..mm-1), Dfull = a^(0..2mm-1) at t1 (the first mm from the force, the rest
+   interpolated).  Interpolated norms are taken net of their noise floor. */
+double orc_dt_criterion_floored(int order, double eta, double h, const double* D0, const double* Dfull,
+                                const double* eps)
+{
+    int mm = order / 2;
+    double n[8], N[4];
+    for (int k = 0; k < 2 * mm; k++) n[k] = norm3d(Dfull + 3 * k);
+    if (!(eps[0] > 0 || eps[1] > 0 || eps[2] > 0 || eps[3] > 0)) return criterion_from_norms(order, eta, n);
+    if (orc_noise_floor(mm, h, D0, Dfull, eps, N)) return NAN;
+    for (int q = 0; q < mm; q++) {
+        double f = n[mm + q] - N[q];
+        n[mm + q] = f > 0 ? f : 0;
+    }
+    return criterion_from_norms(order, eta, n);
 }
 
 /* Largest power-of-two fraction of dt_max that is <= lim, then halved until   */
@@ -407,6 +453,7 @@ int orc_next_block(int64_t n, const double* ti, const double* dti, double* t_blk
 typedef struct {
     double eta, eta_s, dt_max, dt_min, t_end;
     int order, nthreads, init;
+    double noise[4]; /* relative precision of acc, jerk, snap, crackle (0: exact) */
 } orc_params;
 
 int orc_integrate(int64_t n, const double* m, const double* eps2,
@@ -519,7 +566,7 @@ int orc_integrate(int64_t n, const double* m, const double* eps2,
                 for (int c = 0; c < 3; c++) D1c[3 * q + c] = Dfull[3 * q + c];
             double x1[3], v1[3];
             orc_correct(order, h, x + 3 * i, v + 3 * i, D0, D1c, x1, v1);
-            double crit = orc_dt_criterion(order, P->eta, Dfull);
+            double crit = orc_dt_criterion_floored(order, P->eta, h, D0, Dfull, P->noise);
             double lim = crit;
             if (2.0 * h < lim) lim = 2.0 * h;
             double dtn;

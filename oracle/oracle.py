@@ -27,7 +27,7 @@ class OracleError(RuntimeError):
 class _Params(C.Structure):
     _fields_ = [("eta", C.c_double), ("eta_s", C.c_double), ("dt_max", C.c_double),
                 ("dt_min", C.c_double), ("t_end", C.c_double), ("order", C.c_int),
-                ("nthreads", C.c_int), ("init", C.c_int)]
+                ("nthreads", C.c_int), ("init", C.c_int), ("noise", C.c_double * 4)]
 
 
 def lib():
@@ -43,6 +43,9 @@ def lib():
         L.orc_interp.argtypes = [C.c_int, C.c_double, d, d, d]
         L.orc_dt_criterion.argtypes = [C.c_int, C.c_double, d]
         L.orc_dt_criterion.restype = C.c_double
+        L.orc_noise_floor.argtypes = [C.c_int, C.c_double, d, d, d, d]
+        L.orc_dt_criterion_floored.argtypes = [C.c_int, C.c_double, C.c_double, d, d, d]
+        L.orc_dt_criterion_floored.restype = C.c_double
         L.orc_dt_quantise.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, d]
         L.orc_dt_startup.argtypes = [C.c_double, d, d]
         L.orc_dt_startup.restype = C.c_double
@@ -152,6 +155,26 @@ def dt_criterion(order, eta, D):
     return float(lib().orc_dt_criterion(order, float(eta), _p(_f64(D, (order, 3)))))
 
 
+def noise_floor(mm, h, D0, D1, eps):
+    """Noise floors of the interpolated derivatives mm..2mm-1 ([mm])."""
+    out = np.zeros(mm)
+    e = np.zeros(4)
+    e[: len(eps)] = eps
+    rc = lib().orc_noise_floor(mm, float(h), _p(_f64(D0, (mm, 3))), _p(_f64(D1, (mm, 3))), _p(e), _p(out))
+    _check(rc, "orc_noise_floor")
+    return out
+
+
+def dt_criterion_floored(order, eta, h, D0, Dfull, eps):
+    """Step criterion with interpolated norms net of their noise floor."""
+    mm = order // 2
+    e = np.zeros(4)
+    e[: len(eps)] = eps
+    D0 = _f64(np.asarray(D0)[:mm], (mm, 3))
+    return float(lib().orc_dt_criterion_floored(order, float(eta), float(h), _p(D0),
+                                                _p(_f64(Dfull, (2 * mm, 3))), _p(e)))
+
+
 def dt_quantise(lim, t1, dt_max=1.0 / 16, dt_min=2.0 ** -40):
     """Power-of-two step <= lim commensurate with t1; raises on underflow."""
     out = C.c_double()
@@ -197,12 +220,17 @@ class State:
 
 
 def integrate(state: State, order=6, t_end=0.125, eta=0.2, eta_s=0.01, dt_max=1.0 / 16,
-              dt_min=2.0 ** -40, nthreads=1, log=False, log_cap_blocks=1 << 20, log_cap_idx=1 << 26):
+              dt_min=2.0 ** -40, nthreads=1, log=False, log_cap_blocks=1 << 20, log_cap_idx=1 << 26,
+              noise=(0.0, 0.0, 0.0, 0.0)):
     """Advance `state` with block steps until the next block would pass t_end.
 
-    Returns the block log (list of (t_blk, idx array)) if log, else the count.
+    noise: relative precision of the force components (acc, jerk, snap,
+    crackle) used as the noise floor of interpolated derivatives; zeros give
+    the plain criterion.  Returns the block log (list of (t_blk, idx array))
+    if log, else the count.
     """
-    P = _Params(eta, eta_s, dt_max, dt_min, t_end, order, int(nthreads), 0 if state.initialised else 1)
+    P = _Params(eta, eta_s, dt_max, dt_min, t_end, order, int(nthreads), 0 if state.initialised else 1,
+                (C.c_double * 4)(*noise))
     n = state.n
     nb = C.c_int64()
     if log:
@@ -227,4 +255,4 @@ def integrate(state: State, order=6, t_end=0.125, eta=0.2, eta_s=0.01, dt_max=1.
 
 
 __all__ = ["OracleError", "State", "force", "energy", "predict", "correct", "interp", "dt_criterion",
-           "dt_quantise", "dt_startup", "next_block", "integrate", "num_threads", "lib"]
+           "dt_quantise", "dt_startup", "noise_floor", "dt_criterion_floored", "next_block", "integrate", "num_threads", "lib"]

@@ -293,23 +293,57 @@ __device__ double quantise_dt(double lim, double t1, double dt_max, double dt_mi
 
 __device__ __forceinline__ double norm3(const double* p) { return sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]); }
 
-// Generalised Aarseth criterion from acc derivatives H[0..p-1] at t1:
+// Generalised Aarseth criterion from the norms n[k] = |a^(k)| at t1:
 //   p = 4: sqrt(eta (|a||a2| + |a1|^2) / (|a1||a3| + |a2|^2))
 //   p = 6, 8: eta ((sqrt(|a||a2|) + |a1|) / (sqrt(|a(p-3)||a(p-1)|) + |a(p-2)|))^(1/(p-3))
 template <int ORDER>
-__device__ double dt_criterion(double eta, const double (*H)[3])
+__device__ double dt_criterion(double eta, const double* nrm)
 {
-    const double n0 = norm3(H[0]), n1 = norm3(H[1]), n2 = norm3(H[2]);
+    const double n0 = nrm[0], n1 = nrm[1], n2 = nrm[2];
     if (ORDER == 4) {
-        const double n3 = norm3(H[3]);
+        const double n3 = nrm[3];
         const double num = n0 * n2 + n1 * n1, den = n1 * n3 + n2 * n2;
         if (!(den > 0.0)) return INFINITY;
         return sqrt(eta * num / den);
     }
-    const double nlo = norm3(H[ORDER - 3]), nmid = norm3(H[ORDER - 2]), nhi = norm3(H[ORDER - 1]);
+    const double nlo = nrm[ORDER - 3], nmid = nrm[ORDER - 2], nhi = nrm[ORDER - 1];
     const double num = sqrt(n0 * n2) + n1, den = sqrt(nlo * nhi) + nmid;
     if (!(den > 0.0)) return INFINITY;
     return ORDER == 6 ? eta * cbrt(num / den) : eta * pow(num / den, 0.2);
+}
+
+// Noise floor of the interpolated derivatives.  The closed forms below take
+// differences of force values whose relative precision is ea (acc), ej
+// (jerk), es (snap), ec (crackle); a derivative k carries at most
+// N_k = sum |coefficient| * eps * |input| / h^k of that rounding.  The
+// criterion uses max(|a^(k)| - N_k, 0): what the inputs cannot resolve is
+// treated as unknown (zero) rather than as signal.  With all eps = 0 the
+// criterion is the plain one.  nL[r], nR[r] = |a^(r)| at t0 and t1.
+template <int ORDER>
+__device__ void noise_floor(const double* nL, const double* nR, double h, const double* e, double* N)
+{
+    const double ih = 1.0 / h;
+    const double A = e[0] * (nL[0] + nR[0]);
+    if (ORDER == 4) {
+        N[2] = 2.0 * (3.0 * A + h * e[1] * (nL[1] + 2.0 * nR[1])) * ih * ih;
+        N[3] = 6.0 * (2.0 * A + h * e[1] * (nL[1] + nR[1])) * ih * ih * ih;
+    } else if (ORDER == 6) {
+        const double h2 = h * h, ih3 = ih * ih * ih;
+        N[3] = 3.0 * (20.0 * A + h2 * e[2] * (nL[2] + 3.0 * nR[2]) + 4.0 * h * e[1] * (2.0 * nL[1] + 3.0 * nR[1])) * ih3;
+        N[4] = 12.0 * (30.0 * A + h2 * e[2] * (2.0 * nL[2] + 3.0 * nR[2]) + 2.0 * h * e[1] * (7.0 * nL[1] + 8.0 * nR[1])) *
+               ih3 * ih;
+        N[5] = 60.0 * (12.0 * A + h2 * e[2] * (nL[2] + nR[2]) + 6.0 * h * e[1] * (nL[1] + nR[1])) * ih3 * ih * ih;
+    } else {
+        const double h2 = h * h, h3 = h2 * h, ih4 = (ih * ih) * (ih * ih);
+        N[4] = 4.0 * (210.0 * A + h3 * e[3] * (nL[3] + 4.0 * nR[3]) + 15.0 * h2 * e[2] * (nL[2] + 2.0 * nR[2]) +
+                      30.0 * h * e[1] * (3.0 * nL[1] + 4.0 * nR[1])) * ih4;
+        N[5] = 60.0 * (168.0 * A + h3 * e[3] * (nL[3] + 2.0 * nR[3]) + 2.0 * h2 * e[2] * (7.0 * nL[2] + 10.0 * nR[2]) +
+                       6.0 * h * e[1] * (13.0 * nL[1] + 15.0 * nR[1])) * ih4 * ih;
+        N[6] = 120.0 * (420.0 * A + h3 * e[3] * (3.0 * nL[3] + 4.0 * nR[3]) + 3.0 * h2 * e[2] * (13.0 * nL[2] + 15.0 * nR[2]) +
+                        12.0 * h * e[1] * (17.0 * nL[1] + 18.0 * nR[1])) * ih4 * ih * ih;
+        N[7] = 840.0 * (120.0 * A + h3 * e[3] * (nL[3] + nR[3]) + 12.0 * h2 * e[2] * (nL[2] + nR[2]) +
+                        60.0 * h * e[1] * (nL[1] + nR[1])) * ih4 * ih * ih * ih;
+    }
 }
 
 // Corrector, interpolation and new step for the particles of the last force.
@@ -322,7 +356,7 @@ __global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fid
                                                  double* __restrict__ x, double* __restrict__ v,
                                                  double* __restrict__ d, double* __restrict__ t,
                                                  double* __restrict__ dtv, double* __restrict__ pot, double eta,
-                                                 double dt_max, double dt_min, DevScalars* sc)
+                                                 double dt_max, double dt_min, NoiseEps ne, DevScalars* sc)
 {
     constexpr int MM = ORDER / 2;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -401,7 +435,19 @@ __global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fid
         x[c * np + i] = x1;
     }
 
-    double lim = dt_criterion<ORDER>(eta, H);
+    // derivative norms at t1, the interpolated ones net of their noise floor
+    double nrm[8], nL[4], nR[4], N[8];
+#pragma unroll
+    for (int k = 0; k < 2 * MM; ++k) nrm[k] = norm3(H[k]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        nL[k] = norm3(L[k]);
+        nR[k] = k < MM ? nrm[k] : 0.0;
+    }
+    noise_floor<ORDER>(nL, nR, h, ne.e, N);
+#pragma unroll
+    for (int k = MM; k < 2 * MM; ++k) nrm[k] = fmax(nrm[k] - N[k], 0.0);
+    double lim = dt_criterion<ORDER>(eta, nrm);
     if (2.0 * h < lim) lim = 2.0 * h;
     const double dtn = quantise_dt(lim, tf, dt_max, dt_min, sc);
 
@@ -420,7 +466,8 @@ cudaError_t launch_correct(nb_ctx* c)
     const int nb = (int)((c->f_n + nt - 1) / nt);
 #define NB_CORR(O)                                                                                          \
     k_correct<O><<<nb, nt, 0, c->stream>>>(c->f_idx, (int)c->f_n, c->f_t, c->F, c->n, c->np, c->x, c->v,   \
-                                           c->d, c->t, c->dt, c->pot, c->eta, c->dt_max, c->dt_min, c->sc);
+                                           c->d, c->t, c->dt, c->pot, c->eta, c->dt_max, c->dt_min,        \
+                                           c->noise[c->pred_prec == NB_MIXED ? 1 : 0], c->sc);
     if (c->order == 4) {
         NB_CORR(4)
     } else if (c->order == 6) {

@@ -679,6 +679,24 @@ int nb_set_block_step(nb_ctx* c, double dt)
     return NB_OK;
 }
 
+int nb_set_noise_floor(nb_ctx* c, int prec, const double* eps)
+{
+    if (!c) return NB_ERR_ARG;
+    if ((prec != NB_FP64 && prec != NB_MIXED) || !eps) return set_err(c, NB_ERR_ARG, "bad precision or NULL eps");
+    for (int k = 0; k < 4; ++k)
+        if (!(eps[k] >= 0.0) || !std::isfinite(eps[k])) return set_err(c, NB_ERR_ARG, "eps must be finite and >= 0");
+    for (int k = 0; k < 4; ++k) c->noise[prec].e[k] = eps[k];
+    return NB_OK;
+}
+
+int nb_get_noise_floor(nb_ctx* c, int prec, double* eps)
+{
+    if (!c) return NB_ERR_ARG;
+    if ((prec != NB_FP64 && prec != NB_MIXED) || !eps) return set_err(c, NB_ERR_ARG, "bad precision or NULL eps");
+    for (int k = 0; k < 4; ++k) eps[k] = c->noise[prec].e[k];
+    return NB_OK;
+}
+
 int nb_set_profiling(nb_ctx* c, int enable)
 {
     if (!c) return NB_ERR_ARG;

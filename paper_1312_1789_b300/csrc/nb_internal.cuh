@@ -50,6 +50,12 @@ struct DevScalars {
     int pad;
 };
 
+// Relative precision of the force components (acc, jerk, snap, crackle) that
+// sets the noise floor of interpolated derivatives in the time-step criterion.
+struct NoiseEps {
+    double e[4];
+};
+
 __device__ __forceinline__ void raise_status(DevScalars* sc, int code)
 {
     atomicCAS(&sc->status, NB_OK, code);
@@ -143,6 +149,9 @@ struct nb_ctx {
     double eps = 0.0;
     int pair_eps = 0;  // per-particle softening in use
     double eta = 0.2, eta_s = 0.01, dt_max = 1.0 / 16, dt_min = 0x1p-40;
+    // noise floors per precision [NB_FP64, NB_MIXED]: FP64 none (the plain
+    // criterion); mixed from the measured error of the FP32 force chain
+    nb::NoiseEps noise[2] = {{{0.0, 0.0, 0.0, 0.0}}, {{3e-7, 1e-6, 2e-6, 2e-5}}};
     cudaStream_t stream = nullptr;
     int jsplit_force = 0;
     int sm_count = 148;

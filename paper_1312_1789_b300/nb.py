@@ -60,6 +60,8 @@ SIGNATURES = {
     "nb_set_block_step": (C.c_int, [_P, C.c_double]),
     "nb_set_profiling": (C.c_int, [_P, C.c_int]),
     "nb_get_profile": (C.c_int, [_P, _D, _I64, _I64]),
+    "nb_set_noise_floor": (C.c_int, [_P, C.c_int, _D]),
+    "nb_get_noise_floor": (C.c_int, [_P, C.c_int, _D]),
 }
 NB_NPHASES = 6
 PHASES = ("sched", "predict", "force", "reduce", "correct", "other")
@@ -244,6 +246,15 @@ class NBody:
 
     def set_block_step(self, dt: float):
         self._check(self._L.nb_set_block_step(self._h, float(dt)))
+
+    def set_noise_floor(self, precision: int, eps):
+        e = np.ascontiguousarray(eps, dtype=np.float64).reshape(4)
+        self._check(self._L.nb_set_noise_floor(self._h, int(precision), _d(e)))
+
+    def get_noise_floor(self, precision: int):
+        e = np.zeros(4)
+        self._check(self._L.nb_get_noise_floor(self._h, int(precision), _d(e)))
+        return e
 
     def set_profiling(self, enable: bool):
         self._check(self._L.nb_set_profiling(self._h, 1 if enable else 0))

@@ -170,7 +170,7 @@ def test_corrector_parity(prec, order):
         hi = orc.interp(mm, h, D0[:mm], D1)
         Dfull = np.vstack([D1, hi])
         x1, v1 = orc.correct(order, h, S0["x"][i], S0["v"][i], D0, Dfull[:4])
-        lim = min(orc.dt_criterion(order, eta, Dfull), 2 * h)
+        lim = min(orc.dt_criterion_floored(order, eta, h, D0, Dfull, ctx.get_noise_floor(prec)), 2 * h)
         dt_o = orc.dt_quantise(lim, tb, 1.0 / 16, 2.0 ** -40)
         assert S1["t"][i] == tb
         assert S1["dt"][i] == dt_o, (i, S1["dt"][i], dt_o)
@@ -208,6 +208,21 @@ def test_block_sequence_plummer_1k_exact():
     assert np.max(np.abs(S["x"] - st.x)) < 1e-11
     assert np.max(np.abs(S["v"] - st.v)) < 1e-10
     assert np.array_equal(S["dt"], st.dt)
+
+
+def test_mixed_integration_block_sequence_close_to_oracle():
+    # The mixed path integrates the 1k Plummer sphere without step collapse;
+    # the oracle with the same noise floor takes nearly the same blocks.
+    wl = ics.standard_workload(0)
+    ctx = make_ctx(wl.m, wl.x, wl.v, wl.eps2, 6, nb.NB_MIXED)
+    nblk, _ = ctx.step_until(wl.t_end)
+    S = ctx.get_state()
+    assert np.all(S["t"] == wl.t_end)
+    st = orc.State(wl.m, wl.eps2, wl.x, wl.v)
+    nblk_o = orc.integrate(st, order=6, t_end=wl.t_end, eta=wl.eta, nthreads=16,
+                           noise=ctx.get_noise_floor(nb.NB_MIXED))
+    assert abs(nblk - nblk_o) <= 0.1 * nblk_o
+    assert np.max(np.abs(S["x"] - st.x)) < 1e-5
 
 
 def test_mixed_energy_error_close_to_fp64():

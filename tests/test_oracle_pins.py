@@ -490,3 +490,83 @@ def test_hernquist_ic_properties(orc):
     cdf = lambda rr: np.minimum(ics.hernquist_enclosed_mass(rr) / ics.HERNQUIST_MASS_CUT, 1.0)  # noqa: E731
     p = stats.kstest(r, cdf).pvalue
     assert p > 0.01
+
+
+# --------------------------------------------------------------------------
+# Noise floor of interpolated derivatives (reduced-precision reading)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("order", [4, 6, 8])
+def test_noise_floor_brackets_the_true_derivatives(orc, order):
+    # acc(t) an exact polynomial of degree 2mm-1, so the interpolant recovers
+    # its derivatives exactly; perturb every input by relative rounding up to
+    # eps.  The perturbed derivatives must stay within their floors of the true
+    # ones, and the floored norms must never exceed the true norms.
+    mm = order // 2
+    eps = np.array([3e-7, 1e-6, 2e-6, 2e-5])
+    rng = np.random.default_rng(300 + order)
+    for trial in range(50):
+        coef = rng.normal(size=(3, 2 * mm))
+        h = float(2.0 ** -rng.integers(2, 12))
+        D0 = np.array([[P.polyval(0.0, P.polyder(coef[c], k)) for c in range(3)] for k in range(mm)])
+        D1 = np.array([[P.polyval(h, P.polyder(coef[c], k)) for c in range(3)] for k in range(mm)])
+        true = np.array([[P.polyval(h, P.polyder(coef[c], k)) for c in range(3)] for k in range(mm, 2 * mm)])
+
+        def jitter(D):
+            out = D.copy()
+            for r in range(mm):
+                u = rng.normal(size=3)
+                out[r] += eps[r] * np.linalg.norm(D[r]) * rng.uniform(0, 1) * u / np.linalg.norm(u)
+            return out
+
+        P0, P1 = jitter(D0), jitter(D1)
+        got = orc.interp(mm, h, P0, P1)
+        N = orc.noise_floor(mm, h, P0, P1, eps)
+        for q in range(mm):
+            # rounding of the floor itself: relative 1e-12 of the terms
+            slack = 1e-9 * N[q] + 1e-12 * np.linalg.norm(true[q])
+            assert np.linalg.norm(got[q] - true[q]) <= N[q] * (1 + 2 * max(eps)) + slack
+            assert max(np.linalg.norm(got[q]) - N[q], 0.0) <= np.linalg.norm(true[q]) + slack
+
+
+@pytest.mark.parametrize("order", [4, 6, 8])
+def test_zero_noise_floor_is_the_plain_criterion(orc, order):
+    rng = np.random.default_rng(order)
+    mm = order // 2
+    D0 = rng.normal(size=(mm, 3))
+    Dfull = rng.normal(size=(2 * mm, 3))
+    assert orc.dt_criterion_floored(order, 0.2, 0.01, D0, Dfull, [0, 0, 0, 0]) == orc.dt_criterion(order, 0.2, Dfull)
+    # a floor that swamps every interpolated derivative leaves no constraint
+    assert orc.dt_criterion_floored(order, 0.2, 1e-6, D0, Dfull, [1e-3] * 4) == math.inf
+
+
+def test_noisy_forces_do_not_collapse_the_step(orc):
+    # A circular orbit whose forces carry 1e-6 relative rounding, started with
+    # a step far below the resolvable one: with the floor the step grows to the
+    # eta-limited value instead of collapsing.
+    w = 1.0
+    eta = 0.2
+    rng = np.random.default_rng(1)
+
+    def derivs(t, k0, k1):
+        return np.array([[math.cos(w * t + k * math.pi / 2), math.sin(w * t + k * math.pi / 2), 0.0]
+                         for k in range(k0, k1)]) * (-(w ** np.arange(k0, k1)))[:, None]
+
+    for floored in (False, True):
+        eps = [1e-6, 1e-6, 1e-6, 1e-6] if floored else [0, 0, 0, 0]
+        h, t = 2.0 ** -12, 0.0
+        for _ in range(60):
+            D0 = derivs(t, 0, 3) * (1 + 1e-6 * rng.normal(size=(3, 1)))
+            D1 = derivs(t + h, 0, 3) * (1 + 1e-6 * rng.normal(size=(3, 1)))
+            hi = orc.interp(3, h, D0, D1)
+            crit = orc.dt_criterion_floored(6, eta, h, D0, np.vstack([D1, hi]), eps)
+            t += h
+            try:
+                h = orc.dt_quantise(min(crit, 2 * h), t, 1.0, 2.0 ** -40)
+            except orc.OracleError:
+                h = 0.0
+                break
+        if floored:
+            assert h == 0.125  # the largest power of two <= eta / w = 0.2
+        else:
+            assert h < 2.0 ** -12  # the plain criterion shrinks the step on noise
