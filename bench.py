@@ -1,0 +1,350 @@
+#!/usr/bin/env python3
+"""Benchmark: pairwise interactions/s of the block-step Hermite hot path on B300.
+
+One step = one full block cycle of the 6th-order scheme on the galactic-nucleus
+workload (2^20 Plummer stars + two unsoftened 0.005 black holes, star softening
+1e-5): block scheduler, predictor of all N, force of every particle on every
+particle (the synchronised block of a hierarchical block-step run), corrector
+and new steps.  Mixed precision (double-single positions, FP32 pair chain,
+compensated sums) unless --precision fp64.
+
+Printed JSON line (rank 0): value = interactions/s over the timed steps with
+the state resident in HBM; e2e = the same through the C ABI with host state
+copied in and out every step; roofline of the force kernel (CUDA events on its
+stream); the FP64 path on a 4096-particle block of the same system; energy
+error of both paths on the 65536-particle Plummer sphere; the CPU oracle on the
+host cores as a baseline.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pairwise interactions/s & % CUDA-core peak at N=2^20, mixed vs FP64 at stated dE/E"
+FLOPS_PER_INTERACTION = {4: 60, 6: 97, 8: 144}   # direct N-body flop convention
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 148, 128, 2032.0
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 76.96, FMA = 2 flops
+FP64_PEAK_TFLOPS = 1.25                                                     # nominal dense FP64
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    p.add_argument("--block-step", type=float, default=2.0 ** -12)
+    p.add_argument("--quick", action="store_true", help="skip the FP64, energy and CPU legs")
+    return p.parse_args()
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------- helpers
+def nucleus():
+    from paper_1312_1789_b300 import ics
+    return ics.standard_workload(2)
+
+
+def make_ctx(nb, wl, precision, stream):
+    ctx = nb.NBody(wl.n, wl.order, 0.0, precision)
+    ctx.set_stream(stream)
+    ctx.set_softening(np.sqrt(wl.eps2))
+    ctx.set_params(wl.eta, wl.eta_s, wl.dt_max, 2.0 ** -40)
+    ctx.set_particles(wl.m, wl.x, wl.v)
+    return ctx
+
+
+def oracle_rate(wl, n_target_s=12.0, nthreads=None):
+    """Oracle direct-sum interactions/s on the host cores for a sample of
+    active particles against all N (about n_target_s seconds of work)."""
+    import oracle as orc
+    nthreads = nthreads or os.cpu_count() or 1
+    rng = np.random.default_rng(0)
+    n_cal = max(nthreads, 16)
+    idx = rng.choice(wl.n, n_cal, replace=False).astype(np.int32)
+    t0 = time.perf_counter()
+    orc.force(wl.m, wl.eps2, wl.x, wl.v, np.zeros_like(wl.x), None, order=wl.order, idx=idx, nthreads=nthreads)
+    dt_cal = time.perf_counter() - t0
+    n_s = int(min(wl.n, max(n_cal, n_cal * n_target_s / max(dt_cal, 1e-3))))
+    n_s = max(nthreads, (n_s // nthreads) * nthreads)
+    return n_s, nthreads
+
+
+def run_reference(args):
+    """The CPU oracle timed on the host cores on a bounded sample per step."""
+    import oracle as orc
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = nucleus()
+    n_s, nth = oracle_rate(wl, n_target_s=max(2.0, 60.0 / max(1, args.steps + args.warmup)))
+    rng = np.random.default_rng(1)
+    times = []
+    for k in range(args.warmup + args.steps):
+        idx = np.sort(rng.choice(wl.n, n_s, replace=False)).astype(np.int32)
+        t0 = time.perf_counter()
+        orc.force(wl.m, wl.eps2, wl.x, wl.v, np.zeros_like(wl.x), None, order=wl.order, idx=idx, nthreads=nth)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    inter = n_s * wl.n
+    val = inter * len(times) / sum(times)
+    sample = f"force of {n_s} sampled particles on all {wl.n} (long-double direct sum) per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "interactions/s", "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f80 (x87 long double)",
+        "data": "synthetic", "config": {"workload": wl.name, "n": wl.n, "order": wl.order},
+        "cpu_baseline": {"value": val, "unit": "interactions/s", "cores": nth, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+
+    from paper_1312_1789_b300 import build, ics, nb
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+    nb.lib()
+    stream = torch.cuda.current_stream()
+    prec = nb.NB_MIXED if args.precision == "mixed" else nb.NB_FP64
+    wl = nucleus()
+    n = wl.n
+    h = args.block_step
+    ctx = make_ctx(nb, wl, prec, stream)
+    inter_step = n * n
+    flop_pi = FLOPS_PER_INTERACTION[wl.order]
+
+    def step():
+        ctx.set_block_step(h)
+        tb, na = ctx.block_step()
+        assert na == n, (na, n)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.set_profiling(True)
+    _, launches0 = ctx.get_profile()
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof, launches1 = ctx.get_profile()
+    ctx.set_profiling(False)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps * inter_step / (ms * 1e-3)
+    force_ms, force_n = prof["force"]
+    t_force = force_ms / max(force_n, 1) * 1e-3
+    achieved = flop_pi * inter_step / t_force / 1e12
+    out = {
+        "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 pair chain, double-single x, f64 state" if prec == nb.NB_MIXED else "f64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "n": n, "order": wl.order, "n_act": n,
+                   "precision": args.precision, "block_step": h,
+                   "l2": "state (~250 MB) and j-store (64 MB) stream every step; inputs exceed L2",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "tflops_convention": value * flop_pi / world / 1e12 if world else None,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "note": f"force kernel, {flop_pi} flops per interaction (direct N-body convention); peak "
+                             "= 148 SMs x 128 FP32 lanes x 2 x 2032 MHz"},
+        "phases_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "gpu_launches": int(launches1 - launches0),
+        "clocks": clk,
+    }
+    if rank == 0 and not args.quick:
+        extras(args, nb, ics, wl, ctx, stream, out, prec)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def extras(args, nb, ics, wl, ctx, stream, out, prec):
+    import torch
+    n = wl.n
+    h = args.block_step
+    flop_pi = FLOPS_PER_INTERACTION[wl.order]
+    # ---- e2e through the C ABI with host state in and out every step
+    try:
+        S = ctx.get_state()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.set_state(S["x"], S["v"], S["d"], S["t"], S["dt"])
+            ctx.set_block_step(h)
+            ctx.block_step()
+            R = ctx.get_state()
+        el = time.perf_counter() - t0
+        per = 8 * (3 + 3 + 18 + 1 + 1)
+        out["e2e"] = {"value": args.steps * n * n / el, "unit": "interactions/s", "h2d_bytes_per_step": per * n,
+                      "d2h_bytes_per_step": per * n,
+                      "path": "nb_set_state (host) + nb_set_block_step + nb_block_step + nb_get_state (host)"}
+        del R
+    except Exception as e:  # pragma: no cover
+        out["e2e"] = {"error": repr(e)}
+    # ---- FP64 path vs mixed on the same 4096-particle block
+    try:
+        rng = np.random.default_rng(7)
+        blk = np.sort(rng.choice(n, 4096, replace=False)).astype(np.int32)
+        res = {}
+        for name, p in (("fp64", nb.NB_FP64), ("mixed", nb.NB_MIXED)):
+            ctx.set_precision(p)
+            ctx.set_state(S["x"], S["v"], S["d"], S["t"], S["dt"])
+            t_next = float(S["t"][0]) + h
+            ctx.predict(t_next)
+            ctx.force(blk)
+            ctx.set_profiling(True)
+            reps = 2 if name == "fp64" else 10
+            for _ in range(reps):
+                ctx.force(blk)
+            prof, _ = ctx.get_profile()
+            ctx.set_profiling(False)
+            fms = prof["force"][0] / reps
+            res[name] = len(blk) * n / (fms * 1e-3)
+        ctx.set_precision(prec)
+        out["fp64"] = {"interactions_per_s": res["fp64"], "tflops_convention": res["fp64"] * flop_pi / 1e12,
+                       "frac_of_fp64_peak": res["fp64"] * flop_pi / 1e12 / FP64_PEAK_TFLOPS,
+                       "block": f"{len(blk)} active of {n}"}
+        out["mixed_same_block"] = {"interactions_per_s": res["mixed"]}
+        out["mixed_vs_fp64"] = res["mixed"] / res["fp64"]
+    except Exception as e:  # pragma: no cover
+        out["fp64"] = {"error": repr(e)}
+    # ---- energy error of both paths, Plummer N = 65536 to t = 1/16
+    try:
+        pw = ics.standard_workload(1)
+        t_end = 1.0 / 16
+        de = {}
+        for name, p in (("fp64", nb.NB_FP64), ("mixed", nb.NB_MIXED)):
+            c2 = nb.NBody(pw.n, 6, math.sqrt(pw.eps2[0]), p)
+            c2.set_stream(stream)
+            c2.set_params(pw.eta, pw.eta_s, pw.dt_max, 2.0 ** -40)
+            c2.set_particles(pw.m, pw.x, pw.v)
+            c2.set_precision(nb.NB_FP64)
+            e0 = sum(c2.energy())
+            c2.set_precision(p)
+            nblk, ni = c2.step_until(t_end)
+            c2.set_precision(nb.NB_FP64)
+            e1 = sum(c2.energy())
+            de[name] = {"dE_E": (e1 - e0) / abs(e0), "blocks": nblk, "interactions": ni}
+            c2.close()
+        out["energy_budget"] = {"workload": pw.name + f" to t={t_end}", **de,
+                                "mixed_within_2x": abs(de["mixed"]["dE_E"]) <= 2 * abs(de["fp64"]["dE_E"])}
+    except Exception as e:  # pragma: no cover
+        out["energy_budget"] = {"error": repr(e)}
+    # ---- CPU oracle on the host cores (bounded sample)
+    try:
+        import oracle as orc
+        n_s, nth = oracle_rate(wl)
+        idx = np.sort(np.random.default_rng(3).choice(n, n_s, replace=False)).astype(np.int32)
+        t0 = time.perf_counter()
+        orc.force(wl.m, wl.eps2, wl.x, wl.v, np.zeros_like(wl.x), None, order=wl.order, idx=idx, nthreads=nth)
+        el = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": n_s * n / el, "unit": "interactions/s", "cores": nth, "kind": "oracle",
+                               "sample": f"force of {n_s} of {n} particles on all {n} (long-double direct sum), "
+                                         f"{el:.1f} s"}
+    except Exception as e:  # pragma: no cover
+        out["cpu_baseline"] = {"error": repr(e)}
+    torch.cuda.synchronize()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
