@@ -179,11 +179,12 @@ int nb_set_jsplit(nb_ctx* ctx, int j_splits);
 int nb_set_block_step(nb_ctx* ctx, double dt);
 
 /* Relative precision eps[4] of the force components (acc, jerk, snap,
- * crackle) for the given precision mode.  The time-step criterion uses each
- * interpolated derivative net of the rounding its closed form can carry from
- * inputs of that precision (its noise floor): an unresolved derivative counts
- * as zero.  Defaults: NB_FP64 all 0 (the plain criterion); NB_MIXED
- * 3e-7, 1e-6, 2e-6, 2e-5, the measured error of the FP32 force chain.       */
+ * crackle) for the given precision mode, per unit of the particle's
+ * conditioning kappa = sum_j m_j/R_ij^2 / |a| (>= 1).  The time-step criterion
+ * uses each interpolated derivative net of the rounding its closed form can
+ * carry from inputs of that precision (its noise floor): an unresolved
+ * derivative counts as zero.  Defaults: NB_FP64 all 0 (the plain criterion);
+ * NB_MIXED 5e-7, 1e-6, 2e-6, 2e-5, the measured error of the FP32 chain.   */
 int nb_set_noise_floor(nb_ctx* ctx, int precision, const double* eps);
 int nb_get_noise_floor(nb_ctx* ctx, int precision, double* eps);
 

@@ -69,13 +69,14 @@ static ld norm3l(const ld* p)
 }
 
 /* absum receives sum_j |A_ij|, |J_ij|, |S_ij|, |C_ij|, |phi_ij|: the size of
-   the terms each total is made of, i.e. its condition scale. */
+   the terms each total is made of, i.e. its condition scale; absum[5] is
+   B = sum_j m_j / R_ij^2 (>= sum_j |A_ij|), the acc scale the time step uses. */
 static void force_one(int64_t n, const double* m, const double* eps2,
                       const double* x, const double* v, const double* a, const double* jk,
-                      int order, int64_t i, ld A[3], ld J[3], ld S[3], ld C[3], ld* phi, ld absum[5])
+                      int order, int64_t i, ld A[3], ld J[3], ld S[3], ld C[3], ld* phi, ld absum[6])
 {
     for (int k = 0; k < 3; k++) { A[k] = 0; J[k] = 0; S[k] = 0; C[k] = 0; }
-    for (int k = 0; k < 5; k++) absum[k] = 0;
+    for (int k = 0; k < 6; k++) absum[k] = 0;
     *phi = 0;
     for (int64_t j = 0; j < n; j++) {
         if (j == i) continue;
@@ -116,6 +117,7 @@ static void force_one(int64_t n, const double* m, const double* eps2,
         absum[2] += norm3l(pS);
         absum[3] += norm3l(pC);
         absum[4] += (ld)m[j] / R;
+        absum[5] += (ld)m[j] / R2;
     }
 }
 
@@ -135,10 +137,10 @@ int orc_force(int64_t n, const double* m, const double* eps2,
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
 #endif
     for (int64_t p = 0; p < n_act; p++) {
-        ld A[3], J[3], S[3], C[3], phi, ab[5];
+        ld A[3], J[3], S[3], C[3], phi, ab[6];
         force_one(n, m, eps2, x, v, a, jk, order, idx[p], A, J, S, C, &phi, ab);
         if (absum)
-            for (int k = 0; k < 5; k++) absum[5 * p + k] = (double)ab[k];
+            for (int k = 0; k < 6; k++) absum[6 * p + k] = (double)ab[k];
         for (int k = 0; k < 3; k++) {
             if (acc) acc[3 * p + k] = (double)A[k];
             if (jerk) jerk[3 * p + k] = (double)J[k];
@@ -387,15 +389,21 @@ int orc_noise_floor(int mm, double h, const double* D0, const double* D1, const 
 
 /* Step criterion after a step of length h: D0 = held derivatives at t0 (rows
    0..mm-1), Dfull = a^(0..2mm-1) at t1 (the first mm from the force, the rest
-   interpolated).  Interpolated norms are taken net of their noise floor. */
+   interpolated), bacc = sum_j m_j/R_ij^2 of the new force.  Interpolated norms
+   are taken net of their noise floor, the input precisions eps scaled by the
+   conditioning kappa = max(1, bacc / |a|). */
 double orc_dt_criterion_floored(int order, double eta, double h, const double* D0, const double* Dfull,
-                                const double* eps)
+                                const double* eps, double bacc)
 {
     int mm = order / 2;
     double n[8], N[4];
     for (int k = 0; k < 2 * mm; k++) n[k] = norm3d(Dfull + 3 * k);
     if (!(eps[0] > 0 || eps[1] > 0 || eps[2] > 0 || eps[3] > 0)) return criterion_from_norms(order, eta, n);
-    if (orc_noise_floor(mm, h, D0, Dfull, eps, N)) return NAN;
+    double kappa = n[0] > 0 ? bacc / n[0] : 1.0;
+    if (!(kappa > 1.0)) kappa = 1.0;
+    double ek[4];
+    for (int r = 0; r < 4; r++) ek[r] = eps[r] * kappa;
+    if (orc_noise_floor(mm, h, D0, Dfull, ek, N)) return NAN;
     for (int q = 0; q < mm; q++) {
         double f = n[mm + q] - N[q];
         n[mm + q] = f > 0 ? f : 0;
@@ -473,8 +481,9 @@ int orc_integrate(int64_t n, const double* m, const double* eps2,
     double* jp = malloc(sizeof(double) * 3 * n);
     double* F = malloc(sizeof(double) * 12 * n); /* new a, j, s, c per active */
     double* ph = malloc(sizeof(double) * n);
+    double* ab = malloc(sizeof(double) * 6 * n);
     int32_t* idx = malloc(sizeof(int32_t) * n);
-    if (!xp || !vp || !ap || !jp || !F || !ph || !idx) {
+    if (!xp || !vp || !ap || !jp || !F || !ph || !ab || !idx) {
         rc = ORC_ERR_ARG;
         goto done;
     }
@@ -539,7 +548,7 @@ int orc_integrate(int64_t n, const double* m, const double* eps2,
         nb++;
         rc = orc_predict(n, order, tb, t, x, v, d, xp, vp, ap, jp);
         if (rc) goto done;
-        rc = orc_force(n, m, eps2, xp, vp, ap, jp, order, na, idx, F, F + 3 * n, F + 6 * n, F + 9 * n, ph, NULL,
+        rc = orc_force(n, m, eps2, xp, vp, ap, jp, order, na, idx, F, F + 3 * n, F + 6 * n, F + 9 * n, ph, ab,
                        P->nthreads);
         if (rc) goto done;
         for (int64_t p = 0; p < na; p++) {
@@ -566,7 +575,7 @@ int orc_integrate(int64_t n, const double* m, const double* eps2,
                 for (int c = 0; c < 3; c++) D1c[3 * q + c] = Dfull[3 * q + c];
             double x1[3], v1[3];
             orc_correct(order, h, x + 3 * i, v + 3 * i, D0, D1c, x1, v1);
-            double crit = orc_dt_criterion_floored(order, P->eta, h, D0, Dfull, P->noise);
+            double crit = orc_dt_criterion_floored(order, P->eta, h, D0, Dfull, P->noise, ab[6 * p + 5]);
             double lim = crit;
             if (2.0 * h < lim) lim = 2.0 * h;
             double dtn;
@@ -592,6 +601,7 @@ done:
     free(jp);
     free(F);
     free(ph);
+    free(ab);
     free(idx);
     return rc;
 }

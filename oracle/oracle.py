@@ -44,7 +44,7 @@ def lib():
         L.orc_dt_criterion.argtypes = [C.c_int, C.c_double, d]
         L.orc_dt_criterion.restype = C.c_double
         L.orc_noise_floor.argtypes = [C.c_int, C.c_double, d, d, d, d]
-        L.orc_dt_criterion_floored.argtypes = [C.c_int, C.c_double, C.c_double, d, d, d]
+        L.orc_dt_criterion_floored.argtypes = [C.c_int, C.c_double, C.c_double, d, d, d, C.c_double]
         L.orc_dt_criterion_floored.restype = C.c_double
         L.orc_dt_quantise.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, d]
         L.orc_dt_startup.argtypes = [C.c_double, d, d]
@@ -88,8 +88,9 @@ def num_threads() -> int:
 def force(m, eps2, x, v, a=None, jk=None, order=6, idx=None, nthreads=1):
     """Direct-sum acc, jerk, snap, crackle and potential on particles idx.
 
-    Also returns "absum" [n_act][5]: sum over j of |A_ij|, |J_ij|, |S_ij|,
-    |C_ij| and m_j/R_ij, the magnitude of the terms behind each total.
+    Also returns "absum" [n_act][6]: sum over j of |A_ij|, |J_ij|, |S_ij|,
+    |C_ij| and m_j/R_ij, the magnitude of the terms behind each total, and
+    B = sum_j m_j/R_ij^2, the acc scale the noise-floored time step uses.
     """
     m = _f64(m)
     n = m.shape[0]
@@ -102,7 +103,7 @@ def force(m, eps2, x, v, a=None, jk=None, order=6, idx=None, nthreads=1):
     na = idx.shape[0]
     out = {k: np.zeros((na, 3)) for k in ("acc", "jerk", "snap", "crackle")}
     out["pot"] = np.zeros(na)
-    out["absum"] = np.zeros((na, 5))
+    out["absum"] = np.zeros((na, 6))
     rc = lib().orc_force(n, _p(m), _p(eps2), _p(x), _p(v), _p(a), _p(jk), order, na, _p(idx),
                          _p(out["acc"]), _p(out["jerk"]), _p(out["snap"]), _p(out["crackle"]),
                          _p(out["pot"]), _p(out["absum"]), int(nthreads))
@@ -165,14 +166,15 @@ def noise_floor(mm, h, D0, D1, eps):
     return out
 
 
-def dt_criterion_floored(order, eta, h, D0, Dfull, eps):
-    """Step criterion with interpolated norms net of their noise floor."""
+def dt_criterion_floored(order, eta, h, D0, Dfull, eps, bacc=0.0):
+    """Step criterion with interpolated norms net of their noise floor
+    (precisions eps scaled by max(1, bacc / |a|))."""
     mm = order // 2
     e = np.zeros(4)
     e[: len(eps)] = eps
     D0 = _f64(np.asarray(D0)[:mm], (mm, 3))
     return float(lib().orc_dt_criterion_floored(order, float(eta), float(h), _p(D0),
-                                                _p(_f64(Dfull, (2 * mm, 3))), _p(e)))
+                                                _p(_f64(Dfull, (2 * mm, 3))), _p(e), float(bacc)))
 
 
 def dt_quantise(lim, t1, dt_max=1.0 / 16, dt_min=2.0 ** -40):

@@ -120,7 +120,8 @@ __device__ __forceinline__ void tile_mixed(const float4* __restrict__ b, const f
                 acc[11] = fmaf(q, fmaf(c6, dz, fmaf(c5, dvz, fmaf(c4, daz, dkz))), acc[11]);
             }
         }
-        acc[NC - 1] += mr;
+        acc[NC - 2] += mr;
+        acc[NC - 1] = fmaf(mr, rinv, acc[NC - 1]);
     }
 }
 
@@ -266,7 +267,8 @@ __device__ __forceinline__ void tile_fp64(const double2* __restrict__ b, const d
                 acc[11] = fma(q, fma(c6, dz, fma(c5, dvz, fma(c4, daz, dkz))), acc[11]);
             }
         }
-        acc[NC - 1] += mr;
+        acc[NC - 2] += mr;
+        acc[NC - 1] = fma(mr, rinv, acc[NC - 1]);
     }
 }
 
@@ -363,7 +365,8 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_fp64(const double2* __restri
 
 // -------------------------------------------------------------------- K3
 // F[c][p] = sum over splits in fixed order; the potential sum is negated.
-template <int NC>
+// PC = index of the potential component.
+template <int NC, int PC>
 __global__ void k_force_reduce(const double* __restrict__ partial, int jsplit, int n_act,
                                const int32_t* __restrict__ idx, const double* __restrict__ m,
                                const double* __restrict__ eps2, int n, double* __restrict__ F)
@@ -374,7 +377,7 @@ __global__ void k_force_reduce(const double* __restrict__ partial, int jsplit, i
     for (int c = 0; c < NC; ++c) {
         double s = 0.0;
         for (int sp = 0; sp < jsplit; ++sp) s += partial[((size_t)sp * NC + c) * n_act + p];
-        if (c == NC - 1) s = -s;
+        if (c == PC) s = -s;
         F[(size_t)c * n_act + p] = s;
     }
 }
@@ -486,11 +489,11 @@ cudaError_t launch_force_reduce(nb_ctx* c, int order, const int32_t* idx, int64_
     const int nt = 256;
     const int nb = (int)((n_act + nt - 1) / nt);
     const int na = (int)n_act, n = (int)c->n;
-    switch (ncomp(order)) {
-    case 1: k_force_reduce<1><<<nb, nt, 0, c->stream>>>(c->partial, jsplit, na, idx, c->m, c->eps2, n, c->F); break;
-    case 7: k_force_reduce<7><<<nb, nt, 0, c->stream>>>(c->partial, jsplit, na, idx, c->m, c->eps2, n, c->F); break;
-    case 10: k_force_reduce<10><<<nb, nt, 0, c->stream>>>(c->partial, jsplit, na, idx, c->m, c->eps2, n, c->F); break;
-    case 13: k_force_reduce<13><<<nb, nt, 0, c->stream>>>(c->partial, jsplit, na, idx, c->m, c->eps2, n, c->F); break;
+    switch (order) {
+    case 0: k_force_reduce<ncomp(0), pot_comp(0)><<<nb, nt, 0, c->stream>>>(c->partial, jsplit, na, idx, c->m, c->eps2, n, c->F); break;
+    case 4: k_force_reduce<ncomp(4), pot_comp(4)><<<nb, nt, 0, c->stream>>>(c->partial, jsplit, na, idx, c->m, c->eps2, n, c->F); break;
+    case 6: k_force_reduce<ncomp(6), pot_comp(6)><<<nb, nt, 0, c->stream>>>(c->partial, jsplit, na, idx, c->m, c->eps2, n, c->F); break;
+    case 8: k_force_reduce<ncomp(8), pot_comp(8)><<<nb, nt, 0, c->stream>>>(c->partial, jsplit, na, idx, c->m, c->eps2, n, c->F); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -314,7 +314,8 @@ __device__ double dt_criterion(double eta, const double* nrm)
 
 // Noise floor of the interpolated derivatives.  The closed forms below take
 // differences of force values whose relative precision is ea (acc), ej
-// (jerk), es (snap), ec (crackle); a derivative k carries at most
+// (jerk), es (snap), ec (crackle) -- already multiplied by the particle's
+// conditioning kappa = sum_j m_j/R_ij^2 / |a| -- and a derivative k carries at most
 // N_k = sum |coefficient| * eps * |input| / h^k of that rounding.  The
 // criterion uses max(|a^(k)| - N_k, 0): what the inputs cannot resolve is
 // treated as unknown (zero) rather than as signal.  With all eps = 0 the
@@ -381,6 +382,7 @@ __global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fid
 #pragma unroll
         for (int c = 0; c < 3; ++c) H[k][c] = F[(size_t)(3 * k + c) * fn + p];
     const double potn = F[(size_t)(3 * MM) * fn + p];
+    const double bacc = F[(size_t)(3 * MM + 1) * fn + p];  // sum_j m_j / R_ij^2
 
     const double ih = 1.0 / h;
 #pragma unroll
@@ -444,7 +446,10 @@ __global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fid
         nL[k] = norm3(L[k]);
         nR[k] = k < MM ? nrm[k] : 0.0;
     }
-    noise_floor<ORDER>(nL, nR, h, ne.e, N);
+    // rounding of a total scales with the terms it sums: kappa = B / |a| >= 1
+    const double kappa = nR[0] > 0.0 ? fmax(1.0, bacc / nR[0]) : 1.0;
+    const double ek[4] = {ne.e[0] * kappa, ne.e[1] * kappa, ne.e[2] * kappa, ne.e[3] * kappa};
+    noise_floor<ORDER>(nL, nR, h, ek, N);
 #pragma unroll
     for (int k = MM; k < 2 * MM; ++k) nrm[k] = fmax(nrm[k] - N[k], 0.0);
     double lim = dt_criterion<ORDER>(eta, nrm);

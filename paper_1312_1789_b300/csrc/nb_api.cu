@@ -631,7 +631,7 @@ int nb_get_force(nb_ctx* c, double* acc, double* jerk, double* snap, double* cra
             for (int k = 0; k < 3; ++k) outs[q][3 * p + k] = (q < o / 2) ? tmp[(size_t)(3 * q + k) * fn + p] : 0.0;
     }
     if (pot)
-        for (size_t p = 0; p < fn; ++p) pot[p] = tmp[(size_t)(nc - 1) * fn + p];
+        for (size_t p = 0; p < fn; ++p) pot[p] = tmp[(size_t)pot_comp(o) * fn + p];
     return NB_OK;
 }
 

@@ -39,8 +39,11 @@ constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;
 //   w6 = (j.x, j.y)  w7 = (j.z, 0)  [order 8]
 __host__ __device__ constexpr int mixed_rw(int order) { return order == 4 ? 3 : order == 6 ? 4 : 5; }
 __host__ __device__ constexpr int fp64_rw(int order) { return order == 4 ? 4 : order == 6 ? 6 : 8; }
-// components of a force result: acc, jerk[, snap[, crackle]] x 3, then pot.
-__host__ __device__ constexpr int ncomp(int order) { return order == 0 ? 1 : 3 * (order / 2) + 1; }
+// components of a force result: acc, jerk[, snap[, crackle]] x 3, then pot,
+// then (orders >= 4) the acc magnitude scale B = sum_j m_j / R_ij^2, an upper
+// bound of sum_j |A_ij| that sets the rounding level of the acc total.
+__host__ __device__ constexpr int ncomp(int order) { return order == 0 ? 1 : 3 * (order / 2) + 2; }
+__host__ __device__ constexpr int pot_comp(int order) { return order == 0 ? 0 : 3 * (order / 2); }
 
 // Scalars shared between the scheduler, the kernels and the host.
 struct DevScalars {
@@ -151,7 +154,7 @@ struct nb_ctx {
     double eta = 0.2, eta_s = 0.01, dt_max = 1.0 / 16, dt_min = 0x1p-40;
     // noise floors per precision [NB_FP64, NB_MIXED]: FP64 none (the plain
     // criterion); mixed from the measured error of the FP32 force chain
-    nb::NoiseEps noise[2] = {{{0.0, 0.0, 0.0, 0.0}}, {{3e-7, 1e-6, 2e-6, 2e-5}}};
+    nb::NoiseEps noise[2] = {{{0.0, 0.0, 0.0, 0.0}}, {{5e-7, 1e-6, 2e-6, 2e-5}}};
     cudaStream_t stream = nullptr;
     int jsplit_force = 0;
     int sm_count = 148;

@@ -159,6 +159,7 @@ def test_corrector_parity(prec, order):
     ctx.force()
     S0 = ctx.get_state()
     F = ctx.get_force(len(idx))
+    bacc = oracle_force_on_predicted(ctx, m, eps2, idx, order)["absum"][:, 5]
     ctx.correct()
     S1 = ctx.get_state()
     mm = order // 2
@@ -170,7 +171,8 @@ def test_corrector_parity(prec, order):
         hi = orc.interp(mm, h, D0[:mm], D1)
         Dfull = np.vstack([D1, hi])
         x1, v1 = orc.correct(order, h, S0["x"][i], S0["v"][i], D0, Dfull[:4])
-        lim = min(orc.dt_criterion_floored(order, eta, h, D0, Dfull, ctx.get_noise_floor(prec)), 2 * h)
+        crit = orc.dt_criterion_floored(order, eta, h, D0, Dfull, ctx.get_noise_floor(prec), bacc[p])
+        lim = min(crit, 2 * h)
         dt_o = orc.dt_quantise(lim, tb, 1.0 / 16, 2.0 ** -40)
         assert S1["t"][i] == tb
         assert S1["dt"][i] == dt_o, (i, S1["dt"][i], dt_o)
