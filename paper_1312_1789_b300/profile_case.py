@@ -1,0 +1,43 @@
+"""Small, self-contained force case for profilers (ncu) and quick timing.
+
+    python -m paper_1312_1789_b300.profile_case [--n-act 4096] [--precision mixed|fp64] [--repeat 2]
+
+Builds the galactic-nucleus system (2^20 Plummer stars + two black holes),
+runs the start-up (two force launches over every particle), predicts, then
+launches the force kernel --repeat times on one block of --n-act particles.
+With ncu, `-k regex:k_force -s 2 -c 1` captures the first block launch.
+"""
+from __future__ import annotations
+
+import argparse
+
+import numpy as np
+
+from . import ics, nb
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--n-act", type=int, default=4096)
+    p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    p.add_argument("--repeat", type=int, default=2)
+    a = p.parse_args()
+    wl = ics.standard_workload(2)
+    prec = nb.NB_MIXED if a.precision == "mixed" else nb.NB_FP64
+    ctx = nb.NBody(wl.n, wl.order, 0.0, prec)
+    ctx.set_softening(np.sqrt(wl.eps2))
+    ctx.set_particles(wl.m, wl.x, wl.v)
+    ctx.predict(2.0 ** -12)
+    blk = np.sort(np.random.default_rng(7).choice(wl.n, min(a.n_act, wl.n), replace=False)).astype(np.int32)
+    ctx.set_profiling(True)
+    for _ in range(a.repeat):
+        ctx.force(blk)
+    prof, _ = ctx.get_profile()
+    ms = prof["force"][0] / max(prof["force"][1], 1)
+    print(f"{wl.name} {a.precision}: block {len(blk)}, launch {ctx.get_launch()}, force kernel {ms:.3f} ms, "
+          f"{len(blk) * wl.n / (ms * 1e-3):.3e} interactions/s")
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()
