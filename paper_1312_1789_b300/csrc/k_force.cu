@@ -86,35 +86,37 @@ __device__ __forceinline__ void tile_mixed(const float4* __restrict__ b, const f
         }
         const float rinv2 = rinv * rinv;
         const float q = mr * rinv2;
+        const float r3 = -3.0f * rinv2;
         const float4 w2 = b[jj * RW + 2];
         const float dvx = w2.x - i2.x, dvy = w2.y - i2.y, dvz = w2.z - i2.z;
         acc[0] = fmaf(q, dx, acc[0]);
         acc[1] = fmaf(q, dy, acc[1]);
         acc[2] = fmaf(q, dz, acc[2]);
-        const float al = fmaf(dx, dvx, fmaf(dy, dvy, dz * dvz)) * rinv2;
-        const float c1 = -3.0f * al;
-        acc[3] = fmaf(q, fmaf(c1, dx, dvx), acc[3]);
-        acc[4] = fmaf(q, fmaf(c1, dy, dvy), acc[4]);
-        acc[5] = fmaf(q, fmaf(c1, dz, dvz), acc[5]);
+        // a3 = -3 alpha, the jerk coefficient
+        const float a3 = fmaf(dx, dvx, fmaf(dy, dvy, dz * dvz)) * r3;
+        acc[3] = fmaf(q, fmaf(a3, dx, dvx), acc[3]);
+        acc[4] = fmaf(q, fmaf(a3, dy, dvy), acc[4]);
+        acc[5] = fmaf(q, fmaf(a3, dz, dvz), acc[5]);
         if (ORDER >= 6) {
             const float4 w3 = b[jj * RW + 3];
             const float dax = w3.x - i3.x, day = w3.y - i3.y, daz = w3.z - i3.z;
-            const float w =
-                fmaf(dvx, dvx, fmaf(dvy, dvy, fmaf(dvz, dvz, fmaf(dx, dax, fmaf(dy, day, dz * daz))))) * rinv2;
-            const float c2 = -6.0f * al;
-            const float c3 = fmaf(15.0f * al, al, -3.0f * w);
+            // w3 = -3 w; snap coefficients c2 = -6 alpha, c3 = 15 alpha^2 - 3 w
+            const float ww3 = fmaf(dvx, dvx, fmaf(dvy, dvy, fmaf(dvz, dvz, fmaf(dx, dax, fmaf(dy, day, dz * daz))))) * r3;
+            const float c2 = a3 + a3;
+            const float c3 = fmaf((5.0f / 3.0f) * a3, a3, ww3);
             acc[6] = fmaf(q, fmaf(c3, dx, fmaf(c2, dvx, dax)), acc[6]);
             acc[7] = fmaf(q, fmaf(c3, dy, fmaf(c2, dvy, day)), acc[7]);
             acc[8] = fmaf(q, fmaf(c3, dz, fmaf(c2, dvz, daz)), acc[8]);
             if (ORDER >= 8) {
                 const float4 w4 = b[jj * RW + 4];
                 const float dkx = w4.x - i4.x, dky = w4.y - i4.y, dkz = w4.z - i4.z;
-                const float u =
-                    fmaf(3.0f, fmaf(dvx, dax, fmaf(dvy, day, dvz * daz)), fmaf(dx, dkx, fmaf(dy, dky, dz * dkz))) *
-                    rinv2;
-                const float c4 = -9.0f * al;
-                const float c5 = fmaf(45.0f * al, al, -9.0f * w);
-                const float c6 = fmaf(al, fmaf(-105.0f * al, al, 45.0f * w), -3.0f * u);
+                // u3 = -3 u; crackle: c4 = -9 alpha, c5 = 45 alpha^2 - 9 w,
+                // c6 = -105 alpha^3 + 45 alpha w - 3 u
+                const float u3 =
+                    fmaf(3.0f, fmaf(dvx, dax, fmaf(dvy, day, dvz * daz)), fmaf(dx, dkx, fmaf(dy, dky, dz * dkz))) * r3;
+                const float c4 = 3.0f * a3;
+                const float c5 = fmaf(5.0f * a3, a3, 3.0f * ww3);
+                const float c6 = fmaf(a3, fmaf((35.0f / 9.0f) * a3, a3, 5.0f * ww3), u3);
                 acc[9] = fmaf(q, fmaf(c6, dx, fmaf(c5, dvx, fmaf(c4, dax, dkx))), acc[9]);
                 acc[10] = fmaf(q, fmaf(c6, dy, fmaf(c5, dvy, fmaf(c4, day, dky))), acc[10]);
                 acc[11] = fmaf(q, fmaf(c6, dz, fmaf(c5, dvz, fmaf(c4, daz, dkz))), acc[11]);
@@ -129,7 +131,7 @@ __device__ __forceinline__ void tile_mixed(const float4* __restrict__ b, const f
 template <int ORDER, int RW, bool PAIR>
 __global__ void __launch_bounds__(FORCE_NT) k_force_mixed(const float4* __restrict__ js, const int32_t* __restrict__ idx,
                                                           int n_act, int n, int ntiles, int jsplit, float eps2u,
-                                                          double* __restrict__ partial, DevScalars* sc)
+                                                          float eps2max, double* __restrict__ partial, DevScalars* sc)
 {
     constexpr int NC = ncomp(ORDER);
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -168,6 +170,10 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_mixed(const float4* __restri
     if (ORDER >= 6) i3 = ri[3];
     if (ORDER >= 8) i4 = ri[4];
     const float ei2 = PAIR ? i1.w : eps2u;
+    // A warp whose every i-particle is softened at least as much as any
+    // particle pairs with the constant eps_i^2: the per-pair max and the
+    // R^2 = 0 guard drop out (same results, fewer instructions).
+    const bool dom = PAIR && __all_sync(0xffffffffu, ei2 >= eps2max && ei2 > 0.0f);
 
     float hi[NC], lo[NC];
 #pragma unroll
@@ -192,10 +198,15 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_mixed(const float4* __restri
         for (int c = 0; c < NC; ++c) acc[c] = 0.f;
         // the tile holding a lane's own particle takes the masked variant
         const int self_rel = gi - (t0 + k) * JT;
-        if (__any_sync(0xffffffffu, (unsigned)self_rel < (unsigned)JT))
-            tile_mixed<ORDER, RW, PAIR, true>(b, i0, i1, i2, i3, i4, ei2, eps2u, self_rel, acc);
-        else
-            tile_mixed<ORDER, RW, PAIR, false>(b, i0, i1, i2, i3, i4, ei2, eps2u, -1, acc);
+        const bool self_here = __any_sync(0xffffffffu, (unsigned)self_rel < (unsigned)JT);
+        if (!PAIR || dom) {
+            const float e2c = PAIR ? ei2 : eps2u;
+            if (self_here) tile_mixed<ORDER, RW, false, true>(b, i0, i1, i2, i3, i4, e2c, e2c, self_rel, acc);
+            else tile_mixed<ORDER, RW, false, false>(b, i0, i1, i2, i3, i4, e2c, e2c, -1, acc);
+        } else {
+            if (self_here) tile_mixed<ORDER, RW, true, true>(b, i0, i1, i2, i3, i4, ei2, eps2u, self_rel, acc);
+            else tile_mixed<ORDER, RW, true, false>(b, i0, i1, i2, i3, i4, ei2, eps2u, -1, acc);
+        }
 #pragma unroll
         for (int c = 0; c < NC; ++c) ds_add(hi[c], lo[c], acc[c]);
 
@@ -410,7 +421,8 @@ static cudaError_t run_mixed(nb_ctx* c, const int32_t* idx, int n_act, int jspli
     }
     dim3 grid(itiles, jsplit);
     kern<<<grid, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), idx, n_act, (int)c->n,
-                                              (int)(c->np / JT), jsplit, (float)(c->eps * c->eps), c->partial, c->sc);
+                                              (int)(c->np / JT), jsplit, (float)(c->eps * c->eps),
+                                              (float)c->eps2_max, c->partial, c->sc);
     return cudaGetLastError();
 }
 

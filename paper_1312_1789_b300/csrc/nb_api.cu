@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -169,16 +170,29 @@ void choose_shape(nb_ctx* c, int order, int64_t n_act, int* itiles, int* jsplit)
 {
     const int it = (int)((n_act + FORCE_NT - 1) / FORCE_NT);
     const int ntiles = (int)(c->np / JT);
-    int js;
+    int js = 1;
+    auto fits = [&](int s) { return (size_t)s * ncomp(order) * (size_t)n_act <= c->partial_cap; };
     if (c->jsplit_force > 0) {
         js = c->jsplit_force;
     } else {
-        const int target = c->sm_count * force_occupancy(c, order);
-        js = it >= target ? 1 : (target + it - 1) / it;
+        // Equal-work CTAs run in waves of `slots`; the makespan of it*js CTAs,
+        // each 1/js of the j range, is ceil(it*js/slots)/js.  Take the split
+        // with the smallest makespan (ties within 1% to the smaller split).
+        const int slots = c->sm_count * force_occupancy(c, order);
+        const int js_max = std::min(ntiles, std::max(1, 4 * slots / std::max(it, 1) + 4));
+        double best = 1e300;
+        for (int s = 1; s <= js_max && fits(s); ++s) {
+            const double waves = std::ceil((double)it * s / slots);
+            const double span = waves / s;
+            if (span < best * 0.99) {
+                best = span;
+                js = s;
+            }
+        }
     }
     if (js > ntiles) js = ntiles;
     if (js < 1) js = 1;
-    while (js > 1 && (size_t)js * ncomp(order) * (size_t)n_act > c->partial_cap) --js;
+    while (js > 1 && !fits(js)) --js;
     *itiles = it;
     *jsplit = js;
 }
@@ -341,6 +355,8 @@ int nb_set_softening(nb_ctx* c, const double* eps_i)
     NB_CUDA(c, cudaMemcpyAsync(c->eps2, e2.data(), e2.size() * 8, cudaMemcpyHostToDevice, c->stream));
     NB_CUDA(c, cudaStreamSynchronize(c->stream));
     c->pair_eps = eps_i != nullptr;
+    c->eps2_max = 0.0;
+    for (int64_t k = 0; k < c->n; ++k) c->eps2_max = std::max(c->eps2_max, e2[(size_t)k]);
     c->have_pred = 0;
     return NB_OK;
 }

@@ -151,6 +151,7 @@ struct nb_ctx {
     int pred_prec = -1;  // precision of the store written by the last predict
     double eps = 0.0;
     int pair_eps = 0;  // per-particle softening in use
+    double eps2_max = 0.0;  // largest eps_i^2 (per-particle softening)
     double eta = 0.2, eta_s = 0.01, dt_max = 1.0 / 16, dt_min = 0x1p-40;
     // noise floors per precision [NB_FP64, NB_MIXED]: FP64 none (the plain
     // criterion); mixed from the measured error of the FP32 force chain
