@@ -1,397 +1,8 @@
-// k_force.cu -- direct-summation force kernel (K2) and its j-split reduction (K3).
-//
-// For each active particle i and every particle j of the predicted store the
-// kernel sums the Plummer-softened Newtonian acceleration and its time
-// derivatives ("Codes description": the GPUs compute the gravitational forces
-// between particles; abstract: 4th/6th/8th-order Hermite).  With
-// r = x_j - x_i, v = v_j - v_i, a = a_j - a_i, k = jerk_j - jerk_i,
-// R^2 = r.r + eps_ij^2, q = m_j / R^3, alpha = r.v / R^2,
-// w = (v.v + r.a) / R^2, u = (3 v.a + r.k) / R^2, the pair terms are
-//   A = q r
-//   J = q (v - 3 alpha r)
-//   S = q (a - 6 alpha v + (15 alpha^2 - 3 w) r)
-//   C = q (k - 9 alpha a + (45 alpha^2 - 9 w) v + (-105 alpha^3 + 45 alpha w - 3 u) r)
-// which are dA/dt, d2A/dt2, d3A/dt3 rearranged so that every term is q times a
-// combination of the four difference vectors; the potential sum is m_j / R.
-//
-// Layout: one CTA holds FORCE_NT i-particles in registers (one per thread) and
-// streams a contiguous range of j tiles of JT records each through a ring of
-// NSTAGE shared-memory buffers filled by one-dimensional TMA bulk copies
-// (cp.async.bulk + mbarrier).  blockIdx.y splits the j range; each split writes
-// partial sums [split][component][i] which K3 adds in fixed split order, so
-// results are bitwise reproducible for a given launch shape.
-//
-// Mixed precision: positions are double-single (hi + lo floats); the difference
-// (x_hi_j - x_hi_i) + (x_lo_j - x_lo_i) keeps ~44 bits for close pairs, the
-// rest of the chain runs in FP32 (one MUFU rsqrt per pair), each tile's FP32
-// sums are folded into a double-single accumulator with an error-free TwoSum,
-// and the accumulator is widened to FP64 once per CTA.  No FP64 or conversion
-// instruction runs in the j loop.
-//
-// FP64: the same structure in double, tile sums added to double accumulators
-// (blocked summation).
-#include "nb_internal.cuh"
+// k_force.cu -- launchers of the force kernel (K2) and its j-split reduction (K3);
+// the kernels are in force_kernels.cuh.
+#include "force_kernels.cuh"
 
 namespace nb {
-
-// self-term guard: with per-particle softening a pair can have R^2 = 0 (an
-// unsoftened particle meeting itself); its contribution is zero by definition.
-template <bool PAIR>
-__device__ __forceinline__ float guard_rinv(float r2)
-{
-    float ri = rsqrtf(r2);
-    if (PAIR) ri = (r2 > 0.0f) ? ri : 0.0f;
-    return ri;
-}
-
-template <bool PAIR>
-__device__ __forceinline__ double guard_rinv_d(double r2)
-{
-    double ri = rsqrt(r2);
-    if (PAIR) ri = (r2 > 0.0) ? ri : 0.0;
-    return ri;
-}
-
-// Wait for the copies still in flight after a timeout (bounded again), then
-// the caller returns.  Called by thread 0 only.
-__device__ void drain_after_timeout(uint64_t* bars, int k, int nt)
-{
-    for (int kk = k; kk < nt && kk < k + NSTAGE; ++kk) mbar_wait_bounded(&bars[kk % NSTAGE], (kk / NSTAGE) & 1);
-}
-
-// One j tile for one i-particle: accumulates the pair terms into acc.  SELF:
-// the tile may contain the i-particle itself (at position self_rel), whose
-// pair is skipped by zeroing its inverse distance (every term carries it).
-template <int ORDER, int RW, bool PAIR, bool SELF>
-__device__ __forceinline__ void tile_mixed(const float4* __restrict__ b, const float4 i0, const float4 i1,
-                                           const float4 i2, const float4 i3, const float4 i4, const float ei2,
-                                           const float eps2u, const int self_rel, float (&acc)[ncomp(ORDER)])
-{
-    constexpr int NC = ncomp(ORDER);
-#pragma unroll 2
-    for (int jj = 0; jj < JT; ++jj) {
-        const float4 w0 = b[jj * RW + 0];
-        const float4 w1 = b[jj * RW + 1];
-        const float dx = (w0.x - i0.x) + (w1.x - i1.x);
-        const float dy = (w0.y - i0.y) + (w1.y - i1.y);
-        const float dz = (w0.z - i0.z) + (w1.z - i1.z);
-        const float e2 = PAIR ? fmaxf(w1.w, ei2) : eps2u;
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, e2)));
-        float rinv = guard_rinv<PAIR>(r2);
-        if (SELF) rinv = (jj == self_rel) ? 0.0f : rinv;
-        const float mr = w0.w * rinv;
-        if (ORDER == 0) {
-            acc[0] += mr;
-            continue;
-        }
-        const float rinv2 = rinv * rinv;
-        const float q = mr * rinv2;
-        const float r3 = -3.0f * rinv2;
-        const float4 w2 = b[jj * RW + 2];
-        const float dvx = w2.x - i2.x, dvy = w2.y - i2.y, dvz = w2.z - i2.z;
-        acc[0] = fmaf(q, dx, acc[0]);
-        acc[1] = fmaf(q, dy, acc[1]);
-        acc[2] = fmaf(q, dz, acc[2]);
-        // a3 = -3 alpha, the jerk coefficient
-        const float a3 = fmaf(dx, dvx, fmaf(dy, dvy, dz * dvz)) * r3;
-        acc[3] = fmaf(q, fmaf(a3, dx, dvx), acc[3]);
-        acc[4] = fmaf(q, fmaf(a3, dy, dvy), acc[4]);
-        acc[5] = fmaf(q, fmaf(a3, dz, dvz), acc[5]);
-        if (ORDER >= 6) {
-            const float4 w3 = b[jj * RW + 3];
-            const float dax = w3.x - i3.x, day = w3.y - i3.y, daz = w3.z - i3.z;
-            // w3 = -3 w; snap coefficients c2 = -6 alpha, c3 = 15 alpha^2 - 3 w
-            const float ww3 = fmaf(dvx, dvx, fmaf(dvy, dvy, fmaf(dvz, dvz, fmaf(dx, dax, fmaf(dy, day, dz * daz))))) * r3;
-            const float c2 = a3 + a3;
-            const float c3 = fmaf((5.0f / 3.0f) * a3, a3, ww3);
-            acc[6] = fmaf(q, fmaf(c3, dx, fmaf(c2, dvx, dax)), acc[6]);
-            acc[7] = fmaf(q, fmaf(c3, dy, fmaf(c2, dvy, day)), acc[7]);
-            acc[8] = fmaf(q, fmaf(c3, dz, fmaf(c2, dvz, daz)), acc[8]);
-            if (ORDER >= 8) {
-                const float4 w4 = b[jj * RW + 4];
-                const float dkx = w4.x - i4.x, dky = w4.y - i4.y, dkz = w4.z - i4.z;
-                // u3 = -3 u; crackle: c4 = -9 alpha, c5 = 45 alpha^2 - 9 w,
-                // c6 = -105 alpha^3 + 45 alpha w - 3 u
-                const float u3 =
-                    fmaf(3.0f, fmaf(dvx, dax, fmaf(dvy, day, dvz * daz)), fmaf(dx, dkx, fmaf(dy, dky, dz * dkz))) * r3;
-                const float c4 = 3.0f * a3;
-                const float c5 = fmaf(5.0f * a3, a3, 3.0f * ww3);
-                const float c6 = fmaf(a3, fmaf((35.0f / 9.0f) * a3, a3, 5.0f * ww3), u3);
-                acc[9] = fmaf(q, fmaf(c6, dx, fmaf(c5, dvx, fmaf(c4, dax, dkx))), acc[9]);
-                acc[10] = fmaf(q, fmaf(c6, dy, fmaf(c5, dvy, fmaf(c4, day, dky))), acc[10]);
-                acc[11] = fmaf(q, fmaf(c6, dz, fmaf(c5, dvz, fmaf(c4, daz, dkz))), acc[11]);
-            }
-        }
-        acc[NC - 2] += mr;
-        acc[NC - 1] = fmaf(mr, rinv, acc[NC - 1]);
-    }
-}
-
-// ----------------------------------------------------------------- mixed
-template <int ORDER, int RW, bool PAIR>
-__global__ void __launch_bounds__(FORCE_NT) k_force_mixed(const float4* __restrict__ js, const int32_t* __restrict__ idx,
-                                                          int n_act, int n, int ntiles, int jsplit, float eps2u,
-                                                          float eps2max, double* __restrict__ partial, DevScalars* sc)
-{
-    constexpr int NC = ncomp(ORDER);
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    float4* buf = reinterpret_cast<float4*>(smem_raw);
-    __shared__ __align__(8) uint64_t bars[NSTAGE];
-
-    const int tid = threadIdx.x;
-    const int p = blockIdx.x * FORCE_NT + tid;
-    const int split = blockIdx.y;
-    const int t0 = (int)((long long)split * ntiles / jsplit);
-    const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
-    const int nt = t1 - t0;
-    constexpr uint32_t TILE_BYTES = JT * RW * 16;
-
-    if (tid == 0) {
-        for (int k = 0; k < NSTAGE; ++k) mbar_init(&bars[k], 1);
-        fence_barrier_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
-        for (int k = 0; k < NSTAGE && k < nt; ++k) {
-            mbar_expect_tx(&bars[k], TILE_BYTES);
-            bulk_g2s(buf + k * JT * RW, js + (size_t)(t0 + k) * JT * RW, TILE_BYTES, &bars[k]);
-        }
-    }
-
-    // i-particle from the same store (identical predicted values on both sides)
-    int gi = idx[p < n_act ? p : n_act - 1];
-    if ((unsigned)gi >= (unsigned)n) {
-        raise_status(sc, NB_ERR_ARG);
-        gi = 0;
-    }
-    const float4* ri = js + (size_t)gi * RW;
-    const float4 i0 = ri[0], i1 = ri[1], i2 = ri[2];
-    float4 i3 = make_float4(0.f, 0.f, 0.f, 0.f), i4 = i3;
-    if (ORDER >= 6) i3 = ri[3];
-    if (ORDER >= 8) i4 = ri[4];
-    const float ei2 = PAIR ? i1.w : eps2u;
-    // A warp whose every i-particle is softened at least as much as any
-    // particle pairs with the constant eps_i^2: the per-pair max and the
-    // R^2 = 0 guard drop out (same results, fewer instructions).
-    const bool dom = PAIR && __all_sync(0xffffffffu, ei2 >= eps2max && ei2 > 0.0f);
-
-    float hi[NC], lo[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        hi[c] = 0.f;
-        lo[c] = 0.f;
-    }
-
-    for (int k = 0; k < nt; ++k) {
-        const int st = k % NSTAGE;
-        const bool ok = mbar_wait_bounded(&bars[st], (k / NSTAGE) & 1);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                raise_status(sc, NB_ERR_TIMEOUT);
-                drain_after_timeout(bars, k, nt);
-            }
-            return;
-        }
-        const float4* b = buf + st * JT * RW;
-        float acc[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] = 0.f;
-        // the tile holding a lane's own particle takes the masked variant
-        const int self_rel = gi - (t0 + k) * JT;
-        const bool self_here = __any_sync(0xffffffffu, (unsigned)self_rel < (unsigned)JT);
-        if (!PAIR || dom) {
-            const float e2c = PAIR ? ei2 : eps2u;
-            if (self_here) tile_mixed<ORDER, RW, false, true>(b, i0, i1, i2, i3, i4, e2c, e2c, self_rel, acc);
-            else tile_mixed<ORDER, RW, false, false>(b, i0, i1, i2, i3, i4, e2c, e2c, -1, acc);
-        } else {
-            if (self_here) tile_mixed<ORDER, RW, true, true>(b, i0, i1, i2, i3, i4, ei2, eps2u, self_rel, acc);
-            else tile_mixed<ORDER, RW, true, false>(b, i0, i1, i2, i3, i4, ei2, eps2u, -1, acc);
-        }
-#pragma unroll
-        for (int c = 0; c < NC; ++c) ds_add(hi[c], lo[c], acc[c]);
-
-        __syncthreads();  // every thread is done with stage st
-        if (tid == 0 && k + NSTAGE < nt) {
-            mbar_expect_tx(&bars[st], TILE_BYTES);
-            bulk_g2s(buf + st * JT * RW, js + (size_t)(t0 + k + NSTAGE) * JT * RW, TILE_BYTES, &bars[st]);
-        }
-    }
-
-    if (p < n_act) {
-#pragma unroll
-        for (int c = 0; c < NC; ++c)
-            partial[((size_t)split * NC + c) * n_act + p] = (double)hi[c] + (double)lo[c];
-    }
-}
-
-template <int ORDER, int RW, bool PAIR, bool SELF>
-__device__ __forceinline__ void tile_fp64(const double2* __restrict__ b, const double2 i0, const double2 i1,
-                                          const double2 i2, const double2 i3, const double2 i4, const double2 i5,
-                                          const double2 i6, const double2 i7, const double ei2, const double eps2u,
-                                          const int self_rel, double (&acc)[ncomp(ORDER)])
-{
-    constexpr int NC = ncomp(ORDER);
-    for (int jj = 0; jj < JT; ++jj) {
-        const double2 w0 = b[jj * RW + 0], w1 = b[jj * RW + 1];
-        const double dx = w0.x - i0.x, dy = w0.y - i0.y, dz = w1.x - i1.x;
-        const double2 w3 = b[jj * RW + 3];
-        const double e2 = PAIR ? fmax(w3.y, ei2) : eps2u;
-        const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, e2)));
-        double rinv = guard_rinv_d<PAIR>(r2);
-        if (SELF) rinv = (jj == self_rel) ? 0.0 : rinv;
-        const double mr = w1.y * rinv;
-        if (ORDER == 0) {
-            acc[0] += mr;
-            continue;
-        }
-        const double rinv2 = rinv * rinv;
-        const double q = mr * rinv2;
-        const double2 w2 = b[jj * RW + 2];
-        const double dvx = w2.x - i2.x, dvy = w2.y - i2.y, dvz = w3.x - i3.x;
-        acc[0] = fma(q, dx, acc[0]);
-        acc[1] = fma(q, dy, acc[1]);
-        acc[2] = fma(q, dz, acc[2]);
-        const double al = fma(dx, dvx, fma(dy, dvy, dz * dvz)) * rinv2;
-        const double c1 = -3.0 * al;
-        acc[3] = fma(q, fma(c1, dx, dvx), acc[3]);
-        acc[4] = fma(q, fma(c1, dy, dvy), acc[4]);
-        acc[5] = fma(q, fma(c1, dz, dvz), acc[5]);
-        if (ORDER >= 6) {
-            const double2 w4 = b[jj * RW + 4], w5 = b[jj * RW + 5];
-            const double dax = w4.x - i4.x, day = w4.y - i4.y, daz = w5.x - i5.x;
-            const double w = fma(dvx, dvx, fma(dvy, dvy, fma(dvz, dvz, fma(dx, dax, fma(dy, day, dz * daz))))) * rinv2;
-            const double c2 = -6.0 * al;
-            const double c3 = fma(15.0 * al, al, -3.0 * w);
-            acc[6] = fma(q, fma(c3, dx, fma(c2, dvx, dax)), acc[6]);
-            acc[7] = fma(q, fma(c3, dy, fma(c2, dvy, day)), acc[7]);
-            acc[8] = fma(q, fma(c3, dz, fma(c2, dvz, daz)), acc[8]);
-            if (ORDER >= 8) {
-                const double2 w6 = b[jj * RW + 6], w7 = b[jj * RW + 7];
-                const double dkx = w6.x - i6.x, dky = w6.y - i6.y, dkz = w7.x - i7.x;
-                const double u =
-                    fma(3.0, fma(dvx, dax, fma(dvy, day, dvz * daz)), fma(dx, dkx, fma(dy, dky, dz * dkz))) * rinv2;
-                const double c4 = -9.0 * al;
-                const double c5 = fma(45.0 * al, al, -9.0 * w);
-                const double c6 = fma(al, fma(-105.0 * al, al, 45.0 * w), -3.0 * u);
-                acc[9] = fma(q, fma(c6, dx, fma(c5, dvx, fma(c4, dax, dkx))), acc[9]);
-                acc[10] = fma(q, fma(c6, dy, fma(c5, dvy, fma(c4, day, dky))), acc[10]);
-                acc[11] = fma(q, fma(c6, dz, fma(c5, dvz, fma(c4, daz, dkz))), acc[11]);
-            }
-        }
-        acc[NC - 2] += mr;
-        acc[NC - 1] = fma(mr, rinv, acc[NC - 1]);
-    }
-}
-
-// ------------------------------------------------------------------ FP64
-// FP64 record in 16-byte words (double2): w0 = (x.x, x.y), w1 = (x.z, m),
-// w2 = (v.x, v.y), w3 = (v.z, eps2), w4 = (a.x, a.y), w5 = (a.z, 0),
-// w6 = (jerk.x, jerk.y), w7 = (jerk.z, 0).
-template <int ORDER, int RW, bool PAIR>
-__global__ void __launch_bounds__(FORCE_NT) k_force_fp64(const double2* __restrict__ js, const int32_t* __restrict__ idx,
-                                                         int n_act, int n, int ntiles, int jsplit, double eps2u,
-                                                         double* __restrict__ partial, DevScalars* sc)
-{
-    constexpr int NC = ncomp(ORDER);
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    double2* buf = reinterpret_cast<double2*>(smem_raw);
-    __shared__ __align__(8) uint64_t bars[NSTAGE];
-
-    const int tid = threadIdx.x;
-    const int p = blockIdx.x * FORCE_NT + tid;
-    const int split = blockIdx.y;
-    const int t0 = (int)((long long)split * ntiles / jsplit);
-    const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
-    const int nt = t1 - t0;
-    constexpr uint32_t TILE_BYTES = JT * RW * 16;
-
-    if (tid == 0) {
-        for (int k = 0; k < NSTAGE; ++k) mbar_init(&bars[k], 1);
-        fence_barrier_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
-        for (int k = 0; k < NSTAGE && k < nt; ++k) {
-            mbar_expect_tx(&bars[k], TILE_BYTES);
-            bulk_g2s(buf + k * JT * RW, js + (size_t)(t0 + k) * JT * RW, TILE_BYTES, &bars[k]);
-        }
-    }
-
-    int gi = idx[p < n_act ? p : n_act - 1];
-    if ((unsigned)gi >= (unsigned)n) {
-        raise_status(sc, NB_ERR_ARG);
-        gi = 0;
-    }
-    const double2* ri = js + (size_t)gi * RW;
-    const double2 i0 = ri[0], i1 = ri[1], i2 = ri[2], i3 = ri[3];
-    double2 i4 = make_double2(0.0, 0.0), i5 = i4, i6 = i4, i7 = i4;
-    if (ORDER >= 6) {
-        i4 = ri[4];
-        i5 = ri[5];
-    }
-    if (ORDER >= 8) {
-        i6 = ri[6];
-        i7 = ri[7];
-    }
-    const double ei2 = PAIR ? i3.y : eps2u;
-
-    double sum[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) sum[c] = 0.0;
-
-    for (int k = 0; k < nt; ++k) {
-        const int st = k % NSTAGE;
-        const bool ok = mbar_wait_bounded(&bars[st], (k / NSTAGE) & 1);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                raise_status(sc, NB_ERR_TIMEOUT);
-                drain_after_timeout(bars, k, nt);
-            }
-            return;
-        }
-        const double2* b = buf + st * JT * RW;
-        double acc[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] = 0.0;
-        const int self_rel = gi - (t0 + k) * JT;
-        if (__any_sync(0xffffffffu, (unsigned)self_rel < (unsigned)JT))
-            tile_fp64<ORDER, RW, PAIR, true>(b, i0, i1, i2, i3, i4, i5, i6, i7, ei2, eps2u, self_rel, acc);
-        else
-            tile_fp64<ORDER, RW, PAIR, false>(b, i0, i1, i2, i3, i4, i5, i6, i7, ei2, eps2u, -1, acc);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) sum[c] += acc[c];
-
-        __syncthreads();
-        if (tid == 0 && k + NSTAGE < nt) {
-            mbar_expect_tx(&bars[st], TILE_BYTES);
-            bulk_g2s(buf + st * JT * RW, js + (size_t)(t0 + k + NSTAGE) * JT * RW, TILE_BYTES, &bars[st]);
-        }
-    }
-
-    if (p < n_act) {
-#pragma unroll
-        for (int c = 0; c < NC; ++c) partial[((size_t)split * NC + c) * n_act + p] = sum[c];
-    }
-}
-
-// -------------------------------------------------------------------- K3
-// F[c][p] = sum over splits in fixed order; the potential sum is negated.
-// PC = index of the potential component.
-template <int NC, int PC>
-__global__ void k_force_reduce(const double* __restrict__ partial, int jsplit, int n_act,
-                               const int32_t* __restrict__ idx, const double* __restrict__ m,
-                               const double* __restrict__ eps2, int n, double* __restrict__ F)
-{
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n_act) return;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        double s = 0.0;
-        for (int sp = 0; sp < jsplit; ++sp) s += partial[((size_t)sp * NC + c) * n_act + p];
-        if (c == PC) s = -s;
-        F[(size_t)c * n_act + p] = s;
-    }
-}
 
 // ---------------------------------------------------------------- launch
 template <typename KernelT>
