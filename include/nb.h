@@ -212,6 +212,38 @@ int nb_get_profile(nb_ctx* ctx, double* ms, int64_t* launches, int64_t* total_la
 /* Library version string.                                                  */
 const char* nb_version(void);
 
+/* ----------------------------------------------------- allocation-free call */
+
+/* The paper has no counterpart to this call: it serves callers that cannot
+ * allocate device memory when they need a force -- code running inside
+ * another framework's memory pool or arena that forbids allocations outside
+ * its own allocator, or a loop that must not allocate once it has started.
+ *
+ * Force of the n_act particles idx[] (device int32, in [0, n)) from all n
+ * particles given at one instant, with the same kernels as nb_force.  Every
+ * pointer is device memory owned by the caller: m, eps2 [n]; x, v [n][3];
+ * a [n][3] (order >= 6, else may be NULL); jerk [n][3] (order 8, else NULL);
+ * out [ncomp][n_act], component-major: acc xyz, jerk xyz, snap xyz (order
+ * >= 6), crackle xyz (order 8), potential, sum_j m_j/R_ij^2.  ncomp = 8, 11,
+ * 14 for orders 4, 6, 8.  Pair softening max(eps2_i, eps2_j).
+ *
+ * It allocates nothing: the packed records, the j-split partial sums and the
+ * status word live in one fixed array of NB_STATIC_SCRATCH_BYTES that every
+ * GPU loading this part of the library holds until the process exits; n is
+ * limited to NB_STATIC_MAX_N (larger n fails with NB_ERR_ARG).  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress), so
+ * make that first call before any stream capture.  All calls share the array
+ * and it keeps the last call's contents: calls that overlap on the GPU race,
+ * so order them (one stream, or synchronise).  Work runs on `stream` (a
+ * cudaStream_t, NULL = legacy default) and the call returns after it has
+ * finished, reporting device-side errors (an index out of range gives
+ * NB_ERR_ARG).  Messages: nb_last_error(NULL).                              */
+#define NB_STATIC_MAX_N 16384
+#define NB_STATIC_SCRATCH_BYTES (16384 * 128 + (1 << 20) * 8 + 256)
+int nb_force_static(int order, int precision, int64_t n, const double* m, const double* eps2, const double* x,
+                    const double* v, const double* a, const double* jerk, const int32_t* idx, int64_t n_act,
+                    double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -222,6 +222,8 @@ int do_predict(nb_ctx* c, double t)
 
 }  // namespace
 
+void nb::set_global_error(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+
 extern "C" {
 
 const char* nb_version(void) { return "libnb 0.1 (sm_103a)"; }

@@ -225,5 +225,7 @@ int force_occupancy(nb_ctx* c, int order);
 int sched_grid(const nb_ctx* c);
 int sched_chunks(int64_t n);
 int energy_grid(const nb_ctx* c);
+// Message returned by nb_last_error(NULL) (calls made without a context).
+void set_global_error(const char* msg);
 
 }  // namespace nb

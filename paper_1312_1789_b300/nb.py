@@ -62,7 +62,9 @@ SIGNATURES = {
     "nb_get_profile": (C.c_int, [_P, _D, _I64, _I64]),
     "nb_set_noise_floor": (C.c_int, [_P, C.c_int, _D]),
     "nb_get_noise_floor": (C.c_int, [_P, C.c_int, _D]),
+    "nb_force_static": (C.c_int, [C.c_int, C.c_int, C.c_int64, _P, _P, _P, _P, _P, _P, _P, C.c_int64, _P, _P]),
 }
+NB_STATIC_MAX_N = 16384
 NB_NPHASES = 6
 PHASES = ("sched", "predict", "force", "reduce", "correct", "other")
 
