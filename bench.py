@@ -300,6 +300,27 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
         out["mixed_vs_fp64"] = res["mixed"] / res["fp64"]
     except Exception as e:  # pragma: no cover
         out["fp64"] = {"error": repr(e)}
+    # ---- per-N_act curve of the mixed force on the 2^20 store (powers of two)
+    try:
+        ctx.set_state(S["x"], S["v"], S["d"], S["t"], S["dt"])
+        ctx.predict(float(S["t"][0]) + h)
+        rng = np.random.default_rng(11)
+        curve = {}
+        for k in range(0, 21, 2):
+            na = min(1 << k, n)
+            blk = np.sort(rng.choice(n, na, replace=False)).astype(np.int32)
+            ctx.force(blk)
+            ctx.set_profiling(True)
+            reps = 3 if na >= 65536 else 10
+            for _ in range(reps):
+                ctx.force(blk)
+            prof, _ = ctx.get_profile()
+            ctx.set_profiling(False)
+            fms = (prof["force"][0] + prof["reduce"][0]) / reps
+            curve[str(na)] = na * n / (fms * 1e-3)
+        out["nact_curve_interactions_per_s"] = curve
+    except Exception as e:  # pragma: no cover
+        out["nact_curve_interactions_per_s"] = {"error": repr(e)}
     # ---- energy error of both paths, Plummer N = 65536 to t = 1/16
     try:
         pw = ics.standard_workload(1)
@@ -313,10 +334,15 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
             c2.set_precision(nb.NB_FP64)
             e0 = sum(c2.energy())
             c2.set_precision(p)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
             nblk, ni = c2.step_until(t_end)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
             c2.set_precision(nb.NB_FP64)
             e1 = sum(c2.energy())
-            de[name] = {"dE_E": (e1 - e0) / abs(e0), "blocks": nblk, "interactions": ni}
+            de[name] = {"dE_E": (e1 - e0) / abs(e0), "blocks": nblk, "interactions": ni,
+                        "whole_run_interactions_per_s": ni / el, "seconds": el}
             c2.close()
         out["energy_budget"] = {"workload": pw.name + f" to t={t_end}", **de,
                                 "mixed_within_2x": abs(de["mixed"]["dE_E"]) <= 2 * abs(de["fp64"]["dE_E"])}
