@@ -61,76 +61,97 @@ static __device__ void drain_after_timeout(uint64_t* bars, int k, int nt)
     for (int kk = k; kk < nt && kk < k + NSTAGE; ++kk) mbar_wait_bounded(&bars[kk % NSTAGE], (kk / NSTAGE) & 1);
 }
 
-// One j tile for one i-particle: accumulates the pair terms into acc.  SELF:
-// the tile may contain the i-particle itself (at position self_rel), whose
-// pair is skipped by zeroing its inverse distance (every term carries it).
-template <int ORDER, int RW, bool PAIR, bool SELF>
-__device__ __forceinline__ void tile_mixed(const float4* __restrict__ b, const float4 i0, const float4 i1,
-                                           const float4 i2, const float4 i3, const float4 i4, const float ei2,
-                                           const float eps2u, const int self_rel, float (&acc)[ncomp(ORDER)])
+// i-particle data of the mixed kernel, as read from its own record.
+struct IMixed {
+    float4 i0, i1, i2, i3, i4;  // (x_hi, m) (x_lo, eps2) (v) (a) (jerk)
+};
+
+// One pair (i <- j): accumulates the pair terms into acc.  is_self masks the
+// i-particle's own record by zeroing the inverse distance (every term
+// carries it).
+template <int ORDER, bool PAIR, bool SELF>
+__device__ __forceinline__ void pair_mixed(const float4 w0, const float4 w1, const float4 w2, const float4 w3,
+                                           const float4 w4, const IMixed& I, const float ei2, const bool is_self,
+                                           float (&acc)[ncomp(ORDER)])
 {
     constexpr int NC = ncomp(ORDER);
-#pragma unroll 2
+    const float dx = (w0.x - I.i0.x) + (w1.x - I.i1.x);
+    const float dy = (w0.y - I.i0.y) + (w1.y - I.i1.y);
+    const float dz = (w0.z - I.i0.z) + (w1.z - I.i1.z);
+    // PAIR: eps_ij^2 = max(eps_i^2, eps_j^2); otherwise ei2 is the constant pair value
+    const float e2 = PAIR ? fmaxf(w1.w, ei2) : ei2;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, e2)));
+    float rinv = guard_rinv<PAIR>(r2);
+    if (SELF) rinv = is_self ? 0.0f : rinv;
+    const float mr = w0.w * rinv;
+    if (ORDER == 0) {
+        acc[0] += mr;
+        return;
+    }
+    const float rinv2 = rinv * rinv;
+    const float q = mr * rinv2;
+    const float r3 = -3.0f * rinv2;
+    const float dvx = w2.x - I.i2.x, dvy = w2.y - I.i2.y, dvz = w2.z - I.i2.z;
+    acc[0] = fmaf(q, dx, acc[0]);
+    acc[1] = fmaf(q, dy, acc[1]);
+    acc[2] = fmaf(q, dz, acc[2]);
+    // a3 = -3 alpha, the jerk coefficient
+    const float a3 = fmaf(dx, dvx, fmaf(dy, dvy, dz * dvz)) * r3;
+    acc[3] = fmaf(q, fmaf(a3, dx, dvx), acc[3]);
+    acc[4] = fmaf(q, fmaf(a3, dy, dvy), acc[4]);
+    acc[5] = fmaf(q, fmaf(a3, dz, dvz), acc[5]);
+    if (ORDER >= 6) {
+        const float dax = w3.x - I.i3.x, day = w3.y - I.i3.y, daz = w3.z - I.i3.z;
+        // ww3 = -3 w; snap coefficients c2 = -6 alpha, c3 = 15 alpha^2 - 3 w
+        const float ww3 = fmaf(dvx, dvx, fmaf(dvy, dvy, fmaf(dvz, dvz, fmaf(dx, dax, fmaf(dy, day, dz * daz))))) * r3;
+        const float c2 = a3 + a3;
+        const float c3 = fmaf((5.0f / 3.0f) * a3, a3, ww3);
+        acc[6] = fmaf(q, fmaf(c3, dx, fmaf(c2, dvx, dax)), acc[6]);
+        acc[7] = fmaf(q, fmaf(c3, dy, fmaf(c2, dvy, day)), acc[7]);
+        acc[8] = fmaf(q, fmaf(c3, dz, fmaf(c2, dvz, daz)), acc[8]);
+        if (ORDER >= 8) {
+            const float dkx = w4.x - I.i4.x, dky = w4.y - I.i4.y, dkz = w4.z - I.i4.z;
+            // u3 = -3 u; crackle: c4 = -9 alpha, c5 = 45 alpha^2 - 9 w,
+            // c6 = -105 alpha^3 + 45 alpha w - 3 u
+            const float u3 =
+                fmaf(3.0f, fmaf(dvx, dax, fmaf(dvy, day, dvz * daz)), fmaf(dx, dkx, fmaf(dy, dky, dz * dkz))) * r3;
+            const float c4 = 3.0f * a3;
+            const float c5 = fmaf(5.0f * a3, a3, 3.0f * ww3);
+            const float c6 = fmaf(a3, fmaf((35.0f / 9.0f) * a3, a3, 5.0f * ww3), u3);
+            acc[9] = fmaf(q, fmaf(c6, dx, fmaf(c5, dvx, fmaf(c4, dax, dkx))), acc[9]);
+            acc[10] = fmaf(q, fmaf(c6, dy, fmaf(c5, dvy, fmaf(c4, day, dky))), acc[10]);
+            acc[11] = fmaf(q, fmaf(c6, dz, fmaf(c5, dvz, fmaf(c4, daz, dkz))), acc[11]);
+        }
+    }
+    acc[NC - 2] += mr;
+    acc[NC - 1] = fmaf(mr, rinv, acc[NC - 1]);
+}
+
+// One j tile for IPT i-particles: every record is read once from shared
+// memory and applied to each i-particle of the thread.  SELF: the tile may
+// hold one of the thread's own particles (at self_rel[q]).
+template <int ORDER, int RW, bool PAIR, bool SELF, int IPT>
+__device__ __forceinline__ void tile_mixed(const float4* __restrict__ b, const IMixed (&I)[IPT], const float (&ei2)[IPT],
+                                           const int (&self_rel)[IPT], float (&acc)[IPT][ncomp(ORDER)])
+{
+#pragma unroll(IPT == 1 ? 2 : 1)
     for (int jj = 0; jj < JT; ++jj) {
         const float4 w0 = b[jj * RW + 0];
         const float4 w1 = b[jj * RW + 1];
-        const float dx = (w0.x - i0.x) + (w1.x - i1.x);
-        const float dy = (w0.y - i0.y) + (w1.y - i1.y);
-        const float dz = (w0.z - i0.z) + (w1.z - i1.z);
-        const float e2 = PAIR ? fmaxf(w1.w, ei2) : eps2u;
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, e2)));
-        float rinv = guard_rinv<PAIR>(r2);
-        if (SELF) rinv = (jj == self_rel) ? 0.0f : rinv;
-        const float mr = w0.w * rinv;
-        if (ORDER == 0) {
-            acc[0] += mr;
-            continue;
-        }
-        const float rinv2 = rinv * rinv;
-        const float q = mr * rinv2;
-        const float r3 = -3.0f * rinv2;
-        const float4 w2 = b[jj * RW + 2];
-        const float dvx = w2.x - i2.x, dvy = w2.y - i2.y, dvz = w2.z - i2.z;
-        acc[0] = fmaf(q, dx, acc[0]);
-        acc[1] = fmaf(q, dy, acc[1]);
-        acc[2] = fmaf(q, dz, acc[2]);
-        // a3 = -3 alpha, the jerk coefficient
-        const float a3 = fmaf(dx, dvx, fmaf(dy, dvy, dz * dvz)) * r3;
-        acc[3] = fmaf(q, fmaf(a3, dx, dvx), acc[3]);
-        acc[4] = fmaf(q, fmaf(a3, dy, dvy), acc[4]);
-        acc[5] = fmaf(q, fmaf(a3, dz, dvz), acc[5]);
-        if (ORDER >= 6) {
-            const float4 w3 = b[jj * RW + 3];
-            const float dax = w3.x - i3.x, day = w3.y - i3.y, daz = w3.z - i3.z;
-            // w3 = -3 w; snap coefficients c2 = -6 alpha, c3 = 15 alpha^2 - 3 w
-            const float ww3 = fmaf(dvx, dvx, fmaf(dvy, dvy, fmaf(dvz, dvz, fmaf(dx, dax, fmaf(dy, day, dz * daz))))) * r3;
-            const float c2 = a3 + a3;
-            const float c3 = fmaf((5.0f / 3.0f) * a3, a3, ww3);
-            acc[6] = fmaf(q, fmaf(c3, dx, fmaf(c2, dvx, dax)), acc[6]);
-            acc[7] = fmaf(q, fmaf(c3, dy, fmaf(c2, dvy, day)), acc[7]);
-            acc[8] = fmaf(q, fmaf(c3, dz, fmaf(c2, dvz, daz)), acc[8]);
-            if (ORDER >= 8) {
-                const float4 w4 = b[jj * RW + 4];
-                const float dkx = w4.x - i4.x, dky = w4.y - i4.y, dkz = w4.z - i4.z;
-                // u3 = -3 u; crackle: c4 = -9 alpha, c5 = 45 alpha^2 - 9 w,
-                // c6 = -105 alpha^3 + 45 alpha w - 3 u
-                const float u3 =
-                    fmaf(3.0f, fmaf(dvx, dax, fmaf(dvy, day, dvz * daz)), fmaf(dx, dkx, fmaf(dy, dky, dz * dkz))) * r3;
-                const float c4 = 3.0f * a3;
-                const float c5 = fmaf(5.0f * a3, a3, 3.0f * ww3);
-                const float c6 = fmaf(a3, fmaf((35.0f / 9.0f) * a3, a3, 5.0f * ww3), u3);
-                acc[9] = fmaf(q, fmaf(c6, dx, fmaf(c5, dvx, fmaf(c4, dax, dkx))), acc[9]);
-                acc[10] = fmaf(q, fmaf(c6, dy, fmaf(c5, dvy, fmaf(c4, day, dky))), acc[10]);
-                acc[11] = fmaf(q, fmaf(c6, dz, fmaf(c5, dvz, fmaf(c4, daz, dkz))), acc[11]);
-            }
-        }
-        acc[NC - 2] += mr;
-        acc[NC - 1] = fmaf(mr, rinv, acc[NC - 1]);
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 w2 = ORDER >= 4 ? b[jj * RW + 2] : z;
+        const float4 w3 = ORDER >= 6 ? b[jj * RW + 3] : z;
+        const float4 w4 = ORDER >= 8 ? b[jj * RW + 4] : z;
+#pragma unroll
+        for (int q = 0; q < IPT; ++q)
+            pair_mixed<ORDER, PAIR, SELF>(w0, w1, w2, w3, w4, I[q], ei2[q], SELF && jj == self_rel[q], acc[q]);
     }
 }
 
 // ----------------------------------------------------------------- mixed
-template <int ORDER, int RW, bool PAIR>
+// IPT i-particles per thread: CTA i-tile = FORCE_NT * IPT particles, thread t
+// holds particles t and t + FORCE_NT of the tile.
+template <int ORDER, int RW, bool PAIR, int IPT>
 __global__ void __launch_bounds__(FORCE_NT) k_force_mixed(const float4* __restrict__ js, const int32_t* __restrict__ idx,
                                                           int n_act, int n, int ntiles, int jsplit, float eps2u,
                                                           float eps2max, double* __restrict__ partial, DevScalars* sc)
@@ -141,7 +162,7 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_mixed(const float4* __restri
     __shared__ __align__(8) uint64_t bars[NSTAGE];
 
     const int tid = threadIdx.x;
-    const int p = blockIdx.x * FORCE_NT + tid;
+    const int pbase = blockIdx.x * (FORCE_NT * IPT) + tid;
     const int split = blockIdx.y;
     const int t0 = (int)((long long)split * ntiles / jsplit);
     const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
@@ -160,29 +181,41 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_mixed(const float4* __restri
         }
     }
 
-    // i-particle from the same store (identical predicted values on both sides)
-    int gi = idx[p < n_act ? p : n_act - 1];
-    if ((unsigned)gi >= (unsigned)n) {
-        raise_status(sc, NB_ERR_ARG);
-        gi = 0;
+    // i-particles from the same store (identical predicted values on both sides)
+    IMixed I[IPT];
+    float ei2[IPT];
+    int gi[IPT];
+    bool dom_lane = true;
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+        const int p = pbase + q * FORCE_NT;
+        gi[q] = idx[p < n_act ? p : n_act - 1];
+        if ((unsigned)gi[q] >= (unsigned)n) {
+            raise_status(sc, NB_ERR_ARG);
+            gi[q] = 0;
+        }
+        const float4* ri = js + (size_t)gi[q] * RW;
+        I[q].i0 = ri[0];
+        I[q].i1 = ri[1];
+        I[q].i2 = ri[2];
+        I[q].i3 = ORDER >= 6 ? ri[3] : make_float4(0.f, 0.f, 0.f, 0.f);
+        I[q].i4 = ORDER >= 8 ? ri[4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        ei2[q] = PAIR ? I[q].i1.w : eps2u;
+        dom_lane = dom_lane && ei2[q] >= eps2max && ei2[q] > 0.0f;
     }
-    const float4* ri = js + (size_t)gi * RW;
-    const float4 i0 = ri[0], i1 = ri[1], i2 = ri[2];
-    float4 i3 = make_float4(0.f, 0.f, 0.f, 0.f), i4 = i3;
-    if (ORDER >= 6) i3 = ri[3];
-    if (ORDER >= 8) i4 = ri[4];
-    const float ei2 = PAIR ? i1.w : eps2u;
     // A warp whose every i-particle is softened at least as much as any
     // particle pairs with the constant eps_i^2: the per-pair max and the
     // R^2 = 0 guard drop out (same results, fewer instructions).
-    const bool dom = PAIR && __all_sync(0xffffffffu, ei2 >= eps2max && ei2 > 0.0f);
+    const bool dom = PAIR && __all_sync(0xffffffffu, dom_lane);
 
-    float hi[NC], lo[NC];
+    float hi[IPT][NC], lo[IPT][NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        hi[c] = 0.f;
-        lo[c] = 0.f;
-    }
+    for (int q = 0; q < IPT; ++q)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            hi[q][c] = 0.f;
+            lo[q][c] = 0.f;
+        }
 
     for (int k = 0; k < nt; ++k) {
         const int st = k % NSTAGE;
@@ -195,22 +228,33 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_mixed(const float4* __restri
             return;
         }
         const float4* b = buf + st * JT * RW;
-        float acc[NC];
+        float acc[IPT][NC];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] = 0.f;
-        // the tile holding a lane's own particle takes the masked variant
-        const int self_rel = gi - (t0 + k) * JT;
-        const bool self_here = __any_sync(0xffffffffu, (unsigned)self_rel < (unsigned)JT);
+        for (int q = 0; q < IPT; ++q)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[q][c] = 0.f;
+        // the tile holding one of a lane's own particles takes the masked variant
+        int self_rel[IPT];
+        bool mine = false;
+#pragma unroll
+        for (int q = 0; q < IPT; ++q) {
+            self_rel[q] = gi[q] - (t0 + k) * JT;
+            mine = mine || (unsigned)self_rel[q] < (unsigned)JT;
+        }
+        const bool self_here = __any_sync(0xffffffffu, mine);
+        // ei2 holds eps_i^2 (per-particle softening) or the uniform eps^2; on the
+        // uniform and dominant paths it is the pair value itself
         if (!PAIR || dom) {
-            const float e2c = PAIR ? ei2 : eps2u;
-            if (self_here) tile_mixed<ORDER, RW, false, true>(b, i0, i1, i2, i3, i4, e2c, e2c, self_rel, acc);
-            else tile_mixed<ORDER, RW, false, false>(b, i0, i1, i2, i3, i4, e2c, e2c, -1, acc);
+            if (self_here) tile_mixed<ORDER, RW, false, true, IPT>(b, I, ei2, self_rel, acc);
+            else tile_mixed<ORDER, RW, false, false, IPT>(b, I, ei2, self_rel, acc);
         } else {
-            if (self_here) tile_mixed<ORDER, RW, true, true>(b, i0, i1, i2, i3, i4, ei2, eps2u, self_rel, acc);
-            else tile_mixed<ORDER, RW, true, false>(b, i0, i1, i2, i3, i4, ei2, eps2u, -1, acc);
+            if (self_here) tile_mixed<ORDER, RW, true, true, IPT>(b, I, ei2, self_rel, acc);
+            else tile_mixed<ORDER, RW, true, false, IPT>(b, I, ei2, self_rel, acc);
         }
 #pragma unroll
-        for (int c = 0; c < NC; ++c) ds_add(hi[c], lo[c], acc[c]);
+        for (int q = 0; q < IPT; ++q)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) ds_add(hi[q][c], lo[q][c], acc[q][c]);
 
         __syncthreads();  // every thread is done with stage st
         if (tid == 0 && k + NSTAGE < nt) {
@@ -219,10 +263,14 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_mixed(const float4* __restri
         }
     }
 
-    if (p < n_act) {
 #pragma unroll
-        for (int c = 0; c < NC; ++c)
-            partial[((size_t)split * NC + c) * n_act + p] = (double)hi[c] + (double)lo[c];
+    for (int q = 0; q < IPT; ++q) {
+        const int p = pbase + q * FORCE_NT;
+        if (p < n_act) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                partial[((size_t)split * NC + c) * n_act + p] = (double)hi[q][c] + (double)lo[q][c];
+        }
     }
 }
 

@@ -13,10 +13,10 @@ static int occupancy_of(KernelT kern, size_t smem)
     return occ < 1 ? 1 : occ;
 }
 
-template <int ORDER, int RW, bool PAIR>
-static cudaError_t run_mixed(nb_ctx* c, const int32_t* idx, int n_act, int jsplit, int itiles, int* occ_out)
+template <int ORDER, int RW, bool PAIR, int IPT>
+static cudaError_t run_mixed_ipt(nb_ctx* c, const int32_t* idx, int n_act, int jsplit, int itiles, int* occ_out)
 {
-    auto kern = k_force_mixed<ORDER, RW, PAIR>;
+    auto kern = k_force_mixed<ORDER, RW, PAIR, IPT>;
     const size_t smem = (size_t)NSTAGE * JT * RW * 16;
     static bool configured = false;
     static int occ = 1;
@@ -37,8 +37,17 @@ static cudaError_t run_mixed(nb_ctx* c, const int32_t* idx, int n_act, int jspli
     return cudaGetLastError();
 }
 
+// Mixed path: one or two i-particles per thread.
 template <int ORDER, int RW, bool PAIR>
-static cudaError_t run_fp64(nb_ctx* c, const int32_t* idx, int n_act, int jsplit, int itiles, int* occ_out)
+static cudaError_t run_mixed(nb_ctx* c, const int32_t* idx, int n_act, int jsplit, int itiles, int* occ_out, int ipt)
+{
+    if (ipt == 2) return run_mixed_ipt<ORDER, RW, PAIR, 2>(c, idx, n_act, jsplit, itiles, occ_out);
+    return run_mixed_ipt<ORDER, RW, PAIR, 1>(c, idx, n_act, jsplit, itiles, occ_out);
+}
+
+// FP64 path: bound by the FP64 pipe, one i-particle per thread.
+template <int ORDER, int RW, bool PAIR>
+static cudaError_t run_fp64(nb_ctx* c, const int32_t* idx, int n_act, int jsplit, int itiles, int* occ_out, int)
 {
     auto kern = k_force_fp64<ORDER, RW, PAIR>;
     const size_t smem = (size_t)NSTAGE * JT * RW * 16;
@@ -63,13 +72,13 @@ static cudaError_t run_fp64(nb_ctx* c, const int32_t* idx, int n_act, int jsplit
 // Dispatch on (computed order, stored record layout, softening mode, precision).
 // occ_out != nullptr only queries the kernel's occupancy.
 static cudaError_t dispatch(nb_ctx* c, int order, const int32_t* idx, int n_act, int jsplit, int itiles,
-                            int* occ_out)
+                            int* occ_out, int ipt)
 {
     const bool pair = c->pair_eps || !(c->eps > 0.0);
     const int so = c->order;  // stored layout
 #define NB_CASE(PRECFN, RW, O)                                                                  \
-    if (order == O) return pair ? PRECFN<O, RW, true>(c, idx, n_act, jsplit, itiles, occ_out) \
-                                : PRECFN<O, RW, false>(c, idx, n_act, jsplit, itiles, occ_out);
+    if (order == O) return pair ? PRECFN<O, RW, true>(c, idx, n_act, jsplit, itiles, occ_out, ipt) \
+                                : PRECFN<O, RW, false>(c, idx, n_act, jsplit, itiles, occ_out, ipt);
 #define NB_DISPATCH(PRECFN, RWFN)       \
     if (so == 4) {                      \
         NB_CASE(PRECFN, RWFN(4), 0)     \
@@ -95,16 +104,22 @@ static cudaError_t dispatch(nb_ctx* c, int order, const int32_t* idx, int n_act,
     return cudaErrorInvalidValue;
 }
 
-int force_occupancy(nb_ctx* c, int order)
+int force_occupancy(nb_ctx* c, int order, int ipt)
 {
     int occ = 1;
-    if (dispatch(c, order, nullptr, 0, 1, 1, &occ) != cudaSuccess) return 1;
+    if (dispatch(c, order, nullptr, 0, 1, 1, &occ, ipt) != cudaSuccess) return 1;
     return occ;
 }
 
-cudaError_t launch_force(nb_ctx* c, int order, const int32_t* idx, int64_t n_act, int jsplit, int itiles)
+int force_ipt(const nb_ctx* c, int64_t n_act)
 {
-    return dispatch(c, order, idx, (int)n_act, jsplit, itiles, nullptr);
+    const int prec = c->pred_prec >= 0 ? c->pred_prec : c->prec;
+    return (prec == NB_MIXED && n_act >= IPT2_MIN_NACT) ? 2 : 1;
+}
+
+cudaError_t launch_force(nb_ctx* c, int order, const int32_t* idx, int64_t n_act, int jsplit, int itiles, int ipt)
+{
+    return dispatch(c, order, idx, (int)n_act, jsplit, itiles, nullptr, ipt);
 }
 
 cudaError_t launch_force_reduce(nb_ctx* c, int order, const int32_t* idx, int64_t n_act, int jsplit)

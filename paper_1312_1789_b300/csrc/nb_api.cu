@@ -166,9 +166,11 @@ int sync_scalars(nb_ctx* c)
 // Launch shape of the force: FORCE_NT i-particles per CTA; the j range is
 // split so that small active sets still fill every SM (j-split), capped by the
 // partial-sum buffer.
-void choose_shape(nb_ctx* c, int order, int64_t n_act, int* itiles, int* jsplit)
+void choose_shape(nb_ctx* c, int order, int64_t n_act, int* itiles, int* jsplit, int* ipt_out)
 {
-    const int it = (int)((n_act + FORCE_NT - 1) / FORCE_NT);
+    const int ipt = force_ipt(c, n_act);
+    *ipt_out = ipt;
+    const int it = (int)((n_act + FORCE_NT * ipt - 1) / (FORCE_NT * ipt));
     const int ntiles = (int)(c->np / JT);
     int js = 1;
     auto fits = [&](int s) { return (size_t)s * ncomp(order) * (size_t)n_act <= c->partial_cap; };
@@ -178,7 +180,7 @@ void choose_shape(nb_ctx* c, int order, int64_t n_act, int* itiles, int* jsplit)
         // Equal-work CTAs run in waves of `slots`; the makespan of it*js CTAs,
         // each 1/js of the j range, is ceil(it*js/slots)/js.  Take the split
         // with the smallest makespan (ties within 1% to the smaller split).
-        const int slots = c->sm_count * force_occupancy(c, order);
+        const int slots = c->sm_count * force_occupancy(c, order, ipt);
         const int js_max = std::min(ntiles, std::max(1, 4 * slots / std::max(it, 1) + 4));
         double best = 1e300;
         for (int s = 1; s <= js_max && fits(s); ++s) {
@@ -199,13 +201,14 @@ void choose_shape(nb_ctx* c, int order, int64_t n_act, int* itiles, int* jsplit)
 
 int run_force(nb_ctx* c, int order, const int32_t* idx_dev, int64_t n_act)
 {
-    int it, js;
-    choose_shape(c, order, n_act, &it, &js);
-    NB_CUDA(c, timed(c, NB_PHASE_FORCE, 1, [&] { return launch_force(c, order, idx_dev, n_act, js, it); }));
+    int it, js, ipt;
+    choose_shape(c, order, n_act, &it, &js, &ipt);
+    NB_CUDA(c, timed(c, NB_PHASE_FORCE, 1, [&] { return launch_force(c, order, idx_dev, n_act, js, it, ipt); }));
     NB_CUDA(c, timed(c, NB_PHASE_REDUCE, 1, [&] { return launch_force_reduce(c, order, idx_dev, n_act, js); }));
     c->last_itiles = it;
     c->last_jsplit = js;
     c->last_threads = FORCE_NT;
+    c->last_ipt = ipt;
     c->F_order = order;
     c->F_n = n_act;
     return NB_OK;

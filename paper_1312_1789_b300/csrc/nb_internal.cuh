@@ -22,8 +22,10 @@ namespace nb {
 
 // j tile of the force kernel: records staged per bulk copy.
 constexpr int JT = 128;
-// threads (= i-particles) per force CTA.
+// threads per force CTA; each holds 1 or 2 i-particles (IPT).
 constexpr int FORCE_NT = 128;
+// the mixed force uses two i-particles per thread from this active-set size on
+constexpr int IPT2_MIN_NACT = 1024;
 // stages of the force kernel's shared-memory ring.
 constexpr int NSTAGE = 3;
 // spin limit of a bounded mbarrier wait, in SM clock cycles (~2 s at 2 GHz).
@@ -190,7 +192,7 @@ struct nb_ctx {
     int64_t sched_n = 0;        // result of the last scheduler pass
     double sched_t = 0.0;
     int have_sched = 0;
-    int last_itiles = 0, last_jsplit = 0, last_threads = 0;
+    int last_itiles = 0, last_jsplit = 0, last_threads = 0, last_ipt = 1;
     // profiling: event pairs around launches, folded into totals at syncs
     struct ProfRec {
         cudaEvent_t a, b;
@@ -214,14 +216,15 @@ namespace nb {
 // Launchers (k_*.cu); each returns cudaGetLastError() of its launches.
 cudaError_t launch_sched(nb_ctx* c);
 cudaError_t launch_predict(nb_ctx* c, double t);
-cudaError_t launch_force(nb_ctx* c, int order, const int32_t* idx, int64_t n_act, int jsplit, int itiles);
+cudaError_t launch_force(nb_ctx* c, int order, const int32_t* idx, int64_t n_act, int jsplit, int itiles, int ipt);
 cudaError_t launch_force_reduce(nb_ctx* c, int order, const int32_t* idx, int64_t n_act, int jsplit);
 cudaError_t launch_correct(nb_ctx* c);
 cudaError_t launch_startup_store(nb_ctx* c, int order);
 cudaError_t launch_startup_dt(nb_ctx* c);
 cudaError_t launch_energy_sums(nb_ctx* c, int with_pot);
 cudaError_t launch_set_dt(nb_ctx* c, double dt);
-int force_occupancy(nb_ctx* c, int order);
+int force_occupancy(nb_ctx* c, int order, int ipt);
+int force_ipt(const nb_ctx* c, int64_t n_act);
 int sched_grid(const nb_ctx* c);
 int sched_chunks(int64_t n);
 int energy_grid(const nb_ctx* c);

@@ -168,7 +168,7 @@ int run_static(const double* m, const double* eps2, const double* x, const doubl
     const int it = (n_act + FORCE_NT - 1) / FORCE_NT;
     int js;
     if (MIXED) {
-        auto kern = k_force_mixed<ORDER, RW, true>;
+        auto kern = k_force_mixed<ORDER, RW, true, 1>;
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return NB_ERR_CUDA;
         js = choose_split(it, np / JT, NC, n_act, slots_of(kern, smem, sm_count));

@@ -81,6 +81,27 @@ def test_force_parity(prec, order, kind):
     ctx.close()
 
 
+@pytest.mark.parametrize("order", [4, 6, 8])
+@pytest.mark.parametrize("kind", ["plummer", "holes"])
+def test_force_parity_two_particles_per_thread(order, kind):
+    # Active sets of >= 1024 run the mixed kernel with two i-particles per
+    # thread; ragged last i-tile, several split counts.
+    n = 2 * 1024 + 77
+    m, x, v, eps2 = _system(n, 50 + order, kind)
+    ctx = _advanced(m, x, v, eps2, order, nb.NB_MIXED, 1.0 / 256, pair=(kind == "holes"))
+    tb, _ = ctx.next_block()
+    ctx.predict(tb)
+    rng = np.random.default_rng(order + 7)
+    for idx in (np.arange(n, dtype=np.int32), np.sort(rng.choice(n, 1500, replace=False)).astype(np.int32)):
+        O = oracle_force_on_predicted(ctx, m, eps2, idx, order)
+        for js in (0, 1, 5):
+            ctx.set_jsplit(js)
+            ctx.force(idx)
+            G = ctx.get_force(len(idx))
+            assert_force_close(G, O, order, nb.NB_MIXED, f"order {order} {kind} n_act {len(idx)} jsplit {js}")
+    ctx.close()
+
+
 def test_force_jsplit_changes_only_rounding():
     # FP64 results of different split counts agree to rounding; a given
     # launch shape is bitwise reproducible.
