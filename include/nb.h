@@ -163,9 +163,10 @@ int nb_get_force(nb_ctx* ctx, double* acc, double* jerk, double* snap, double* c
  * velocity/acc/jerk): xp, vp, ap, jp [n][3] (NULL to skip).  Synchronises. */
 int nb_get_predicted(nb_ctx* ctx, double* xp, double* vp, double* ap, double* jp);
 
-/* Kernel launch shape of the last nb_force: CTAs along i, j-splits, threads
- * per CTA (any output may be NULL).                                       */
-int nb_get_launch(nb_ctx* ctx, int* i_tiles, int* j_splits, int* threads);
+/* Kernel launch shape of the last nb_force: CTAs along i, j-splits and
+ * i-particles per CTA (128 threads holding one or two particles each); any
+ * output may be NULL.                                                       */
+int nb_get_launch(nb_ctx* ctx, int* i_tiles, int* j_splits, int* i_per_cta);
 
 /* Force the j-split count of later nb_force calls (0 = automatic).         */
 int nb_set_jsplit(nb_ctx* ctx, int j_splits);

@@ -207,7 +207,7 @@ int run_force(nb_ctx* c, int order, const int32_t* idx_dev, int64_t n_act)
     NB_CUDA(c, timed(c, NB_PHASE_REDUCE, 1, [&] { return launch_force_reduce(c, order, idx_dev, n_act, js); }));
     c->last_itiles = it;
     c->last_jsplit = js;
-    c->last_threads = FORCE_NT;
+    c->last_threads = FORCE_NT * ipt;
     c->last_ipt = ipt;
     c->F_order = order;
     c->F_n = n_act;

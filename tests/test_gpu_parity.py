@@ -298,8 +298,8 @@ def test_nucleus_2pow20_sampled_parity():
     ctx = make_ctx(wl.m, wl.x, wl.v, wl.eps2, 6, nb.NB_MIXED, pair=True)
     ctx.predict(2.0 ** -12)
     ctx.force(np.arange(n, dtype=np.int32))
-    it, js, nt = ctx.get_launch()
-    assert it * nt >= n and js >= 1
+    it, js, per_cta = ctx.get_launch()
+    assert it * per_cta >= n > (it - 1) * per_cta and js >= 1
     G = ctx.get_force(n)
     rng = np.random.default_rng(0)
     sample = np.concatenate([rng.choice(n - 2, 22, replace=False), [n - 2, n - 1]]).astype(np.int32)
