@@ -149,12 +149,15 @@ __device__ __forceinline__ void tile_mixed(const float4* __restrict__ b, const I
 }
 
 // ----------------------------------------------------------------- mixed
-// IPT i-particles per thread: CTA i-tile = FORCE_NT * IPT particles, thread t
-// holds particles t and t + FORCE_NT of the tile.
+// One CTA's work: the i-particles idx[p] for p = pbase + q * FORCE_NT < plim
+// (q < IPT; thread t holds positions t and t + FORCE_NT of the i-tile) against
+// the j tiles [t0, t0 + nt), partial sums to row `split`, column p of a
+// [split][component][ncol] array.
 template <int ORDER, int RW, bool PAIR, int IPT>
-__global__ void __launch_bounds__(FORCE_NT) k_force_mixed(const float4* __restrict__ js, const int32_t* __restrict__ idx,
-                                                          int n_act, int n, int ntiles, int jsplit, float eps2u,
-                                                          float eps2max, double* __restrict__ partial, DevScalars* sc)
+__device__ __forceinline__ void force_block_mixed(const float4* __restrict__ js, const int32_t* __restrict__ idx,
+                                                  const int pbase0, const int plim, const int n, const int t0,
+                                                  const int nt, const int split, const int ncol, const float eps2u,
+                                                  const float eps2max, double* __restrict__ partial, DevScalars* sc)
 {
     constexpr int NC = ncomp(ORDER);
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -162,11 +165,7 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_mixed(const float4* __restri
     __shared__ __align__(8) uint64_t bars[NSTAGE];
 
     const int tid = threadIdx.x;
-    const int pbase = blockIdx.x * (FORCE_NT * IPT) + tid;
-    const int split = blockIdx.y;
-    const int t0 = (int)((long long)split * ntiles / jsplit);
-    const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
-    const int nt = t1 - t0;
+    const int pbase = pbase0 + tid;
     constexpr uint32_t TILE_BYTES = JT * RW * 16;
 
     if (tid == 0) {
@@ -189,7 +188,7 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_mixed(const float4* __restri
 #pragma unroll
     for (int q = 0; q < IPT; ++q) {
         const int p = pbase + q * FORCE_NT;
-        gi[q] = idx[p < n_act ? p : n_act - 1];
+        gi[q] = idx[p < plim ? p : plim - 1];
         if ((unsigned)gi[q] >= (unsigned)n) {
             raise_status(sc, NB_ERR_ARG);
             gi[q] = 0;
@@ -266,12 +265,26 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_mixed(const float4* __restri
 #pragma unroll
     for (int q = 0; q < IPT; ++q) {
         const int p = pbase + q * FORCE_NT;
-        if (p < n_act) {
+        if (p < plim) {
 #pragma unroll
             for (int c = 0; c < NC; ++c)
-                partial[((size_t)split * NC + c) * n_act + p] = (double)hi[q][c] + (double)lo[q][c];
+                partial[((size_t)split * NC + c) * ncol + p] = (double)hi[q][c] + (double)lo[q][c];
         }
     }
+}
+
+// One system: blockIdx.x = i-tile of FORCE_NT * IPT active particles,
+// blockIdx.y = j-split of the whole store.
+template <int ORDER, int RW, bool PAIR, int IPT>
+__global__ void __launch_bounds__(FORCE_NT) k_force_mixed(const float4* __restrict__ js, const int32_t* __restrict__ idx,
+                                                          int n_act, int n, int ntiles, int jsplit, float eps2u,
+                                                          float eps2max, double* __restrict__ partial, DevScalars* sc)
+{
+    const int split = blockIdx.y;
+    const int t0 = (int)((long long)split * ntiles / jsplit);
+    const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
+    force_block_mixed<ORDER, RW, PAIR, IPT>(js, idx, blockIdx.x * (FORCE_NT * IPT), n_act, n, t0, t1 - t0, split, n_act,
+                                            eps2u, eps2max, partial, sc);
 }
 
 template <int ORDER, int RW, bool PAIR, bool SELF>
@@ -337,10 +350,12 @@ __device__ __forceinline__ void tile_fp64(const double2* __restrict__ b, const d
 // FP64 record in 16-byte words (double2): w0 = (x.x, x.y), w1 = (x.z, m),
 // w2 = (v.x, v.y), w3 = (v.z, eps2), w4 = (a.x, a.y), w5 = (a.z, 0),
 // w6 = (jerk.x, jerk.y), w7 = (jerk.z, 0).
+// One CTA's work (one i-particle per thread), as force_block_mixed.
 template <int ORDER, int RW, bool PAIR>
-__global__ void __launch_bounds__(FORCE_NT) k_force_fp64(const double2* __restrict__ js, const int32_t* __restrict__ idx,
-                                                         int n_act, int n, int ntiles, int jsplit, double eps2u,
-                                                         double* __restrict__ partial, DevScalars* sc)
+__device__ __forceinline__ void force_block_fp64(const double2* __restrict__ js, const int32_t* __restrict__ idx,
+                                                 const int pbase0, const int plim, const int n, const int t0,
+                                                 const int nt, const int split, const int ncol, const double eps2u,
+                                                 double* __restrict__ partial, DevScalars* sc)
 {
     constexpr int NC = ncomp(ORDER);
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -348,11 +363,7 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_fp64(const double2* __restri
     __shared__ __align__(8) uint64_t bars[NSTAGE];
 
     const int tid = threadIdx.x;
-    const int p = blockIdx.x * FORCE_NT + tid;
-    const int split = blockIdx.y;
-    const int t0 = (int)((long long)split * ntiles / jsplit);
-    const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
-    const int nt = t1 - t0;
+    const int p = pbase0 + tid;
     constexpr uint32_t TILE_BYTES = JT * RW * 16;
 
     if (tid == 0) {
@@ -367,7 +378,7 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_fp64(const double2* __restri
         }
     }
 
-    int gi = idx[p < n_act ? p : n_act - 1];
+    int gi = idx[p < plim ? p : plim - 1];
     if ((unsigned)gi >= (unsigned)n) {
         raise_status(sc, NB_ERR_ARG);
         gi = 0;
@@ -418,10 +429,22 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_fp64(const double2* __restri
         }
     }
 
-    if (p < n_act) {
+    if (p < plim) {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) partial[((size_t)split * NC + c) * n_act + p] = sum[c];
+        for (int c = 0; c < NC; ++c) partial[((size_t)split * NC + c) * ncol + p] = sum[c];
     }
+}
+
+template <int ORDER, int RW, bool PAIR>
+__global__ void __launch_bounds__(FORCE_NT) k_force_fp64(const double2* __restrict__ js, const int32_t* __restrict__ idx,
+                                                         int n_act, int n, int ntiles, int jsplit, double eps2u,
+                                                         double* __restrict__ partial, DevScalars* sc)
+{
+    const int split = blockIdx.y;
+    const int t0 = (int)((long long)split * ntiles / jsplit);
+    const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
+    force_block_fp64<ORDER, RW, PAIR>(js, idx, blockIdx.x * FORCE_NT, n_act, n, t0, t1 - t0, split, n_act, eps2u,
+                                      partial, sc);
 }
 
 // -------------------------------------------------------------------- K3

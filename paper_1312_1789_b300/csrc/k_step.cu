@@ -174,14 +174,26 @@ template <int ORDER, bool MIXED>
 __global__ void __launch_bounds__(256) k_predict(const double* __restrict__ m, const double* __restrict__ eps2,
                                                  const double* __restrict__ x, const double* __restrict__ v,
                                                  const double* __restrict__ d, const double* __restrict__ t,
-                                                 int64_t n, int64_t np, double tp, void* __restrict__ jstore)
+                                                 int64_t n, int64_t np, double tp, void* __restrict__ jstore,
+                                                 const double* __restrict__ tpc, const int32_t* __restrict__ cid)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
     constexpr int RW = MIXED ? mixed_rw(ORDER) : fp64_rw(ORDER);
     double xp[3] = {0, 0, 0}, vp[3] = {0, 0, 0}, ap[3] = {0, 0, 0}, jp[3] = {0, 0, 0};
     double mi = 0.0, ei = 1.0;
-    if (i < n) {
+    bool real = i < n;
+    if (real && tpc) {
+        // ensemble: each particle to its own cluster's block time; cid < 0 marks
+        // padding between clusters, an infinite time an idle cluster
+        const int k = cid[i];
+        if (k < 0) real = false;
+        else {
+            tp = tpc[k];
+            if (!(tp < INFINITY)) return;
+        }
+    }
+    if (real) {
         mi = m[i];
         ei = eps2[i];
         const double h = tp - t[i];
@@ -237,7 +249,7 @@ __global__ void __launch_bounds__(256) k_predict(const double* __restrict__ m, c
     }
 }
 
-cudaError_t launch_predict(nb_ctx* c, double t)
+cudaError_t launch_predict(nb_ctx* c, double t, const double* tpc, const int32_t* cid)
 {
     const int nt = 256;
     const int nb = (int)((c->np + nt - 1) / nt);
@@ -245,10 +257,10 @@ cudaError_t launch_predict(nb_ctx* c, double t)
 #define NB_PRED(O)                                                                                       \
     if (mixed)                                                                                           \
         k_predict<O, true><<<nb, nt, 0, c->stream>>>(c->m, c->eps2, c->x, c->v, c->d, c->t, c->n, c->np, \
-                                                     t, c->jstore);                                      \
+                                                     t, c->jstore, tpc, cid);                            \
     else                                                                                                 \
         k_predict<O, false><<<nb, nt, 0, c->stream>>>(c->m, c->eps2, c->x, c->v, c->d, c->t, c->n,      \
-                                                      c->np, t, c->jstore);
+                                                      c->np, t, c->jstore, tpc, cid);
     if (c->order == 4) {
         NB_PRED(4)
     } else if (c->order == 6) {
@@ -357,7 +369,8 @@ __global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fid
                                                  double* __restrict__ x, double* __restrict__ v,
                                                  double* __restrict__ d, double* __restrict__ t,
                                                  double* __restrict__ dtv, double* __restrict__ pot, double eta,
-                                                 double dt_max, double dt_min, NoiseEps ne, DevScalars* sc)
+                                                 double dt_max, double dt_min, NoiseEps ne, DevScalars* sc,
+                                                 const double* __restrict__ tfc, const int32_t* __restrict__ cid)
 {
     constexpr int MM = ORDER / 2;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -367,6 +380,7 @@ __global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fid
         raise_status(sc, NB_ERR_ARG);
         return;
     }
+    if (tfc) tf = tfc[cid[i]];  // ensemble: the particle's cluster block time
     const double h = tf - t[i];
     if (!(h > 0.0)) {
         raise_status(sc, NB_ERR_ARG);
@@ -465,14 +479,14 @@ __global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fid
     pot[i] = potn;
 }
 
-cudaError_t launch_correct(nb_ctx* c)
+cudaError_t launch_correct(nb_ctx* c, const double* tfc, const int32_t* cid)
 {
     const int nt = 128;
     const int nb = (int)((c->f_n + nt - 1) / nt);
 #define NB_CORR(O)                                                                                          \
     k_correct<O><<<nb, nt, 0, c->stream>>>(c->f_idx, (int)c->f_n, c->f_t, c->F, c->n, c->np, c->x, c->v,   \
                                            c->d, c->t, c->dt, c->pot, c->eta, c->dt_max, c->dt_min,        \
-                                           c->noise[c->pred_prec == NB_MIXED ? 1 : 0], c->sc);
+                                           c->noise[c->pred_prec == NB_MIXED ? 1 : 0], c->sc, tfc, cid);
     if (c->order == 4) {
         NB_CORR(4)
     } else if (c->order == 6) {

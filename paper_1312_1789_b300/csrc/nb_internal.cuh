@@ -215,10 +215,11 @@ namespace nb {
 
 // Launchers (k_*.cu); each returns cudaGetLastError() of its launches.
 cudaError_t launch_sched(nb_ctx* c);
-cudaError_t launch_predict(nb_ctx* c, double t);
+// tpc, cid (ensembles): per-cluster prediction time and cluster of each slot; NULL for one system
+cudaError_t launch_predict(nb_ctx* c, double t, const double* tpc = nullptr, const int32_t* cid = nullptr);
 cudaError_t launch_force(nb_ctx* c, int order, const int32_t* idx, int64_t n_act, int jsplit, int itiles, int ipt);
 cudaError_t launch_force_reduce(nb_ctx* c, int order, const int32_t* idx, int64_t n_act, int jsplit);
-cudaError_t launch_correct(nb_ctx* c);
+cudaError_t launch_correct(nb_ctx* c, const double* tfc = nullptr, const int32_t* cid = nullptr);
 cudaError_t launch_startup_store(nb_ctx* c, int order);
 cudaError_t launch_startup_dt(nb_ctx* c);
 cudaError_t launch_energy_sums(nb_ctx* c, int with_pot);
