@@ -213,6 +213,45 @@ int nb_get_profile(nb_ctx* ctx, double* ms, int64_t* launches, int64_t* total_la
 /* Library version string.                                                  */
 const char* nb_version(void);
 
+/* ------------------------------------------------------------- ensembles */
+
+/* Many independent clusters integrated side by side, each with its own
+ * hierarchical block times (abstract: individual block time-steps): every
+ * cycle advances each unfinished cluster by one of its blocks, with one launch
+ * per kernel for all clusters (the force runs over a table of (cluster,
+ * i-tile, j-split) items, each restricted to its cluster's particles).       */
+typedef struct nb_batch nb_batch;
+
+/* n_clusters >= 1 clusters of n_per_cluster[k] >= 1 particles, Hermite order
+ * 4/6/8, uniform softening eps; defaults as nb_create.                      */
+int nb_batch_create(nb_batch** out, int n_clusters, const int64_t* n_per_cluster, int order, double eps);
+void nb_batch_destroy(nb_batch* b);
+const char* nb_batch_last_error(const nb_batch* b);
+int nb_batch_set_stream(nb_batch* b, void* cuda_stream);
+int nb_batch_set_precision(nb_batch* b, int mode);
+int nb_batch_set_params(nb_batch* b, double eta, double eta_s, double dt_max, double dt_min);
+
+/* Host arrays of all clusters concatenated in cluster order (no padding):
+ * m [N], x, v [N][3] with N = sum n_per_cluster.  Starts every cluster at
+ * t = 0 as nb_set_particles does for one system.                            */
+int nb_batch_set_particles(nb_batch* b, const double* m, const double* x, const double* v);
+
+/* One cycle: each cluster whose next block time is <= t_end takes that block.
+ * Outputs (NULL to skip): clusters stepped (0 once all are past t_end) and
+ * interactions evaluated (sum of n_act_k * n_k).                           */
+int nb_batch_cycle(nb_batch* b, double t_end, int* n_stepped, int64_t* n_interactions);
+
+/* Cycles until no cluster has a block at or before t_end.                   */
+int nb_batch_step_until(nb_batch* b, double t_end, int64_t* n_cycles, int64_t* n_interactions);
+
+/* Per-cluster kinetic and potential energy (arrays [n_clusters]); every
+ * cluster must be synchronised within itself, else NB_ERR_NOT_SYNC.         */
+int nb_batch_energy(nb_batch* b, double* ekin, double* epot);
+
+/* State of all clusters concatenated as in nb_batch_set_particles (any
+ * output may be NULL): x, v [N][3], t, dt [N].  Synchronises.               */
+int nb_batch_get_state(nb_batch* b, double* x, double* v, double* t, double* dt);
+
 /* ----------------------------------------------------- allocation-free call */
 
 /* The paper has no counterpart to this call: it serves callers that cannot

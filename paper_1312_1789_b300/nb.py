@@ -63,6 +63,17 @@ SIGNATURES = {
     "nb_set_noise_floor": (C.c_int, [_P, C.c_int, _D]),
     "nb_get_noise_floor": (C.c_int, [_P, C.c_int, _D]),
     "nb_force_static": (C.c_int, [C.c_int, C.c_int, C.c_int64, _P, _P, _P, _P, _P, _P, _P, C.c_int64, _P, _P]),
+    "nb_batch_create": (C.c_int, [C.POINTER(_P), C.c_int, _I64, C.c_int, C.c_double]),
+    "nb_batch_destroy": (None, [_P]),
+    "nb_batch_last_error": (C.c_char_p, [_P]),
+    "nb_batch_set_stream": (C.c_int, [_P, _P]),
+    "nb_batch_set_precision": (C.c_int, [_P, C.c_int]),
+    "nb_batch_set_params": (C.c_int, [_P, C.c_double, C.c_double, C.c_double, C.c_double]),
+    "nb_batch_set_particles": (C.c_int, [_P, _D, _D, _D]),
+    "nb_batch_cycle": (C.c_int, [_P, C.c_double, C.POINTER(C.c_int), _I64]),
+    "nb_batch_step_until": (C.c_int, [_P, C.c_double, _I64, _I64]),
+    "nb_batch_energy": (C.c_int, [_P, _D, _D]),
+    "nb_batch_get_state": (C.c_int, [_P, _D, _D, _D, _D]),
 }
 NB_STATIC_MAX_N = 16384
 NB_NPHASES = 6
@@ -273,6 +284,74 @@ class NBody:
         a, b, c = C.c_int(), C.c_int(), C.c_int()
         self._check(self._L.nb_get_launch(self._h, C.byref(a), C.byref(b), C.byref(c)))
         return a.value, b.value, c.value
+
+
+class Batch:
+    """An ensemble of independent clusters advanced together (nb_batch_*)."""
+
+    def __init__(self, sizes, order: int = 6, eps: float = 0.0, precision: int = NB_MIXED):
+        self._L = lib()
+        self._h = _P()
+        self.sizes = np.ascontiguousarray(sizes, dtype=np.int64)
+        rc = self._L.nb_batch_create(C.byref(self._h), len(self.sizes), self.sizes.ctypes.data_as(_I64), int(order),
+                                     float(eps))
+        if rc != NB_OK:
+            raise NBError(rc, "nb_batch_create failed")
+        self.n = int(self.sizes.sum())
+        self.k = len(self.sizes)
+        self._check(self._L.nb_batch_set_precision(self._h, int(precision)))
+
+    def _check(self, rc):
+        if rc != NB_OK:
+            raise NBError(rc, self._L.nb_batch_last_error(self._h).decode())
+
+    def close(self):
+        if self._h:
+            self._L.nb_batch_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        handle = getattr(stream, "cuda_stream", stream)
+        self._check(self._L.nb_batch_set_stream(self._h, _P(handle or 0)))
+
+    def set_precision(self, mode: int):
+        self._check(self._L.nb_batch_set_precision(self._h, int(mode)))
+
+    def set_params(self, eta=0.2, eta_s=0.01, dt_max=1.0 / 16, dt_min=2.0 ** -40):
+        self._check(self._L.nb_batch_set_params(self._h, eta, eta_s, dt_max, dt_min))
+
+    def set_particles(self, m, x, v):
+        m = np.ascontiguousarray(m, dtype=np.float64)
+        self._check(self._L.nb_batch_set_particles(self._h, _d(m), _d(_vec(x, self.n)), _d(_vec(v, self.n))))
+
+    def cycle(self, t_end: float):
+        k = C.c_int()
+        ni = C.c_int64()
+        self._check(self._L.nb_batch_cycle(self._h, float(t_end), C.byref(k), C.byref(ni)))
+        return k.value, ni.value
+
+    def step_until(self, t_end: float):
+        nc = C.c_int64()
+        ni = C.c_int64()
+        self._check(self._L.nb_batch_step_until(self._h, float(t_end), C.byref(nc), C.byref(ni)))
+        return nc.value, ni.value
+
+    def energy(self):
+        ek, ep = np.zeros(self.k), np.zeros(self.k)
+        self._check(self._L.nb_batch_energy(self._h, _d(ek), _d(ep)))
+        return ek, ep
+
+    def get_state(self):
+        x, v = np.zeros((self.n, 3)), np.zeros((self.n, 3))
+        t, dt = np.zeros(self.n), np.zeros(self.n)
+        self._check(self._L.nb_batch_get_state(self._h, _d(x), _d(v), _d(t), _d(dt)))
+        return {"x": x, "v": v, "t": t, "dt": dt}
 
 
 class TorchAllocator:

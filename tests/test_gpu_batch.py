@@ -1,0 +1,93 @@
+"""Ensembles (nb_batch_*): independent clusters advanced together with one
+launch per kernel; each cluster must evolve exactly as if it were alone."""
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_1312_1789_b300 import ics, nb
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1312_1789_b300 import build
+    build.build()
+    nb.lib()
+
+
+def _clusters(sizes, eps=1e-4):
+    ms, xs, vs = [], [], []
+    for k, n in enumerate(sizes):
+        m, x, v = ics.plummer(int(n), 500 + k)
+        ms.append(m)
+        xs.append(x)
+        vs.append(v)
+    return ms, xs, vs
+
+
+@pytest.mark.parametrize("order", [4, 6, 8])
+def test_batch_fp64_matches_each_cluster_alone(order):
+    # Ragged cluster sizes (not multiples of the 128-record tile, one below it).
+    sizes = [300, 129, 1000, 64, 700]
+    ms, xs, vs = _clusters(sizes)
+    eta = 0.02 if order == 4 else 0.2
+    b = nb.Batch(sizes, order, 1e-4, nb.NB_FP64)
+    b.set_params(eta, 0.01, 1.0 / 16, 2.0 ** -40)
+    b.set_particles(np.concatenate(ms), np.concatenate(xs), np.concatenate(vs))
+    ncyc, ninter = b.step_until(1.0 / 16)
+    assert ncyc > 0 and ninter > 0
+    S = b.get_state()
+    assert np.all(S["t"] == 1.0 / 16)
+    off = 0
+    for k, n in enumerate(sizes):
+        st = orc.State(ms[k], 1e-8, xs[k], vs[k])
+        orc.integrate(st, order=order, t_end=1.0 / 16, eta=eta, nthreads=16)
+        sl = slice(off, off + n)
+        assert np.array_equal(S["dt"][sl], st.dt), f"cluster {k}: steps differ"
+        assert np.max(np.abs(S["x"][sl] - st.x)) < 1e-11, f"cluster {k}"
+        assert np.max(np.abs(S["v"][sl] - st.v)) < 1e-10, f"cluster {k}"
+        off += n
+    b.close()
+
+
+@pytest.mark.parametrize("prec", [nb.NB_FP64, nb.NB_MIXED])
+def test_batch_energy_per_cluster(prec):
+    sizes = [500, 257, 900]
+    ms, xs, vs = _clusters(sizes)
+    b = nb.Batch(sizes, 6, 1e-4, prec)
+    b.set_particles(np.concatenate(ms), np.concatenate(xs), np.concatenate(vs))
+    ek, ep = b.energy()
+    for k in range(len(sizes)):
+        ek_o, ep_o = orc.energy(ms[k], 1e-8, xs[k], vs[k])
+        assert ek[k] == pytest.approx(ek_o, rel=1e-14)
+        assert ep[k] == pytest.approx(ep_o, rel=1e-13 if prec == nb.NB_FP64 else 1e-6)
+    e0 = ek + ep
+    b.step_until(1.0 / 16)
+    ek, ep = b.energy()
+    de = (ek + ep - e0) / np.abs(e0)
+    assert np.all(np.abs(de) < 1e-6), de
+    b.close()
+
+
+def test_batch_matches_separate_contexts_mixed():
+    # The ensemble path and one context per cluster take the same blocks; the
+    # mixed forces of both use the same kernels, so states agree to rounding.
+    sizes = [640, 384, 1100]
+    ms, xs, vs = _clusters(sizes)
+    b = nb.Batch(sizes, 6, 1e-4, nb.NB_MIXED)
+    b.set_particles(np.concatenate(ms), np.concatenate(xs), np.concatenate(vs))
+    b.step_until(1.0 / 32)
+    S = b.get_state()
+    off = 0
+    for k, n in enumerate(sizes):
+        c = nb.NBody(n, 6, 1e-4, nb.NB_MIXED)
+        c.set_particles(ms[k], xs[k], vs[k])
+        c.step_until(1.0 / 32)
+        R = c.get_state()
+        sl = slice(off, off + n)
+        assert np.max(np.abs(S["x"][sl] - R["x"])) < 1e-9
+        assert np.mean(S["dt"][sl] == R["dt"]) > 0.99
+        c.close()
+        off += n
+    b.close()
