@@ -49,7 +49,8 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     p.add_argument("--block-step", type=float, default=2.0 ** -12)
-    p.add_argument("--quick", action="store_true", help="skip the FP64, energy and CPU legs")
+    p.add_argument("--quick", action="store_true", help="skip the FP64, energy, ensemble and CPU legs")
+    p.add_argument("--ensemble-t", type=float, default=1.0 / 64, help="end time of the ensemble leg")
     return p.parse_args()
 
 
@@ -348,6 +349,44 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
                                 "mixed_within_2x": abs(de["mixed"]["dE_E"]) <= 2 * abs(de["fp64"]["dE_E"])}
     except Exception as e:  # pragma: no cover
         out["energy_budget"] = {"error": repr(e)}
+    # ---- ensemble: 256 Plummer clusters, batched vs one context per cluster
+    try:
+        clusters = ics.ensemble()
+        sizes = [c.n for c in clusters]
+        t_ens = args.ensemble_t
+        m = np.concatenate([c.m for c in clusters])
+        x = np.concatenate([c.x for c in clusters])
+        v = np.concatenate([c.v for c in clusters])
+        bt = nb.Batch(sizes, 6, math.sqrt(clusters[0].eps2[0]), nb.NB_MIXED)
+        bt.set_stream(stream)
+        bt.set_params(0.2, 0.01, 1.0 / 16, 2.0 ** -40)
+        bt.set_particles(m, x, v)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ncyc, ni_b = bt.step_until(t_ens)
+        torch.cuda.synchronize()
+        el_b = time.perf_counter() - t0
+        bt.close()
+        ni_s, el_s = 0, 0.0
+        for c in clusters:
+            cx = nb.NBody(c.n, 6, math.sqrt(c.eps2[0]), nb.NB_MIXED)
+            cx.set_stream(stream)
+            cx.set_particles(c.m, c.x, c.v)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, ni = cx.step_until(t_ens)
+            torch.cuda.synchronize()
+            el_s += time.perf_counter() - t0
+            ni_s += ni
+            cx.close()
+        out["ensemble"] = {"workload": f"{len(sizes)} Plummer clusters, N_k log-uniform in [1024, 32768] "
+                                       f"({int(sum(sizes))} particles), order 6, mixed, to t={t_ens}",
+                           "batched_interactions_per_s": ni_b / el_b, "batched_cycles": ncyc,
+                           "batched_seconds": el_b, "per_cluster_interactions_per_s": ni_s / el_s,
+                           "per_cluster_seconds": el_s, "interactions": ni_b,
+                           "speedup": (ni_b / el_b) / (ni_s / el_s)}
+    except Exception as e:  # pragma: no cover
+        out["ensemble"] = {"error": repr(e)}
     # ---- CPU oracle on the host cores (bounded sample)
     try:
         import oracle as orc
