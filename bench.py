@@ -104,6 +104,22 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+# ---------------------------------------------------------------- ranks
+def aggregate(ms_local: float, steps: int, inter_per_step: float, dist=None, device="cpu"):
+    """Whole-job throughput over ranks that each ran `steps` steps of their own
+    replica: elapsed = the slowest rank's (MAX over ranks), value = every
+    rank's interactions / that elapsed time.  Returns (ms_max, value, world)."""
+    world = 1
+    ms = float(ms_local)
+    if dist is not None and dist.is_initialized():
+        import torch
+        world = dist.get_world_size()
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * steps * inter_per_step / (ms * 1e-3), world
+
+
 # ------------------------------------------------------------------- helpers
 def nucleus():
     from paper_1312_1789_b300 import ics
@@ -217,11 +233,7 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     prof, launches1 = ctx.get_profile()
     ctx.set_profiling(False)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps * inter_step / (ms * 1e-3)
+    ms, value, world = aggregate(ms, args.steps, inter_step, dist, device="cuda")
     force_ms, force_n = prof["force"]
     t_force = force_ms / max(force_n, 1) * 1e-3
     achieved = flop_pi * inter_step / t_force / 1e12
