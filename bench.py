@@ -338,8 +338,10 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
     try:
         pw = ics.standard_workload(1)
         t_end = 1.0 / 16
-        de = {}
-        for name, p in (("fp64", nb.NB_FP64), ("mixed", nb.NB_MIXED)):
+        de, final = {}, {}
+        # host-driven cycles for both precisions, then the mixed run again as
+        # CUDA-graph replays of 64 device-driven cycles
+        for name, p, cyc in (("fp64", nb.NB_FP64, 0), ("mixed", nb.NB_MIXED, 0), ("mixed_graph", nb.NB_MIXED, 64)):
             c2 = nb.NBody(pw.n, 6, math.sqrt(pw.eps2[0]), p)
             c2.set_stream(stream)
             c2.set_params(pw.eta, pw.eta_s, pw.dt_max, 2.0 ** -40)
@@ -347,16 +349,19 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
             c2.set_precision(nb.NB_FP64)
             e0 = sum(c2.energy())
             c2.set_precision(p)
+            c2.set_graph(cyc)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             nblk, ni = c2.step_until(t_end)
             torch.cuda.synchronize()
             el = time.perf_counter() - t0
+            final[name] = c2.get_state()["x"]
             c2.set_precision(nb.NB_FP64)
             e1 = sum(c2.energy())
             de[name] = {"dE_E": (e1 - e0) / abs(e0), "blocks": nblk, "interactions": ni,
                         "whole_run_interactions_per_s": ni / el, "seconds": el}
             c2.close()
+        de["mixed_graph"]["same_state_as_host_driven"] = bool(np.array_equal(final["mixed"], final["mixed_graph"]))
         out["energy_budget"] = {"workload": pw.name + f" to t={t_end}", **de,
                                 "mixed_within_2x": abs(de["mixed"]["dE_E"]) <= 2 * abs(de["fp64"]["dE_E"])}
     except Exception as e:  # pragma: no cover

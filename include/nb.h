@@ -168,6 +168,14 @@ int nb_get_predicted(nb_ctx* ctx, double* xp, double* vp, double* ap, double* jp
  * output may be NULL.                                                       */
 int nb_get_launch(nb_ctx* ctx, int* i_tiles, int* j_splits, int* i_per_cta);
 
+/* cycles > 0: nb_step_until replays a CUDA graph of that many device-driven
+ * block cycles (scheduler, predictor, force, corrector with the active-set
+ * size, block time and force launch shape decided on the device), checking
+ * on the host only once per replay; 0 (default): one host-driven cycle per
+ * block.  Both take the same blocks with the same kernels' arithmetic.  The
+ * graph is captured on first use and again after a parameter change.       */
+int nb_set_graph(nb_ctx* ctx, int cycles);
+
 /* Force the j-split count of later nb_force calls (0 = automatic).         */
 int nb_set_jsplit(nb_ctx* ctx, int j_splits);
 

@@ -447,22 +447,130 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_fp64(const double2* __restri
                                       partial, sc);
 }
 
-// -------------------------------------------------------------------- K3
-// F[c][p] = sum over splits in fixed order; the potential sum is negated.
-// PC = index of the potential component.
-template <int NC, int PC>
-__global__ void k_force_reduce(const double* __restrict__ partial, int jsplit, int n_act,
-                               const int32_t* __restrict__ idx, const double* __restrict__ m,
-                               const double* __restrict__ eps2, int n, double* __restrict__ F)
+// ------------------------------------------------------- device-driven cycle
+// Launch shape from the scheduler's n_act, chosen on the device with the
+// host's rule (makespan ceil(it*js/slots)/js, ties within 1% to fewer splits,
+// capped by the partial-sum buffer); an active set past t_end makes the
+// cycle idle.
+
+// Persistent force: a fixed grid walks the (i-tile, split) items of the
+// device-chosen shape; a variant with another i-particles-per-thread count
+// returns at once.
+template <int ORDER, int RW, bool PAIR, int IPT>
+__global__ void __launch_bounds__(FORCE_NT) k_force_mixed_dyn(const float4* __restrict__ js,
+                                                              const int32_t* __restrict__ idx, int n, int ntiles,
+                                                              float eps2u, float eps2max, double* __restrict__ partial,
+                                                              DevScalars* sc)
 {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n_act) return;
+    if (sc->idle || sc->ipt != IPT) return;
+    const int n_act = (int)sc->n_act, it = sc->itiles, jsplit = sc->jsplit;
+    for (int w = blockIdx.x; w < it * jsplit; w += gridDim.x) {
+        const int itile = w % it, split = w / it;
+        const int t0 = (int)((long long)split * ntiles / jsplit);
+        const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
+        force_block_mixed<ORDER, RW, PAIR, IPT>(js, idx, itile * (FORCE_NT * IPT), n_act, n, t0, t1 - t0, split,
+                                                n_act, eps2u, eps2max, partial, sc);
+        // every thread is done before the next item re-arms the ring; a
+        // status raised by any CTA ends the walk
+        if (__syncthreads_or(threadIdx.x == 0 && *(volatile int*)&sc->status != 0)) return;
+    }
+}
+
+template <int ORDER, int RW, bool PAIR>
+__global__ void __launch_bounds__(FORCE_NT) k_force_fp64_dyn(const double2* __restrict__ js,
+                                                             const int32_t* __restrict__ idx, int n, int ntiles,
+                                                             double eps2u, double* __restrict__ partial,
+                                                             DevScalars* sc)
+{
+    if (sc->idle) return;
+    const int n_act = (int)sc->n_act, it = sc->itiles, jsplit = sc->jsplit;
+    for (int w = blockIdx.x; w < it * jsplit; w += gridDim.x) {
+        const int itile = w % it, split = w / it;
+        const int t0 = (int)((long long)split * ntiles / jsplit);
+        const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
+        force_block_fp64<ORDER, RW, PAIR>(js, idx, itile * FORCE_NT, n_act, n, t0, t1 - t0, split, n_act, eps2u,
+                                          partial, sc);
+        if (__syncthreads_or(threadIdx.x == 0 && *(volatile int*)&sc->status != 0)) return;
+    }
+}
+
+// -------------------------------------------------------------------- K3
+// F[c][p] = the sum of the j-split partials of component c of active particle
+// p; the potential sum is negated (PC = index of the potential component).
+// The summation order depends on (jsplit, n_act) alone, so every launcher
+// (per-launch, device-driven, static) gives the same bits:
+//   by warp   : lane l adds splits l, l+32, ... in turn, then the 32 lane
+//               sums meet in a butterfly (every lane ends with the same bits,
+//               as a + b == b + a exactly);
+//   sequential: one thread adds the splits in turn.
+// The warp form serves many splits over few particles, where a thread per
+// particle would leave the GPU idle behind one long chain of loads.
+constexpr int RED_WARP_MIN_SPLIT = 9;
+constexpr int RED_WARP_MAX_NACT = 4096;
+constexpr int RED_NT = 256;
+__host__ __device__ __forceinline__ bool reduce_by_warp(int jsplit, int n_act)
+{
+    return jsplit >= RED_WARP_MIN_SPLIT && n_act < RED_WARP_MAX_NACT;
+}
+// per-launch grid of k_force_reduce for NC components
+__host__ __forceinline__ int reduce_grid(int jsplit, int n_act, int nc)
+{
+    return reduce_by_warp(jsplit, n_act) ? (n_act * nc + RED_NT / 32 - 1) / (RED_NT / 32)
+                                         : (n_act + RED_NT - 1) / RED_NT;
+}
+
+template <int NC, int PC>
+__device__ __forceinline__ void reduce_seq(const double* __restrict__ partial, int jsplit, int n_act, int p,
+                                           double* __restrict__ F)
+{
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         double s = 0.0;
         for (int sp = 0; sp < jsplit; ++sp) s += partial[((size_t)sp * NC + c) * n_act + p];
-        if (c == PC) s = -s;
-        F[(size_t)c * n_act + p] = s;
+        F[(size_t)c * n_act + p] = c == PC ? -s : s;
+    }
+}
+
+// q = p * NC + c; called by a whole warp
+template <int NC, int PC>
+__device__ __forceinline__ void reduce_warp(const double* __restrict__ partial, int jsplit, int n_act, int q,
+                                            int lane, double* __restrict__ F)
+{
+    const int p = q / NC, c = q - p * NC;
+    double s = 0.0;
+    for (int sp = lane; sp < jsplit; sp += 32) s += partial[((size_t)sp * NC + c) * n_act + p];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) F[(size_t)c * n_act + p] = c == PC ? -s : s;
+}
+
+template <int NC, int PC>
+__global__ void __launch_bounds__(RED_NT) k_force_reduce(const double* __restrict__ partial, int jsplit, int n_act,
+                                                         double* __restrict__ F)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (reduce_by_warp(jsplit, n_act)) {
+        const int q = g >> 5;  // warp-uniform
+        if (q < n_act * NC) reduce_warp<NC, PC>(partial, jsplit, n_act, q, threadIdx.x & 31, F);
+    } else if (g < n_act) {
+        reduce_seq<NC, PC>(partial, jsplit, n_act, g, F);
+    }
+}
+
+// Device-driven form: a fixed grid strides over the block the scheduler chose.
+template <int NC, int PC>
+__global__ void __launch_bounds__(RED_NT) k_force_reduce_dyn(const double* __restrict__ partial,
+                                                             const DevScalars* __restrict__ sc,
+                                                             double* __restrict__ F)
+{
+    if (sc->idle) return;
+    const int n_act = (int)sc->n_act, jsplit = sc->jsplit;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    if (reduce_by_warp(jsplit, n_act)) {
+        for (int q = g >> 5; q < n_act * NC; q += stride >> 5)
+            reduce_warp<NC, PC>(partial, jsplit, n_act, q, threadIdx.x & 31, F);
+    } else {
+        for (int p = g; p < n_act; p += stride) reduce_seq<NC, PC>(partial, jsplit, n_act, p, F);
     }
 }
 

@@ -124,16 +124,113 @@ cudaError_t launch_force(nb_ctx* c, int order, const int32_t* idx, int64_t n_act
 
 cudaError_t launch_force_reduce(nb_ctx* c, int order, const int32_t* idx, int64_t n_act, int jsplit)
 {
-    const int nt = 256;
-    const int nb = (int)((n_act + nt - 1) / nt);
-    const int na = (int)n_act, n = (int)c->n;
+    (void)idx;
+    const int na = (int)n_act;
+#define NB_RED(O)                                                                                              \
+    k_force_reduce<ncomp(O), pot_comp(O)><<<reduce_grid(jsplit, na, ncomp(O)), RED_NT, 0, c->stream>>>(c->partial, \
+                                                                                                      jsplit, na, c->F)
     switch (order) {
-    case 0: k_force_reduce<ncomp(0), pot_comp(0)><<<nb, nt, 0, c->stream>>>(c->partial, jsplit, na, idx, c->m, c->eps2, n, c->F); break;
-    case 4: k_force_reduce<ncomp(4), pot_comp(4)><<<nb, nt, 0, c->stream>>>(c->partial, jsplit, na, idx, c->m, c->eps2, n, c->F); break;
-    case 6: k_force_reduce<ncomp(6), pot_comp(6)><<<nb, nt, 0, c->stream>>>(c->partial, jsplit, na, idx, c->m, c->eps2, n, c->F); break;
-    case 8: k_force_reduce<ncomp(8), pot_comp(8)><<<nb, nt, 0, c->stream>>>(c->partial, jsplit, na, idx, c->m, c->eps2, n, c->F); break;
+    case 0: NB_RED(0); break;
+    case 4: NB_RED(4); break;
+    case 6: NB_RED(6); break;
+    case 8: NB_RED(8); break;
     default: return cudaErrorInvalidValue;
     }
+#undef NB_RED
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- device-driven cycle
+// One thread: close the cycle when the next block lies past t_end, otherwise
+// pick the force launch shape exactly as the host rule does for a block of
+// that size (same slot counts, same makespan split, same forced split).
+__global__ void k_cycle_gate(DevScalars* sc, long long n, int ntiles, int slots1, int slots2, long long cap, int nc,
+                             int mixed, int js_force)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const long long na = sc->n_act;
+    if (!(sc->t_blk <= sc->t_end) || na <= 0) {
+        sc->idle = 1;
+        return;
+    }
+    sc->idle = 0;
+    const int ipt = (mixed && na >= IPT2_MIN_NACT) ? 2 : 1;
+    const int slots = ipt == 2 ? slots2 : slots1;
+    const int it = (int)((na + FORCE_NT * ipt - 1) / (FORCE_NT * ipt));
+    sc->ipt = ipt;
+    sc->itiles = it;
+    const long long cap_splits = cap / ((long long)nc * na);
+    int js = js_force > 0 ? js_force : makespan_split(it, ntiles, slots, cap_splits);
+    if (js > ntiles) js = ntiles;
+    if (js > cap_splits) js = (int)cap_splits;
+    sc->jsplit = js < 1 ? 1 : js;
+    sc->blocks += 1;
+    sc->inter += na * n;
+}
+
+template <typename K>
+static int dyn_slots(nb_ctx* c, K kern, size_t smem)
+{
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return c->sm_count * occupancy_of(kern, smem);
+}
+
+// Launch (or, query_only, size) the persistent force kernels of the context's
+// order: both i-particles-per-thread variants on the mixed path.
+template <int O>
+static cudaError_t force_dyn_o(nb_ctx* c, int* s1, int* s2, bool query_only)
+{
+    const bool pair = c->pair_eps || !(c->eps > 0.0);
+    const int ntiles = (int)(c->np / JT);
+    if (c->prec == NB_MIXED) {
+        constexpr int RW = mixed_rw(O);
+        const size_t smem = (size_t)NSTAGE * JT * RW * 16;
+        auto k1 = pair ? k_force_mixed_dyn<O, RW, true, 1> : k_force_mixed_dyn<O, RW, false, 1>;
+        auto k2 = pair ? k_force_mixed_dyn<O, RW, true, 2> : k_force_mixed_dyn<O, RW, false, 2>;
+        if (query_only) {
+            *s1 = dyn_slots(c, k1, smem);
+            *s2 = dyn_slots(c, k2, smem);
+            return cudaSuccess;
+        }
+        const float e2 = (float)(c->eps * c->eps), e2max = (float)c->eps2_max;
+        k1<<<*s1, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), c->act_idx, (int)c->n,
+                                               ntiles, e2, e2max, c->partial, c->sc);
+        k2<<<*s2, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), c->act_idx, (int)c->n,
+                                               ntiles, e2, e2max, c->partial, c->sc);
+    } else {
+        constexpr int RW = fp64_rw(O);
+        const size_t smem = (size_t)NSTAGE * JT * RW * 16;
+        auto k1 = pair ? k_force_fp64_dyn<O, RW, true> : k_force_fp64_dyn<O, RW, false>;
+        if (query_only) {
+            *s1 = *s2 = dyn_slots(c, k1, smem);
+            return cudaSuccess;
+        }
+        k1<<<*s1, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const double2*>(c->jstore), c->act_idx, (int)c->n,
+                                               ntiles, c->eps * c->eps, c->partial, c->sc);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_force_dyn(nb_ctx* c, int* slots1, int* slots2, bool query_only)
+{
+    if (c->order == 4) return force_dyn_o<4>(c, slots1, slots2, query_only);
+    if (c->order == 6) return force_dyn_o<6>(c, slots1, slots2, query_only);
+    return force_dyn_o<8>(c, slots1, slots2, query_only);
+}
+
+cudaError_t launch_cycle_gate(nb_ctx* c, int slots1, int slots2)
+{
+    k_cycle_gate<<<1, 32, 0, c->stream>>>(c->sc, c->n, (int)(c->np / JT), slots1, slots2, (long long)c->partial_cap,
+                                          ncomp(c->order), c->prec == NB_MIXED, c->jsplit_force);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_force_reduce_dyn(nb_ctx* c)
+{
+    const int nb = c->sm_count * 8;
+    if (c->order == 4) k_force_reduce_dyn<ncomp(4), pot_comp(4)><<<nb, RED_NT, 0, c->stream>>>(c->partial, c->sc, c->F);
+    else if (c->order == 6) k_force_reduce_dyn<ncomp(6), pot_comp(6)><<<nb, RED_NT, 0, c->stream>>>(c->partial, c->sc, c->F);
+    else k_force_reduce_dyn<ncomp(8), pot_comp(8)><<<nb, RED_NT, 0, c->stream>>>(c->partial, c->sc, c->F);
     return cudaGetLastError();
 }
 

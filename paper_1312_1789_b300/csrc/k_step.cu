@@ -175,10 +175,15 @@ __global__ void __launch_bounds__(256) k_predict(const double* __restrict__ m, c
                                                  const double* __restrict__ x, const double* __restrict__ v,
                                                  const double* __restrict__ d, const double* __restrict__ t,
                                                  int64_t n, int64_t np, double tp, void* __restrict__ jstore,
-                                                 const double* __restrict__ tpc, const int32_t* __restrict__ cid)
+                                                 const double* __restrict__ tpc, const int32_t* __restrict__ cid,
+                                                 const DevScalars* dyn)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
+    if (dyn) {
+        if (dyn->idle) return;
+        tp = dyn->t_blk;
+    }
     constexpr int RW = MIXED ? mixed_rw(ORDER) : fp64_rw(ORDER);
     double xp[3] = {0, 0, 0}, vp[3] = {0, 0, 0}, ap[3] = {0, 0, 0}, jp[3] = {0, 0, 0};
     double mi = 0.0, ei = 1.0;
@@ -249,7 +254,7 @@ __global__ void __launch_bounds__(256) k_predict(const double* __restrict__ m, c
     }
 }
 
-cudaError_t launch_predict(nb_ctx* c, double t, const double* tpc, const int32_t* cid)
+cudaError_t launch_predict(nb_ctx* c, double t, const double* tpc, const int32_t* cid, const DevScalars* dyn)
 {
     const int nt = 256;
     const int nb = (int)((c->np + nt - 1) / nt);
@@ -257,10 +262,10 @@ cudaError_t launch_predict(nb_ctx* c, double t, const double* tpc, const int32_t
 #define NB_PRED(O)                                                                                       \
     if (mixed)                                                                                           \
         k_predict<O, true><<<nb, nt, 0, c->stream>>>(c->m, c->eps2, c->x, c->v, c->d, c->t, c->n, c->np, \
-                                                     t, c->jstore, tpc, cid);                            \
+                                                     t, c->jstore, tpc, cid, dyn);                       \
     else                                                                                                 \
         k_predict<O, false><<<nb, nt, 0, c->stream>>>(c->m, c->eps2, c->x, c->v, c->d, c->t, c->n,      \
-                                                      c->np, t, c->jstore, tpc, cid);
+                                                      c->np, t, c->jstore, tpc, cid, dyn);
     if (c->order == 4) {
         NB_PRED(4)
     } else if (c->order == 6) {
@@ -370,10 +375,16 @@ __global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fid
                                                  double* __restrict__ d, double* __restrict__ t,
                                                  double* __restrict__ dtv, double* __restrict__ pot, double eta,
                                                  double dt_max, double dt_min, NoiseEps ne, DevScalars* sc,
-                                                 const double* __restrict__ tfc, const int32_t* __restrict__ cid)
+                                                 const double* __restrict__ tfc, const int32_t* __restrict__ cid,
+                                                 const DevScalars* dyn)
 {
     constexpr int MM = ORDER / 2;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (dyn) {  // device-driven cycle: the block of the scheduler, unless idle
+        if (dyn->idle) return;
+        fn = (int)dyn->n_act;
+        tf = dyn->t_blk;
+    }
     if (p >= fn) return;
     const int i = fidx[p];
     if ((unsigned)i >= (unsigned)n) {
@@ -479,14 +490,15 @@ __global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fid
     pot[i] = potn;
 }
 
-cudaError_t launch_correct(nb_ctx* c, const double* tfc, const int32_t* cid)
+cudaError_t launch_correct(nb_ctx* c, const double* tfc, const int32_t* cid, const DevScalars* dyn)
 {
     const int nt = 128;
-    const int nb = (int)((c->f_n + nt - 1) / nt);
+    const int nb = (int)(((dyn ? c->n : c->f_n) + nt - 1) / nt);
 #define NB_CORR(O)                                                                                          \
-    k_correct<O><<<nb, nt, 0, c->stream>>>(c->f_idx, (int)c->f_n, c->f_t, c->F, c->n, c->np, c->x, c->v,   \
+    k_correct<O><<<nb, nt, 0, c->stream>>>(dyn ? c->act_idx : c->f_idx, (int)c->f_n, c->f_t, c->F, c->n, c->np, \
+                                           c->x, c->v,                                                      \
                                            c->d, c->t, c->dt, c->pot, c->eta, c->dt_max, c->dt_min,        \
-                                           c->noise[c->pred_prec == NB_MIXED ? 1 : 0], c->sc, tfc, cid);
+                                           c->noise[c->pred_prec == NB_MIXED ? 1 : 0], c->sc, tfc, cid, dyn);
     if (c->order == 4) {
         NB_CORR(4)
     } else if (c->order == 6) {

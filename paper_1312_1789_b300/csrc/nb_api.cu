@@ -172,29 +172,13 @@ void choose_shape(nb_ctx* c, int order, int64_t n_act, int* itiles, int* jsplit,
     *ipt_out = ipt;
     const int it = (int)((n_act + FORCE_NT * ipt - 1) / (FORCE_NT * ipt));
     const int ntiles = (int)(c->np / JT);
-    int js = 1;
-    auto fits = [&](int s) { return (size_t)s * ncomp(order) * (size_t)n_act <= c->partial_cap; };
-    if (c->jsplit_force > 0) {
-        js = c->jsplit_force;
-    } else {
-        // Equal-work CTAs run in waves of `slots`; the makespan of it*js CTAs,
-        // each 1/js of the j range, is ceil(it*js/slots)/js.  Take the split
-        // with the smallest makespan (ties within 1% to the smaller split).
-        const int slots = c->sm_count * force_occupancy(c, order, ipt);
-        const int js_max = std::min(ntiles, std::max(1, 4 * slots / std::max(it, 1) + 4));
-        double best = 1e300;
-        for (int s = 1; s <= js_max && fits(s); ++s) {
-            const double waves = std::ceil((double)it * s / slots);
-            const double span = waves / s;
-            if (span < best * 0.99) {
-                best = span;
-                js = s;
-            }
-        }
-    }
+    const long long cap_splits = (long long)(c->partial_cap / ((size_t)ncomp(order) * (size_t)n_act));
+    int js = c->jsplit_force > 0
+                 ? c->jsplit_force
+                 : makespan_split(it, ntiles, c->sm_count * force_occupancy(c, order, ipt), cap_splits);
     if (js > ntiles) js = ntiles;
+    if (js > cap_splits) js = (int)cap_splits;
     if (js < 1) js = 1;
-    while (js > 1 && !fits(js)) --js;
     *itiles = it;
     *jsplit = js;
 }
@@ -211,6 +195,88 @@ int run_force(nb_ctx* c, int order, const int32_t* idx_dev, int64_t n_act)
     c->last_ipt = ipt;
     c->F_order = order;
     c->F_n = n_act;
+    return NB_OK;
+}
+
+// ------------------------------------------------- device-driven cycles
+void destroy_graph(nb_ctx* c)
+{
+    if (c->graph_exec) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+    }
+}
+
+// Capture graph_cycles device-driven block cycles (scheduler, shape gate,
+// predictor, persistent force, reduction, corrector) into one CUDA graph.
+// Every kernel reads n_act / t_blk / the launch shape from the device
+// scalars, so the graph replays with no host round trip.
+int build_graph(nb_ctx* c)
+{
+    destroy_graph(c);
+    int s1 = 0, s2 = 0;
+    c->pred_prec = c->prec;
+    NB_CUDA(c, launch_force_dyn(c, &s1, &s2, true));
+    // the split rule sees the per-launch kernels' slot counts, so a block
+    // gets the same shape (and the same summation order) in both modes
+    const int sh1 = c->sm_count * force_occupancy(c, c->order, 1);
+    const int sh2 = c->prec == NB_MIXED ? c->sm_count * force_occupancy(c, c->order, 2) : sh1;
+    if (!c->graph_stream) NB_CUDA(c, cudaStreamCreateWithFlags(&c->graph_stream, cudaStreamNonBlocking));
+    cudaStream_t saved = c->stream;
+    c->stream = c->graph_stream;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->graph_stream, cudaStreamCaptureModeThreadLocal);
+    for (int r = 0; e == cudaSuccess && r < c->graph_cycles; ++r) {
+        if ((e = launch_sched(c)) != cudaSuccess) break;
+        if ((e = launch_cycle_gate(c, sh1, sh2)) != cudaSuccess) break;
+        if ((e = launch_predict(c, 0.0, nullptr, nullptr, c->sc)) != cudaSuccess) break;
+        if ((e = launch_force_dyn(c, &s1, &s2, false)) != cudaSuccess) break;
+        if ((e = launch_force_reduce_dyn(c)) != cudaSuccess) break;
+        if ((e = launch_correct(c, nullptr, nullptr, c->sc)) != cudaSuccess) break;
+    }
+    const cudaError_t e2 = cudaStreamEndCapture(c->graph_stream, &g);
+    c->stream = saved;
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        destroy_graph(c);
+        return set_err(c, NB_ERR_CUDA, "block-cycle graph capture failed: %s", cudaGetErrorString(e));
+    }
+    return NB_OK;
+}
+
+int step_until_graph(nb_ctx* c, double t_end, int64_t* n_blocks, int64_t* n_inter)
+{
+    if (!c->graph_exec) NB_TRY(build_graph(c));
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    DevScalars* h = c->h_sc;
+    NB_CUDA(c, cudaMemcpy(h, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost));
+    h->t_end = t_end;
+    h->idle = 0;
+    h->blocks = 0;
+    h->inter = 0;
+    NB_CUDA(c, cudaMemcpy(c->sc, h, sizeof(DevScalars), cudaMemcpyHostToDevice));
+    // scheduler 3, gate, predictor, force (both i-per-thread variants on the
+    // mixed path), reduction, corrector
+    const long long per_cycle = 3 + 1 + 1 + (c->prec == NB_MIXED ? 2 : 1) + 1 + 1;
+    for (;;) {
+        NB_CUDA(c, cudaGraphLaunch(c->graph_exec, c->graph_stream));
+        c->n_launch += per_cycle * c->graph_cycles;
+        NB_CUDA(c, cudaMemcpyAsync(h, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->graph_stream));
+        NB_CUDA(c, cudaStreamSynchronize(c->graph_stream));
+        if (h->status != NB_OK) {
+            const int st = h->status;
+            NB_CUDA(c, cudaMemset(&c->sc->status, 0, sizeof(int)));
+            return set_err(c, st, "device kernel reported: %s", code_name(st));
+        }
+        if (h->idle) break;
+    }
+    if (n_blocks) *n_blocks = h->blocks;
+    if (n_inter) *n_inter = h->inter;
+    c->have_pred = c->have_force = c->have_sched = 0;
+    c->F_order = -1;
     return NB_OK;
 }
 
@@ -255,6 +321,8 @@ void nb_destroy(nb_ctx* c)
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
     }
+    destroy_graph(c);
+    if (c->graph_stream) cudaStreamDestroy(c->graph_stream);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
 }
@@ -342,6 +410,7 @@ int nb_set_precision(nb_ctx* c, int mode)
 {
     if (!c) return NB_ERR_ARG;
     if (mode != NB_FP64 && mode != NB_MIXED) return set_err(c, NB_ERR_ARG, "precision %d not NB_FP64 or NB_MIXED", mode);
+    if (c->prec != mode) destroy_graph(c);
     c->prec = mode;
     return NB_OK;
 }
@@ -359,6 +428,7 @@ int nb_set_softening(nb_ctx* c, const double* eps_i)
     }
     NB_CUDA(c, cudaMemcpyAsync(c->eps2, e2.data(), e2.size() * 8, cudaMemcpyHostToDevice, c->stream));
     NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    destroy_graph(c);
     c->pair_eps = eps_i != nullptr;
     c->eps2_max = 0.0;
     for (int64_t k = 0; k < c->n; ++k) c->eps2_max = std::max(c->eps2_max, e2[(size_t)k]);
@@ -373,6 +443,7 @@ int nb_set_params(nb_ctx* c, double eta, double eta_s, double dt_max, double dt_
         return set_err(c, NB_ERR_ARG, "eta and eta_s must be positive and finite");
     if (!is_pow2(dt_max)) return set_err(c, NB_ERR_ARG, "dt_max must be a power of two");
     if (!(dt_min > 0.0) || !(dt_min <= dt_max)) return set_err(c, NB_ERR_ARG, "need 0 < dt_min <= dt_max");
+    destroy_graph(c);
     c->eta = eta;
     c->eta_s = eta_s;
     c->dt_max = dt_max;
@@ -380,10 +451,20 @@ int nb_set_params(nb_ctx* c, double eta, double eta_s, double dt_max, double dt_
     return NB_OK;
 }
 
+int nb_set_graph(nb_ctx* c, int cycles)
+{
+    if (!c) return NB_ERR_ARG;
+    if (cycles < 0 || cycles > 4096) return set_err(c, NB_ERR_ARG, "cycles must be in [0, 4096]");
+    destroy_graph(c);
+    c->graph_cycles = cycles;
+    return NB_OK;
+}
+
 int nb_set_jsplit(nb_ctx* c, int js)
 {
     if (!c) return NB_ERR_ARG;
     if (js < 0) return set_err(c, NB_ERR_ARG, "j_splits must be >= 0");
+    if (js != c->jsplit_force) destroy_graph(c);
     c->jsplit_force = js;
     return NB_OK;
 }
@@ -549,6 +630,8 @@ int nb_step_until(nb_ctx* c, double t_end, int64_t* n_blocks, int64_t* n_inter)
 {
     if (!c) return NB_ERR_ARG;
     if (!std::isfinite(t_end)) return set_err(c, NB_ERR_ARG, "t_end must be finite");
+    if (!c->have_particles) return set_err(c, NB_ERR_ARG, "nb_step_until before nb_set_particles");
+    if (c->graph_cycles > 0) return step_until_graph(c, t_end, n_blocks, n_inter);
     int64_t nb = 0, ni = 0;
     for (;;) {
         double tb;
@@ -706,6 +789,7 @@ int nb_set_noise_floor(nb_ctx* c, int prec, const double* eps)
     if ((prec != NB_FP64 && prec != NB_MIXED) || !eps) return set_err(c, NB_ERR_ARG, "bad precision or NULL eps");
     for (int k = 0; k < 4; ++k)
         if (!(eps[k] >= 0.0) || !std::isfinite(eps[k])) return set_err(c, NB_ERR_ARG, "eps must be finite and >= 0");
+    destroy_graph(c);
     for (int k = 0; k < 4; ++k) c->noise[prec].e[k] = eps[k];
     return NB_OK;
 }

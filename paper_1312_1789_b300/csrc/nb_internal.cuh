@@ -47,12 +47,47 @@ __host__ __device__ constexpr int fp64_rw(int order) { return order == 4 ? 4 : o
 __host__ __device__ constexpr int ncomp(int order) { return order == 0 ? 1 : 3 * (order / 2) + 2; }
 __host__ __device__ constexpr int pot_comp(int order) { return order == 0 ? 0 : 3 * (order / 2); }
 
+// j-split count of a force launch with the shortest makespan.  it i-tiles x s
+// splits of equal work run in waves of `slots` CTAs and take
+// ceil(it*s/slots)/s of the one-split time.  For w waves the best s is the
+// largest with it*s <= w*slots, so only those candidates (in increasing s,
+// clamped to s_max) are scored; a candidate replaces the running best only
+// when its span is over 1% shorter.  s_max bounds s by the j tiles, the
+// partial buffer (cap_splits) and about four waves' worth of splits.
+// Integer arithmetic only: the host and the device-driven gate agree exactly.
+__host__ __device__ inline int makespan_split(int it, int ntiles, int slots, long long cap_splits)
+{
+    if (it < 1) it = 1;
+    if (slots < 1) slots = 1;
+    long long s_max = 4LL * slots / it + 4;
+    if (s_max > ntiles) s_max = ntiles;
+    if (s_max > cap_splits) s_max = cap_splits;
+    if (s_max <= 1) return 1;
+    long long best_s = 1, best_w = (it + slots - 1) / slots;
+    const long long w_last = ((long long)it * s_max + slots - 1) / slots;
+    for (long long w = best_w; w <= w_last; ++w) {
+        long long s = w * slots / it;
+        if (s > s_max) s = s_max;
+        if (s <= best_s) continue;
+        const long long ws = ((long long)it * s + slots - 1) / slots;
+        // ws / s < 0.99 * best_w / best_s
+        if (100 * ws * best_s < 99 * best_w * s) {
+            best_s = s;
+            best_w = ws;
+        }
+    }
+    return (int)best_s;
+}
+
 // Scalars shared between the scheduler, the kernels and the host.
 struct DevScalars {
     long long n_act;  // size of the active list
     double t_blk;     // block time
     int status;       // first error raised by a kernel (NB_OK if none)
-    int pad;
+    int idle;         // device-driven cycle: the block is past t_end, do nothing
+    double t_end;     // device-driven cycle: stop time
+    int itiles, jsplit, ipt, pad2;  // device-driven cycle: force launch shape
+    long long blocks, inter;        // device-driven cycle: blocks taken, interactions
 };
 
 // Relative precision of the force components (acc, jerk, snap, crackle) that
@@ -204,6 +239,10 @@ struct nb_ctx {
     double prof_ms[NB_NPHASES] = {0};
     int64_t prof_n[NB_NPHASES] = {0};
     int64_t n_launch = 0;  // kernel launches since creation
+    // device-driven cycles captured in a CUDA graph (nb_set_graph)
+    int graph_cycles = 0;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t graph_stream = nullptr;
     // allocator captured at creation
     void* (*alloc_fn)(size_t, void*) = nullptr;
     void (*free_fn)(void*, void*) = nullptr;
@@ -215,11 +254,19 @@ namespace nb {
 
 // Launchers (k_*.cu); each returns cudaGetLastError() of its launches.
 cudaError_t launch_sched(nb_ctx* c);
-// tpc, cid (ensembles): per-cluster prediction time and cluster of each slot; NULL for one system
-cudaError_t launch_predict(nb_ctx* c, double t, const double* tpc = nullptr, const int32_t* cid = nullptr);
+// tpc, cid (ensembles): per-cluster prediction time and cluster of each slot; NULL for one system.
+// dyn (device-driven cycle): take the time from dyn->t_blk and do nothing when dyn->idle.
+cudaError_t launch_predict(nb_ctx* c, double t, const double* tpc = nullptr, const int32_t* cid = nullptr,
+                           const DevScalars* dyn = nullptr);
 cudaError_t launch_force(nb_ctx* c, int order, const int32_t* idx, int64_t n_act, int jsplit, int itiles, int ipt);
 cudaError_t launch_force_reduce(nb_ctx* c, int order, const int32_t* idx, int64_t n_act, int jsplit);
-cudaError_t launch_correct(nb_ctx* c, const double* tfc = nullptr, const int32_t* cid = nullptr);
+cudaError_t launch_correct(nb_ctx* c, const double* tfc = nullptr, const int32_t* cid = nullptr,
+                           const DevScalars* dyn = nullptr);
+// Device-driven block cycle (CUDA-graph capturable): shape gate, persistent
+// force over device-chosen items, reduction; all read n_act / t_blk on the device.
+cudaError_t launch_cycle_gate(nb_ctx* c, int slots1, int slots2);
+cudaError_t launch_force_dyn(nb_ctx* c, int* slots1, int* slots2, bool query_only);
+cudaError_t launch_force_reduce_dyn(nb_ctx* c);
 cudaError_t launch_startup_store(nb_ctx* c, int order);
 cudaError_t launch_startup_dt(nb_ctx* c);
 cudaError_t launch_energy_sums(nb_ctx* c, int with_pot);

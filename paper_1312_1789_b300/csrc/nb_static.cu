@@ -136,18 +136,7 @@ int slots_of(K kern, size_t smem, int sm_count)
 // Same makespan rule as the context path, capped by the fixed partial region.
 int choose_split(int it, int ntiles, int nc, int n_act, int slots)
 {
-    auto fits = [&](int s) { return (size_t)s * nc * (size_t)n_act <= PARTIAL_DOUBLES; };
-    int js = 1;
-    const int js_max = std::min(ntiles, std::max(1, 4 * slots / std::max(it, 1) + 4));
-    double best = 1e300;
-    for (int s = 1; s <= js_max && fits(s); ++s) {
-        const double span = std::ceil((double)it * s / slots) / s;
-        if (span < best * 0.99) {
-            best = span;
-            js = s;
-        }
-    }
-    return js;
+    return makespan_split(it, ntiles, slots, (long long)(PARTIAL_DOUBLES / ((size_t)nc * (size_t)n_act)));
 }
 
 template <int ORDER, bool MIXED>
@@ -182,8 +171,7 @@ int run_static(const double* m, const double* eps2, const double* x, const doubl
         kern<<<dim3(it, js), FORCE_NT, smem, st>>>(reinterpret_cast<const double2*>(rec), idx, n_act, n, np / JT, js,
                                                    0.0, partial, sc);
     }
-    k_force_reduce<NC, pot_comp(ORDER)><<<(n_act + 255) / 256, 256, 0, st>>>(partial, js, n_act, idx, nullptr, nullptr,
-                                                                             n, out);
+    k_force_reduce<NC, pot_comp(ORDER)><<<reduce_grid(js, n_act, NC), RED_NT, 0, st>>>(partial, js, n_act, out);
     if (cudaGetLastError() != cudaSuccess) return NB_ERR_CUDA;
     // wait for the work so that device-side argument errors are reported here
     DevScalars h;

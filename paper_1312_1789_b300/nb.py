@@ -63,6 +63,7 @@ SIGNATURES = {
     "nb_set_noise_floor": (C.c_int, [_P, C.c_int, _D]),
     "nb_get_noise_floor": (C.c_int, [_P, C.c_int, _D]),
     "nb_force_static": (C.c_int, [C.c_int, C.c_int, C.c_int64, _P, _P, _P, _P, _P, _P, _P, C.c_int64, _P, _P]),
+    "nb_set_graph": (C.c_int, [_P, C.c_int]),
     "nb_batch_create": (C.c_int, [C.POINTER(_P), C.c_int, _I64, C.c_int, C.c_double]),
     "nb_batch_destroy": (None, [_P]),
     "nb_batch_last_error": (C.c_char_p, [_P]),
@@ -174,6 +175,10 @@ class NBody:
 
     def set_params(self, eta=0.2, eta_s=0.01, dt_max=1.0 / 16, dt_min=2.0 ** -40):
         self._check(self._L.nb_set_params(self._h, eta, eta_s, dt_max, dt_min))
+
+    def set_graph(self, cycles: int):
+        """cycles > 0: step_until replays a CUDA graph of that many device-driven block cycles."""
+        self._check(self._L.nb_set_graph(self._h, int(cycles)))
 
     def set_jsplit(self, js: int):
         self._check(self._L.nb_set_jsplit(self._h, int(js)))
