@@ -273,6 +273,134 @@ __device__ __forceinline__ void force_block_mixed(const float4* __restrict__ js,
     }
 }
 
+// j-parallel form for small active sets: NI = FORCE_NT / JP i-particles per
+// CTA; thread (il, jl) = (tid % NI, tid / NI) takes i-particle il and the
+// records jl, jl + JP, ... of every j tile.  Each thread keeps a
+// double-single sum (FP32 tile sums folded every FOLD tiles); at the end the
+// JP sums of an i-particle are added in jl order through the (then idle)
+// ring buffer, so the result depends on the launch shape only.
+template <int ORDER, int RW, bool PAIR, int JP>
+__device__ __forceinline__ void force_block_mixed_jp(const float4* __restrict__ js, const int32_t* __restrict__ idx,
+                                                     const int pbase0, const int plim, const int n, const int t0,
+                                                     const int nt, const int split, const int ncol,
+                                                     const float eps2u, const float eps2max,
+                                                     double* __restrict__ partial, DevScalars* sc)
+{
+    constexpr int NC = ncomp(ORDER);
+    constexpr int NI = FORCE_NT / JP;
+    constexpr int FOLD = JP >= 16 ? JP / 4 : 1;
+    static_assert(NSTAGE * JT * RW * 16 >= NC * FORCE_NT * 8, "ring too small for the lane reduction");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float4* buf = reinterpret_cast<float4*>(smem_raw);
+    __shared__ __align__(8) uint64_t bars[NSTAGE];
+
+    const int tid = threadIdx.x, il = tid % NI, jl = tid / NI;
+    constexpr uint32_t TILE_BYTES = JT * RW * 16;
+
+    if (tid == 0) {
+        for (int k = 0; k < NSTAGE; ++k) mbar_init(&bars[k], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int k = 0; k < NSTAGE && k < nt; ++k) {
+            mbar_expect_tx(&bars[k], TILE_BYTES);
+            bulk_g2s(buf + k * JT * RW, js + (size_t)(t0 + k) * JT * RW, TILE_BYTES, &bars[k]);
+        }
+    }
+
+    const int p = pbase0 + il;
+    int gi = idx[p < plim ? p : plim - 1];
+    if ((unsigned)gi >= (unsigned)n) {
+        raise_status(sc, NB_ERR_ARG);
+        gi = 0;
+    }
+    IMixed I[1];
+    {
+        const float4* ri = js + (size_t)gi * RW;
+        I[0].i0 = ri[0];
+        I[0].i1 = ri[1];
+        I[0].i2 = ri[2];
+        I[0].i3 = ORDER >= 6 ? ri[3] : make_float4(0.f, 0.f, 0.f, 0.f);
+        I[0].i4 = ORDER >= 8 ? ri[4] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float ei2 = PAIR ? I[0].i1.w : eps2u;
+    const bool dom = PAIR && __all_sync(0xffffffffu, ei2 >= eps2max && ei2 > 0.0f);
+
+    float hi[NC], lo[NC], acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) hi[c] = lo[c] = acc[c] = 0.f;
+
+    for (int k = 0; k < nt; ++k) {
+        const int st = k % NSTAGE;
+        const bool ok = mbar_wait_bounded(&bars[st], (k / NSTAGE) & 1);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                raise_status(sc, NB_ERR_TIMEOUT);
+                drain_after_timeout(bars, k, nt);
+            }
+            return;
+        }
+        const float4* b = buf + st * JT * RW;
+        const int self_rel = gi - (t0 + k) * JT;
+        const bool self_here = __any_sync(0xffffffffu, (unsigned)self_rel < (unsigned)JT);
+#define NB_JP_LOOP(PP, SS)                                                                                   \
+    for (int jj = jl; jj < JT; jj += JP)                                                                     \
+        pair_mixed<ORDER, PP, SS>(b[jj * RW + 0], b[jj * RW + 1], b[jj * RW + 2],                            \
+                                  ORDER >= 6 ? b[jj * RW + 3] : make_float4(0.f, 0.f, 0.f, 0.f),             \
+                                  ORDER >= 8 ? b[jj * RW + 4] : make_float4(0.f, 0.f, 0.f, 0.f), I[0], ei2, \
+                                  SS && jj == self_rel, acc);
+        if (!PAIR || dom) {
+            if (self_here) { NB_JP_LOOP(false, true) } else { NB_JP_LOOP(false, false) }
+        } else {
+            if (self_here) { NB_JP_LOOP(true, true) } else { NB_JP_LOOP(true, false) }
+        }
+#undef NB_JP_LOOP
+        if ((k + 1) % FOLD == 0 || k + 1 == nt) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                ds_add(hi[c], lo[c], acc[c]);
+                acc[c] = 0.f;
+            }
+        }
+        __syncthreads();  // every thread is done with stage st
+        if (tid == 0 && k + NSTAGE < nt) {
+            mbar_expect_tx(&bars[st], TILE_BYTES);
+            bulk_g2s(buf + st * JT * RW, js + (size_t)(t0 + k + NSTAGE) * JT * RW, TILE_BYTES, &bars[st]);
+        }
+    }
+    // every copy has landed and been consumed: the ring holds the lane sums
+    float2* lane = reinterpret_cast<float2*>(smem_raw);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) lane[c * FORCE_NT + tid] = make_float2(hi[c], lo[c]);
+    __syncthreads();
+    for (int o = tid; o < NI * NC; o += FORCE_NT) {
+        const int oi = o % NI, c = o / NI;
+        float h = 0.f, l = 0.f;
+        for (int q = 0; q < JP; ++q) {
+            const float2 v = lane[c * FORCE_NT + q * NI + oi];
+            ds_add_ds(h, l, v.x, v.y);
+        }
+        const int pp = pbase0 + oi;
+        if (pp < plim) partial[((size_t)split * NC + c) * ncol + pp] = (double)h + (double)l;
+    }
+}
+
+// One system, j-parallel form: blockIdx.x = i-tile of FORCE_NT / JP active
+// particles, blockIdx.y = j-split of the whole store.
+template <int ORDER, int RW, bool PAIR, int JP>
+__global__ void __launch_bounds__(FORCE_NT) k_force_mixed_jp(const float4* __restrict__ js,
+                                                             const int32_t* __restrict__ idx, int n_act, int n,
+                                                             int ntiles, int jsplit, float eps2u, float eps2max,
+                                                             double* __restrict__ partial, DevScalars* sc)
+{
+    const int split = blockIdx.y;
+    const int t0 = (int)((long long)split * ntiles / jsplit);
+    const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
+    force_block_mixed_jp<ORDER, RW, PAIR, JP>(js, idx, blockIdx.x * (FORCE_NT / JP), n_act, n, t0, t1 - t0, split,
+                                              n_act, eps2u, eps2max, partial, sc);
+}
+
 // One system: blockIdx.x = i-tile of FORCE_NT * IPT active particles,
 // blockIdx.y = j-split of the whole store.
 template <int ORDER, int RW, bool PAIR, int IPT>
@@ -454,22 +582,35 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_fp64(const double2* __restri
 // cycle idle.
 
 // Persistent force: a fixed grid walks the (i-tile, split) items of the
-// device-chosen shape; a variant with another i-particles-per-thread count
-// returns at once.
-template <int ORDER, int RW, bool PAIR, int IPT>
-__global__ void __launch_bounds__(FORCE_NT) k_force_mixed_dyn(const float4* __restrict__ js,
+// device-chosen shape.  SMALL: the variants of up to FORCE_NT i-particles per
+// CTA (4, 32, 128); otherwise the two-per-thread variant (256).  The kernel
+// not matching the chosen variant returns at once.
+template <int ORDER, int RW, bool PAIR, bool SMALL>
+__global__ void __launch_bounds__(FORCE_NT, SMALL ? 1 : (ORDER >= 8 ? 3 : 4)) k_force_mixed_dyn(const float4* __restrict__ js,
                                                               const int32_t* __restrict__ idx, int n, int ntiles,
                                                               float eps2u, float eps2max, double* __restrict__ partial,
                                                               DevScalars* sc)
 {
-    if (sc->idle || sc->ipt != IPT) return;
+    if (sc->idle) return;
+    const int ni = sc->ni;
+    if (SMALL != (ni <= FORCE_NT)) return;
     const int n_act = (int)sc->n_act, it = sc->itiles, jsplit = sc->jsplit;
     for (int w = blockIdx.x; w < it * jsplit; w += gridDim.x) {
         const int itile = w % it, split = w / it;
         const int t0 = (int)((long long)split * ntiles / jsplit);
         const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
-        force_block_mixed<ORDER, RW, PAIR, IPT>(js, idx, itile * (FORCE_NT * IPT), n_act, n, t0, t1 - t0, split,
-                                                n_act, eps2u, eps2max, partial, sc);
+        if (!SMALL)
+            force_block_mixed<ORDER, RW, PAIR, 2>(js, idx, itile * ni, n_act, n, t0, t1 - t0, split, n_act, eps2u,
+                                                  eps2max, partial, sc);
+        else if (ni == FORCE_NT)
+            force_block_mixed<ORDER, RW, PAIR, 1>(js, idx, itile * ni, n_act, n, t0, t1 - t0, split, n_act, eps2u,
+                                                  eps2max, partial, sc);
+        else if (ni == FORCE_NT / 4)
+            force_block_mixed_jp<ORDER, RW, PAIR, 4>(js, idx, itile * ni, n_act, n, t0, t1 - t0, split, n_act,
+                                                     eps2u, eps2max, partial, sc);
+        else
+            force_block_mixed_jp<ORDER, RW, PAIR, 32>(js, idx, itile * ni, n_act, n, t0, t1 - t0, split, n_act,
+                                                      eps2u, eps2max, partial, sc);
         // every thread is done before the next item re-arms the ring; a
         // status raised by any CTA ends the walk
         if (__syncthreads_or(threadIdx.x == 0 && *(volatile int*)&sc->status != 0)) return;

@@ -37,12 +37,41 @@ static cudaError_t run_mixed_ipt(nb_ctx* c, const int32_t* idx, int n_act, int j
     return cudaGetLastError();
 }
 
-// Mixed path: one or two i-particles per thread.
-template <int ORDER, int RW, bool PAIR>
-static cudaError_t run_mixed(nb_ctx* c, const int32_t* idx, int n_act, int jsplit, int itiles, int* occ_out, int ipt)
+template <int ORDER, int RW, bool PAIR, int JP>
+static cudaError_t run_mixed_jp(nb_ctx* c, const int32_t* idx, int n_act, int jsplit, int itiles, int* occ_out)
 {
-    if (ipt == 2) return run_mixed_ipt<ORDER, RW, PAIR, 2>(c, idx, n_act, jsplit, itiles, occ_out);
-    return run_mixed_ipt<ORDER, RW, PAIR, 1>(c, idx, n_act, jsplit, itiles, occ_out);
+    auto kern = k_force_mixed_jp<ORDER, RW, PAIR, JP>;
+    const size_t smem = (size_t)NSTAGE * JT * RW * 16;
+    static bool configured = false;
+    static int occ = 1;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        occ = occupancy_of(kern, smem);
+        configured = true;
+    }
+    if (occ_out) {
+        *occ_out = occ;
+        return cudaSuccess;
+    }
+    dim3 grid(itiles, jsplit);
+    kern<<<grid, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), idx, n_act, (int)c->n,
+                                              (int)(c->np / JT), jsplit, (float)(c->eps * c->eps),
+                                              (float)c->eps2_max, c->partial, c->sc);
+    return cudaGetLastError();
+}
+
+// Mixed path: the variant with ni i-particles per CTA (mixed_ni).
+template <int ORDER, int RW, bool PAIR>
+static cudaError_t run_mixed(nb_ctx* c, const int32_t* idx, int n_act, int jsplit, int itiles, int* occ_out, int ni)
+{
+    switch (ni) {
+    case 2 * FORCE_NT: return run_mixed_ipt<ORDER, RW, PAIR, 2>(c, idx, n_act, jsplit, itiles, occ_out);
+    case FORCE_NT: return run_mixed_ipt<ORDER, RW, PAIR, 1>(c, idx, n_act, jsplit, itiles, occ_out);
+    case FORCE_NT / 4: return run_mixed_jp<ORDER, RW, PAIR, 4>(c, idx, n_act, jsplit, itiles, occ_out);
+    case FORCE_NT / 32: return run_mixed_jp<ORDER, RW, PAIR, 32>(c, idx, n_act, jsplit, itiles, occ_out);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 // FP64 path: bound by the FP64 pipe, one i-particle per thread.
@@ -72,13 +101,13 @@ static cudaError_t run_fp64(nb_ctx* c, const int32_t* idx, int n_act, int jsplit
 // Dispatch on (computed order, stored record layout, softening mode, precision).
 // occ_out != nullptr only queries the kernel's occupancy.
 static cudaError_t dispatch(nb_ctx* c, int order, const int32_t* idx, int n_act, int jsplit, int itiles,
-                            int* occ_out, int ipt)
+                            int* occ_out, int ni)
 {
     const bool pair = c->pair_eps || !(c->eps > 0.0);
     const int so = c->order;  // stored layout
 #define NB_CASE(PRECFN, RW, O)                                                                  \
-    if (order == O) return pair ? PRECFN<O, RW, true>(c, idx, n_act, jsplit, itiles, occ_out, ipt) \
-                                : PRECFN<O, RW, false>(c, idx, n_act, jsplit, itiles, occ_out, ipt);
+    if (order == O) return pair ? PRECFN<O, RW, true>(c, idx, n_act, jsplit, itiles, occ_out, ni) \
+                                : PRECFN<O, RW, false>(c, idx, n_act, jsplit, itiles, occ_out, ni);
 #define NB_DISPATCH(PRECFN, RWFN)       \
     if (so == 4) {                      \
         NB_CASE(PRECFN, RWFN(4), 0)     \
@@ -104,22 +133,22 @@ static cudaError_t dispatch(nb_ctx* c, int order, const int32_t* idx, int n_act,
     return cudaErrorInvalidValue;
 }
 
-int force_occupancy(nb_ctx* c, int order, int ipt)
+int force_occupancy(nb_ctx* c, int order, int ni)
 {
     int occ = 1;
-    if (dispatch(c, order, nullptr, 0, 1, 1, &occ, ipt) != cudaSuccess) return 1;
+    if (dispatch(c, order, nullptr, 0, 1, 1, &occ, ni) != cudaSuccess) return 1;
     return occ;
 }
 
-int force_ipt(const nb_ctx* c, int64_t n_act)
+int force_ni(const nb_ctx* c, int64_t n_act)
 {
     const int prec = c->pred_prec >= 0 ? c->pred_prec : c->prec;
-    return (prec == NB_MIXED && n_act >= IPT2_MIN_NACT) ? 2 : 1;
+    return prec == NB_MIXED ? mixed_ni(n_act) : FORCE_NT;
 }
 
-cudaError_t launch_force(nb_ctx* c, int order, const int32_t* idx, int64_t n_act, int jsplit, int itiles, int ipt)
+cudaError_t launch_force(nb_ctx* c, int order, const int32_t* idx, int64_t n_act, int jsplit, int itiles, int ni)
 {
-    return dispatch(c, order, idx, (int)n_act, jsplit, itiles, nullptr, ipt);
+    return dispatch(c, order, idx, (int)n_act, jsplit, itiles, nullptr, ni);
 }
 
 cudaError_t launch_force_reduce(nb_ctx* c, int order, const int32_t* idx, int64_t n_act, int jsplit)
@@ -143,9 +172,11 @@ cudaError_t launch_force_reduce(nb_ctx* c, int order, const int32_t* idx, int64_
 // ------------------------------------------------------- device-driven cycle
 // One thread: close the cycle when the next block lies past t_end, otherwise
 // pick the force launch shape exactly as the host rule does for a block of
-// that size (same slot counts, same makespan split, same forced split).
-__global__ void k_cycle_gate(DevScalars* sc, long long n, int ntiles, int slots1, int slots2, long long cap, int nc,
-                             int mixed, int js_force)
+// that size (same variant rule, same slot counts, same makespan split, same
+// forced split).  slots = SMs x occupancy of the per-launch kernels with 4,
+// 32, 128 and 256 i-particles per CTA.
+__global__ void k_cycle_gate(DevScalars* sc, long long n, int ntiles, int4 slots, long long cap, int nc, int mixed,
+                             int js_force)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const long long na = sc->n_act;
@@ -154,13 +185,13 @@ __global__ void k_cycle_gate(DevScalars* sc, long long n, int ntiles, int slots1
         return;
     }
     sc->idle = 0;
-    const int ipt = (mixed && na >= IPT2_MIN_NACT) ? 2 : 1;
-    const int slots = ipt == 2 ? slots2 : slots1;
-    const int it = (int)((na + FORCE_NT * ipt - 1) / (FORCE_NT * ipt));
-    sc->ipt = ipt;
+    const int ni = mixed ? mixed_ni(na) : FORCE_NT;
+    const int sl = ni == 4 ? slots.x : ni == 32 ? slots.y : ni == FORCE_NT ? slots.z : slots.w;
+    const int it = (int)((na + ni - 1) / ni);
+    sc->ni = ni;
     sc->itiles = it;
     const long long cap_splits = cap / ((long long)nc * na);
-    int js = js_force > 0 ? js_force : makespan_split(it, ntiles, slots, cap_splits);
+    int js = js_force > 0 ? js_force : makespan_split(it, ntiles, sl, cap_splits);
     if (js > ntiles) js = ntiles;
     if (js > cap_splits) js = (int)cap_splits;
     sc->jsplit = js < 1 ? 1 : js;
@@ -176,51 +207,53 @@ static int dyn_slots(nb_ctx* c, K kern, size_t smem)
 }
 
 // Launch (or, query_only, size) the persistent force kernels of the context's
-// order: both i-particles-per-thread variants on the mixed path.
+// order: on the mixed path one for the variants of up to FORCE_NT i-particles
+// per CTA and one for two per thread.
 template <int O>
-static cudaError_t force_dyn_o(nb_ctx* c, int* s1, int* s2, bool query_only)
+static cudaError_t force_dyn_o(nb_ctx* c, int* g_small, int* g_big, bool query_only)
 {
     const bool pair = c->pair_eps || !(c->eps > 0.0);
     const int ntiles = (int)(c->np / JT);
     if (c->prec == NB_MIXED) {
         constexpr int RW = mixed_rw(O);
         const size_t smem = (size_t)NSTAGE * JT * RW * 16;
-        auto k1 = pair ? k_force_mixed_dyn<O, RW, true, 1> : k_force_mixed_dyn<O, RW, false, 1>;
-        auto k2 = pair ? k_force_mixed_dyn<O, RW, true, 2> : k_force_mixed_dyn<O, RW, false, 2>;
+        auto k1 = pair ? k_force_mixed_dyn<O, RW, true, true> : k_force_mixed_dyn<O, RW, false, true>;
+        auto k2 = pair ? k_force_mixed_dyn<O, RW, true, false> : k_force_mixed_dyn<O, RW, false, false>;
         if (query_only) {
-            *s1 = dyn_slots(c, k1, smem);
-            *s2 = dyn_slots(c, k2, smem);
+            *g_small = dyn_slots(c, k1, smem);
+            *g_big = dyn_slots(c, k2, smem);
             return cudaSuccess;
         }
         const float e2 = (float)(c->eps * c->eps), e2max = (float)c->eps2_max;
-        k1<<<*s1, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), c->act_idx, (int)c->n,
-                                               ntiles, e2, e2max, c->partial, c->sc);
-        k2<<<*s2, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), c->act_idx, (int)c->n,
-                                               ntiles, e2, e2max, c->partial, c->sc);
+        k1<<<*g_small, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), c->act_idx,
+                                                    (int)c->n, ntiles, e2, e2max, c->partial, c->sc);
+        k2<<<*g_big, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), c->act_idx,
+                                                  (int)c->n, ntiles, e2, e2max, c->partial, c->sc);
     } else {
         constexpr int RW = fp64_rw(O);
         const size_t smem = (size_t)NSTAGE * JT * RW * 16;
         auto k1 = pair ? k_force_fp64_dyn<O, RW, true> : k_force_fp64_dyn<O, RW, false>;
         if (query_only) {
-            *s1 = *s2 = dyn_slots(c, k1, smem);
+            *g_small = *g_big = dyn_slots(c, k1, smem);
             return cudaSuccess;
         }
-        k1<<<*s1, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const double2*>(c->jstore), c->act_idx, (int)c->n,
-                                               ntiles, c->eps * c->eps, c->partial, c->sc);
+        k1<<<*g_small, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const double2*>(c->jstore), c->act_idx,
+                                                    (int)c->n, ntiles, c->eps * c->eps, c->partial, c->sc);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_force_dyn(nb_ctx* c, int* slots1, int* slots2, bool query_only)
+cudaError_t launch_force_dyn(nb_ctx* c, int* g_small, int* g_big, bool query_only)
 {
-    if (c->order == 4) return force_dyn_o<4>(c, slots1, slots2, query_only);
-    if (c->order == 6) return force_dyn_o<6>(c, slots1, slots2, query_only);
-    return force_dyn_o<8>(c, slots1, slots2, query_only);
+    if (c->order == 4) return force_dyn_o<4>(c, g_small, g_big, query_only);
+    if (c->order == 6) return force_dyn_o<6>(c, g_small, g_big, query_only);
+    return force_dyn_o<8>(c, g_small, g_big, query_only);
 }
 
-cudaError_t launch_cycle_gate(nb_ctx* c, int slots1, int slots2)
+cudaError_t launch_cycle_gate(nb_ctx* c, const int* shape_slots)
 {
-    k_cycle_gate<<<1, 32, 0, c->stream>>>(c->sc, c->n, (int)(c->np / JT), slots1, slots2, (long long)c->partial_cap,
+    const int4 sl = make_int4(shape_slots[0], shape_slots[1], shape_slots[2], shape_slots[3]);
+    k_cycle_gate<<<1, 32, 0, c->stream>>>(c->sc, c->n, (int)(c->np / JT), sl, (long long)c->partial_cap,
                                           ncomp(c->order), c->prec == NB_MIXED, c->jsplit_force);
     return cudaGetLastError();
 }

@@ -13,14 +13,15 @@ namespace nb {
 // ===================================================================== K5
 // Block scheduler (abstract: individual hierarchical block time-steps):
 // t_blk = min_i (t_i + dt_i), active = {i : t_i + dt_i == t_blk} ascending.
-// Three passes, no atomics, deterministic:
-//   1. per-CTA minima -> red[]
-//   2. every chunk CTA reduces red[] to t_blk and counts its matches
-//   3. every chunk CTA adds the counts of the chunks before it and scatters
-//      its matches in index order using warp ballots and prefix sums.
+// Two passes, no atomics, deterministic.  Chunk b = SCHED_NT threads x `per`
+// consecutive particles each (per from sched_layout).
+//   1. chunk b publishes m_b = its minimum of t_i + dt_i and c_b = how many of
+//      its particles reach m_b;
+//   2. every chunk reads the table: t_blk = min_b m_b, its offset = sum of c_b'
+//      over earlier chunks with m_b' == t_blk; a chunk with m_b == t_blk
+//      writes its matches in index order (one block-wide exclusive scan).
 constexpr int SCHED_NT = 256;
-constexpr int SCHED_PER = 8;
-constexpr int SCHED_CHUNK = SCHED_NT * SCHED_PER;
+constexpr int SCHED_PER_MAX = 16;
 
 __device__ __forceinline__ double warp_min(double v)
 {
@@ -40,127 +41,131 @@ __device__ __forceinline__ int warp_isum(int v)
     return v;
 }
 
-__global__ void __launch_bounds__(SCHED_NT) k_sched_min(const double* __restrict__ t, const double* __restrict__ dt,
-                                                        int64_t n, double* __restrict__ red, DevScalars* sc)
+// minimum over the CTA; every thread gets it
+__device__ __forceinline__ double block_min(double v, double* ws)
 {
-    __shared__ double ws[SCHED_NT / 32];
+    v = warp_min(v);
+    __syncthreads();  // ws reuse
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double b = ws[0];
+    for (int w = 1; w < SCHED_NT / 32; ++w) b = fmin(b, ws[w]);
+    return b;
+}
+
+// sum over the CTA; every thread gets it
+__device__ __forceinline__ int block_isum(int v, int* ws)
+{
+    v = warp_isum(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+    __syncthreads();
+    int s = 0;
+    for (int w = 0; w < SCHED_NT / 32; ++w) s += ws[w];
+    return s;
+}
+
+__global__ void __launch_bounds__(SCHED_NT) k_sched_chunk(const double* __restrict__ t, const double* __restrict__ dt,
+                                                          int64_t n, int per, double* __restrict__ cmin,
+                                                          int32_t* __restrict__ ccnt, DevScalars* sc)
+{
+    __shared__ double wd[SCHED_NT / 32];
+    __shared__ int wi[SCHED_NT / 32];
+    const int64_t i0 = ((int64_t)blockIdx.x * SCHED_NT + threadIdx.x) * per;
+    double tn[SCHED_PER_MAX];
     double mn = INFINITY;
     bool bad = false;
-    for (int64_t i = (int64_t)blockIdx.x * SCHED_NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * SCHED_NT) {
-        const double tn = t[i] + dt[i];
-        bad |= !(tn == tn);
-        mn = fmin(mn, tn);
+#pragma unroll
+    for (int k = 0; k < SCHED_PER_MAX; ++k) {
+        tn[k] = INFINITY;
+        if (k < per && i0 + k < n) {
+            tn[k] = t[i0 + k] + dt[i0 + k];
+            bad |= !(tn[k] == tn[k]);
+            mn = fmin(mn, tn[k]);
+        }
     }
     if (bad) raise_status(sc, NB_ERR_NAN);
-    mn = warp_min(mn);
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = mn;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double b = ws[0];
-        for (int w = 1; w < SCHED_NT / 32; ++w) b = fmin(b, ws[w]);
-        red[blockIdx.x] = b;
-    }
-}
-
-__device__ double block_min_of(const double* red, int nred)
-{
-    __shared__ double ws[SCHED_NT / 32];
-    __shared__ double res;
-    double mn = INFINITY;
-    for (int k = threadIdx.x; k < nred; k += SCHED_NT) mn = fmin(mn, red[k]);
-    mn = warp_min(mn);
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = mn;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double b = ws[0];
-        for (int w = 1; w < SCHED_NT / 32; ++w) b = fmin(b, ws[w]);
-        res = b;
-    }
-    __syncthreads();
-    return res;
-}
-
-__global__ void __launch_bounds__(SCHED_NT) k_sched_count(const double* __restrict__ t, const double* __restrict__ dt,
-                                                          int64_t n, const double* __restrict__ red, int nred,
-                                                          int32_t* __restrict__ cnt, DevScalars* sc)
-{
-    __shared__ int wc[SCHED_NT / 32];
-    const double tb = block_min_of(red, nred);
-    if (blockIdx.x == 0 && threadIdx.x == 0) sc->t_blk = tb;
-    const int64_t base = (int64_t)blockIdx.x * SCHED_CHUNK;
+    const double m_b = block_min(mn, wd);
     int c = 0;
-    for (int it = 0; it < SCHED_PER; ++it) {
-        const int64_t i = base + it * SCHED_NT + threadIdx.x;
-        if (i < n && t[i] + dt[i] == tb) ++c;
-    }
-    c = warp_isum(c);
-    if ((threadIdx.x & 31) == 0) wc[threadIdx.x >> 5] = c;
-    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < SCHED_PER_MAX; ++k) c += (k < per && i0 + k < n && tn[k] == m_b) ? 1 : 0;
+    c = block_isum(c, wi);
     if (threadIdx.x == 0) {
-        int s = 0;
-        for (int w = 0; w < SCHED_NT / 32; ++w) s += wc[w];
-        cnt[blockIdx.x] = s;
+        cmin[blockIdx.x] = m_b;
+        ccnt[blockIdx.x] = c;
     }
 }
 
-__global__ void __launch_bounds__(SCHED_NT) k_sched_scatter(const double* __restrict__ t, const double* __restrict__ dt,
-                                                            int64_t n, const int32_t* __restrict__ cnt, int nchunks,
+__global__ void __launch_bounds__(SCHED_NT) k_sched_compact(const double* __restrict__ t,
+                                                            const double* __restrict__ dt, int64_t n, int per,
+                                                            const double* __restrict__ cmin,
+                                                            const int32_t* __restrict__ ccnt, int nch,
                                                             int32_t* __restrict__ idx, DevScalars* sc)
 {
-    __shared__ int wtot[SCHED_NT / 32];
-    __shared__ int s_base;
+    __shared__ double wd[SCHED_NT / 32];
+    __shared__ int wi[SCHED_NT / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // offset of this chunk = sum of the counts before it
-    int o = 0;
-    for (int k = threadIdx.x; k < (int)blockIdx.x; k += SCHED_NT) o += cnt[k];
-    o = warp_isum(o);
-    if (lane == 0) wtot[warp] = o;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int s = 0;
-        for (int w = 0; w < SCHED_NT / 32; ++w) s += wtot[w];
-        s_base = s;
+    double mn = INFINITY;
+    for (int k = threadIdx.x; k < nch; k += SCHED_NT) mn = fmin(mn, cmin[k]);
+    const double tb = block_min(mn, wd);
+    int before = 0, total = 0;
+    for (int k = threadIdx.x; k < nch; k += SCHED_NT) {
+        const int ck = cmin[k] == tb ? ccnt[k] : 0;
+        total += ck;
+        if (k < (int)blockIdx.x) before += ck;
     }
-    __syncthreads();
-    int base = s_base;
-    const double tb = sc->t_blk;
-    const int64_t c0 = (int64_t)blockIdx.x * SCHED_CHUNK;
-    for (int it = 0; it < SCHED_PER; ++it) {
-        __syncthreads();  // wtot reuse
-        const int64_t i = c0 + it * SCHED_NT + threadIdx.x;
-        const bool f = i < n && t[i] + dt[i] == tb;
-        const unsigned bal = __ballot_sync(0xffffffffu, f);
-        if (lane == 0) wtot[warp] = __popc(bal);
-        __syncthreads();
-        int woff = 0, tot = 0;
-        for (int w = 0; w < SCHED_NT / 32; ++w) {
-            const int x = wtot[w];
-            if (w < warp) woff += x;
-            tot += x;
-        }
-        if (f) idx[base + woff + __popc(bal & ((1u << lane) - 1u))] = (int32_t)i;
-        base += tot;
+    total = block_isum(total, wi);
+    const int off = block_isum(before, wi);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc->t_blk = tb;
+        sc->n_act = total;
     }
-    if (blockIdx.x == nchunks - 1 && threadIdx.x == 0) sc->n_act = base;
+    if (cmin[blockIdx.x] != tb) return;  // CTA-uniform
+    const int64_t i0 = ((int64_t)blockIdx.x * SCHED_NT + threadIdx.x) * per;
+    unsigned flags = 0;
+#pragma unroll
+    for (int k = 0; k < SCHED_PER_MAX; ++k)
+        if (k < per && i0 + k < n && t[i0 + k] + dt[i0 + k] == tb) flags |= 1u << k;
+    // exclusive scan of the per-thread match counts over the CTA
+    const int mine = __popc(flags);
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    __syncthreads();  // wi reuse
+    if (lane == 31) wi[warp] = incl;
+    __syncthreads();
+    int wbase = 0;
+    for (int w = 0; w < warp; ++w) wbase += wi[w];
+    int pos = off + wbase + incl - mine;
+    while (flags) {
+        const int k = __ffs(flags) - 1;
+        flags &= flags - 1;
+        idx[pos++] = (int32_t)(i0 + k);
+    }
 }
 
-int sched_grid(const nb_ctx* c)
+// Particles per scheduler thread (about one wave of CTAs, at most
+// SCHED_PER_MAX) and the number of chunks.
+void sched_layout(int64_t n, int sm_count, int* per, int* nch)
 {
-    int g = c->sm_count * 2;
-    const int64_t need = (c->n + SCHED_NT - 1) / SCHED_NT;
-    if (need < g) g = (int)need;
-    return g < 1 ? 1 : g;
+    const int64_t lanes = (int64_t)SCHED_NT * (sm_count > 0 ? sm_count : 1);
+    int64_t p = (n + lanes - 1) / lanes;
+    if (p < 1) p = 1;
+    if (p > SCHED_PER_MAX) p = SCHED_PER_MAX;
+    *per = (int)p;
+    *nch = (int)((n + (int64_t)SCHED_NT * p - 1) / ((int64_t)SCHED_NT * p));
 }
-
-int sched_chunks(int64_t n) { return (int)((n + SCHED_CHUNK - 1) / SCHED_CHUNK); }
 
 cudaError_t launch_sched(nb_ctx* c)
 {
-    const int g = sched_grid(c);
-    const int nch = sched_chunks(c->n);
-    k_sched_min<<<g, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, c->red, c->sc);
-    k_sched_count<<<nch, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, c->red, g, c->chunk_cnt, c->sc);
-    k_sched_scatter<<<nch, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, c->chunk_cnt, nch, c->act_idx, c->sc);
+    int per, nch;
+    sched_layout(c->n, c->sm_count, &per, &nch);
+    k_sched_chunk<<<nch, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, per, c->chunk_min, c->chunk_cnt, c->sc);
+    k_sched_compact<<<nch, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, per, c->chunk_min, c->chunk_cnt, nch,
+                                                     c->act_idx, c->sc);
     return cudaGetLastError();
 }
 
@@ -278,8 +283,35 @@ cudaError_t launch_predict(nb_ctx* c, double t, const double* tpc, const int32_t
 }
 
 // ===================================================================== K4
+// 2^j, the largest power of two that divides the dyadic t1 exactly: a normal
+// t1 is mant * 2^(e - 1075) with an integer 53-bit mant, so j = e - 1075 +
+// (trailing zeros of mant).  +inf for t1 == 0 (every step divides it).
+__device__ __forceinline__ double pow2_dividing(double t1)
+{
+    const long long b = __double_as_longlong(t1);
+    const int e = (int)((b >> 52) & 0x7FF);
+    const long long mant = (b & 0xFFFFFFFFFFFFFLL) | (e ? (1LL << 52) : 0LL);
+    if (mant == 0) return INFINITY;
+    const int j = (e ? e : 1) - 1075 + (__ffsll(mant) - 1);
+    if (j > 1023) return INFINITY;
+    if (j < -1022) return 0.0;
+    return __longlong_as_double((long long)(j + 1023) << 52);
+}
+
+// 1/h; exact bit arithmetic when h is a power of two (the usual case: an
+// active particle's h is its own step), else a division (same result).
+__device__ __forceinline__ double recip(double h)
+{
+    const long long b = __double_as_longlong(h);
+    const int e = (int)((b >> 52) & 0x7FF);
+    if ((b & 0xFFFFFFFFFFFFFLL) == 0 && e > 1 && e < 2045)
+        return __longlong_as_double((b & (long long)0x8000000000000000ULL) | ((long long)(2046 - e) << 52));
+    return 1.0 / h;
+}
+
 // Quantised block step: the largest power of two <= min(lim, dt_max) that
-// divides t1 (all block times are dyadic, so the divisibility test is exact).
+// divides t1 (all block times are dyadic, so divisibility is exact): the
+// mantissa-cleared lim, capped by the largest power of two dividing t1.
 __device__ double quantise_dt(double lim, double t1, double dt_max, double dt_min, DevScalars* sc)
 {
     if (!(lim == lim)) {
@@ -296,11 +328,7 @@ __device__ double quantise_dt(double lim, double t1, double dt_max, double dt_mi
         // clear the mantissa: 2^floor(log2(lim)) for a positive normal double
         dt = __longlong_as_double(__double_as_longlong(lim) & 0xFFF0000000000000LL);
     }
-    while (dt >= dt_min) {
-        const double q = t1 / dt;
-        if (q == floor(q)) break;
-        dt *= 0.5;
-    }
+    dt = fmin(dt, pow2_dividing(t1));
     if (dt < dt_min) {
         raise_status(sc, NB_ERR_DT_UNDERFLOW);
         return dt_min;
@@ -338,9 +366,8 @@ __device__ double dt_criterion(double eta, const double* nrm)
 // treated as unknown (zero) rather than as signal.  With all eps = 0 the
 // criterion is the plain one.  nL[r], nR[r] = |a^(r)| at t0 and t1.
 template <int ORDER>
-__device__ void noise_floor(const double* nL, const double* nR, double h, const double* e, double* N)
+__device__ void noise_floor(const double* nL, const double* nR, double h, double ih, const double* e, double* N)
 {
-    const double ih = 1.0 / h;
     const double A = e[0] * (nL[0] + nR[0]);
     if (ORDER == 4) {
         N[2] = 2.0 * (3.0 * A + h * e[1] * (nL[1] + 2.0 * nR[1])) * ih * ih;
@@ -409,7 +436,7 @@ __global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fid
     const double potn = F[(size_t)(3 * MM) * fn + p];
     const double bacc = F[(size_t)(3 * MM + 1) * fn + p];  // sum_j m_j / R_ij^2
 
-    const double ih = 1.0 / h;
+    const double ih = recip(h);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const double L0 = L[0][c], L1 = L[1][c], L2 = L[2][c], L3 = L[3][c];
@@ -474,7 +501,7 @@ __global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fid
     // rounding of a total scales with the terms it sums: kappa = B / |a| >= 1
     const double kappa = nR[0] > 0.0 ? fmax(1.0, bacc / nR[0]) : 1.0;
     const double ek[4] = {ne.e[0] * kappa, ne.e[1] * kappa, ne.e[2] * kappa, ne.e[3] * kappa};
-    noise_floor<ORDER>(nL, nR, h, ek, N);
+    noise_floor<ORDER>(nL, nR, h, ih, ek, N);
 #pragma unroll
     for (int k = MM; k < 2 * MM; ++k) nrm[k] = fmax(nrm[k] - N[k], 0.0);
     double lim = dt_criterion<ORDER>(eta, nrm);

@@ -166,16 +166,16 @@ int sync_scalars(nb_ctx* c)
 // Launch shape of the force: FORCE_NT i-particles per CTA; the j range is
 // split so that small active sets still fill every SM (j-split), capped by the
 // partial-sum buffer.
-void choose_shape(nb_ctx* c, int order, int64_t n_act, int* itiles, int* jsplit, int* ipt_out)
+void choose_shape(nb_ctx* c, int order, int64_t n_act, int* itiles, int* jsplit, int* ni_out)
 {
-    const int ipt = force_ipt(c, n_act);
-    *ipt_out = ipt;
-    const int it = (int)((n_act + FORCE_NT * ipt - 1) / (FORCE_NT * ipt));
+    const int ni = force_ni(c, n_act);
+    *ni_out = ni;
+    const int it = (int)((n_act + ni - 1) / ni);
     const int ntiles = (int)(c->np / JT);
     const long long cap_splits = (long long)(c->partial_cap / ((size_t)ncomp(order) * (size_t)n_act));
     int js = c->jsplit_force > 0
                  ? c->jsplit_force
-                 : makespan_split(it, ntiles, c->sm_count * force_occupancy(c, order, ipt), cap_splits);
+                 : makespan_split(it, ntiles, c->sm_count * force_occupancy(c, order, ni), cap_splits);
     if (js > ntiles) js = ntiles;
     if (js > cap_splits) js = (int)cap_splits;
     if (js < 1) js = 1;
@@ -185,14 +185,13 @@ void choose_shape(nb_ctx* c, int order, int64_t n_act, int* itiles, int* jsplit,
 
 int run_force(nb_ctx* c, int order, const int32_t* idx_dev, int64_t n_act)
 {
-    int it, js, ipt;
-    choose_shape(c, order, n_act, &it, &js, &ipt);
-    NB_CUDA(c, timed(c, NB_PHASE_FORCE, 1, [&] { return launch_force(c, order, idx_dev, n_act, js, it, ipt); }));
+    int it, js, ni;
+    choose_shape(c, order, n_act, &it, &js, &ni);
+    NB_CUDA(c, timed(c, NB_PHASE_FORCE, 1, [&] { return launch_force(c, order, idx_dev, n_act, js, it, ni); }));
     NB_CUDA(c, timed(c, NB_PHASE_REDUCE, 1, [&] { return launch_force_reduce(c, order, idx_dev, n_act, js); }));
     c->last_itiles = it;
     c->last_jsplit = js;
-    c->last_threads = FORCE_NT * ipt;
-    c->last_ipt = ipt;
+    c->last_threads = ni;
     c->F_order = order;
     c->F_n = n_act;
     return NB_OK;
@@ -219,8 +218,10 @@ int build_graph(nb_ctx* c)
     NB_CUDA(c, launch_force_dyn(c, &s1, &s2, true));
     // the split rule sees the per-launch kernels' slot counts, so a block
     // gets the same shape (and the same summation order) in both modes
-    const int sh1 = c->sm_count * force_occupancy(c, c->order, 1);
-    const int sh2 = c->prec == NB_MIXED ? c->sm_count * force_occupancy(c, c->order, 2) : sh1;
+    int shape_slots[4];
+    const int variants[4] = {4, 32, FORCE_NT, 2 * FORCE_NT};
+    for (int k = 0; k < 4; ++k)
+        shape_slots[k] = c->sm_count * force_occupancy(c, c->order, c->prec == NB_MIXED ? variants[k] : FORCE_NT);
     if (!c->graph_stream) NB_CUDA(c, cudaStreamCreateWithFlags(&c->graph_stream, cudaStreamNonBlocking));
     cudaStream_t saved = c->stream;
     c->stream = c->graph_stream;
@@ -228,7 +229,7 @@ int build_graph(nb_ctx* c)
     cudaError_t e = cudaStreamBeginCapture(c->graph_stream, cudaStreamCaptureModeThreadLocal);
     for (int r = 0; e == cudaSuccess && r < c->graph_cycles; ++r) {
         if ((e = launch_sched(c)) != cudaSuccess) break;
-        if ((e = launch_cycle_gate(c, sh1, sh2)) != cudaSuccess) break;
+        if ((e = launch_cycle_gate(c, shape_slots)) != cudaSuccess) break;
         if ((e = launch_predict(c, 0.0, nullptr, nullptr, c->sc)) != cudaSuccess) break;
         if ((e = launch_force_dyn(c, &s1, &s2, false)) != cudaSuccess) break;
         if ((e = launch_force_reduce_dyn(c)) != cudaSuccess) break;
@@ -258,9 +259,9 @@ int step_until_graph(nb_ctx* c, double t_end, int64_t* n_blocks, int64_t* n_inte
     h->blocks = 0;
     h->inter = 0;
     NB_CUDA(c, cudaMemcpy(c->sc, h, sizeof(DevScalars), cudaMemcpyHostToDevice));
-    // scheduler 3, gate, predictor, force (both i-per-thread variants on the
+    // scheduler 2, gate, predictor, force (both i-per-thread variants on the
     // mixed path), reduction, corrector
-    const long long per_cycle = 3 + 1 + 1 + (c->prec == NB_MIXED ? 2 : 1) + 1 + 1;
+    const long long per_cycle = 2 + 1 + 1 + (c->prec == NB_MIXED ? 2 : 1) + 1 + 1;
     for (;;) {
         NB_CUDA(c, cudaGraphLaunch(c->graph_exec, c->graph_stream));
         c->n_launch += per_cycle * c->graph_cycles;
@@ -313,7 +314,7 @@ void nb_destroy(nb_ctx* c)
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     void* ptrs[] = {c->m, c->eps2, c->x, c->v, c->d, c->t, c->dt, c->pot, c->jstore, c->act_idx, c->all_idx,
-                    c->chunk_cnt, c->sc, c->red, c->f_idx, c->partial, c->F};
+                    c->chunk_cnt, c->chunk_min, c->sc, c->red, c->f_idx, c->partial, c->F};
     for (void* p : ptrs) dfree(c, p);
     if (c->h_sc) cudaFreeHost(c->h_sc);
     if (c->h_red) cudaFreeHost(c->h_red);
@@ -358,7 +359,8 @@ int nb_create(nb_ctx** out, int64_t n, int order, double eps)
     const size_t np = (size_t)c->np;
     const int nc = ncomp(order);
     const size_t rec = (size_t)(fp64_rw(order) > mixed_rw(order) ? fp64_rw(order) : mixed_rw(order)) * 16;
-    c->n_chunks = sched_chunks(n);
+    int sched_per = 1;
+    sched_layout(n, c->sm_count, &sched_per, &c->n_chunks);
     c->red_len = 4 * c->sm_count + 8;
     if (c->red_len < 2 * c->sm_count) c->red_len = 2 * c->sm_count;
     const size_t span = (size_t)2 * 16 * c->sm_count * FORCE_NT;
@@ -369,6 +371,7 @@ int nb_create(nb_ctx** out, int64_t n, int order, double eps)
         (rc = dalloc(c, reinterpret_cast<unsigned char**>(&c->jstore), np * rec)) ||
         (rc = dalloc(c, &c->act_idx, (size_t)n)) || (rc = dalloc(c, &c->all_idx, (size_t)n)) ||
         (rc = dalloc(c, &c->f_idx, (size_t)n)) || (rc = dalloc(c, &c->chunk_cnt, (size_t)c->n_chunks)) ||
+        (rc = dalloc(c, &c->chunk_min, (size_t)c->n_chunks)) ||
         (rc = dalloc(c, &c->sc, 1)) || (rc = dalloc(c, &c->red, (size_t)c->red_len)) ||
         (rc = dalloc(c, &c->partial, c->partial_cap)) || (rc = dalloc(c, &c->F, (size_t)nc * (size_t)n)))
         return fail(rc);
@@ -537,7 +540,7 @@ int nb_next_block(nb_ctx* c, double* t_blk, int32_t* idx_out, int64_t* n_act)
 {
     if (!c) return NB_ERR_ARG;
     if (!c->have_particles) return set_err(c, NB_ERR_ARG, "nb_next_block before nb_set_particles");
-    NB_CUDA(c, timed(c, NB_PHASE_SCHED, 3, [&] { return launch_sched(c); }));
+    NB_CUDA(c, timed(c, NB_PHASE_SCHED, 2, [&] { return launch_sched(c); }));
     NB_TRY(sync_scalars(c));
     c->sched_t = c->h_sc->t_blk;
     c->sched_n = c->h_sc->n_act;

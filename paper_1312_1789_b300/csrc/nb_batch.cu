@@ -29,11 +29,12 @@ namespace {
 
 struct BatchItem {
     int list_off;  // first position in the active list
-    int count;     // i-particles of this item (<= FORCE_NT)
+    int count;     // i-particles of this item (<= ni)
     int jt0;       // first j tile (global)
     int nt;        // j tiles
     int split;     // row of the partial sums
-    int pad[3];
+    int ni;        // mixed launch variant: 4, 32 or FORCE_NT i-particles per CTA
+    int pad[2];
 };
 
 }  // namespace
@@ -204,7 +205,10 @@ __global__ void k_batch_counts(int K, const int32_t* __restrict__ kstart, int32_
     if (k < K && kcount[k] > 0) kcount[k] -= kstart[k];
 }
 
-template <int ORDER, int RW, int IPT>
+// One item per CTA, in the item's launch variant (the cluster's active-set
+// size picks it with the rule of a single system, mixed_ni, capped at one
+// i-particle per thread).
+template <int ORDER, int RW>
 __global__ void __launch_bounds__(FORCE_NT) k_batch_force_mixed(const float4* __restrict__ js,
                                                                 const int32_t* __restrict__ list,
                                                                 const BatchItem* __restrict__ items, int n_act, int n,
@@ -212,8 +216,16 @@ __global__ void __launch_bounds__(FORCE_NT) k_batch_force_mixed(const float4* __
                                                                 DevScalars* sc)
 {
     const BatchItem it = items[blockIdx.x];
-    force_block_mixed<ORDER, RW, true, IPT>(js, list, it.list_off, it.list_off + it.count, n, it.jt0, it.nt, it.split,
-                                            n_act, 0.0f, eps2max, partial, sc);
+    const int lim = it.list_off + it.count;
+    if (it.ni == FORCE_NT)
+        force_block_mixed<ORDER, RW, true, 1>(js, list, it.list_off, lim, n, it.jt0, it.nt, it.split, n_act, 0.0f,
+                                              eps2max, partial, sc);
+    else if (it.ni == FORCE_NT / 4)
+        force_block_mixed_jp<ORDER, RW, true, 4>(js, list, it.list_off, lim, n, it.jt0, it.nt, it.split, n_act, 0.0f,
+                                                 eps2max, partial, sc);
+    else
+        force_block_mixed_jp<ORDER, RW, true, 32>(js, list, it.list_off, lim, n, it.jt0, it.nt, it.split, n_act,
+                                                  0.0f, eps2max, partial, sc);
 }
 
 template <int ORDER, int RW>
@@ -402,7 +414,7 @@ int batch_force_dispatch(nb_batch* b, int order, const int32_t* list, int n_act,
         if (mixed) {                                                                                              \
             constexpr int RW = mixed_rw(SO);                                                                      \
             const size_t smem = (size_t)NSTAGE * JT * RW * 16;                                                    \
-            auto kern = k_batch_force_mixed<O, RW, 1>;                                                            \
+            auto kern = k_batch_force_mixed<O, RW>;                                                            \
             const int occ = occ_of(kern, smem);                                                                   \
             if (occ_only) return occ;                                                                             \
             kern<<<nitems, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), list,         \
@@ -469,16 +481,18 @@ int batch_force(nb_batch* b, int order, const int32_t* list, int n_act, const in
     const double target = std::max(work / (4.0 * occ * c->sm_count), (double)FORCE_NT * JT);
     int smax = 1;
     size_t nitems = 0;
+    const bool mixed = c->pred_prec == NB_MIXED;  // the kernel batch_force_call launches
+    auto variant = [&](int count) { return mixed ? std::min(mixed_ni(count), FORCE_NT) : FORCE_NT; };
     for (int k = 0; k < b->K; ++k) {
         b->h_ksplit[k] = 1;
         if (h_count[k] <= 0) continue;
-        const int jt = (int)(b->pk[k] / JT);
-        const double item_work = (double)std::min(h_count[k], FORCE_NT) * (double)b->pk[k];
+        const int jt = (int)(b->pk[k] / JT), ni = variant(h_count[k]);
+        const double item_work = (double)std::min(h_count[k], ni) * (double)b->pk[k];
         int s = (int)std::ceil(item_work / target);
         s = std::max(1, std::min(s, jt));
         b->h_ksplit[k] = s;
         smax = std::max(smax, s);
-        nitems += (size_t)((h_count[k] + FORCE_NT - 1) / FORCE_NT) * s;
+        nitems += (size_t)((h_count[k] + ni - 1) / ni) * s;
     }
     while (smax > 1 && (size_t)smax * nc * (size_t)n_act > c->partial_cap) {
         --smax;
@@ -498,11 +512,13 @@ int batch_force(nb_batch* b, int order, const int32_t* list, int n_act, const in
     for (int k = 0; k < b->K; ++k) {
         if (h_count[k] <= 0) continue;
         const int jt = (int)(b->pk[k] / JT), jt0 = (int)(b->off[k] / JT), s_k = b->h_ksplit[k];
-        for (int i0 = 0; i0 < h_count[k]; i0 += FORCE_NT)
+        const int ni = variant(h_count[k]);
+        for (int i0 = 0; i0 < h_count[k]; i0 += ni)
             for (int s = 0; s < s_k; ++s) {
                 BatchItem it{};
                 it.list_off = h_start[k] + i0;
-                it.count = std::min(FORCE_NT, h_count[k] - i0);
+                it.count = std::min(ni, h_count[k] - i0);
+                it.ni = ni;
                 const int a = (int)((long long)s * jt / s_k), e = (int)((long long)(s + 1) * jt / s_k);
                 it.jt0 = jt0 + a;
                 it.nt = e - a;

@@ -26,6 +26,23 @@ constexpr int JT = 128;
 constexpr int FORCE_NT = 128;
 // the mixed force uses two i-particles per thread from this active-set size on
 constexpr int IPT2_MIN_NACT = 1024;
+
+// Launch variant of the mixed force, named by its i-particles per CTA:
+//   256: two per thread (n_act >= IPT2_MIN_NACT);
+//   128: one per thread (n_act > 96);
+//   32, 4: j-parallel -- 4 or 32 threads share an i-particle, each taking
+//          every 4th / 32nd record of a j tile, so that a few active
+//          particles still keep a CTA's threads busy (n_act <= 96: at most
+//          three i-tiles; n_act <= 4: one).
+// More i-tiles would each stream the whole j range again, so the smaller
+// variants stop where they would need more than three.  The FP64 force
+// always runs 128.
+__host__ __device__ inline int mixed_ni(long long n_act)
+{
+    if (n_act >= IPT2_MIN_NACT) return 2 * FORCE_NT;
+    if (n_act > 96) return FORCE_NT;
+    return n_act > 4 ? 32 : 4;
+}
 // stages of the force kernel's shared-memory ring.
 constexpr int NSTAGE = 3;
 // spin limit of a bounded mbarrier wait, in SM clock cycles (~2 s at 2 GHz).
@@ -86,7 +103,7 @@ struct DevScalars {
     int status;       // first error raised by a kernel (NB_OK if none)
     int idle;         // device-driven cycle: the block is past t_end, do nothing
     double t_end;     // device-driven cycle: stop time
-    int itiles, jsplit, ipt, pad2;  // device-driven cycle: force launch shape
+    int itiles, jsplit, ni, pad2;  // device-driven cycle: force launch shape
     long long blocks, inter;        // device-driven cycle: blocks taken, interactions
 };
 
@@ -176,6 +193,16 @@ __device__ __forceinline__ void ds_add(float& hi, float& lo, float x)
     lo += e;
 }
 
+// (hi, lo) += (bh, bl), compensated (double-single sum).
+__device__ __forceinline__ void ds_add_ds(float& hi, float& lo, float bh, float bl)
+{
+    float s, e;
+    two_sum(hi, bh, s, e);
+    e += lo + bl;
+    hi = s + e;
+    lo = e - (hi - s);
+}
+
 }  // namespace nb
 
 // ------------------------------------------------------------ the context
@@ -205,7 +232,8 @@ struct nb_ctx {
     // scheduler
     int32_t* act_idx = nullptr;   // [n] active list
     int32_t* all_idx = nullptr;   // [n] 0..n-1
-    int32_t* chunk_cnt = nullptr; // per-chunk counts
+    int32_t* chunk_cnt = nullptr; // scheduler: per-chunk match counts
+    double* chunk_min = nullptr;  // scheduler: per-chunk minima of t + dt
     int n_chunks = 0;
     nb::DevScalars* sc = nullptr;
     nb::DevScalars* h_sc = nullptr;  // pinned
@@ -227,7 +255,7 @@ struct nb_ctx {
     int64_t sched_n = 0;        // result of the last scheduler pass
     double sched_t = 0.0;
     int have_sched = 0;
-    int last_itiles = 0, last_jsplit = 0, last_threads = 0, last_ipt = 1;
+    int last_itiles = 0, last_jsplit = 0, last_threads = 0;
     // profiling: event pairs around launches, folded into totals at syncs
     struct ProfRec {
         cudaEvent_t a, b;
@@ -258,23 +286,24 @@ cudaError_t launch_sched(nb_ctx* c);
 // dyn (device-driven cycle): take the time from dyn->t_blk and do nothing when dyn->idle.
 cudaError_t launch_predict(nb_ctx* c, double t, const double* tpc = nullptr, const int32_t* cid = nullptr,
                            const DevScalars* dyn = nullptr);
-cudaError_t launch_force(nb_ctx* c, int order, const int32_t* idx, int64_t n_act, int jsplit, int itiles, int ipt);
+// ni: the launch variant, i-particles per CTA (force_ni)
+cudaError_t launch_force(nb_ctx* c, int order, const int32_t* idx, int64_t n_act, int jsplit, int itiles, int ni);
 cudaError_t launch_force_reduce(nb_ctx* c, int order, const int32_t* idx, int64_t n_act, int jsplit);
 cudaError_t launch_correct(nb_ctx* c, const double* tfc = nullptr, const int32_t* cid = nullptr,
                            const DevScalars* dyn = nullptr);
 // Device-driven block cycle (CUDA-graph capturable): shape gate, persistent
 // force over device-chosen items, reduction; all read n_act / t_blk on the device.
-cudaError_t launch_cycle_gate(nb_ctx* c, int slots1, int slots2);
-cudaError_t launch_force_dyn(nb_ctx* c, int* slots1, int* slots2, bool query_only);
+// shape_slots[4]: SMs x occupancy of the per-launch kernels with 4, 32, 128, 256 i-particles per CTA
+cudaError_t launch_cycle_gate(nb_ctx* c, const int* shape_slots);
+cudaError_t launch_force_dyn(nb_ctx* c, int* grid_small, int* grid_big, bool query_only);
 cudaError_t launch_force_reduce_dyn(nb_ctx* c);
 cudaError_t launch_startup_store(nb_ctx* c, int order);
 cudaError_t launch_startup_dt(nb_ctx* c);
 cudaError_t launch_energy_sums(nb_ctx* c, int with_pot);
 cudaError_t launch_set_dt(nb_ctx* c, double dt);
-int force_occupancy(nb_ctx* c, int order, int ipt);
-int force_ipt(const nb_ctx* c, int64_t n_act);
-int sched_grid(const nb_ctx* c);
-int sched_chunks(int64_t n);
+int force_occupancy(nb_ctx* c, int order, int ni);
+int force_ni(const nb_ctx* c, int64_t n_act);
+void sched_layout(int64_t n, int sm_count, int* per, int* nch);
 int energy_grid(const nb_ctx* c);
 // Message returned by nb_last_error(NULL) (calls made without a context).
 void set_global_error(const char* msg);

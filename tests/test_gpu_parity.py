@@ -102,6 +102,44 @@ def test_force_parity_two_particles_per_thread(order, kind):
     ctx.close()
 
 
+# i-particles per CTA of the mixed force for an active-set size: 4 up to 4
+# active, 32 up to 96, 128 below 1024, then 256 (two per thread).
+def _expected_ni(n_act):
+    return 256 if n_act >= 1024 else 128 if n_act > 96 else 32 if n_act > 4 else 4
+
+
+@pytest.mark.parametrize("order", [4, 6, 8])
+@pytest.mark.parametrize("kind", ["plummer", "holes"])
+def test_force_parity_small_active_sets(order, kind):
+    # Active sets of a few particles run the j-parallel variants (32 or 4
+    # threads per i-particle, lane sums added in a fixed order); cover each
+    # variant's full and ragged i-tiles, a particle with itself in the
+    # store, and several split counts.
+    n = 5 * 128 + 19
+    m, x, v, eps2 = _system(n, 70 + order, kind)
+    ctx = _advanced(m, x, v, eps2, order, nb.NB_MIXED, 1.0 / 256, pair=(kind == "holes"))
+    tb, _ = ctx.next_block()
+    ctx.predict(tb)
+    rng = np.random.default_rng(order + 11)
+    seen = set()
+    for na in (1, 3, 4, 5, 9, 31, 32, 33, 100, 130, 600):
+        idx = np.sort(rng.choice(n, na, replace=False)).astype(np.int32)
+        if kind == "holes" and na >= 2:
+            idx[-1] = n - 1  # an unsoftened hole among the active particles
+            idx = np.unique(idx)
+        O = oracle_force_on_predicted(ctx, m, eps2, idx, order)
+        for js in (0, 1, 6):
+            ctx.set_jsplit(js)
+            ctx.force(idx)
+            it, jsplit, ni = ctx.get_launch()
+            assert ni == _expected_ni(len(idx)) and it * ni >= len(idx)
+            seen.add(ni)
+            G = ctx.get_force(len(idx))
+            assert_force_close(G, O, order, nb.NB_MIXED, f"order {order} {kind} n_act {len(idx)} jsplit {js}")
+    assert seen >= {4, 32, 128}
+    ctx.close()
+
+
 def test_force_jsplit_changes_only_rounding():
     # FP64 results of different split counts agree to rounding; a given
     # launch shape is bitwise reproducible.
