@@ -61,6 +61,72 @@ static __device__ void drain_after_timeout(uint64_t* bars, int k, int nt)
     for (int kk = k; kk < nt && kk < k + NSTAGE; ++kk) mbar_wait_bounded(&bars[kk % NSTAGE], (kk / NSTAGE) & 1);
 }
 
+// -------------------------------------------------------------------- K3
+// F[c][p] = the sum of the j-split partials of component c of active particle
+// p; the potential sum is negated (PC = index of the potential component).
+// The summation order depends on (jsplit, n_act) alone, so every launcher
+// (per-launch, device-driven, static) gives the same bits:
+//   by warp   : lane l adds splits l, l+32, ... in turn, then the 32 lane
+//               sums meet in a butterfly (every lane ends with the same bits,
+//               as a + b == b + a exactly);
+//   sequential: one thread adds the splits in turn.
+// The warp form serves many splits over few particles, where a thread per
+// particle would leave the GPU idle behind one long chain of loads.
+constexpr int RED_WARP_MIN_SPLIT = 9;
+constexpr int RED_WARP_MAX_NACT = 4096;
+constexpr int RED_NT = 256;
+__host__ __device__ __forceinline__ bool reduce_by_warp(int jsplit, int n_act)
+{
+    return jsplit >= RED_WARP_MIN_SPLIT && n_act < RED_WARP_MAX_NACT;
+}
+// per-launch grid of k_force_reduce for NC components
+__host__ __forceinline__ int reduce_grid(int jsplit, int n_act, int nc)
+{
+    return reduce_by_warp(jsplit, n_act) ? (n_act * nc + RED_NT / 32 - 1) / (RED_NT / 32)
+                                         : (n_act + RED_NT - 1) / RED_NT;
+}
+
+template <int NC, int PC>
+__device__ __forceinline__ void reduce_seq(const double* __restrict__ partial, int jsplit, int n_act, int p,
+                                           double* __restrict__ F)
+{
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        double s = 0.0;
+        for (int sp = 0; sp < jsplit; ++sp) s += partial[((size_t)sp * NC + c) * n_act + p];
+        F[(size_t)c * n_act + p] = c == PC ? -s : s;
+    }
+}
+
+// q = p * NC + c; called by a whole warp
+template <int NC, int PC>
+__device__ __forceinline__ void reduce_warp(const double* __restrict__ partial, int jsplit, int n_act, int q,
+                                            int lane, double* __restrict__ F)
+{
+    const int p = q / NC, c = q - p * NC;
+    double s = 0.0;
+    for (int sp = lane; sp < jsplit; sp += 32) s += partial[((size_t)sp * NC + c) * n_act + p];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) F[(size_t)c * n_act + p] = c == PC ? -s : s;
+}
+
+// With one j-split the CTA holds the complete sums of its i-particles and
+// writes the result straight to F (potential negated); otherwise it writes
+// its partial row for the split reduction.  F == nullptr: partials always.
+struct TileSum {
+    double* F;  // [ncomp][ncol] result
+    int jsplit;
+};
+
+template <int NC, int PC>
+__device__ __forceinline__ void store_result(double* __restrict__ partial, int split, int ncol, int p, int c,
+                                             double val, const TileSum& ts)
+{
+    if (ts.F && ts.jsplit == 1) ts.F[(size_t)c * ncol + p] = c == PC ? -val : val;
+    else partial[((size_t)split * NC + c) * ncol + p] = val;
+}
+
 // i-particle data of the mixed kernel, as read from its own record.
 struct IMixed {
     float4 i0, i1, i2, i3, i4;  // (x_hi, m) (x_lo, eps2) (v) (a) (jerk)
@@ -157,7 +223,8 @@ template <int ORDER, int RW, bool PAIR, int IPT>
 __device__ __forceinline__ void force_block_mixed(const float4* __restrict__ js, const int32_t* __restrict__ idx,
                                                   const int pbase0, const int plim, const int n, const int t0,
                                                   const int nt, const int split, const int ncol, const float eps2u,
-                                                  const float eps2max, double* __restrict__ partial, DevScalars* sc)
+                                                  const float eps2max, double* __restrict__ partial, DevScalars* sc,
+                                                  const TileSum ts = TileSum{})
 {
     constexpr int NC = ncomp(ORDER);
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -268,7 +335,7 @@ __device__ __forceinline__ void force_block_mixed(const float4* __restrict__ js,
         if (p < plim) {
 #pragma unroll
             for (int c = 0; c < NC; ++c)
-                partial[((size_t)split * NC + c) * ncol + p] = (double)hi[q][c] + (double)lo[q][c];
+                store_result<NC, pot_comp(ORDER)>(partial, split, ncol, p, c, (double)hi[q][c] + (double)lo[q][c], ts);
         }
     }
 }
@@ -284,7 +351,8 @@ __device__ __forceinline__ void force_block_mixed_jp(const float4* __restrict__ 
                                                      const int pbase0, const int plim, const int n, const int t0,
                                                      const int nt, const int split, const int ncol,
                                                      const float eps2u, const float eps2max,
-                                                     double* __restrict__ partial, DevScalars* sc)
+                                                     double* __restrict__ partial, DevScalars* sc,
+                                                     const TileSum ts = TileSum{})
 {
     constexpr int NC = ncomp(ORDER);
     constexpr int NI = FORCE_NT / JP;
@@ -382,7 +450,7 @@ __device__ __forceinline__ void force_block_mixed_jp(const float4* __restrict__ 
             ds_add_ds(h, l, v.x, v.y);
         }
         const int pp = pbase0 + oi;
-        if (pp < plim) partial[((size_t)split * NC + c) * ncol + pp] = (double)h + (double)l;
+        if (pp < plim) store_result<NC, pot_comp(ORDER)>(partial, split, ncol, pp, c, (double)h + (double)l, ts);
     }
 }
 
@@ -392,13 +460,14 @@ template <int ORDER, int RW, bool PAIR, int JP>
 __global__ void __launch_bounds__(FORCE_NT) k_force_mixed_jp(const float4* __restrict__ js,
                                                              const int32_t* __restrict__ idx, int n_act, int n,
                                                              int ntiles, int jsplit, float eps2u, float eps2max,
-                                                             double* __restrict__ partial, DevScalars* sc)
+                                                             double* __restrict__ partial, DevScalars* sc, double* F)
 {
     const int split = blockIdx.y;
     const int t0 = (int)((long long)split * ntiles / jsplit);
     const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
     force_block_mixed_jp<ORDER, RW, PAIR, JP>(js, idx, blockIdx.x * (FORCE_NT / JP), n_act, n, t0, t1 - t0, split,
-                                              n_act, eps2u, eps2max, partial, sc);
+                                              n_act, eps2u, eps2max, partial, sc,
+                                              TileSum{F, jsplit});
 }
 
 // One system: blockIdx.x = i-tile of FORCE_NT * IPT active particles,
@@ -406,13 +475,14 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_mixed_jp(const float4* __res
 template <int ORDER, int RW, bool PAIR, int IPT>
 __global__ void __launch_bounds__(FORCE_NT) k_force_mixed(const float4* __restrict__ js, const int32_t* __restrict__ idx,
                                                           int n_act, int n, int ntiles, int jsplit, float eps2u,
-                                                          float eps2max, double* __restrict__ partial, DevScalars* sc)
+                                                          float eps2max, double* __restrict__ partial, DevScalars* sc,
+                                                          double* F)
 {
     const int split = blockIdx.y;
     const int t0 = (int)((long long)split * ntiles / jsplit);
     const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
     force_block_mixed<ORDER, RW, PAIR, IPT>(js, idx, blockIdx.x * (FORCE_NT * IPT), n_act, n, t0, t1 - t0, split, n_act,
-                                            eps2u, eps2max, partial, sc);
+                                            eps2u, eps2max, partial, sc, TileSum{F, jsplit});
 }
 
 template <int ORDER, int RW, bool PAIR, bool SELF>
@@ -483,7 +553,8 @@ template <int ORDER, int RW, bool PAIR>
 __device__ __forceinline__ void force_block_fp64(const double2* __restrict__ js, const int32_t* __restrict__ idx,
                                                  const int pbase0, const int plim, const int n, const int t0,
                                                  const int nt, const int split, const int ncol, const double eps2u,
-                                                 double* __restrict__ partial, DevScalars* sc)
+                                                 double* __restrict__ partial, DevScalars* sc,
+                                                 const TileSum ts = TileSum{})
 {
     constexpr int NC = ncomp(ORDER);
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -559,20 +630,21 @@ __device__ __forceinline__ void force_block_fp64(const double2* __restrict__ js,
 
     if (p < plim) {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) partial[((size_t)split * NC + c) * ncol + p] = sum[c];
+        for (int c = 0; c < NC; ++c) store_result<NC, pot_comp(ORDER)>(partial, split, ncol, p, c, sum[c], ts);
     }
 }
 
+// F: result of a one-split launch (nullptr: partials only)
 template <int ORDER, int RW, bool PAIR>
 __global__ void __launch_bounds__(FORCE_NT) k_force_fp64(const double2* __restrict__ js, const int32_t* __restrict__ idx,
                                                          int n_act, int n, int ntiles, int jsplit, double eps2u,
-                                                         double* __restrict__ partial, DevScalars* sc)
+                                                         double* __restrict__ partial, DevScalars* sc, double* F)
 {
     const int split = blockIdx.y;
     const int t0 = (int)((long long)split * ntiles / jsplit);
     const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
     force_block_fp64<ORDER, RW, PAIR>(js, idx, blockIdx.x * FORCE_NT, n_act, n, t0, t1 - t0, split, n_act, eps2u,
-                                      partial, sc);
+                                      partial, sc, TileSum{F, jsplit});
 }
 
 // ------------------------------------------------------- device-driven cycle
@@ -586,10 +658,10 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_fp64(const double2* __restri
 // CTA (4, 32, 128); otherwise the two-per-thread variant (256).  The kernel
 // not matching the chosen variant returns at once.
 template <int ORDER, int RW, bool PAIR, bool SMALL>
-__global__ void __launch_bounds__(FORCE_NT, SMALL ? 1 : (ORDER >= 8 ? 3 : 4)) k_force_mixed_dyn(const float4* __restrict__ js,
+__global__ void __launch_bounds__(FORCE_NT, SMALL ? 5 : (ORDER >= 8 ? 3 : 4)) k_force_mixed_dyn(const float4* __restrict__ js,
                                                               const int32_t* __restrict__ idx, int n, int ntiles,
                                                               float eps2u, float eps2max, double* __restrict__ partial,
-                                                              DevScalars* sc)
+                                                              DevScalars* sc, double* F)
 {
     if (sc->idle) return;
     const int ni = sc->ni;
@@ -599,18 +671,19 @@ __global__ void __launch_bounds__(FORCE_NT, SMALL ? 1 : (ORDER >= 8 ? 3 : 4)) k_
         const int itile = w % it, split = w / it;
         const int t0 = (int)((long long)split * ntiles / jsplit);
         const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
+        const TileSum tsum{F, jsplit};
         if (!SMALL)
             force_block_mixed<ORDER, RW, PAIR, 2>(js, idx, itile * ni, n_act, n, t0, t1 - t0, split, n_act, eps2u,
-                                                  eps2max, partial, sc);
+                                                  eps2max, partial, sc, tsum);
         else if (ni == FORCE_NT)
             force_block_mixed<ORDER, RW, PAIR, 1>(js, idx, itile * ni, n_act, n, t0, t1 - t0, split, n_act, eps2u,
-                                                  eps2max, partial, sc);
+                                                  eps2max, partial, sc, tsum);
         else if (ni == FORCE_NT / 4)
             force_block_mixed_jp<ORDER, RW, PAIR, 4>(js, idx, itile * ni, n_act, n, t0, t1 - t0, split, n_act,
-                                                     eps2u, eps2max, partial, sc);
+                                                     eps2u, eps2max, partial, sc, tsum);
         else
             force_block_mixed_jp<ORDER, RW, PAIR, 32>(js, idx, itile * ni, n_act, n, t0, t1 - t0, split, n_act,
-                                                      eps2u, eps2max, partial, sc);
+                                                      eps2u, eps2max, partial, sc, tsum);
         // every thread is done before the next item re-arms the ring; a
         // status raised by any CTA ends the walk
         if (__syncthreads_or(threadIdx.x == 0 && *(volatile int*)&sc->status != 0)) return;
@@ -621,7 +694,7 @@ template <int ORDER, int RW, bool PAIR>
 __global__ void __launch_bounds__(FORCE_NT) k_force_fp64_dyn(const double2* __restrict__ js,
                                                              const int32_t* __restrict__ idx, int n, int ntiles,
                                                              double eps2u, double* __restrict__ partial,
-                                                             DevScalars* sc)
+                                                             DevScalars* sc, double* F)
 {
     if (sc->idle) return;
     const int n_act = (int)sc->n_act, it = sc->itiles, jsplit = sc->jsplit;
@@ -630,59 +703,27 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_fp64_dyn(const double2* __re
         const int t0 = (int)((long long)split * ntiles / jsplit);
         const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
         force_block_fp64<ORDER, RW, PAIR>(js, idx, itile * FORCE_NT, n_act, n, t0, t1 - t0, split, n_act, eps2u,
-                                          partial, sc);
+                                          partial, sc, TileSum{F, jsplit});
         if (__syncthreads_or(threadIdx.x == 0 && *(volatile int*)&sc->status != 0)) return;
     }
 }
 
-// -------------------------------------------------------------------- K3
-// F[c][p] = the sum of the j-split partials of component c of active particle
-// p; the potential sum is negated (PC = index of the potential component).
-// The summation order depends on (jsplit, n_act) alone, so every launcher
-// (per-launch, device-driven, static) gives the same bits:
-//   by warp   : lane l adds splits l, l+32, ... in turn, then the 32 lane
-//               sums meet in a butterfly (every lane ends with the same bits,
-//               as a + b == b + a exactly);
-//   sequential: one thread adds the splits in turn.
-// The warp form serves many splits over few particles, where a thread per
-// particle would leave the GPU idle behind one long chain of loads.
-constexpr int RED_WARP_MIN_SPLIT = 9;
-constexpr int RED_WARP_MAX_NACT = 4096;
-constexpr int RED_NT = 256;
-__host__ __device__ __forceinline__ bool reduce_by_warp(int jsplit, int n_act)
-{
-    return jsplit >= RED_WARP_MIN_SPLIT && n_act < RED_WARP_MAX_NACT;
-}
-// per-launch grid of k_force_reduce for NC components
-__host__ __forceinline__ int reduce_grid(int jsplit, int n_act, int nc)
-{
-    return reduce_by_warp(jsplit, n_act) ? (n_act * nc + RED_NT / 32 - 1) / (RED_NT / 32)
-                                         : (n_act + RED_NT - 1) / RED_NT;
-}
-
+// Device-driven form: a fixed grid strides over the block the scheduler
+// chose; nothing to do after a one-split launch (the force wrote F).
 template <int NC, int PC>
-__device__ __forceinline__ void reduce_seq(const double* __restrict__ partial, int jsplit, int n_act, int p,
-                                           double* __restrict__ F)
+__global__ void __launch_bounds__(RED_NT) k_force_reduce_dyn(const double* __restrict__ partial,
+                                                             const DevScalars* __restrict__ sc,
+                                                             double* __restrict__ F)
 {
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        double s = 0.0;
-        for (int sp = 0; sp < jsplit; ++sp) s += partial[((size_t)sp * NC + c) * n_act + p];
-        F[(size_t)c * n_act + p] = c == PC ? -s : s;
+    if (sc->idle || sc->jsplit == 1) return;
+    const int n_act = (int)sc->n_act, jsplit = sc->jsplit;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    if (reduce_by_warp(jsplit, n_act)) {
+        for (int q = g >> 5; q < n_act * NC; q += stride >> 5)
+            reduce_warp<NC, PC>(partial, jsplit, n_act, q, threadIdx.x & 31, F);
+    } else {
+        for (int p = g; p < n_act; p += stride) reduce_seq<NC, PC>(partial, jsplit, n_act, p, F);
     }
-}
-
-// q = p * NC + c; called by a whole warp
-template <int NC, int PC>
-__device__ __forceinline__ void reduce_warp(const double* __restrict__ partial, int jsplit, int n_act, int q,
-                                            int lane, double* __restrict__ F)
-{
-    const int p = q / NC, c = q - p * NC;
-    double s = 0.0;
-    for (int sp = lane; sp < jsplit; sp += 32) s += partial[((size_t)sp * NC + c) * n_act + p];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) F[(size_t)c * n_act + p] = c == PC ? -s : s;
 }
 
 template <int NC, int PC>
@@ -698,21 +739,5 @@ __global__ void __launch_bounds__(RED_NT) k_force_reduce(const double* __restric
     }
 }
 
-// Device-driven form: a fixed grid strides over the block the scheduler chose.
-template <int NC, int PC>
-__global__ void __launch_bounds__(RED_NT) k_force_reduce_dyn(const double* __restrict__ partial,
-                                                             const DevScalars* __restrict__ sc,
-                                                             double* __restrict__ F)
-{
-    if (sc->idle) return;
-    const int n_act = (int)sc->n_act, jsplit = sc->jsplit;
-    const int g = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-    if (reduce_by_warp(jsplit, n_act)) {
-        for (int q = g >> 5; q < n_act * NC; q += stride >> 5)
-            reduce_warp<NC, PC>(partial, jsplit, n_act, q, threadIdx.x & 31, F);
-    } else {
-        for (int p = g; p < n_act; p += stride) reduce_seq<NC, PC>(partial, jsplit, n_act, p, F);
-    }
-}
 
 }  // namespace nb

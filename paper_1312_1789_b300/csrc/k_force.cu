@@ -33,7 +33,7 @@ static cudaError_t run_mixed_ipt(nb_ctx* c, const int32_t* idx, int n_act, int j
     dim3 grid(itiles, jsplit);
     kern<<<grid, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), idx, n_act, (int)c->n,
                                               (int)(c->np / JT), jsplit, (float)(c->eps * c->eps),
-                                              (float)c->eps2_max, c->partial, c->sc);
+                                              (float)c->eps2_max, c->partial, c->sc, c->F);
     return cudaGetLastError();
 }
 
@@ -57,7 +57,7 @@ static cudaError_t run_mixed_jp(nb_ctx* c, const int32_t* idx, int n_act, int js
     dim3 grid(itiles, jsplit);
     kern<<<grid, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), idx, n_act, (int)c->n,
                                               (int)(c->np / JT), jsplit, (float)(c->eps * c->eps),
-                                              (float)c->eps2_max, c->partial, c->sc);
+                                              (float)c->eps2_max, c->partial, c->sc, c->F);
     return cudaGetLastError();
 }
 
@@ -94,7 +94,8 @@ static cudaError_t run_fp64(nb_ctx* c, const int32_t* idx, int n_act, int jsplit
     }
     dim3 grid(itiles, jsplit);
     kern<<<grid, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const double2*>(c->jstore), idx, n_act, (int)c->n,
-                                              (int)(c->np / JT), jsplit, c->eps * c->eps, c->partial, c->sc);
+                                              (int)(c->np / JT), jsplit, c->eps * c->eps, c->partial, c->sc,
+                                              c->F);
     return cudaGetLastError();
 }
 
@@ -226,9 +227,9 @@ static cudaError_t force_dyn_o(nb_ctx* c, int* g_small, int* g_big, bool query_o
         }
         const float e2 = (float)(c->eps * c->eps), e2max = (float)c->eps2_max;
         k1<<<*g_small, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), c->act_idx,
-                                                    (int)c->n, ntiles, e2, e2max, c->partial, c->sc);
+                                                    (int)c->n, ntiles, e2, e2max, c->partial, c->sc, c->F);
         k2<<<*g_big, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), c->act_idx,
-                                                  (int)c->n, ntiles, e2, e2max, c->partial, c->sc);
+                                                  (int)c->n, ntiles, e2, e2max, c->partial, c->sc, c->F);
     } else {
         constexpr int RW = fp64_rw(O);
         const size_t smem = (size_t)NSTAGE * JT * RW * 16;
@@ -238,7 +239,8 @@ static cudaError_t force_dyn_o(nb_ctx* c, int* g_small, int* g_big, bool query_o
             return cudaSuccess;
         }
         k1<<<*g_small, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const double2*>(c->jstore), c->act_idx,
-                                                    (int)c->n, ntiles, c->eps * c->eps, c->partial, c->sc);
+                                                    (int)c->n, ntiles, c->eps * c->eps, c->partial, c->sc,
+                                                    c->F);
     }
     return cudaGetLastError();
 }
@@ -257,6 +259,7 @@ cudaError_t launch_cycle_gate(nb_ctx* c, const int* shape_slots)
                                           ncomp(c->order), c->prec == NB_MIXED, c->jsplit_force);
     return cudaGetLastError();
 }
+
 
 cudaError_t launch_force_reduce_dyn(nb_ctx* c)
 {

@@ -149,6 +149,14 @@ cudaError_t timed(nb_ctx* c, int phase, int nk, F&& launch)
 
 // Read the device scalars (waits for the stream) and turn a raised status into
 // an error code; the status word is cleared for the next call.
+// After a device error: clear the status word.
+int clear_device_status(nb_ctx* c, cudaStream_t st)
+{
+    NB_CUDA(c, cudaMemsetAsync(&c->sc->status, 0, sizeof(int), st));
+    NB_CUDA(c, cudaStreamSynchronize(st));
+    return NB_OK;
+}
+
 int sync_scalars(nb_ctx* c)
 {
     NB_CUDA(c, cudaMemcpyAsync(c->h_sc, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
@@ -156,8 +164,7 @@ int sync_scalars(nb_ctx* c)
     if (!c->prof_recs.empty()) prof_fold(c);
     const int st = c->h_sc->status;
     if (st != NB_OK) {
-        NB_CUDA(c, cudaMemsetAsync(&c->sc->status, 0, sizeof(int), c->stream));
-        NB_CUDA(c, cudaStreamSynchronize(c->stream));
+        NB_TRY(clear_device_status(c, c->stream));
         return set_err(c, st, "device kernel reported: %s", code_name(st));
     }
     return NB_OK;
@@ -188,7 +195,8 @@ int run_force(nb_ctx* c, int order, const int32_t* idx_dev, int64_t n_act)
     int it, js, ni;
     choose_shape(c, order, n_act, &it, &js, &ni);
     NB_CUDA(c, timed(c, NB_PHASE_FORCE, 1, [&] { return launch_force(c, order, idx_dev, n_act, js, it, ni); }));
-    NB_CUDA(c, timed(c, NB_PHASE_REDUCE, 1, [&] { return launch_force_reduce(c, order, idx_dev, n_act, js); }));
+    if (js > 1)
+        NB_CUDA(c, timed(c, NB_PHASE_REDUCE, 1, [&] { return launch_force_reduce(c, order, idx_dev, n_act, js); }));
     c->last_itiles = it;
     c->last_jsplit = js;
     c->last_threads = ni;
@@ -259,7 +267,7 @@ int step_until_graph(nb_ctx* c, double t_end, int64_t* n_blocks, int64_t* n_inte
     h->blocks = 0;
     h->inter = 0;
     NB_CUDA(c, cudaMemcpy(c->sc, h, sizeof(DevScalars), cudaMemcpyHostToDevice));
-    // scheduler 2, gate, predictor, force (both i-per-thread variants on the
+    // scheduler 2, gate, predictor, force (two persistent kernels on the
     // mixed path), reduction, corrector
     const long long per_cycle = 2 + 1 + 1 + (c->prec == NB_MIXED ? 2 : 1) + 1 + 1;
     for (;;) {
@@ -269,7 +277,7 @@ int step_until_graph(nb_ctx* c, double t_end, int64_t* n_blocks, int64_t* n_inte
         NB_CUDA(c, cudaStreamSynchronize(c->graph_stream));
         if (h->status != NB_OK) {
             const int st = h->status;
-            NB_CUDA(c, cudaMemset(&c->sc->status, 0, sizeof(int)));
+            NB_TRY(clear_device_status(c, c->graph_stream));
             return set_err(c, st, "device kernel reported: %s", code_name(st));
         }
         if (h->idle) break;

@@ -286,13 +286,16 @@ cudaError_t launch_sched(nb_ctx* c);
 // dyn (device-driven cycle): take the time from dyn->t_blk and do nothing when dyn->idle.
 cudaError_t launch_predict(nb_ctx* c, double t, const double* tpc = nullptr, const int32_t* cid = nullptr,
                            const DevScalars* dyn = nullptr);
-// ni: the launch variant, i-particles per CTA (force_ni)
+// ni: the launch variant, i-particles per CTA (force_ni).  A one-split
+// launch writes the result to c->F itself; otherwise launch_force_reduce
+// adds the split partials into c->F.
 cudaError_t launch_force(nb_ctx* c, int order, const int32_t* idx, int64_t n_act, int jsplit, int itiles, int ni);
 cudaError_t launch_force_reduce(nb_ctx* c, int order, const int32_t* idx, int64_t n_act, int jsplit);
 cudaError_t launch_correct(nb_ctx* c, const double* tfc = nullptr, const int32_t* cid = nullptr,
                            const DevScalars* dyn = nullptr);
 // Device-driven block cycle (CUDA-graph capturable): shape gate, persistent
-// force over device-chosen items, reduction; all read n_act / t_blk on the device.
+// force over device-chosen items, split reduction; all read n_act / t_blk on
+// the device.
 // shape_slots[4]: SMs x occupancy of the per-launch kernels with 4, 32, 128, 256 i-particles per CTA
 cudaError_t launch_cycle_gate(nb_ctx* c, const int* shape_slots);
 cudaError_t launch_force_dyn(nb_ctx* c, int* grid_small, int* grid_big, bool query_only);

@@ -162,14 +162,14 @@ int run_static(const double* m, const double* eps2, const double* x, const doubl
             return NB_ERR_CUDA;
         js = choose_split(it, np / JT, NC, n_act, slots_of(kern, smem, sm_count));
         kern<<<dim3(it, js), FORCE_NT, smem, st>>>(reinterpret_cast<const float4*>(rec), idx, n_act, n, np / JT, js,
-                                                   0.0f, INFINITY, partial, sc);
+                                                   0.0f, INFINITY, partial, sc, nullptr);
     } else {
         auto kern = k_force_fp64<ORDER, RW, true>;
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return NB_ERR_CUDA;
         js = choose_split(it, np / JT, NC, n_act, slots_of(kern, smem, sm_count));
         kern<<<dim3(it, js), FORCE_NT, smem, st>>>(reinterpret_cast<const double2*>(rec), idx, n_act, n, np / JT, js,
-                                                   0.0, partial, sc);
+                                                   0.0, partial, sc, nullptr);
     }
     k_force_reduce<NC, pot_comp(ORDER)><<<reduce_grid(js, n_act, NC), RED_NT, 0, st>>>(partial, js, n_act, out);
     if (cudaGetLastError() != cudaSuccess) return NB_ERR_CUDA;
