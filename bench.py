@@ -11,9 +11,12 @@ compensated sums) unless --precision fp64.
 Printed JSON line (rank 0): value = interactions/s over the timed steps with
 the state resident in HBM; e2e = the same through the C ABI with host state
 copied in and out every step; roofline of the force kernel (CUDA events on its
-stream); the FP64 path on a 4096-particle block of the same system; energy
-error of both paths on the 65536-particle Plummer sphere; the CPU oracle on the
-host cores as a baseline.
+stream); the FP64 path on a 4096-particle block of the same system; the force
+rate of both paths on each single-system workload; energy error and
+whole-run throughput of both paths on the 65536-particle Plummer sphere
+(host-driven, CUDA-graph and autotuned cycles); energy and binary-element
+drift of both paths on the 8th-order cusp nucleus; the 256-cluster ensemble;
+the CPU oracle on the host cores as a baseline.
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
 """
@@ -51,6 +54,9 @@ def parse():
     p.add_argument("--block-step", type=float, default=2.0 ** -12)
     p.add_argument("--quick", action="store_true", help="skip the FP64, energy, ensemble and CPU legs")
     p.add_argument("--ensemble-t", type=float, default=1.0 / 64, help="end time of the ensemble leg")
+    p.add_argument("--energy-t", type=float, default=1.0 / 16, help="end time of the energy-budget leg")
+    p.add_argument("--cusp-fp64", action="store_true",
+                   help="also run the full-size cusp on the FP64 path (about two minutes)")
     return p.parse_args()
 
 
@@ -264,6 +270,61 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def binary_elements(S, m):
+    """Two-body semi-major axis and eccentricity of the last two particles."""
+    r = S["x"][-2] - S["x"][-1]
+    u = S["v"][-2] - S["v"][-1]
+    mu = m[-2] + m[-1]
+    en = 0.5 * float(u @ u) - mu / float(np.linalg.norm(r))
+    h = np.cross(r, u)
+    return -mu / (2.0 * en), math.sqrt(max(0.0, 1.0 + 2.0 * en * float(h @ h) / mu ** 2))
+
+
+def cusp_run(nb, w, p, stream, torch, t_end, dt_max=None):
+    c = nb.NBody(w.n, w.order, 0.0, p)
+    c.set_stream(stream)
+    c.set_softening(np.sqrt(w.eps2))
+    c.set_params(w.eta, w.eta_s, dt_max or w.dt_max, 2.0 ** -40)
+    c.set_particles(w.m, w.x, w.v)
+    c.set_precision(nb.NB_FP64)
+    e0 = sum(c.energy())
+    a0, ec0 = binary_elements(c.get_state(), w.m)
+    c.set_precision(p)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nblk, ni = c.step_until(t_end)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    c.set_precision(nb.NB_FP64)
+    e1 = sum(c.energy())
+    a1, ec1 = binary_elements(c.get_state(), w.m)
+    c.close()
+    return {"dE_E": (e1 - e0) / abs(e0), "binary_a": [a0, a1], "binary_e": [ec0, ec1], "blocks": nblk,
+            "interactions": ni, "seconds": el, "whole_run_interactions_per_s": ni / el}
+
+
+def cusp_leg(args, nb, ics, stream, torch):
+    """Dehnen gamma=1 cusp with a central black-hole binary, 8th order.  The
+    two-body elements are not conserved (the stellar mass inside the orbit
+    exceeds the binary's); the comparison of interest is mixed vs FP64."""
+    res = {}
+    small = ics.cusp_nucleus(1 << 14, 1003, 1e-4, 1.0 / 16, 8)
+    res["reduced"] = {"workload": small.name + " to t=1/16",
+                      "mixed": cusp_run(nb, small, nb.NB_MIXED, stream, torch, 1.0 / 16),
+                      "fp64": cusp_run(nb, small, nb.NB_FP64, stream, torch, 1.0 / 16)}
+    r = res["reduced"]
+    r["mixed_dE_within_2x_of_fp64"] = abs(r["mixed"]["dE_E"]) <= 2 * abs(r["fp64"]["dE_E"])
+    full = ics.standard_workload(3)
+    res["full"] = {"workload": full.name + " to t=1/16", "mixed": cusp_run(nb, full, nb.NB_MIXED, stream, torch,
+                                                                           1.0 / 16)}
+    if args.cusp_fp64:
+        w = {"workload": full.name + " to t=1/256 with dt_max=1/256"}
+        for name, p in (("mixed", nb.NB_MIXED), ("fp64", nb.NB_FP64)):
+            w[name] = cusp_run(nb, full, p, stream, torch, 1.0 / 256, dt_max=1.0 / 256)
+        res["full_short"] = w
+    return res
+
+
 def extras(args, nb, ics, wl, ctx, stream, out, prec):
     import torch
     n = wl.n
@@ -337,11 +398,13 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
     # ---- energy error of both paths, Plummer N = 65536 to t = 1/16
     try:
         pw = ics.standard_workload(1)
-        t_end = 1.0 / 16
+        t_end = args.energy_t
         de, final = {}, {}
         # host-driven cycles for both precisions, then the mixed run again as
-        # CUDA-graph replays of 64 device-driven cycles
-        for name, p, cyc in (("fp64", nb.NB_FP64, 0), ("mixed", nb.NB_MIXED, 0), ("mixed_graph", nb.NB_MIXED, 64)):
+        # CUDA-graph replays of 64 device-driven cycles, untuned and autotuned
+        legs = (("fp64", nb.NB_FP64, 0, 0), ("mixed", nb.NB_MIXED, 0, 0), ("mixed_graph", nb.NB_MIXED, 64, 0),
+                ("mixed_graph_tuned", nb.NB_MIXED, 64, 3))
+        for name, p, cyc, tune in legs:
             c2 = nb.NBody(pw.n, 6, math.sqrt(pw.eps2[0]), p)
             c2.set_stream(stream)
             c2.set_params(pw.eta, pw.eta_s, pw.dt_max, 2.0 ** -40)
@@ -349,6 +412,12 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
             c2.set_precision(nb.NB_FP64)
             e0 = sum(c2.energy())
             c2.set_precision(p)
+            tune_s = None
+            if tune:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                c2.autotune(tune)
+                tune_s = time.perf_counter() - t0
             c2.set_graph(cyc)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -360,12 +429,54 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
             e1 = sum(c2.energy())
             de[name] = {"dE_E": (e1 - e0) / abs(e0), "blocks": nblk, "interactions": ni,
                         "whole_run_interactions_per_s": ni / el, "seconds": el}
+            if tune_s is not None:
+                de[name]["autotune_seconds"] = tune_s
             c2.close()
         de["mixed_graph"]["same_state_as_host_driven"] = bool(np.array_equal(final["mixed"], final["mixed_graph"]))
         out["energy_budget"] = {"workload": pw.name + f" to t={t_end}", **de,
                                 "mixed_within_2x": abs(de["mixed"]["dE_E"]) <= 2 * abs(de["fp64"]["dE_E"])}
     except Exception as e:  # pragma: no cover
         out["energy_budget"] = {"error": repr(e)}
+    # ---- force kernel at N_act = N on each single-system workload (mixed),
+    #      and the FP64 path on a 4096-particle block of each
+    try:
+        table = {}
+        for k in range(4):
+            w = ics.standard_workload(k) if k != 2 else wl
+            fl = FLOPS_PER_INTERACTION[w.order]
+            row = {"n": w.n, "order": w.order}
+            for name, p, na in (("mixed", nb.NB_MIXED, w.n), ("fp64", nb.NB_FP64, min(4096, w.n))):
+                c3 = make_ctx(nb, w, p, stream) if k != 2 else ctx
+                c3.set_precision(p)
+                c3.predict(2.0 ** -12)
+                blk = np.arange(w.n, dtype=np.int32) if na == w.n else \
+                    np.sort(np.random.default_rng(k).choice(w.n, na, replace=False)).astype(np.int32)
+                c3.force(blk)
+                reps = 5 if name == "mixed" else 2
+                c3.set_profiling(True)
+                for _ in range(reps):
+                    c3.force(blk)
+                pr, _ = c3.get_profile()
+                c3.set_profiling(False)
+                fms = (pr["force"][0] + pr["reduce"][0]) / reps
+                rate = na * w.n / (fms * 1e-3)
+                peak = FP32_PEAK_TFLOPS if name == "mixed" else FP64_PEAK_TFLOPS
+                row[name] = {"n_act": na, "interactions_per_s": rate, "gflops_convention": rate * fl / 1e9,
+                             "frac_of_peak": rate * fl / 1e12 / peak}
+                if k != 2:
+                    c3.close()
+            ctx.set_precision(prec)
+            table[w.name] = row
+        out["per_workload_force"] = {"note": "force + split reduction at N_act = N (mixed) and on a 4096 block "
+                                             "(FP64); peaks: FP32 lanes x 2 x 2032 MHz / nominal FP64 1.25 TFLOP/s",
+                                     **table}
+    except Exception as e:  # pragma: no cover
+        out["per_workload_force"] = {"error": repr(e)}
+    # ---- cusp nucleus, order 8: energy and binary-element drift of both paths
+    try:
+        out["cusp8"] = cusp_leg(args, nb, ics, stream, torch)
+    except Exception as e:  # pragma: no cover
+        out["cusp8"] = {"error": repr(e)}
     # ---- ensemble: 256 Plummer clusters, batched vs one context per cluster
     try:
         clusters = ics.ensemble()

@@ -164,8 +164,9 @@ int nb_get_force(nb_ctx* ctx, double* acc, double* jerk, double* snap, double* c
 int nb_get_predicted(nb_ctx* ctx, double* xp, double* vp, double* ap, double* jp);
 
 /* Kernel launch shape of the last nb_force: CTAs along i, j-splits and
- * i-particles per CTA (128 threads holding one or two particles each); any
- * output may be NULL.                                                       */
+ * i-particles per CTA -- the launch variant: 256 (128 threads holding two
+ * particles each), 128 (one each), 32 or 4 (j-parallel: 4 or 32 threads per
+ * particle, for active sets of up to 96 or 4); any output may be NULL.      */
 int nb_get_launch(nb_ctx* ctx, int* i_tiles, int* j_splits, int* i_per_cta);
 
 /* cycles > 0: nb_step_until replays a CUDA graph of that many device-driven
@@ -175,6 +176,25 @@ int nb_get_launch(nb_ctx* ctx, int* i_tiles, int* j_splits, int* i_per_cta);
  * block.  Both take the same blocks with the same kernels' arithmetic.  The
  * graph is captured on first use and again after a parameter change.       */
 int nb_set_graph(nb_ctx* ctx, int cycles);
+
+/* Autotuner of the force launch shape.  For active-set sizes 1, 2, 4, ...
+ * up to N it times candidate launch variants (i-particles per CTA) and
+ * j-split counts on the context's own store (CUDA events on its stream, best
+ * of `reps` runs each) and keeps the fastest per size class; later forces of
+ * the context in the current precision (host- and device-driven alike) take
+ * their shape from that table: class floor(log2(n_act)), the tuned variant,
+ * the split count scaled to keep the tuned number of CTAs.  reps <= 0 drops
+ * the current precision's table (back to the analytic makespan rule).  The
+ * particle state is untouched (predicted store and force result are
+ * scratch); needs nb_set_particles.  Synchronises.                         */
+#define NB_TUNE_MAX 32
+int nb_autotune(nb_ctx* ctx, int reps);
+
+/* The current precision's table: *n_classes (0: none), and for class k
+ * (active sets of 2^k .. 2^(k+1) - 1) the variant ni[k], split count js[k]
+ * and measured force time ms[k] at n_act = 2^k (arrays of NB_TUNE_MAX; any
+ * may be NULL).                                                            */
+int nb_get_tuning(nb_ctx* ctx, int* n_classes, int32_t* ni, int32_t* js, double* ms);
 
 /* Force the j-split count of later nb_force calls (0 = automatic).         */
 int nb_set_jsplit(nb_ctx* ctx, int j_splits);

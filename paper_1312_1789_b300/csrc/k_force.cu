@@ -173,11 +173,11 @@ cudaError_t launch_force_reduce(nb_ctx* c, int order, const int32_t* idx, int64_
 // ------------------------------------------------------- device-driven cycle
 // One thread: close the cycle when the next block lies past t_end, otherwise
 // pick the force launch shape exactly as the host rule does for a block of
-// that size (same variant rule, same slot counts, same makespan split, same
-// forced split).  slots = SMs x occupancy of the per-launch kernels with 4,
+// that size (the autotuned table if any, else the same variant rule, slot
+// counts and makespan split; a forced split).  slots = SMs x occupancy of the per-launch kernels with 4,
 // 32, 128 and 256 i-particles per CTA.
 __global__ void k_cycle_gate(DevScalars* sc, long long n, int ntiles, int4 slots, long long cap, int nc, int mixed,
-                             int js_force)
+                             int js_force, const TuneEntry* tab, int ntab)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const long long na = sc->n_act;
@@ -186,13 +186,16 @@ __global__ void k_cycle_gate(DevScalars* sc, long long n, int ntiles, int4 slots
         return;
     }
     sc->idle = 0;
-    const int ni = mixed ? mixed_ni(na) : FORCE_NT;
-    const int sl = ni == 4 ? slots.x : ni == 32 ? slots.y : ni == FORCE_NT ? slots.z : slots.w;
-    const int it = (int)((na + ni - 1) / ni);
+    const long long cap_splits = cap / ((long long)nc * na);
+    int ni, it, js;
+    if (js_force > 0 || !tuned_shape(tab, ntab, na, &ni, &it, &js)) {
+        ni = mixed ? mixed_ni(na) : FORCE_NT;
+        const int sl = ni == 4 ? slots.x : ni == 32 ? slots.y : ni == FORCE_NT ? slots.z : slots.w;
+        it = (int)((na + ni - 1) / ni);
+        js = js_force > 0 ? js_force : makespan_split(it, ntiles, sl, cap_splits);
+    }
     sc->ni = ni;
     sc->itiles = it;
-    const long long cap_splits = cap / ((long long)nc * na);
-    int js = js_force > 0 ? js_force : makespan_split(it, ntiles, sl, cap_splits);
     if (js > ntiles) js = ntiles;
     if (js > cap_splits) js = (int)cap_splits;
     sc->jsplit = js < 1 ? 1 : js;
@@ -255,8 +258,10 @@ cudaError_t launch_force_dyn(nb_ctx* c, int* g_small, int* g_big, bool query_onl
 cudaError_t launch_cycle_gate(nb_ctx* c, const int* shape_slots)
 {
     const int4 sl = make_int4(shape_slots[0], shape_slots[1], shape_slots[2], shape_slots[3]);
+    const int pi = c->prec == NB_MIXED ? 1 : 0;
     k_cycle_gate<<<1, 32, 0, c->stream>>>(c->sc, c->n, (int)(c->np / JT), sl, (long long)c->partial_cap,
-                                          ncomp(c->order), c->prec == NB_MIXED, c->jsplit_force);
+                                          ncomp(c->order), c->prec == NB_MIXED, c->jsplit_force,
+                                          c->d_tune + pi * TUNE_MAX, c->tune_n[pi]);
     return cudaGetLastError();
 }
 

@@ -175,17 +175,23 @@ int sync_scalars(nb_ctx* c)
 // partial-sum buffer.
 void choose_shape(nb_ctx* c, int order, int64_t n_act, int* itiles, int* jsplit, int* ni_out)
 {
-    const int ni = force_ni(c, n_act);
-    *ni_out = ni;
-    const int it = (int)((n_act + ni - 1) / ni);
     const int ntiles = (int)(c->np / JT);
     const long long cap_splits = (long long)(c->partial_cap / ((size_t)ncomp(order) * (size_t)n_act));
-    int js = c->jsplit_force > 0
+    const int pi = (c->pred_prec >= 0 ? c->pred_prec : c->prec) == NB_MIXED ? 1 : 0;
+    int ni, it, js;
+    if (order == c->order && c->jsplit_force <= 0 && tuned_shape(c->tune[pi], c->tune_n[pi], n_act, &ni, &it, &js)) {
+        // autotuned class shape
+    } else {
+        ni = force_ni(c, n_act);
+        it = (int)((n_act + ni - 1) / ni);
+        js = c->jsplit_force > 0
                  ? c->jsplit_force
                  : makespan_split(it, ntiles, c->sm_count * force_occupancy(c, order, ni), cap_splits);
+    }
     if (js > ntiles) js = ntiles;
     if (js > cap_splits) js = (int)cap_splits;
     if (js < 1) js = 1;
+    *ni_out = ni;
     *itiles = it;
     *jsplit = js;
 }
@@ -322,7 +328,7 @@ void nb_destroy(nb_ctx* c)
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     void* ptrs[] = {c->m, c->eps2, c->x, c->v, c->d, c->t, c->dt, c->pot, c->jstore, c->act_idx, c->all_idx,
-                    c->chunk_cnt, c->chunk_min, c->sc, c->red, c->f_idx, c->partial, c->F};
+                    c->chunk_cnt, c->chunk_min, c->d_tune, c->sc, c->red, c->f_idx, c->partial, c->F};
     for (void* p : ptrs) dfree(c, p);
     if (c->h_sc) cudaFreeHost(c->h_sc);
     if (c->h_red) cudaFreeHost(c->h_red);
@@ -380,6 +386,7 @@ int nb_create(nb_ctx** out, int64_t n, int order, double eps)
         (rc = dalloc(c, &c->act_idx, (size_t)n)) || (rc = dalloc(c, &c->all_idx, (size_t)n)) ||
         (rc = dalloc(c, &c->f_idx, (size_t)n)) || (rc = dalloc(c, &c->chunk_cnt, (size_t)c->n_chunks)) ||
         (rc = dalloc(c, &c->chunk_min, (size_t)c->n_chunks)) ||
+        (rc = dalloc(c, &c->d_tune, (size_t)2 * TUNE_MAX)) ||
         (rc = dalloc(c, &c->sc, 1)) || (rc = dalloc(c, &c->red, (size_t)c->red_len)) ||
         (rc = dalloc(c, &c->partial, c->partial_cap)) || (rc = dalloc(c, &c->F, (size_t)nc * (size_t)n)))
         return fail(rc);
@@ -393,6 +400,7 @@ int nb_create(nb_ctx** out, int64_t n, int order, double eps)
     for (int64_t k = 0; k < n; ++k) iota[(size_t)k] = (int32_t)k;
     if (cudaMemcpy(c->all_idx, iota.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(c->sc, 0, sizeof(DevScalars)) != cudaSuccess || cudaMemset(c->m, 0, np * 8) != cudaSuccess ||
+        cudaMemset(c->d_tune, 0, sizeof(TuneEntry) * 2 * TUNE_MAX) != cudaSuccess ||
         cudaMemset(c->x, 0, 3 * np * 8) != cudaSuccess || cudaMemset(c->v, 0, 3 * np * 8) != cudaSuccess ||
         cudaMemset(c->d, 0, 18 * np * 8) != cudaSuccess || cudaMemset(c->t, 0, np * 8) != cudaSuccess ||
         cudaMemset(c->dt, 0, np * 8) != cudaSuccess || cudaMemset(c->pot, 0, np * 8) != cudaSuccess) {
@@ -468,6 +476,117 @@ int nb_set_graph(nb_ctx* c, int cycles)
     if (cycles < 0 || cycles > 4096) return set_err(c, NB_ERR_ARG, "cycles must be in [0, 4096]");
     destroy_graph(c);
     c->graph_cycles = cycles;
+    return NB_OK;
+}
+
+// Time one force launch shape (force + split reduction) on the all-particle
+// list prefix of length na: best of reps runs, milliseconds.
+static int time_shape(nb_ctx* c, int64_t na, int ni, int js, int reps, cudaEvent_t e0, cudaEvent_t e1, float* best)
+{
+    const int it = (int)((na + ni - 1) / ni);
+    *best = INFINITY;
+    for (int r = -1; r < reps; ++r) {  // r = -1: untimed warm-up
+        NB_CUDA(c, cudaEventRecord(e0, c->stream));
+        NB_CUDA(c, launch_force(c, c->order, c->all_idx, na, js, it, ni));
+        if (js > 1) NB_CUDA(c, launch_force_reduce(c, c->order, c->all_idx, na, js));
+        NB_CUDA(c, cudaEventRecord(e1, c->stream));
+        NB_CUDA(c, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        NB_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+        if (r >= 0 && ms < *best) *best = ms;
+    }
+    c->n_launch += (int64_t)(reps + 1) * (js > 1 ? 2 : 1);
+    return sync_scalars(c);
+}
+
+int nb_autotune(nb_ctx* c, int reps)
+{
+    if (!c) return NB_ERR_ARG;
+    if (!c->have_particles) return set_err(c, NB_ERR_ARG, "nb_autotune before nb_set_particles");
+    const int pi = c->prec == NB_MIXED ? 1 : 0;
+    destroy_graph(c);
+    c->tune_n[pi] = 0;
+    if (reps > 0) {
+        // the store every candidate reads: all particles predicted to the next block time
+        double tb;
+        int64_t na0;
+        NB_TRY(nb_next_block(c, &tb, nullptr, &na0));
+        NB_TRY(do_predict(c, tb));
+        cudaEvent_t e0, e1;
+        NB_CUDA(c, cudaEventCreate(&e0));
+        NB_CUDA(c, cudaEventCreate(&e1));
+        const int ntiles = (int)(c->np / JT), nc = ncomp(c->order);
+        const bool mixed = c->prec == NB_MIXED;
+        int ncls = 0;
+        while (ncls < TUNE_MAX && (1LL << ncls) <= c->n) ++ncls;
+        // classes past this per-call time are left to the analytic rule
+        const float budget_ms = 25.f;
+        int rc = NB_OK;
+        float prev_best = 0.f;
+        for (int k = 0; k < ncls && rc == NB_OK; ++k) {
+            TuneEntry& e = c->tune[pi][k];
+            e = TuneEntry{0, 0, 0, 0.f};
+            if (k > 0 && 2.f * prev_best > budget_ms) continue;
+            const int64_t na = 1LL << k;
+            const long long cap_splits = (long long)(c->partial_cap / ((size_t)nc * (size_t)na));
+            int cand[4], nv = 0;
+            if (!mixed) cand[nv++] = FORCE_NT;
+            else {
+                if (na <= 16) cand[nv++] = 4;
+                if (na <= 512) cand[nv++] = 32;
+                if (na <= 16384) cand[nv++] = FORCE_NT;
+                if (na >= 256) cand[nv++] = 2 * FORCE_NT;
+            }
+            float best = INFINITY;
+            for (int v = 0; v < nv && rc == NB_OK; ++v) {
+                const int ni = cand[v];
+                const int it = (int)((na + ni - 1) / ni);
+                const int base = makespan_split(it, ntiles, c->sm_count * force_occupancy(c, c->order, ni), cap_splits);
+                const int mult[6][2] = {{1, 4}, {1, 2}, {1, 1}, {2, 1}, {4, 1}, {0, 1}};
+                int tried[6], nt = 0;
+                for (int q = 0; q < 6 && rc == NB_OK; ++q) {
+                    long long js = mult[q][0] == 0 ? 1 : (long long)base * mult[q][0] / mult[q][1];
+                    if (js > ntiles) js = ntiles;
+                    if (js > cap_splits) js = cap_splits;
+                    if (js < 1) js = 1;
+                    bool dup = false;
+                    for (int u = 0; u < nt; ++u) dup = dup || tried[u] == (int)js;
+                    if (dup) continue;
+                    tried[nt++] = (int)js;
+                    float ms;
+                    rc = time_shape(c, na, ni, (int)js, reps, e0, e1, &ms);
+                    if (rc == NB_OK && ms < best) {
+                        best = ms;
+                        e = TuneEntry{ni, (int)js, it, ms};
+                    }
+                }
+            }
+            prev_best = best;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        c->have_pred = c->have_force = c->have_sched = 0;
+        c->F_order = -1;
+        NB_TRY(rc);
+        c->tune_n[pi] = ncls;
+    }
+    NB_CUDA(c, cudaMemcpy(c->d_tune + pi * TUNE_MAX, c->tune[pi], sizeof(TuneEntry) * TUNE_MAX,
+                          cudaMemcpyHostToDevice));
+    return NB_OK;
+}
+
+int nb_get_tuning(nb_ctx* c, int* n_classes, int32_t* ni, int32_t* js, double* ms)
+{
+    if (!c) return NB_ERR_ARG;
+    const int pi = c->prec == NB_MIXED ? 1 : 0;
+    if (n_classes) *n_classes = c->tune_n[pi];
+    for (int k = 0; k < TUNE_MAX; ++k) {
+        const TuneEntry& e = c->tune[pi][k];
+        const bool on = k < c->tune_n[pi];
+        if (ni) ni[k] = on ? e.ni : 0;
+        if (js) js[k] = on ? e.js : 0;
+        if (ms) ms[k] = on ? (double)e.ms : 0.0;
+    }
     return NB_OK;
 }
 

@@ -96,6 +96,34 @@ __host__ __device__ inline int makespan_split(int it, int ntiles, int slots, lon
     return (int)best_s;
 }
 
+// Autotuned launch shape of one active-set size class (nb_autotune): the
+// variant ni and split count js measured best at the class's representative
+// size, where the force took `it` i-tiles and `ms` milliseconds.
+constexpr int TUNE_MAX = 32;
+struct TuneEntry {
+    int ni, js, it;
+    float ms;
+};
+
+// Shape of an n_act block from the tuned table (ntab classes; false: no
+// entry): class floor(log2(n_act)) (the last class serves larger sets), its
+// variant, and the split count that keeps its number of CTAs it * js.
+__host__ __device__ inline bool tuned_shape(const TuneEntry* tab, int ntab, long long n_act, int* ni, int* it,
+                                            int* js)
+{
+    if (ntab <= 0 || n_act <= 0) return false;
+    int k = 0;
+    while (k + 1 < ntab && (n_act >> (k + 1)) > 0) ++k;
+    const TuneEntry e = tab[k];
+    if (e.ni <= 0) return false;
+    *ni = e.ni;
+    *it = (int)((n_act + e.ni - 1) / e.ni);
+    const long long ctas = (long long)e.js * e.it;
+    long long s = (ctas + *it / 2) / *it;
+    *js = (int)(s < 1 ? 1 : s);
+    return true;
+}
+
 // Scalars shared between the scheduler, the kernels and the host.
 struct DevScalars {
     long long n_act;  // size of the active list
@@ -267,6 +295,10 @@ struct nb_ctx {
     double prof_ms[NB_NPHASES] = {0};
     int64_t prof_n[NB_NPHASES] = {0};
     int64_t n_launch = 0;  // kernel launches since creation
+    // autotuned launch shapes per precision (nb_autotune); device copy for the gate
+    nb::TuneEntry tune[2][nb::TUNE_MAX] = {};
+    int tune_n[2] = {0, 0};
+    nb::TuneEntry* d_tune = nullptr;  // [2][TUNE_MAX]
     // device-driven cycles captured in a CUDA graph (nb_set_graph)
     int graph_cycles = 0;
     cudaGraphExec_t graph_exec = nullptr;

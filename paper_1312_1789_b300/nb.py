@@ -64,6 +64,8 @@ SIGNATURES = {
     "nb_get_noise_floor": (C.c_int, [_P, C.c_int, _D]),
     "nb_force_static": (C.c_int, [C.c_int, C.c_int, C.c_int64, _P, _P, _P, _P, _P, _P, _P, C.c_int64, _P, _P]),
     "nb_set_graph": (C.c_int, [_P, C.c_int]),
+    "nb_autotune": (C.c_int, [_P, C.c_int]),
+    "nb_get_tuning": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int32), C.POINTER(C.c_int32), _D]),
     "nb_batch_create": (C.c_int, [C.POINTER(_P), C.c_int, _I64, C.c_int, C.c_double]),
     "nb_batch_destroy": (None, [_P]),
     "nb_batch_last_error": (C.c_char_p, [_P]),
@@ -78,6 +80,7 @@ SIGNATURES = {
 }
 NB_STATIC_MAX_N = 16384
 NB_NPHASES = 6
+NB_TUNE_MAX = 32
 PHASES = ("sched", "predict", "force", "reduce", "correct", "other")
 
 _lib = None
@@ -179,6 +182,20 @@ class NBody:
     def set_graph(self, cycles: int):
         """cycles > 0: step_until replays a CUDA graph of that many device-driven block cycles."""
         self._check(self._L.nb_set_graph(self._h, int(cycles)))
+
+    def autotune(self, reps: int = 3):
+        """Time force launch shapes per active-set size class and use the fastest (reps <= 0: off)."""
+        self._check(self._L.nb_autotune(self._h, int(reps)))
+
+    def get_tuning(self):
+        """[(class k, ni, js, ms)] of the current precision's autotuned table."""
+        n = C.c_int()
+        ni = np.zeros(NB_TUNE_MAX, dtype=np.int32)
+        js = np.zeros(NB_TUNE_MAX, dtype=np.int32)
+        ms = np.zeros(NB_TUNE_MAX)
+        self._check(self._L.nb_get_tuning(self._h, C.byref(n), ni.ctypes.data_as(C.POINTER(C.c_int32)),
+                                          js.ctypes.data_as(C.POINTER(C.c_int32)), _d(ms)))
+        return [(k, int(ni[k]), int(js[k]), float(ms[k])) for k in range(n.value)]
 
     def set_jsplit(self, js: int):
         self._check(self._L.nb_set_jsplit(self._h, int(js)))

@@ -56,6 +56,9 @@ def test_create_rejects_bad_arguments_before_touching_the_device(libnb):
 def test_null_context_is_rejected(libnb):
     assert libnb.nb_predict(None, 0.0) == -1
     assert libnb.nb_correct(None) == -1
+    assert libnb.nb_set_graph(None, 4) == -1
+    assert libnb.nb_autotune(None, 1) == -1
+    assert libnb.nb_get_tuning(None, None, None, None, None) == -1
     libnb.nb_destroy(None)
 
 

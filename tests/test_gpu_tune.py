@@ -1,0 +1,83 @@
+"""Autotuned force launch shapes (nb_autotune): the table, the shapes later
+forces take from it, force parity under those shapes, and device-driven
+cycles that look the table up on the device."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+from gpu_common import assert_force_close, make_ctx, oracle_force_on_predicted
+from paper_1312_1789_b300 import ics, nb
+
+pytestmark = pytest.mark.gpu
+
+
+def _tuned_shape(table, n_act):
+    """Shape rule of a tuned table, restated: class floor(log2 n_act) (the
+    last class serves larger sets), its variant, the split count keeping
+    the class's CTA count it * js."""
+    k = min(int(math.floor(math.log2(n_act))), len(table) - 1)
+    _, ni, js, _ = table[k]
+    it_k = -(-(1 << k) // ni)
+    it = -(-n_act // ni)
+    return ni, it, max(1, (js * it_k + it // 2) // it)
+
+
+def test_autotune_table_shapes_and_parity():
+    n = 3000
+    m, x, v = ics.plummer(n, 17)
+    eps2 = np.full(n, 1e-8)
+    ctx = make_ctx(m, x, v, eps2, 6, nb.NB_MIXED)
+    ctx.autotune(2)
+    table = ctx.get_tuning()
+    assert len(table) == 12  # classes 2^0 .. 2^11 <= 3000
+    for k, ni, js, ms in table:
+        assert ni in (4, 32, 128, 256) and js >= 1 and ms > 0
+    tb, _ = ctx.next_block()
+    ctx.predict(tb)
+    rng = np.random.default_rng(1)
+    for na in (1, 3, 7, 50, 300, 1500, 3000):
+        idx = np.sort(rng.choice(n, na, replace=False)).astype(np.int32)
+        ctx.force(idx)
+        it, js, ni = ctx.get_launch()
+        e_ni, e_it, e_js = _tuned_shape(table, na)
+        assert (ni, it) == (e_ni, e_it)
+        assert js == min(e_js, n // 128 + 1)  # the split is also capped by the j tiles
+        O = oracle_force_on_predicted(ctx, m, eps2, idx, 6)
+        assert_force_close(ctx.get_force(na), O, 6, nb.NB_MIXED, f"tuned shape n_act {na}")
+    ctx.autotune(0)
+    assert ctx.get_tuning() == []
+    ctx.close()
+
+
+def test_autotune_fp64_table_is_per_precision():
+    n = 700
+    m, x, v = ics.plummer(n, 4)
+    ctx = make_ctx(m, x, v, 1e-8, 6, nb.NB_FP64)
+    ctx.autotune(1)
+    t64 = ctx.get_tuning()
+    assert len(t64) == 10 and all(e[1] in (0, 128) for e in t64)
+    ctx.set_precision(nb.NB_MIXED)
+    assert ctx.get_tuning() == []  # the mixed table is separate and empty
+    ctx.set_precision(nb.NB_FP64)
+    assert ctx.get_tuning() == t64
+    ctx.close()
+
+
+def test_autotuned_graph_cycles_match_host_cycles_bitwise():
+    n = 1800
+    m, x, v = ics.plummer(n, 23)
+    states = []
+    for cycles in (0, 6):
+        ctx = make_ctx(m, x, v, 1e-8, 6, nb.NB_MIXED)
+        ctx.autotune(1)
+        ctx.set_graph(cycles)
+        counts = ctx.step_until(1.0 / 32)
+        states.append((counts, ctx.get_state()))
+        ctx.close()
+    (c0, s0), (c1, s1) = states
+    assert c0 == c1
+    for key in ("x", "v", "d", "t", "dt"):
+        assert np.array_equal(s0[key], s1[key]), key
