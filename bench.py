@@ -485,16 +485,21 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
         m = np.concatenate([c.m for c in clusters])
         x = np.concatenate([c.x for c in clusters])
         v = np.concatenate([c.v for c in clusters])
-        bt = nb.Batch(sizes, 6, math.sqrt(clusters[0].eps2[0]), nb.NB_MIXED)
-        bt.set_stream(stream)
-        bt.set_params(0.2, 0.01, 1.0 / 16, 2.0 ** -40)
-        bt.set_particles(m, x, v)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ncyc, ni_b = bt.step_until(t_ens)
-        torch.cuda.synchronize()
-        el_b = time.perf_counter() - t0
-        bt.close()
+        runs = {}
+        for name, cyc in (("host", 0), ("graph", 32)):
+            bt = nb.Batch(sizes, 6, math.sqrt(clusters[0].eps2[0]), nb.NB_MIXED)
+            bt.set_stream(stream)
+            bt.set_params(0.2, 0.01, 1.0 / 16, 2.0 ** -40)
+            bt.set_graph(cyc)
+            bt.set_particles(m, x, v)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ncyc, ni_b = bt.step_until(t_ens)
+            torch.cuda.synchronize()
+            runs[name] = (ncyc, ni_b, time.perf_counter() - t0, bt.get_state()["x"])
+            bt.close()
+        ncyc, ni_b, el_b, xb = runs["graph"]
+        same = bool(np.array_equal(xb, runs["host"][3]))
         ni_s, el_s = 0, 0.0
         for c in clusters:
             cx = nb.NBody(c.n, 6, math.sqrt(c.eps2[0]), nb.NB_MIXED)
@@ -510,7 +515,10 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
         out["ensemble"] = {"workload": f"{len(sizes)} Plummer clusters, N_k log-uniform in [1024, 32768] "
                                        f"({int(sum(sizes))} particles), order 6, mixed, to t={t_ens}",
                            "batched_interactions_per_s": ni_b / el_b, "batched_cycles": ncyc,
-                           "batched_seconds": el_b, "per_cluster_interactions_per_s": ni_s / el_s,
+                           "batched_seconds": el_b, "batched": "CUDA-graph replays of 32 device-planned cycles",
+                           "batched_host_cycles_interactions_per_s": runs["host"][1] / runs["host"][2],
+                           "graph_state_equals_host_cycles": same,
+                           "per_cluster_interactions_per_s": ni_s / el_s,
                            "per_cluster_seconds": el_s, "interactions": ni_b,
                            "speedup": (ni_b / el_b) / (ni_s / el_s)}
     except Exception as e:  # pragma: no cover

@@ -196,6 +196,13 @@ int nb_autotune(nb_ctx* ctx, int reps);
  * may be NULL).                                                            */
 int nb_get_tuning(nb_ctx* ctx, int* n_classes, int32_t* ni, int32_t* js, double* ms);
 
+/* Install a table for the current precision -- one nb_get_tuning returned,
+ * e.g. from an earlier run on the same N: n_classes <= NB_TUNE_MAX classes,
+ * ni[k] the variant of class k (0: untuned, the analytic rule; else 4, 32,
+ * 128 or 256 mixed, 128 FP64), js[k] >= 1 its split count at n_act = 2^k.
+ * n_classes = 0 drops the table.                                           */
+int nb_set_tuning(nb_ctx* ctx, int n_classes, const int32_t* ni, const int32_t* js);
+
 /* Force the j-split count of later nb_force calls (0 = automatic).         */
 int nb_set_jsplit(nb_ctx* ctx, int j_splits);
 
@@ -265,12 +272,23 @@ int nb_batch_set_params(nb_batch* b, double eta, double eta_s, double dt_max, do
 int nb_batch_set_particles(nb_batch* b, const double* m, const double* x, const double* v);
 
 /* One cycle: each cluster whose next block time is <= t_end takes that block.
- * Outputs (NULL to skip): clusters stepped (0 once all are past t_end) and
- * interactions evaluated (sum of n_act_k * n_k).                           */
+ * The whole cycle is planned on the device: active list, per-cluster
+ * segments, the force's (cluster, i-tile, j-split) items, predictor, one
+ * persistent force kernel over the items, reduction, corrector.  Outputs
+ * (NULL to skip): clusters stepped (0 once all are past t_end) and
+ * interactions evaluated (sum of n_act_k * n_k).  Synchronises.            */
 int nb_batch_cycle(nb_batch* b, double t_end, int* n_stepped, int64_t* n_interactions);
 
-/* Cycles until no cluster has a block at or before t_end.                   */
+/* Cycles until no cluster has a block at or before t_end: one nb_batch_cycle
+ * after another, or with nb_batch_set_graph(b, c > 0) replays of a CUDA graph
+ * of c such cycles, checked on the host once per replay (same cycles, same
+ * arithmetic).                                                             */
 int nb_batch_step_until(nb_batch* b, double t_end, int64_t* n_cycles, int64_t* n_interactions);
+
+/* cycles > 0: nb_batch_step_until replays a CUDA graph of that many cycles;
+ * 0 (default): one host-checked cycle at a time.  Captured on first use and
+ * again after a parameter change.                                          */
+int nb_batch_set_graph(nb_batch* b, int cycles);
 
 /* Per-cluster kinetic and potential energy (arrays [n_clusters]); every
  * cluster must be synchronised within itself, else NB_ERR_NOT_SYNC.         */

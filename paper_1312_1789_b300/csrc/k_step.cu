@@ -175,6 +175,14 @@ cudaError_t launch_sched(nb_ctx* c)
 //   order 8: x to a^(5) (dt^7), v to dt^6, a to dt^5, jerk to dt^4
 // Writes the j-particle store in the requested precision; padding records
 // (i >= n) get m = 0 and eps2 = 1 so they contribute exactly zero.
+//
+// FP64 store: every term in FP64.  Mixed store: x = x0 + h (v0 + h T) in FP64
+// (then split into hi + lo floats), with the Taylor tail T = a/2 + h j/6 + ...
+// and the predicted v, a, jerk evaluated in FP32, the precision they are
+// stored in: the FP64 pipe (1/64 of the FP32 rate here) does only the
+// position.  The tail's FP32 rounding is a few float ulps of its terms,
+// scaled by h^2 -- far below the pair separations that need the
+// double-single position.
 template <int ORDER, bool MIXED>
 __global__ void __launch_bounds__(256) k_predict(const double* __restrict__ m, const double* __restrict__ eps2,
                                                  const double* __restrict__ x, const double* __restrict__ v,
@@ -191,6 +199,7 @@ __global__ void __launch_bounds__(256) k_predict(const double* __restrict__ m, c
     }
     constexpr int RW = MIXED ? mixed_rw(ORDER) : fp64_rw(ORDER);
     double xp[3] = {0, 0, 0}, vp[3] = {0, 0, 0}, ap[3] = {0, 0, 0}, jp[3] = {0, 0, 0};
+    float vf[3] = {0.f, 0.f, 0.f}, af[3] = {0.f, 0.f, 0.f}, jf[3] = {0.f, 0.f, 0.f};
     double mi = 0.0, ei = 1.0;
     bool real = i < n;
     if (real && tpc) {
@@ -207,25 +216,50 @@ __global__ void __launch_bounds__(256) k_predict(const double* __restrict__ m, c
         mi = m[i];
         ei = eps2[i];
         const double h = tp - t[i];
+        const float hf = (float)h;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const double a0 = d[(0 * 3 + c) * np + i], j0 = d[(1 * 3 + c) * np + i];
-            const double s0 = d[(2 * 3 + c) * np + i], c0 = d[(3 * 3 + c) * np + i];
             const double x0 = x[c * np + i], v0 = v[c * np + i];
-            if (ORDER == 8) {
-                const double d4 = d[(4 * 3 + c) * np + i], d5 = d[(5 * 3 + c) * np + i];
-                xp[c] = x0 + h * (v0 + h * (a0 * (1.0 / 2) + h * (j0 * (1.0 / 6) + h * (s0 * (1.0 / 24) +
-                        h * (c0 * (1.0 / 120) + h * (d4 * (1.0 / 720) + h * d5 * (1.0 / 5040)))))));
-                vp[c] = v0 + h * (a0 + h * (j0 * (1.0 / 2) + h * (s0 * (1.0 / 6) + h * (c0 * (1.0 / 24) +
-                        h * (d4 * (1.0 / 120) + h * d5 * (1.0 / 720))))));
-                ap[c] = a0 + h * (j0 + h * (s0 * (1.0 / 2) + h * (c0 * (1.0 / 6) + h * (d4 * (1.0 / 24) +
-                        h * d5 * (1.0 / 120)))));
-                jp[c] = j0 + h * (s0 + h * (c0 * (1.0 / 2) + h * (d4 * (1.0 / 6) + h * d5 * (1.0 / 24))));
+            if (MIXED) {
+                const float a0 = (float)d[(0 * 3 + c) * np + i], j0 = (float)d[(1 * 3 + c) * np + i];
+                const float s0 = (float)d[(2 * 3 + c) * np + i], c0 = (float)d[(3 * 3 + c) * np + i];
+                float T;
+                if (ORDER == 8) {
+                    const float d4 = (float)d[(4 * 3 + c) * np + i], d5 = (float)d[(5 * 3 + c) * np + i];
+                    T = fmaf(hf, fmaf(hf, fmaf(hf, fmaf(hf, fmaf(hf, d5 * (1.f / 5040), d4 * (1.f / 720)),
+                                                         c0 * (1.f / 120)), s0 * (1.f / 24)), j0 * (1.f / 6)),
+                             a0 * 0.5f);
+                    vf[c] = fmaf(hf, fmaf(hf, fmaf(hf, fmaf(hf, fmaf(hf, fmaf(hf, d5 * (1.f / 720), d4 * (1.f / 120)),
+                                                                     c0 * (1.f / 24)), s0 * (1.f / 6)), j0 * 0.5f), a0),
+                                 (float)v0);
+                    af[c] = fmaf(hf, fmaf(hf, fmaf(hf, fmaf(hf, fmaf(hf, d5 * (1.f / 120), d4 * (1.f / 24)),
+                                                           c0 * (1.f / 6)), s0 * 0.5f), j0), a0);
+                    jf[c] = fmaf(hf, fmaf(hf, fmaf(hf, fmaf(hf, d5 * (1.f / 24), d4 * (1.f / 6)), c0 * 0.5f), s0), j0);
+                } else {
+                    T = fmaf(hf, fmaf(hf, fmaf(hf, c0 * (1.f / 120), s0 * (1.f / 24)), j0 * (1.f / 6)), a0 * 0.5f);
+                    vf[c] = fmaf(hf, fmaf(hf, fmaf(hf, fmaf(hf, c0 * (1.f / 24), s0 * (1.f / 6)), j0 * 0.5f), a0),
+                                 (float)v0);
+                    af[c] = fmaf(hf, fmaf(hf, fmaf(hf, c0 * (1.f / 6), s0 * 0.5f), j0), a0);
+                }
+                xp[c] = fma(h, fma(h, (double)T, v0), x0);
             } else {
-                xp[c] = x0 + h * (v0 + h * (a0 * (1.0 / 2) + h * (j0 * (1.0 / 6) + h * (s0 * (1.0 / 24) +
-                        h * c0 * (1.0 / 120)))));
-                vp[c] = v0 + h * (a0 + h * (j0 * (1.0 / 2) + h * (s0 * (1.0 / 6) + h * c0 * (1.0 / 24))));
-                ap[c] = a0 + h * (j0 + h * (s0 * (1.0 / 2) + h * c0 * (1.0 / 6)));
+                const double a0 = d[(0 * 3 + c) * np + i], j0 = d[(1 * 3 + c) * np + i];
+                const double s0 = d[(2 * 3 + c) * np + i], c0 = d[(3 * 3 + c) * np + i];
+                if (ORDER == 8) {
+                    const double d4 = d[(4 * 3 + c) * np + i], d5 = d[(5 * 3 + c) * np + i];
+                    xp[c] = x0 + h * (v0 + h * (a0 * (1.0 / 2) + h * (j0 * (1.0 / 6) + h * (s0 * (1.0 / 24) +
+                            h * (c0 * (1.0 / 120) + h * (d4 * (1.0 / 720) + h * d5 * (1.0 / 5040)))))));
+                    vp[c] = v0 + h * (a0 + h * (j0 * (1.0 / 2) + h * (s0 * (1.0 / 6) + h * (c0 * (1.0 / 24) +
+                            h * (d4 * (1.0 / 120) + h * d5 * (1.0 / 720))))));
+                    ap[c] = a0 + h * (j0 + h * (s0 * (1.0 / 2) + h * (c0 * (1.0 / 6) + h * (d4 * (1.0 / 24) +
+                            h * d5 * (1.0 / 120)))));
+                    jp[c] = j0 + h * (s0 + h * (c0 * (1.0 / 2) + h * (d4 * (1.0 / 6) + h * d5 * (1.0 / 24))));
+                } else {
+                    xp[c] = x0 + h * (v0 + h * (a0 * (1.0 / 2) + h * (j0 * (1.0 / 6) + h * (s0 * (1.0 / 24) +
+                            h * c0 * (1.0 / 120)))));
+                    vp[c] = v0 + h * (a0 + h * (j0 * (1.0 / 2) + h * (s0 * (1.0 / 6) + h * c0 * (1.0 / 24))));
+                    ap[c] = a0 + h * (j0 + h * (s0 * (1.0 / 2) + h * c0 * (1.0 / 6)));
+                }
             }
         }
     }
@@ -239,9 +273,9 @@ __global__ void __launch_bounds__(256) k_predict(const double* __restrict__ m, c
         }
         r[0] = make_float4(hx[0], hx[1], hx[2], (float)mi);
         r[1] = make_float4(lx[0], lx[1], lx[2], (float)ei);
-        r[2] = make_float4((float)vp[0], (float)vp[1], (float)vp[2], 0.f);
-        if (ORDER >= 6) r[3] = make_float4((float)ap[0], (float)ap[1], (float)ap[2], 0.f);
-        if (ORDER >= 8) r[4] = make_float4((float)jp[0], (float)jp[1], (float)jp[2], 0.f);
+        r[2] = make_float4(vf[0], vf[1], vf[2], 0.f);
+        if (ORDER >= 6) r[3] = make_float4(af[0], af[1], af[2], 0.f);
+        if (ORDER >= 8) r[4] = make_float4(jf[0], jf[1], jf[2], 0.f);
     } else {
         double2* r = reinterpret_cast<double2*>(jstore) + (size_t)i * RW;
         r[0] = make_double2(xp[0], xp[1]);

@@ -575,6 +575,31 @@ int nb_autotune(nb_ctx* c, int reps)
     return NB_OK;
 }
 
+int nb_set_tuning(nb_ctx* c, int n_classes, const int32_t* ni, const int32_t* js)
+{
+    if (!c) return NB_ERR_ARG;
+    if (n_classes < 0 || n_classes > TUNE_MAX || (n_classes > 0 && (!ni || !js)))
+        return set_err(c, NB_ERR_ARG, "need 0 <= n_classes <= %d and both arrays", TUNE_MAX);
+    const bool mixed = c->prec == NB_MIXED;
+    for (int k = 0; k < n_classes; ++k) {
+        const bool ok = ni[k] == 0 || ni[k] == FORCE_NT ||
+                        (mixed && (ni[k] == 4 || ni[k] == 32 || ni[k] == 2 * FORCE_NT));
+        if (!ok || (ni[k] != 0 && js[k] < 1))
+            return set_err(c, NB_ERR_ARG, "class %d: variant %d / split %d not valid here", k, ni[k], js[k]);
+    }
+    const int pi = mixed ? 1 : 0;
+    destroy_graph(c);
+    for (int k = 0; k < TUNE_MAX; ++k) {
+        TuneEntry e{0, 0, 0, 0.f};
+        if (k < n_classes && ni[k] > 0) e = TuneEntry{ni[k], js[k], (int)(((1LL << k) + ni[k] - 1) / ni[k]), 0.f};
+        c->tune[pi][k] = e;
+    }
+    c->tune_n[pi] = n_classes;
+    NB_CUDA(c, cudaMemcpy(c->d_tune + pi * TUNE_MAX, c->tune[pi], sizeof(TuneEntry) * TUNE_MAX,
+                          cudaMemcpyHostToDevice));
+    return NB_OK;
+}
+
 int nb_get_tuning(nb_ctx* c, int* n_classes, int32_t* ni, int32_t* js, double* ms)
 {
     if (!c) return NB_ERR_ARG;

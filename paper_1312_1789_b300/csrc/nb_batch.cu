@@ -53,8 +53,18 @@ struct nb_batch {
     int32_t* kcount = nullptr;    // [K] active particles of the cluster
     int32_t* ksplit = nullptr;    // [K] j-splits of the cluster this cycle
     int32_t* chunk_cnt = nullptr;
-    BatchItem* items = nullptr;
+    BatchItem* items = nullptr;   // host-planned items (start-up, energy)
     size_t items_cap = 0;
+    // device-driven cycle: plan and items built on the device
+    int64_t* d_pk = nullptr;      // [K] padded sizes
+    int32_t* kni = nullptr;       // [K] launch variant of the cluster this cycle
+    int32_t* koff = nullptr;      // [K] first item of the cluster this cycle
+    BatchItem* d_items = nullptr;
+    int d_items_cap = 0;
+    int force_slots = 0;          // SMs x occupancy of the persistent force kernel
+    int graph_cycles = 0;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t graph_stream = nullptr;
     double* esum = nullptr;  // [3K] per-cluster kinetic, potential, sync flag
     // pinned mirrors
     double* h_tblk = nullptr;
@@ -94,9 +104,10 @@ constexpr int BNT = 256;
 
 // Block time of each cluster (one CTA per cluster); past t_end -> idle (+inf).
 __global__ void k_batch_min(const double* __restrict__ t, const double* __restrict__ dt,
-                            const int64_t* __restrict__ off, const int64_t* __restrict__ nk, double t_end,
+                            const int64_t* __restrict__ off, const int64_t* __restrict__ nk,
                             double* __restrict__ tblk, DevScalars* sc)
 {
+    const double t_end = sc->t_end;
     __shared__ double ws[BNT / 32];
     const int k = blockIdx.x;
     double mn = INFINITY;
@@ -185,7 +196,10 @@ __global__ void k_batch_scatter(const double* __restrict__ t, const double* __re
         if (f) idx[base + woff + __popc(bal & ((1u << lane) - 1u))] = (int32_t)i;
         base += tot;
     }
-    if (blockIdx.x == nchunks - 1 && threadIdx.x == 0) sc->n_act = base;
+    if (blockIdx.x == nchunks - 1 && threadIdx.x == 0) {
+        sc->n_act = base;
+        sc->idle = base == 0;
+    }
 }
 
 // Segment of each cluster in the (cluster-major, ascending) active list.
@@ -226,6 +240,229 @@ __global__ void __launch_bounds__(FORCE_NT) k_batch_force_mixed(const float4* __
     else
         force_block_mixed_jp<ORDER, RW, true, 32>(js, list, it.list_off, lim, n, it.jt0, it.nt, it.split, n_act,
                                                   0.0f, eps2max, partial, sc);
+}
+
+// ------------------------------------------------ device-driven cycle
+// The cycle's active-set size lives in sc->n_act; a fixed grid strides.
+__global__ void k_batch_bounds_dyn(const int32_t* __restrict__ list, const DevScalars* __restrict__ sc,
+                                   const int32_t* __restrict__ cid, int32_t* __restrict__ kstart,
+                                   int32_t* __restrict__ kcount)
+{
+    const int n_act = (int)sc->n_act;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_act; p += gridDim.x * blockDim.x) {
+        const int k = cid[list[p]];
+        if (p == 0 || cid[list[p - 1]] != k) kstart[k] = p;
+        if (p == n_act - 1 || cid[list[p + 1]] != k) kcount[k] = p + 1;
+    }
+}
+
+// Plan of the cycle's force (one CTA): each cluster with cnt active takes the
+// launch variant ni = mixed_ni(cnt) (at most one i-particle per thread) and
+// s j-splits, s = ceil(min(cnt, ni) * pk / target) in [1, pk / JT], with
+// target = max(work / (4 slots), FORCE_NT * JT) and work = sum cnt * pk: items
+// of about equal work, about four waves of them.  The largest split is then
+// capped by the partial-sum buffer.  Writes ksplit, kni, koff (exclusive
+// item offsets, cluster order), n_items, the clusters stepped and the
+// interactions of the cycle.
+__global__ void __launch_bounds__(BNT) k_batch_plan(int K, const int32_t* __restrict__ kcount,
+                                                    const int64_t* __restrict__ pk, const int64_t* __restrict__ nk,
+                                                    int slots, long long cap, int nc, int mixed, int items_cap,
+                                                    int32_t* __restrict__ ksplit, int32_t* __restrict__ kni,
+                                                    int32_t* __restrict__ koff, DevScalars* sc)
+{
+    __shared__ long long s_ll[BNT / 32];
+    __shared__ int s_i[BNT / 32];
+    __shared__ double s_target;
+    __shared__ int s_smax;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (sc->idle) {
+        if (tid == 0) {
+            sc->n_items = 0;
+            sc->stepped = 0;
+        }
+        return;
+    }
+    auto block_sum = [&](long long v) {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        __syncthreads();
+        if (lane == 0) s_ll[warp] = v;
+        __syncthreads();
+        long long t = 0;
+        for (int w = 0; w < BNT / 32; ++w) t += s_ll[w];
+        return t;
+    };
+    long long work = 0, inter = 0, stepped = 0;
+    for (int k = tid; k < K; k += BNT) {
+        const long long cnt = kcount[k];
+        if (cnt > 0) {
+            work += cnt * pk[k];
+            inter += cnt * nk[k];
+            ++stepped;
+        }
+    }
+    work = block_sum(work);
+    inter = block_sum(inter);
+    stepped = block_sum(stepped);
+    if (tid == 0) s_target = fmax((double)work / (4.0 * slots), (double)FORCE_NT * JT);
+    __syncthreads();
+    const double target = s_target;
+    int smax = 1;
+    for (int k = tid; k < K; k += BNT) {
+        const int cnt = kcount[k];
+        const int ni = mixed ? min(mixed_ni(cnt), FORCE_NT) : FORCE_NT;
+        const int jt = (int)(pk[k] / JT);
+        int sk = 1;
+        if (cnt > 0) {
+            sk = (int)ceil((double)min(cnt, ni) * (double)pk[k] / target);
+            sk = max(1, min(sk, jt));
+        }
+        ksplit[k] = sk;
+        kni[k] = ni;
+        smax = max(smax, sk);
+    }
+    for (int o = 16; o > 0; o >>= 1) smax = max(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+    __syncthreads();
+    if (lane == 0) s_i[warp] = smax;
+    __syncthreads();
+    if (tid == 0) {
+        int m = 1;
+        for (int w = 0; w < BNT / 32; ++w) m = max(m, s_i[w]);
+        const long long n_act = sc->n_act;
+        while (m > 1 && (long long)m * nc * n_act > cap) --m;
+        s_smax = m;
+    }
+    __syncthreads();
+    const int scap = s_smax;
+    // items per cluster and their exclusive scan, BNT clusters at a time
+    int running = 0;
+    for (int base = 0; base < K; base += BNT) {
+        const int k = base + tid;
+        int items = 0;
+        if (k < K) {
+            const int cnt = kcount[k];
+            int sk = ksplit[k];
+            if (sk > scap) {
+                sk = scap;
+                ksplit[k] = sk;
+            }
+            if (cnt > 0) items = (cnt + kni[k] - 1) / kni[k] * sk;
+        }
+        int incl = items;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        __syncthreads();
+        if (lane == 31) s_i[warp] = incl;
+        __syncthreads();
+        int wbase = 0, tot = 0;
+        for (int w = 0; w < BNT / 32; ++w) {
+            if (w < warp) wbase += s_i[w];
+            tot += s_i[w];
+        }
+        if (k < K) koff[k] = running + wbase + incl - items;
+        running += tot;
+    }
+    if (tid == 0) {
+        if (running > items_cap) {
+            raise_status(sc, NB_ERR_ARG);
+            running = items_cap;
+        }
+        sc->n_items = running;
+        sc->stepped = (int)stepped;
+        sc->blocks += stepped > 0 ? 1 : 0;
+        sc->inter += inter;
+    }
+}
+
+// Items of cluster k = blockIdx.x in (i-tile, split) order at koff[k].
+__global__ void __launch_bounds__(BNT) k_batch_items(const int32_t* __restrict__ kstart,
+                                                     const int32_t* __restrict__ kcount,
+                                                     const int32_t* __restrict__ ksplit,
+                                                     const int32_t* __restrict__ kni, const int32_t* __restrict__ koff,
+                                                     const int64_t* __restrict__ off, const int64_t* __restrict__ pk,
+                                                     int items_cap, BatchItem* __restrict__ items)
+{
+    const int k = blockIdx.x;
+    const int cnt = kcount[k];
+    if (cnt <= 0) return;
+    const int sk = ksplit[k], ni = kni[k], it = (cnt + ni - 1) / ni;
+    const int jt = (int)(pk[k] / JT), jt0 = (int)(off[k] / JT), o = koff[k];
+    for (int q = threadIdx.x; q < it * sk; q += BNT) {
+        if (o + q >= items_cap) return;
+        const int i_tile = q / sk, s = q - i_tile * sk;
+        BatchItem e{};
+        e.list_off = kstart[k] + i_tile * ni;
+        e.count = min(ni, cnt - i_tile * ni);
+        const int a = (int)((long long)s * jt / sk), b = (int)((long long)(s + 1) * jt / sk);
+        e.jt0 = jt0 + a;
+        e.nt = b - a;
+        e.split = s;
+        e.ni = ni;
+        items[o + q] = e;
+    }
+}
+
+// Persistent force over the cycle's items (count in sc->n_items).
+template <int ORDER, int RW>
+__global__ void __launch_bounds__(FORCE_NT) k_batch_force_mixed_dyn(const float4* __restrict__ js,
+                                                                    const int32_t* __restrict__ list,
+                                                                    const BatchItem* __restrict__ items, int n,
+                                                                    float eps2max, double* __restrict__ partial,
+                                                                    DevScalars* sc)
+{
+    if (sc->idle) return;
+    const int n_items = sc->n_items, n_act = (int)sc->n_act;
+    for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+        const BatchItem it = items[w];
+        const int lim = it.list_off + it.count;
+        if (it.ni == FORCE_NT)
+            force_block_mixed<ORDER, RW, true, 1>(js, list, it.list_off, lim, n, it.jt0, it.nt, it.split, n_act, 0.0f,
+                                                  eps2max, partial, sc);
+        else if (it.ni == FORCE_NT / 4)
+            force_block_mixed_jp<ORDER, RW, true, 4>(js, list, it.list_off, lim, n, it.jt0, it.nt, it.split, n_act,
+                                                     0.0f, eps2max, partial, sc);
+        else
+            force_block_mixed_jp<ORDER, RW, true, 32>(js, list, it.list_off, lim, n, it.jt0, it.nt, it.split, n_act,
+                                                      0.0f, eps2max, partial, sc);
+        if (__syncthreads_or(threadIdx.x == 0 && *(volatile int*)&sc->status != 0)) return;
+    }
+}
+
+template <int ORDER, int RW>
+__global__ void __launch_bounds__(FORCE_NT) k_batch_force_fp64_dyn(const double2* __restrict__ js,
+                                                                   const int32_t* __restrict__ list,
+                                                                   const BatchItem* __restrict__ items, int n,
+                                                                   double* __restrict__ partial, DevScalars* sc)
+{
+    if (sc->idle) return;
+    const int n_items = sc->n_items, n_act = (int)sc->n_act;
+    for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+        const BatchItem it = items[w];
+        force_block_fp64<ORDER, RW, true>(js, list, it.list_off, it.list_off + it.count, n, it.jt0, it.nt, it.split,
+                                          n_act, 0.0, partial, sc);
+        if (__syncthreads_or(threadIdx.x == 0 && *(volatile int*)&sc->status != 0)) return;
+    }
+}
+
+// F[c][p] = sum over the particle's cluster splits (fixed order); a fixed
+// grid strides over the cycle's active list.
+template <int NC, int PC>
+__global__ void k_batch_reduce_dyn(const double* __restrict__ partial, const int32_t* __restrict__ list,
+                                   const int32_t* __restrict__ cid, const int32_t* __restrict__ ksplit,
+                                   const DevScalars* __restrict__ sc, double* __restrict__ F)
+{
+    if (sc->idle) return;
+    const int n_act = (int)sc->n_act;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_act; p += gridDim.x * blockDim.x) {
+        const int S = ksplit[cid[list[p]]];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            double s = 0.0;
+            for (int sp = 0; sp < S; ++sp) s += partial[((size_t)sp * NC + c) * n_act + p];
+            F[(size_t)c * n_act + p] = c == PC ? -s : s;
+        }
+    }
 }
 
 template <int ORDER, int RW>
@@ -539,6 +776,151 @@ int batch_force(nb_batch* b, int order, const int32_t* list, int n_act, const in
     return NB_OK;
 }
 
+// ------------------------------------------------ device-driven cycle (host)
+// scheduler 3, bounds 2, plan, items, predictor, force, reduction, corrector
+constexpr int BATCH_CYCLE_LAUNCHES = 11;
+
+void batch_destroy_graph(nb_batch* b)
+{
+    if (b->graph_exec) {
+        cudaGraphExecDestroy(b->graph_exec);
+        b->graph_exec = nullptr;
+    }
+}
+
+template <int SO>
+int batch_force_dyn_o(nb_batch* b, bool occ_only)
+{
+    nb_ctx* c = b->c;
+    if (c->prec == NB_MIXED) {
+        constexpr int RW = mixed_rw(SO);
+        const size_t smem = (size_t)NSTAGE * JT * RW * 16;
+        auto kern = k_batch_force_mixed_dyn<SO, RW>;
+        if (occ_only) return occ_of(kern, smem);
+        kern<<<b->force_slots, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), c->act_idx,
+                                                             b->d_items, (int)c->n, (float)c->eps2_max, c->partial,
+                                                             c->sc);
+    } else {
+        constexpr int RW = fp64_rw(SO);
+        const size_t smem = (size_t)NSTAGE * JT * RW * 16;
+        auto kern = k_batch_force_fp64_dyn<SO, RW>;
+        if (occ_only) return occ_of(kern, smem);
+        kern<<<b->force_slots, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const double2*>(c->jstore), c->act_idx,
+                                                             b->d_items, (int)c->n, c->partial, c->sc);
+    }
+    return cudaGetLastError() == cudaSuccess ? NB_OK : NB_ERR_CUDA;
+}
+
+int batch_force_dyn(nb_batch* b, bool occ_only)
+{
+    switch (b->c->order) {
+    case 4: return batch_force_dyn_o<4>(b, occ_only);
+    case 6: return batch_force_dyn_o<6>(b, occ_only);
+    default: return batch_force_dyn_o<8>(b, occ_only);
+    }
+}
+
+// Slots of the persistent force in the current precision and an item buffer
+// that holds every plan: items <= 4 slots + np/64 + 3K (each cluster's split
+// count rounds up by at most one, its i-tiles number at most cnt/128 + 3).
+int batch_prepare(nb_batch* b)
+{
+    nb_ctx* c = b->c;
+    const int slots = c->sm_count * batch_force_dyn(b, true);
+    const long long need = 8LL * slots + c->np / 32 + 4LL * b->K + 1024;
+    if (slots != b->force_slots || need > b->d_items_cap) {
+        batch_destroy_graph(b);
+        b->force_slots = slots;
+    }
+    if (need > b->d_items_cap) {
+        B_CUDA(b, cudaStreamSynchronize(c->stream));
+        if (b->d_items) cudaFree(b->d_items);
+        b->d_items = nullptr;
+        b->d_items_cap = 0;
+        B_TRY(balloc(b, &b->d_items, (size_t)need));
+        b->d_items_cap = (int)need;
+    }
+    c->pred_prec = c->prec;
+    return NB_OK;
+}
+
+// t_end of the coming cycles, counters cleared.
+int batch_reset_scalars(nb_batch* b, double t_end, cudaStream_t st)
+{
+    nb_ctx* c = b->c;
+    DevScalars* h = c->h_sc;
+    B_CUDA(b, cudaStreamSynchronize(c->stream));
+    B_CUDA(b, cudaMemcpy(h, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost));
+    h->t_end = t_end;
+    h->idle = 0;
+    h->blocks = 0;
+    h->inter = 0;
+    h->stepped = 0;
+    B_CUDA(b, cudaMemcpyAsync(c->sc, h, sizeof(DevScalars), cudaMemcpyHostToDevice, st));
+    B_CUDA(b, cudaStreamSynchronize(st));
+    return NB_OK;
+}
+
+// The launches of one ensemble cycle, every size read on the device: block
+// time per cluster (idle past t_end), active list, cluster segments, the
+// force plan and its items, predictor, persistent force, reduction,
+// corrector.
+cudaError_t batch_cycle_launches(nb_batch* b)
+{
+    nb_ctx* c = b->c;
+    const int K = b->K, nch = (int)((c->n + BCHUNK - 1) / BCHUNK), g = c->sm_count * 4;
+    k_batch_min<<<K, BNT, 0, c->stream>>>(c->t, c->dt, b->d_off, b->d_nk, b->tblk, c->sc);
+    k_batch_count<<<nch, BNT, 0, c->stream>>>(c->t, c->dt, b->cid, b->tblk, c->n, b->chunk_cnt);
+    k_batch_scatter<<<nch, BNT, 0, c->stream>>>(c->t, c->dt, b->cid, b->tblk, c->n, b->chunk_cnt, nch, c->act_idx,
+                                                c->sc);
+    cudaError_t e = cudaMemsetAsync(b->kcount, 0, K * sizeof(int32_t), c->stream);
+    if (e != cudaSuccess) return e;
+    k_batch_bounds_dyn<<<g, 256, 0, c->stream>>>(c->act_idx, c->sc, b->cid, b->kstart, b->kcount);
+    k_batch_counts<<<(K + 255) / 256, 256, 0, c->stream>>>(K, b->kstart, b->kcount);
+    k_batch_plan<<<1, BNT, 0, c->stream>>>(K, b->kcount, b->d_pk, b->d_nk, b->force_slots,
+                                           (long long)c->partial_cap, ncomp(c->order), c->prec == NB_MIXED,
+                                           b->d_items_cap, b->ksplit, b->kni, b->koff, c->sc);
+    k_batch_items<<<K, BNT, 0, c->stream>>>(b->kstart, b->kcount, b->ksplit, b->kni, b->koff, b->d_off, b->d_pk,
+                                            b->d_items_cap, b->d_items);
+    if ((e = launch_predict(c, 0.0, b->tblk, b->cid, c->sc)) != cudaSuccess) return e;
+    if (batch_force_dyn(b, false) != NB_OK) return cudaGetLastError();
+#define BRED(O)                                                                                                   \
+    k_batch_reduce_dyn<ncomp(O), pot_comp(O)><<<g, 256, 0, c->stream>>>(c->partial, c->act_idx, b->cid, b->ksplit, \
+                                                                        c->sc, c->F)
+    if (c->order == 4) BRED(4);
+    else if (c->order == 6) BRED(6);
+    else BRED(8);
+#undef BRED
+    if ((e = launch_correct(c, b->tblk, b->cid, c->sc)) != cudaSuccess) return e;
+    c->n_launch += BATCH_CYCLE_LAUNCHES;
+    return cudaGetLastError();
+}
+
+int batch_build_graph(nb_batch* b)
+{
+    nb_ctx* c = b->c;
+    batch_destroy_graph(b);
+    if (!b->graph_stream) B_CUDA(b, cudaStreamCreateWithFlags(&b->graph_stream, cudaStreamNonBlocking));
+    cudaStream_t saved = c->stream;
+    const int64_t launches = c->n_launch;
+    c->stream = b->graph_stream;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->graph_stream, cudaStreamCaptureModeThreadLocal);
+    for (int r = 0; e == cudaSuccess && r < b->graph_cycles; ++r) e = batch_cycle_launches(b);
+    const cudaError_t e2 = cudaStreamEndCapture(b->graph_stream, &g);
+    c->stream = saved;
+    c->n_launch = launches;  // counted per replay
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph_exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        batch_destroy_graph(b);
+        return berr(b, NB_ERR_CUDA, "ensemble cycle graph capture failed: %s", cudaGetErrorString(e));
+    }
+    return NB_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -549,8 +931,10 @@ void nb_batch_destroy(nb_batch* b)
 {
     if (!b) return;
     if (b->c) cudaStreamSynchronize(b->c->stream);
+    batch_destroy_graph(b);
+    if (b->graph_stream) cudaStreamDestroy(b->graph_stream);
     void* d[] = {b->cid, b->real_idx, b->d_off, b->d_nk, b->tblk, b->kstart, b->kcount, b->ksplit, b->chunk_cnt,
-                 b->items, b->esum};
+                 b->items, b->esum, b->d_pk, b->kni, b->koff, b->d_items};
     for (void* p : d)
         if (p) cudaFree(p);
     void* h[] = {b->h_tblk, b->h_kstart, b->h_kcount, b->h_ksplit, b->h_items, b->h_esum};
@@ -591,6 +975,7 @@ int nb_batch_create(nb_batch** out, int n_clusters, const int64_t* n_per_cluster
     if ((rc = balloc(b, &b->cid, (size_t)b->c->np)) || (rc = balloc(b, &b->real_idx, (size_t)b->n_real)) ||
         (rc = balloc(b, &b->d_off, K)) || (rc = balloc(b, &b->d_nk, K)) || (rc = balloc(b, &b->tblk, K)) ||
         (rc = balloc(b, &b->kstart, K)) || (rc = balloc(b, &b->kcount, K)) || (rc = balloc(b, &b->ksplit, K)) ||
+        (rc = balloc(b, &b->kni, K)) || (rc = balloc(b, &b->koff, K)) || (rc = balloc(b, &b->d_pk, K)) ||
         (rc = balloc(b, &b->chunk_cnt, (size_t)((slots + BCHUNK - 1) / BCHUNK))) ||
         (rc = balloc(b, &b->esum, 3 * (size_t)K))) {
         nb_batch_destroy(b);
@@ -613,7 +998,8 @@ int nb_batch_create(nb_batch** out, int n_clusters, const int64_t* n_per_cluster
     if (cudaMemcpy(b->cid, cid.data(), cid.size() * 4, cudaMemcpyHostToDevice) ||
         cudaMemcpy(b->real_idx, real.data(), real.size() * 4, cudaMemcpyHostToDevice) ||
         cudaMemcpy(b->d_off, b->off.data(), K * 8, cudaMemcpyHostToDevice) ||
-        cudaMemcpy(b->d_nk, b->nk.data(), K * 8, cudaMemcpyHostToDevice)) {
+        cudaMemcpy(b->d_nk, b->nk.data(), K * 8, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(b->d_pk, b->pk.data(), K * 8, cudaMemcpyHostToDevice)) {
         cudaGetLastError();
         nb_batch_destroy(b);
         return NB_ERR_CUDA;
@@ -625,11 +1011,17 @@ int nb_batch_create(nb_batch** out, int n_clusters, const int64_t* n_per_cluster
 
 int nb_batch_set_stream(nb_batch* b, void* stream) { return b ? nb_set_stream(b->c, stream) : NB_ERR_ARG; }
 
-int nb_batch_set_precision(nb_batch* b, int mode) { return b ? nb_set_precision(b->c, mode) : NB_ERR_ARG; }
+int nb_batch_set_precision(nb_batch* b, int mode)
+{
+    if (!b) return NB_ERR_ARG;
+    batch_destroy_graph(b);
+    return nb_set_precision(b->c, mode);
+}
 
 int nb_batch_set_params(nb_batch* b, double eta, double eta_s, double dt_max, double dt_min)
 {
     if (!b) return NB_ERR_ARG;
+    batch_destroy_graph(b);
     int rc = nb_set_params(b->c, eta, eta_s, dt_max, dt_min);
     if (rc != NB_OK) berr(b, rc, "%s", nb_last_error(b->c));
     return rc;
@@ -639,6 +1031,7 @@ int nb_batch_set_particles(nb_batch* b, const double* m, const double* x, const 
 {
     if (!b || !m || !x || !v) return NB_ERR_ARG;
     nb_ctx* c = b->c;
+    batch_destroy_graph(b);
     const size_t np = (size_t)c->np;
     std::vector<double> hm(np, 0.0), he(np, 1.0), hx(3 * np, 0.0), hv(3 * np, 0.0), ht(np, INFINITY), hdt(np, 0.0);
     const double e2 = c->eps * c->eps;
@@ -698,55 +1091,62 @@ int nb_batch_cycle(nb_batch* b, double t_end, int* n_stepped, int64_t* n_inter)
     if (!b) return NB_ERR_ARG;
     nb_ctx* c = b->c;
     if (!c->have_particles) return berr(b, NB_ERR_ARG, "nb_batch_cycle before nb_batch_set_particles");
-    const int K = b->K;
-    const int nch = (int)((c->n + BCHUNK - 1) / BCHUNK);
-    k_batch_min<<<K, BNT, 0, c->stream>>>(c->t, c->dt, b->d_off, b->d_nk, t_end, b->tblk, c->sc);
-    k_batch_count<<<nch, BNT, 0, c->stream>>>(c->t, c->dt, b->cid, b->tblk, c->n, b->chunk_cnt);
-    k_batch_scatter<<<nch, BNT, 0, c->stream>>>(c->t, c->dt, b->cid, b->tblk, c->n, b->chunk_cnt, nch, c->act_idx,
-                                                c->sc);
-    B_CUDA(b, cudaMemsetAsync(b->kcount, 0, K * sizeof(int32_t), c->stream));
+    if (!std::isfinite(t_end)) return berr(b, NB_ERR_ARG, "t_end must be finite");
+    B_TRY(batch_prepare(b));
+    B_TRY(batch_reset_scalars(b, t_end, c->stream));
+    B_CUDA(b, batch_cycle_launches(b));
     B_TRY(bsync(b));
-    const int n_act = (int)c->h_sc->n_act;
-    if (n_stepped) *n_stepped = 0;
-    if (n_inter) *n_inter = 0;
-    if (n_act == 0) return NB_OK;
-    k_batch_bounds<<<(n_act + 255) / 256, 256, 0, c->stream>>>(c->act_idx, n_act, b->cid, b->kstart, b->kcount);
-    k_batch_counts<<<(K + 255) / 256, 256, 0, c->stream>>>(K, b->kstart, b->kcount);
-    B_CUDA(b, cudaMemcpyAsync(b->h_kstart, b->kstart, K * 4, cudaMemcpyDeviceToHost, c->stream));
-    B_CUDA(b, cudaMemcpyAsync(b->h_kcount, b->kcount, K * 4, cudaMemcpyDeviceToHost, c->stream));
-    B_CUDA(b, cudaStreamSynchronize(c->stream));
-    c->n_launch += 6;
-    B_CUDA(b, launch_predict(c, 0.0, b->tblk, b->cid));
-    c->pred_prec = c->prec;
-    c->n_launch += 1;
-    B_TRY(batch_force(b, c->order, c->act_idx, n_act, b->h_kstart, b->h_kcount));
-    B_CUDA(b, cudaMemcpyAsync(c->f_idx, c->act_idx, (size_t)n_act * 4, cudaMemcpyDeviceToDevice, c->stream));
-    c->f_n = n_act;
-    B_CUDA(b, launch_correct(c, b->tblk, b->cid));
-    c->n_launch += 1;
-    int stepped = 0;
-    int64_t inter = 0;
-    for (int k = 0; k < K; ++k)
-        if (b->h_kcount[k] > 0) {
-            ++stepped;
-            inter += (int64_t)b->h_kcount[k] * b->nk[k];
-        }
-    if (n_stepped) *n_stepped = stepped;
-    if (n_inter) *n_inter = inter;
+    if (n_stepped) *n_stepped = c->h_sc->stepped;
+    if (n_inter) *n_inter = c->h_sc->inter;
+    return NB_OK;
+}
+
+int nb_batch_set_graph(nb_batch* b, int cycles)
+{
+    if (!b) return NB_ERR_ARG;
+    if (cycles < 0 || cycles > 4096) return berr(b, NB_ERR_ARG, "cycles must be in [0, 4096]");
+    batch_destroy_graph(b);
+    b->graph_cycles = cycles;
     return NB_OK;
 }
 
 int nb_batch_step_until(nb_batch* b, double t_end, int64_t* n_cycles, int64_t* n_inter)
 {
     if (!b) return NB_ERR_ARG;
+    nb_ctx* c = b->c;
+    if (!c->have_particles) return berr(b, NB_ERR_ARG, "nb_batch_step_until before nb_batch_set_particles");
+    if (!std::isfinite(t_end)) return berr(b, NB_ERR_ARG, "t_end must be finite");
     int64_t cycles = 0, inter = 0;
-    for (;;) {
-        int stepped = 0;
-        int64_t ni = 0;
-        B_TRY(nb_batch_cycle(b, t_end, &stepped, &ni));
-        if (stepped == 0) break;
-        ++cycles;
-        inter += ni;
+    if (b->graph_cycles > 0) {
+        B_TRY(batch_prepare(b));
+        if (!b->graph_exec) B_TRY(batch_build_graph(b));
+        B_CUDA(b, cudaStreamSynchronize(c->stream));
+        B_TRY(batch_reset_scalars(b, t_end, b->graph_stream));
+        DevScalars* h = c->h_sc;
+        for (;;) {
+            B_CUDA(b, cudaGraphLaunch(b->graph_exec, b->graph_stream));
+            c->n_launch += (int64_t)b->graph_cycles * BATCH_CYCLE_LAUNCHES;
+            B_CUDA(b, cudaMemcpyAsync(h, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, b->graph_stream));
+            B_CUDA(b, cudaStreamSynchronize(b->graph_stream));
+            if (h->status != NB_OK) {
+                const int st = h->status;
+                B_CUDA(b, cudaMemsetAsync(&c->sc->status, 0, sizeof(int), b->graph_stream));
+                B_CUDA(b, cudaStreamSynchronize(b->graph_stream));
+                return berr(b, st, "device kernel reported error %d", st);
+            }
+            if (h->idle) break;
+        }
+        cycles = h->blocks;
+        inter = h->inter;
+    } else {
+        for (;;) {
+            int stepped = 0;
+            int64_t ni = 0;
+            B_TRY(nb_batch_cycle(b, t_end, &stepped, &ni));
+            if (stepped == 0) break;
+            ++cycles;
+            inter += ni;
+        }
     }
     if (n_cycles) *n_cycles = cycles;
     if (n_inter) *n_inter = inter;

@@ -131,8 +131,10 @@ struct DevScalars {
     int status;       // first error raised by a kernel (NB_OK if none)
     int idle;         // device-driven cycle: the block is past t_end, do nothing
     double t_end;     // device-driven cycle: stop time
-    int itiles, jsplit, ni, pad2;  // device-driven cycle: force launch shape
-    long long blocks, inter;        // device-driven cycle: blocks taken, interactions
+    int itiles, jsplit, ni;        // device-driven cycle: force launch shape
+    int n_items;                   // ensemble cycle: force work items
+    long long blocks, inter;       // device-driven cycle: blocks (cycles) taken, interactions
+    int stepped, pad3;             // ensemble cycle: clusters stepped in the last cycle
 };
 
 // Relative precision of the force components (acc, jerk, snap, crackle) that

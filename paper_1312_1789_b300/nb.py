@@ -66,6 +66,7 @@ SIGNATURES = {
     "nb_set_graph": (C.c_int, [_P, C.c_int]),
     "nb_autotune": (C.c_int, [_P, C.c_int]),
     "nb_get_tuning": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int32), C.POINTER(C.c_int32), _D]),
+    "nb_set_tuning": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "nb_batch_create": (C.c_int, [C.POINTER(_P), C.c_int, _I64, C.c_int, C.c_double]),
     "nb_batch_destroy": (None, [_P]),
     "nb_batch_last_error": (C.c_char_p, [_P]),
@@ -75,6 +76,7 @@ SIGNATURES = {
     "nb_batch_set_particles": (C.c_int, [_P, _D, _D, _D]),
     "nb_batch_cycle": (C.c_int, [_P, C.c_double, C.POINTER(C.c_int), _I64]),
     "nb_batch_step_until": (C.c_int, [_P, C.c_double, _I64, _I64]),
+    "nb_batch_set_graph": (C.c_int, [_P, C.c_int]),
     "nb_batch_energy": (C.c_int, [_P, _D, _D]),
     "nb_batch_get_state": (C.c_int, [_P, _D, _D, _D, _D]),
 }
@@ -196,6 +198,13 @@ class NBody:
         self._check(self._L.nb_get_tuning(self._h, C.byref(n), ni.ctypes.data_as(C.POINTER(C.c_int32)),
                                           js.ctypes.data_as(C.POINTER(C.c_int32)), _d(ms)))
         return [(k, int(ni[k]), int(js[k]), float(ms[k])) for k in range(n.value)]
+
+    def set_tuning(self, table):
+        """Install [(k, ni, js, ...)] (as get_tuning returns) for the current precision; [] drops it."""
+        ni = np.array([e[1] for e in table] or [0], dtype=np.int32)
+        js = np.array([e[2] for e in table] or [0], dtype=np.int32)
+        self._check(self._L.nb_set_tuning(self._h, len(table), ni.ctypes.data_as(C.POINTER(C.c_int32)),
+                                          js.ctypes.data_as(C.POINTER(C.c_int32))))
 
     def set_jsplit(self, js: int):
         self._check(self._L.nb_set_jsplit(self._h, int(js)))
@@ -351,6 +360,10 @@ class Batch:
     def set_particles(self, m, x, v):
         m = np.ascontiguousarray(m, dtype=np.float64)
         self._check(self._L.nb_batch_set_particles(self._h, _d(m), _d(_vec(x, self.n)), _d(_vec(v, self.n))))
+
+    def set_graph(self, cycles: int):
+        """cycles > 0: step_until replays a CUDA graph of that many ensemble cycles."""
+        self._check(self._L.nb_batch_set_graph(self._h, int(cycles)))
 
     def cycle(self, t_end: float):
         k = C.c_int()

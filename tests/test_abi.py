@@ -59,6 +59,8 @@ def test_null_context_is_rejected(libnb):
     assert libnb.nb_set_graph(None, 4) == -1
     assert libnb.nb_autotune(None, 1) == -1
     assert libnb.nb_get_tuning(None, None, None, None, None) == -1
+    assert libnb.nb_batch_set_graph(None, 2) == -1
+    assert libnb.nb_set_tuning(None, 0, None, None) == -1
     libnb.nb_destroy(None)
 
 

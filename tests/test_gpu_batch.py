@@ -26,14 +26,17 @@ def _clusters(sizes, eps=1e-4):
     return ms, xs, vs
 
 
+@pytest.mark.parametrize("graph", [0, 7], ids=["host_cycles", "graph_cycles"])
 @pytest.mark.parametrize("order", [4, 6, 8])
-def test_batch_fp64_matches_each_cluster_alone(order):
-    # Ragged cluster sizes (not multiples of the 128-record tile, one below it).
+def test_batch_fp64_matches_each_cluster_alone(order, graph):
+    # Ragged cluster sizes (not multiples of the 128-record tile, one below it);
+    # cycles checked on the host one by one, or replayed 7 at a time as a graph.
     sizes = [300, 129, 1000, 64, 700]
     ms, xs, vs = _clusters(sizes)
     eta = 0.02 if order == 4 else 0.2
     b = nb.Batch(sizes, order, 1e-4, nb.NB_FP64)
     b.set_params(eta, 0.01, 1.0 / 16, 2.0 ** -40)
+    b.set_graph(graph)
     b.set_particles(np.concatenate(ms), np.concatenate(xs), np.concatenate(vs))
     ncyc, ninter = b.step_until(1.0 / 16)
     assert ncyc > 0 and ninter > 0
@@ -91,3 +94,25 @@ def test_batch_matches_separate_contexts_mixed():
         c.close()
         off += n
     b.close()
+
+
+@pytest.mark.parametrize("prec", [nb.NB_FP64, nb.NB_MIXED])
+def test_batch_graph_cycles_match_host_cycles_bitwise(prec):
+    # The device plans every cycle in both modes, so a graph replay of the
+    # cycles reproduces the host-checked cycles bit for bit, including the
+    # cycles where only some clusters step and the idle tail past t_end.
+    sizes = [2000, 130, 5, 900, 3000, 64]
+    ms, xs, vs = _clusters(sizes)
+    out = []
+    for cycles in (0, 9):
+        b = nb.Batch(sizes, 6, 1e-4, prec)
+        b.set_graph(cycles)
+        b.set_particles(np.concatenate(ms), np.concatenate(xs), np.concatenate(vs))
+        first = b.step_until(1.0 / 64)
+        second = b.step_until(1.0 / 32)
+        out.append(((first, second), b.get_state()))
+        b.close()
+    (c0, s0), (c1, s1) = out
+    assert c0 == c1 and c0[0][0] > 0
+    for key in ("x", "v", "t", "dt"):
+        assert np.array_equal(s0[key], s1[key]), key

@@ -181,13 +181,30 @@ def test_predictor_parity(prec, order):
         if order >= 8:
             assert np.all(np.abs(jg - jo) <= 1e-13 * np.maximum(np.abs(jo), 1.0))
     else:
-        # double-single position: |hi + lo - x| <= 2^-48 |x|; the rest is one float rounding
-        assert np.all(np.abs(xg - xo) <= 2e-14 * np.maximum(np.abs(xo), 1e-3))
-        assert np.all(np.abs(vg - vo) <= 1.2e-7 * np.abs(vo) + 1e-15)
+        # x = x0 + h (v0 + h T) in FP64, stored double-single (|hi + lo - x| <=
+        # 2^-48 |x|); the tail T and the predicted v, a, jerk are FP32 Horner
+        # sums: a few float roundings (2^-21) of the magnitudes of their terms.
+        h = np.abs(tb - S["t"])[:, None]
+        D = np.abs(S["d"])  # [n][6][3]: a, j, s, c, d4a, d5a
+        nd = 6 if order == 8 else 4
+        fact = [math.factorial(k) for k in range(10)]
+
+        def mag(first, start, kmin):
+            # |first| + sum_{k >= kmin} |d_(start + k - kmin)| h^k / k!
+            out = np.abs(first).copy() if first is not None else 0.0
+            for q in range(start, nd):
+                k = kmin + q - start
+                out = out + D[:, q, :] * h ** k / fact[k]
+            return out
+
+        u = 2.0 ** -21
+        tail_x = mag(None, 0, 2)
+        assert np.all(np.abs(xg - xo) <= 2e-14 * np.maximum(np.abs(xo), 1e-3) + u * tail_x)
+        assert np.all(np.abs(vg - vo) <= u * mag(S["v"], 0, 1) + 1e-15)
         if order >= 6:
-            assert np.all(np.abs(ag - ao) <= 1.2e-7 * np.abs(ao) + 1e-14)
+            assert np.all(np.abs(ag - ao) <= u * mag(S["d"][:, 0, :], 1, 1) + 1e-14)
         if order >= 8:
-            assert np.all(np.abs(jg - jo) <= 1.2e-7 * np.abs(jo) + 1e-13)
+            assert np.all(np.abs(jg - jo) <= u * mag(S["d"][:, 1, :], 2, 1) + 1e-13)
 
 
 # -------------------------------------------------------------------- scheduler

@@ -49,6 +49,8 @@ def test_autotune_table_shapes_and_parity():
         assert_force_close(ctx.get_force(na), O, 6, nb.NB_MIXED, f"tuned shape n_act {na}")
     ctx.autotune(0)
     assert ctx.get_tuning() == []
+    with pytest.raises(nb.NBError):
+        ctx.set_tuning([(0, 64, 1, 0.0)])  # no such variant
     ctx.close()
 
 
@@ -67,12 +69,19 @@ def test_autotune_fp64_table_is_per_precision():
 
 
 def test_autotuned_graph_cycles_match_host_cycles_bitwise():
+    # One measured table, installed in both contexts (a second measurement
+    # could pick other shapes, whose rounding differs).
     n = 1800
     m, x, v = ics.plummer(n, 23)
+    ctx = make_ctx(m, x, v, 1e-8, 6, nb.NB_MIXED)
+    ctx.autotune(1)
+    table = ctx.get_tuning()
+    ctx.close()
     states = []
     for cycles in (0, 6):
         ctx = make_ctx(m, x, v, 1e-8, 6, nb.NB_MIXED)
-        ctx.autotune(1)
+        ctx.set_tuning(table)
+        assert [e[:3] for e in ctx.get_tuning()] == [e[:3] for e in table]
         ctx.set_graph(cycles)
         counts = ctx.step_until(1.0 / 32)
         states.append((counts, ctx.get_state()))
