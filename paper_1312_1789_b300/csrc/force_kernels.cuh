@@ -193,6 +193,94 @@ __device__ __forceinline__ void pair_mixed(const float4 w0, const float4 w1, con
     acc[NC - 1] = fmaf(mr, rinv, acc[NC - 1]);
 }
 
+// Two i-particles in the two lanes of packed FP32x2 arithmetic (FFMA2 and
+// kin on sm_100+), the j record broadcast to both: one instruction does the
+// work of two.  Same pair terms and operation order as pair_mixed.  The i
+// values are held negated (n*) so that every difference is an add.
+struct IMixed2 {
+    float2 nxh[3], nxl[3], nv[3], na[3], nk[3];
+    float2 e2;  // eps_i^2 (per-particle softening) or the uniform pair value
+};
+
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+
+template <int ORDER, bool PAIR>
+__device__ __forceinline__ void pair_mixed_x2(const float4 w0, const float4 w1, const float4 w2, const float4 w3,
+                                              const float4 w4, const IMixed2& I, float2 (&acc)[ncomp(ORDER)])
+{
+    constexpr int NC = ncomp(ORDER);
+    const float2 dx = __fadd2_rn(__fadd2_rn(bc2(w0.x), I.nxh[0]), __fadd2_rn(bc2(w1.x), I.nxl[0]));
+    const float2 dy = __fadd2_rn(__fadd2_rn(bc2(w0.y), I.nxh[1]), __fadd2_rn(bc2(w1.y), I.nxl[1]));
+    const float2 dz = __fadd2_rn(__fadd2_rn(bc2(w0.z), I.nxh[2]), __fadd2_rn(bc2(w1.z), I.nxl[2]));
+    const float2 e2 = PAIR ? make_float2(fmaxf(w1.w, I.e2.x), fmaxf(w1.w, I.e2.y)) : I.e2;
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+    const float2 rinv = make_float2(guard_rinv<PAIR>(r2.x), guard_rinv<PAIR>(r2.y));
+    const float2 mr = __fmul2_rn(bc2(w0.w), rinv);
+    if (ORDER == 0) {
+        acc[0] = __fadd2_rn(acc[0], mr);
+        return;
+    }
+    const float2 rinv2 = __fmul2_rn(rinv, rinv);
+    const float2 q = __fmul2_rn(mr, rinv2);
+    const float2 r3 = __fmul2_rn(bc2(-3.0f), rinv2);
+    const float2 dvx = __fadd2_rn(bc2(w2.x), I.nv[0]), dvy = __fadd2_rn(bc2(w2.y), I.nv[1]),
+                 dvz = __fadd2_rn(bc2(w2.z), I.nv[2]);
+    acc[0] = __ffma2_rn(q, dx, acc[0]);
+    acc[1] = __ffma2_rn(q, dy, acc[1]);
+    acc[2] = __ffma2_rn(q, dz, acc[2]);
+    const float2 a3 = __fmul2_rn(__ffma2_rn(dx, dvx, __ffma2_rn(dy, dvy, __fmul2_rn(dz, dvz))), r3);
+    acc[3] = __ffma2_rn(q, __ffma2_rn(a3, dx, dvx), acc[3]);
+    acc[4] = __ffma2_rn(q, __ffma2_rn(a3, dy, dvy), acc[4]);
+    acc[5] = __ffma2_rn(q, __ffma2_rn(a3, dz, dvz), acc[5]);
+    if (ORDER >= 6) {
+        const float2 dax = __fadd2_rn(bc2(w3.x), I.na[0]), day = __fadd2_rn(bc2(w3.y), I.na[1]),
+                     daz = __fadd2_rn(bc2(w3.z), I.na[2]);
+        const float2 ww3 = __fmul2_rn(
+            __ffma2_rn(dvx, dvx,
+                       __ffma2_rn(dvy, dvy,
+                                  __ffma2_rn(dvz, dvz, __ffma2_rn(dx, dax, __ffma2_rn(dy, day, __fmul2_rn(dz, daz)))))),
+            r3);
+        const float2 c2 = __fadd2_rn(a3, a3);
+        const float2 c3 = __ffma2_rn(__fmul2_rn(bc2(5.0f / 3.0f), a3), a3, ww3);
+        acc[6] = __ffma2_rn(q, __ffma2_rn(c3, dx, __ffma2_rn(c2, dvx, dax)), acc[6]);
+        acc[7] = __ffma2_rn(q, __ffma2_rn(c3, dy, __ffma2_rn(c2, dvy, day)), acc[7]);
+        acc[8] = __ffma2_rn(q, __ffma2_rn(c3, dz, __ffma2_rn(c2, dvz, daz)), acc[8]);
+        if (ORDER >= 8) {
+            const float2 dkx = __fadd2_rn(bc2(w4.x), I.nk[0]), dky = __fadd2_rn(bc2(w4.y), I.nk[1]),
+                         dkz = __fadd2_rn(bc2(w4.z), I.nk[2]);
+            const float2 u3 = __fmul2_rn(
+                __ffma2_rn(bc2(3.0f), __ffma2_rn(dvx, dax, __ffma2_rn(dvy, day, __fmul2_rn(dvz, daz))),
+                           __ffma2_rn(dx, dkx, __ffma2_rn(dy, dky, __fmul2_rn(dz, dkz)))),
+                r3);
+            const float2 c4 = __fmul2_rn(bc2(3.0f), a3);
+            const float2 c5 = __ffma2_rn(__fmul2_rn(bc2(5.0f), a3), a3, __fmul2_rn(bc2(3.0f), ww3));
+            const float2 c6 =
+                __ffma2_rn(a3, __ffma2_rn(__fmul2_rn(bc2(35.0f / 9.0f), a3), a3, __fmul2_rn(bc2(5.0f), ww3)), u3);
+            acc[9] = __ffma2_rn(q, __ffma2_rn(c6, dx, __ffma2_rn(c5, dvx, __ffma2_rn(c4, dax, dkx))), acc[9]);
+            acc[10] = __ffma2_rn(q, __ffma2_rn(c6, dy, __ffma2_rn(c5, dvy, __ffma2_rn(c4, day, dky))), acc[10]);
+            acc[11] = __ffma2_rn(q, __ffma2_rn(c6, dz, __ffma2_rn(c5, dvz, __ffma2_rn(c4, daz, dkz))), acc[11]);
+        }
+    }
+    acc[NC - 2] = __fadd2_rn(acc[NC - 2], mr);
+    acc[NC - 1] = __ffma2_rn(mr, rinv, acc[NC - 1]);
+}
+
+template <int ORDER, int RW, bool PAIR>
+__device__ __forceinline__ void tile_mixed_x2(const float4* __restrict__ b, const IMixed2& I,
+                                              float2 (&acc)[ncomp(ORDER)])
+{
+#pragma unroll 1
+    for (int jj = 0; jj < JT; ++jj) {
+        const float4 w0 = b[jj * RW + 0];
+        const float4 w1 = b[jj * RW + 1];
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 w2 = ORDER >= 4 ? b[jj * RW + 2] : z;
+        const float4 w3 = ORDER >= 6 ? b[jj * RW + 3] : z;
+        const float4 w4 = ORDER >= 8 ? b[jj * RW + 4] : z;
+        pair_mixed_x2<ORDER, PAIR>(w0, w1, w2, w3, w4, I, acc);
+    }
+}
+
 // One j tile for IPT i-particles: every record is read once from shared
 // memory and applied to each i-particle of the thread.  SELF: the tile may
 // hold one of the thread's own particles (at self_rel[q]).
@@ -273,6 +361,27 @@ __device__ __forceinline__ void force_block_mixed(const float4* __restrict__ js,
     // particle pairs with the constant eps_i^2: the per-pair max and the
     // R^2 = 0 guard drop out (same results, fewer instructions).
     const bool dom = PAIR && __all_sync(0xffffffffu, dom_lane);
+    IMixed2 I2;
+    if (IPT == 2) {
+        const IMixed& a = I[0];
+        const IMixed& z = I[IPT - 1];
+        I2.nxh[0] = make_float2(-a.i0.x, -z.i0.x);
+        I2.nxh[1] = make_float2(-a.i0.y, -z.i0.y);
+        I2.nxh[2] = make_float2(-a.i0.z, -z.i0.z);
+        I2.nxl[0] = make_float2(-a.i1.x, -z.i1.x);
+        I2.nxl[1] = make_float2(-a.i1.y, -z.i1.y);
+        I2.nxl[2] = make_float2(-a.i1.z, -z.i1.z);
+        I2.nv[0] = make_float2(-a.i2.x, -z.i2.x);
+        I2.nv[1] = make_float2(-a.i2.y, -z.i2.y);
+        I2.nv[2] = make_float2(-a.i2.z, -z.i2.z);
+        I2.na[0] = make_float2(-a.i3.x, -z.i3.x);
+        I2.na[1] = make_float2(-a.i3.y, -z.i3.y);
+        I2.na[2] = make_float2(-a.i3.z, -z.i3.z);
+        I2.nk[0] = make_float2(-a.i4.x, -z.i4.x);
+        I2.nk[1] = make_float2(-a.i4.y, -z.i4.y);
+        I2.nk[2] = make_float2(-a.i4.z, -z.i4.z);
+        I2.e2 = make_float2(ei2[0], ei2[IPT - 1]);
+    }
 
     float hi[IPT][NC], lo[IPT][NC];
 #pragma unroll
@@ -310,7 +419,19 @@ __device__ __forceinline__ void force_block_mixed(const float4* __restrict__ js,
         const bool self_here = __any_sync(0xffffffffu, mine);
         // ei2 holds eps_i^2 (per-particle softening) or the uniform eps^2; on the
         // uniform and dominant paths it is the pair value itself
-        if (!PAIR || dom) {
+        if (IPT == 2 && !self_here) {
+            // both i-particles in the lanes of packed FP32x2 instructions
+            float2 acc2[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc2[c] = make_float2(0.f, 0.f);
+            if (!PAIR || dom) tile_mixed_x2<ORDER, RW, false>(b, I2, acc2);
+            else tile_mixed_x2<ORDER, RW, true>(b, I2, acc2);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                acc[0][c] = acc2[c].x;
+                acc[IPT - 1][c] = acc2[c].y;
+            }
+        } else if (!PAIR || dom) {
             if (self_here) tile_mixed<ORDER, RW, false, true, IPT>(b, I, ei2, self_rel, acc);
             else tile_mixed<ORDER, RW, false, false, IPT>(b, I, ei2, self_rel, acc);
         } else {

@@ -217,15 +217,21 @@ __global__ void __launch_bounds__(256) k_predict(const double* __restrict__ m, c
         ei = eps2[i];
         const double h = tp - t[i];
         const float hf = (float)h;
+        // Mixed: the FP32 tail needs every derivative within the float range
+        // (interpolated high derivatives of a particle just out of a close
+        // encounter can exceed it); such a particle takes the FP64 series.
+        bool fp64_series = !MIXED;
+        if (MIXED) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const double x0 = x[c * np + i], v0 = v[c * np + i];
-            if (MIXED) {
+            for (int c = 0; c < 3; ++c) {
+                const double x0 = x[c * np + i], v0 = v[c * np + i];
                 const float a0 = (float)d[(0 * 3 + c) * np + i], j0 = (float)d[(1 * 3 + c) * np + i];
                 const float s0 = (float)d[(2 * 3 + c) * np + i], c0 = (float)d[(3 * 3 + c) * np + i];
                 float T;
+                bool fin = isfinite(a0) && isfinite(j0) && isfinite(s0) && isfinite(c0);
                 if (ORDER == 8) {
                     const float d4 = (float)d[(4 * 3 + c) * np + i], d5 = (float)d[(5 * 3 + c) * np + i];
+                    fin = fin && isfinite(d4) && isfinite(d5);
                     T = fmaf(hf, fmaf(hf, fmaf(hf, fmaf(hf, fmaf(hf, d5 * (1.f / 5040), d4 * (1.f / 720)),
                                                          c0 * (1.f / 120)), s0 * (1.f / 24)), j0 * (1.f / 6)),
                              a0 * 0.5f);
@@ -241,8 +247,15 @@ __global__ void __launch_bounds__(256) k_predict(const double* __restrict__ m, c
                                  (float)v0);
                     af[c] = fmaf(hf, fmaf(hf, fmaf(hf, c0 * (1.f / 6), s0 * 0.5f), j0), a0);
                 }
+                fin = fin && isfinite(T) && isfinite(vf[c]) && isfinite(af[c]) && isfinite(jf[c]);
+                fp64_series = fp64_series || !fin;
                 xp[c] = fma(h, fma(h, (double)T, v0), x0);
-            } else {
+            }
+        }
+        if (fp64_series) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double x0 = x[c * np + i], v0 = v[c * np + i];
                 const double a0 = d[(0 * 3 + c) * np + i], j0 = d[(1 * 3 + c) * np + i];
                 const double s0 = d[(2 * 3 + c) * np + i], c0 = d[(3 * 3 + c) * np + i];
                 if (ORDER == 8) {
@@ -260,6 +273,9 @@ __global__ void __launch_bounds__(256) k_predict(const double* __restrict__ m, c
                     vp[c] = v0 + h * (a0 + h * (j0 * (1.0 / 2) + h * (s0 * (1.0 / 6) + h * c0 * (1.0 / 24))));
                     ap[c] = a0 + h * (j0 + h * (s0 * (1.0 / 2) + h * c0 * (1.0 / 6)));
                 }
+                vf[c] = (float)vp[c];
+                af[c] = (float)ap[c];
+                jf[c] = (float)jp[c];
             }
         }
     }
@@ -501,6 +517,7 @@ __global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fid
     }
 
     // two-point Hermite corrector of order p for v' = a, then x' = v
+    bool finite_state = true;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const double v0 = v[c * np + i], x0 = x[c * np + i];
@@ -521,12 +538,18 @@ __global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fid
         }
         v[c * np + i] = v1;
         x[c * np + i] = x1;
+        finite_state = finite_state && fabs(v1) < INFINITY && fabs(x1) < INFINITY;
     }
 
     // derivative norms at t1, the interpolated ones net of their noise floor
     double nrm[8], nL[4], nR[4], N[8];
 #pragma unroll
-    for (int k = 0; k < 2 * MM; ++k) nrm[k] = norm3(H[k]);
+    for (int k = 0; k < 2 * MM; ++k) {
+        nrm[k] = norm3(H[k]);
+        finite_state = finite_state && nrm[k] < INFINITY;  // false for inf and NaN
+    }
+    // the floored criterion below would read a non-finite derivative as zero
+    if (!finite_state) raise_status(sc, NB_ERR_NAN);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         nL[k] = norm3(L[k]);

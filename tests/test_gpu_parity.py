@@ -207,6 +207,34 @@ def test_predictor_parity(prec, order):
             assert np.all(np.abs(jg - jo) <= u * mag(S["d"][:, 1, :], 2, 1) + 1e-13)
 
 
+def test_mixed_predictor_takes_fp64_series_past_the_float_range():
+    # Interpolated high derivatives of a particle just out of a close
+    # encounter can exceed the float range: the mixed predictor must then
+    # evaluate that particle's series in FP64 (no inf/NaN, the FP64 result),
+    # both for h = 0 (the particle is at the block time) and for small h.
+    n = 300
+    m, x, v, eps2 = _system(n, 33, "plummer")
+    ctx = make_ctx(m, x, v, eps2, 8, nb.NB_MIXED)
+    S = ctx.get_state()
+    d = S["d"].copy()
+    t = np.zeros(n)
+    dt = np.full(n, 2.0 ** -4)
+    d[5, 4, 0] = 1e45    # d4a beyond FLT_MAX; particle 5 predicted with h = 0
+    d[7, 4, 1] = -2e45   # particle 7 predicted with h = 2^-24
+    d[7, 5, 2] = 3e50
+    t[7] = -(2.0 ** -24)
+    ctx.set_state(S["x"], S["v"], d, t, dt)
+    ctx.predict(0.0)
+    xg, vg, ag, jg = ctx.get_predicted()
+    assert np.all(np.isfinite(xg)) and np.all(np.isfinite(vg)) and np.all(np.isfinite(ag)) and np.all(np.isfinite(jg))
+    xo, vo, ao, jo = orc.predict(8, 0.0, t, S["x"], S["v"], d)
+    for i in (5, 7):
+        scale = np.abs(xo[i]) + np.abs(S["x"][i]) + 1.0
+        assert np.all(np.abs(xg[i] - xo[i]) <= 1e-13 * scale), (i, xg[i], xo[i])
+        assert np.all(np.abs(vg[i] - vo[i]) <= 1.2e-7 * (np.abs(vo[i]) + np.abs(S["v"][i])) + 1e-15)
+    ctx.close()
+
+
 # -------------------------------------------------------------------- scheduler
 def test_scheduler_parity():
     n = 2048 + 300  # more than one scheduler chunk, ragged
