@@ -204,9 +204,10 @@ struct IMixed2 {
 
 __device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
 
-template <int ORDER, bool PAIR>
+template <int ORDER, bool PAIR, bool SELF = false>
 __device__ __forceinline__ void pair_mixed_x2(const float4 w0, const float4 w1, const float4 w2, const float4 w3,
-                                              const float4 w4, const IMixed2& I, float2 (&acc)[ncomp(ORDER)])
+                                              const float4 w4, const IMixed2& I, float2 (&acc)[ncomp(ORDER)],
+                                              const int2 srel = make_int2(-1, -1), const int jj = 0)
 {
     constexpr int NC = ncomp(ORDER);
     const float2 dx = __fadd2_rn(__fadd2_rn(bc2(w0.x), I.nxh[0]), __fadd2_rn(bc2(w1.x), I.nxl[0]));
@@ -214,7 +215,11 @@ __device__ __forceinline__ void pair_mixed_x2(const float4 w0, const float4 w1, 
     const float2 dz = __fadd2_rn(__fadd2_rn(bc2(w0.z), I.nxh[2]), __fadd2_rn(bc2(w1.z), I.nxl[2]));
     const float2 e2 = PAIR ? make_float2(fmaxf(w1.w, I.e2.x), fmaxf(w1.w, I.e2.y)) : I.e2;
     const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
-    const float2 rinv = make_float2(guard_rinv<PAIR>(r2.x), guard_rinv<PAIR>(r2.y));
+    float2 rinv = make_float2(guard_rinv<PAIR>(r2.x), guard_rinv<PAIR>(r2.y));
+    if (SELF) {  // a lane's own record: every term carries rinv
+        if (jj == srel.x) rinv.x = 0.0f;
+        if (jj == srel.y) rinv.y = 0.0f;
+    }
     const float2 mr = __fmul2_rn(bc2(w0.w), rinv);
     if (ORDER == 0) {
         acc[0] = __fadd2_rn(acc[0], mr);
@@ -265,9 +270,11 @@ __device__ __forceinline__ void pair_mixed_x2(const float4 w0, const float4 w1, 
     acc[NC - 1] = __ffma2_rn(mr, rinv, acc[NC - 1]);
 }
 
-template <int ORDER, int RW, bool PAIR>
-__device__ __forceinline__ void tile_mixed_x2(const float4* __restrict__ b, const IMixed2& I,
-                                              float2 (&acc)[ncomp(ORDER)])
+// One j tile for NP lane-pairs (2 NP i-particles) of a thread: every record
+// is read once from shared memory and applied to each pair.
+template <int ORDER, int RW, bool PAIR, bool SELF, int NP>
+__device__ __forceinline__ void tile_mixed_xn(const float4* __restrict__ b, const IMixed2 (&I)[NP],
+                                              const int2 (&srel)[NP], float2 (&acc)[NP][ncomp(ORDER)])
 {
 #pragma unroll 1
     for (int jj = 0; jj < JT; ++jj) {
@@ -277,8 +284,39 @@ __device__ __forceinline__ void tile_mixed_x2(const float4* __restrict__ b, cons
         const float4 w2 = ORDER >= 4 ? b[jj * RW + 2] : z;
         const float4 w3 = ORDER >= 6 ? b[jj * RW + 3] : z;
         const float4 w4 = ORDER >= 8 ? b[jj * RW + 4] : z;
-        pair_mixed_x2<ORDER, PAIR>(w0, w1, w2, w3, w4, I, acc);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) pair_mixed_x2<ORDER, PAIR, SELF>(w0, w1, w2, w3, w4, I[p], acc[p], srel[p], jj);
     }
+}
+
+__device__ __forceinline__ IMixed2 pack_pair(const IMixed& a, const IMixed& z, float ea, float ez)
+{
+    IMixed2 r;
+    r.nxh[0] = make_float2(-a.i0.x, -z.i0.x);
+    r.nxh[1] = make_float2(-a.i0.y, -z.i0.y);
+    r.nxh[2] = make_float2(-a.i0.z, -z.i0.z);
+    r.nxl[0] = make_float2(-a.i1.x, -z.i1.x);
+    r.nxl[1] = make_float2(-a.i1.y, -z.i1.y);
+    r.nxl[2] = make_float2(-a.i1.z, -z.i1.z);
+    r.nv[0] = make_float2(-a.i2.x, -z.i2.x);
+    r.nv[1] = make_float2(-a.i2.y, -z.i2.y);
+    r.nv[2] = make_float2(-a.i2.z, -z.i2.z);
+    r.na[0] = make_float2(-a.i3.x, -z.i3.x);
+    r.na[1] = make_float2(-a.i3.y, -z.i3.y);
+    r.na[2] = make_float2(-a.i3.z, -z.i3.z);
+    r.nk[0] = make_float2(-a.i4.x, -z.i4.x);
+    r.nk[1] = make_float2(-a.i4.y, -z.i4.y);
+    r.nk[2] = make_float2(-a.i4.z, -z.i4.z);
+    r.e2 = make_float2(ea, ez);
+    return r;
+}
+
+// Dynamic shared memory of the force variants that keep their double-single
+// sums in shared memory (NP lane-pairs per thread): the TMA ring, then
+// (hi, lo) float2 [NC][2 NP][FORCE_NT].
+__host__ __device__ constexpr size_t xs_smem(int order, int rw, int np)
+{
+    return (size_t)NSTAGE * JT * rw * 16 + (size_t)ncomp(order) * 2 * np * FORCE_NT * 8;
 }
 
 // One j tile for IPT i-particles: every record is read once from shared
@@ -361,27 +399,6 @@ __device__ __forceinline__ void force_block_mixed(const float4* __restrict__ js,
     // particle pairs with the constant eps_i^2: the per-pair max and the
     // R^2 = 0 guard drop out (same results, fewer instructions).
     const bool dom = PAIR && __all_sync(0xffffffffu, dom_lane);
-    IMixed2 I2;
-    if (IPT == 2) {
-        const IMixed& a = I[0];
-        const IMixed& z = I[IPT - 1];
-        I2.nxh[0] = make_float2(-a.i0.x, -z.i0.x);
-        I2.nxh[1] = make_float2(-a.i0.y, -z.i0.y);
-        I2.nxh[2] = make_float2(-a.i0.z, -z.i0.z);
-        I2.nxl[0] = make_float2(-a.i1.x, -z.i1.x);
-        I2.nxl[1] = make_float2(-a.i1.y, -z.i1.y);
-        I2.nxl[2] = make_float2(-a.i1.z, -z.i1.z);
-        I2.nv[0] = make_float2(-a.i2.x, -z.i2.x);
-        I2.nv[1] = make_float2(-a.i2.y, -z.i2.y);
-        I2.nv[2] = make_float2(-a.i2.z, -z.i2.z);
-        I2.na[0] = make_float2(-a.i3.x, -z.i3.x);
-        I2.na[1] = make_float2(-a.i3.y, -z.i3.y);
-        I2.na[2] = make_float2(-a.i3.z, -z.i3.z);
-        I2.nk[0] = make_float2(-a.i4.x, -z.i4.x);
-        I2.nk[1] = make_float2(-a.i4.y, -z.i4.y);
-        I2.nk[2] = make_float2(-a.i4.z, -z.i4.z);
-        I2.e2 = make_float2(ei2[0], ei2[IPT - 1]);
-    }
 
     float hi[IPT][NC], lo[IPT][NC];
 #pragma unroll
@@ -419,19 +436,7 @@ __device__ __forceinline__ void force_block_mixed(const float4* __restrict__ js,
         const bool self_here = __any_sync(0xffffffffu, mine);
         // ei2 holds eps_i^2 (per-particle softening) or the uniform eps^2; on the
         // uniform and dominant paths it is the pair value itself
-        if (IPT == 2 && !self_here) {
-            // both i-particles in the lanes of packed FP32x2 instructions
-            float2 acc2[NC];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) acc2[c] = make_float2(0.f, 0.f);
-            if (!PAIR || dom) tile_mixed_x2<ORDER, RW, false>(b, I2, acc2);
-            else tile_mixed_x2<ORDER, RW, true>(b, I2, acc2);
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                acc[0][c] = acc2[c].x;
-                acc[IPT - 1][c] = acc2[c].y;
-            }
-        } else if (!PAIR || dom) {
+        if (!PAIR || dom) {
             if (self_here) tile_mixed<ORDER, RW, false, true, IPT>(b, I, ei2, self_rel, acc);
             else tile_mixed<ORDER, RW, false, false, IPT>(b, I, ei2, self_rel, acc);
         } else {
@@ -459,6 +464,152 @@ __device__ __forceinline__ void force_block_mixed(const float4* __restrict__ js,
                 store_result<NC, pot_comp(ORDER)>(partial, split, ncol, p, c, (double)hi[q][c] + (double)lo[q][c], ts);
         }
     }
+}
+
+// Packed form with 2 NP i-particles per thread (positions t + q FORCE_NT,
+// q < 2 NP, paired as lanes (2p, 2p+1)): every tile in packed FP32x2
+// arithmetic, the self tile with per-lane masking; the double-single sums
+// live in shared memory behind the ring (folded once per tile), so that the
+// registers hold only the i-data and one tile's FP32 sums.
+template <int ORDER, int RW, bool PAIR, int NP>
+__device__ __forceinline__ void force_block_mixed_xs(const float4* __restrict__ js, const int32_t* __restrict__ idx,
+                                                     const int pbase0, const int plim, const int n, const int t0,
+                                                     const int nt, const int split, const int ncol,
+                                                     const float eps2u, const float eps2max,
+                                                     double* __restrict__ partial, DevScalars* sc,
+                                                     const TileSum ts = TileSum{})
+{
+    constexpr int NC = ncomp(ORDER);
+    constexpr int NQ = 2 * NP;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float4* buf = reinterpret_cast<float4*>(smem_raw);
+    float2* dsum = reinterpret_cast<float2*>(smem_raw + (size_t)NSTAGE * JT * RW * 16);
+    __shared__ __align__(8) uint64_t bars[NSTAGE];
+
+    const int tid = threadIdx.x;
+    const int pbase = pbase0 + tid;
+    constexpr uint32_t TILE_BYTES = JT * RW * 16;
+
+    if (tid == 0) {
+        for (int k = 0; k < NSTAGE; ++k) mbar_init(&bars[k], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int k = 0; k < NSTAGE && k < nt; ++k) {
+            mbar_expect_tx(&bars[k], TILE_BYTES);
+            bulk_g2s(buf + k * JT * RW, js + (size_t)(t0 + k) * JT * RW, TILE_BYTES, &bars[k]);
+        }
+    }
+
+    IMixed2 I2[NP];
+    int gi[NQ];
+    bool dom_lane = true;
+#pragma unroll
+    for (int pp = 0; pp < NP; ++pp) {
+        IMixed I[2];
+        float e[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int q = 2 * pp + h;
+            const int p = pbase + q * FORCE_NT;
+            gi[q] = idx[p < plim ? p : plim - 1];
+            if ((unsigned)gi[q] >= (unsigned)n) {
+                raise_status(sc, NB_ERR_ARG);
+                gi[q] = 0;
+            }
+            const float4* ri = js + (size_t)gi[q] * RW;
+            I[h].i0 = ri[0];
+            I[h].i1 = ri[1];
+            I[h].i2 = ri[2];
+            I[h].i3 = ORDER >= 6 ? ri[3] : make_float4(0.f, 0.f, 0.f, 0.f);
+            I[h].i4 = ORDER >= 8 ? ri[4] : make_float4(0.f, 0.f, 0.f, 0.f);
+            e[h] = PAIR ? I[h].i1.w : eps2u;
+            dom_lane = dom_lane && e[h] >= eps2max && e[h] > 0.0f;
+        }
+        I2[pp] = pack_pair(I[0], I[1], e[0], e[1]);
+    }
+    const bool dom = PAIR && __all_sync(0xffffffffu, dom_lane);
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) dsum[(c * NQ + q) * FORCE_NT + tid] = make_float2(0.f, 0.f);
+
+    for (int k = 0; k < nt; ++k) {
+        const int st = k % NSTAGE;
+        const bool ok = mbar_wait_bounded(&bars[st], (k / NSTAGE) & 1);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                raise_status(sc, NB_ERR_TIMEOUT);
+                drain_after_timeout(bars, k, nt);
+            }
+            return;
+        }
+        const float4* b = buf + st * JT * RW;
+        float2 acc[NP][NC];
+#pragma unroll
+        for (int pp = 0; pp < NP; ++pp)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[pp][c] = make_float2(0.f, 0.f);
+        int2 srel[NP];
+        bool mine = false;
+#pragma unroll
+        for (int pp = 0; pp < NP; ++pp) {
+            srel[pp] = make_int2(gi[2 * pp] - (t0 + k) * JT, gi[2 * pp + 1] - (t0 + k) * JT);
+            mine = mine || (unsigned)srel[pp].x < (unsigned)JT || (unsigned)srel[pp].y < (unsigned)JT;
+        }
+        const bool self_here = __any_sync(0xffffffffu, mine);
+        if (!PAIR || dom) {
+            if (self_here) tile_mixed_xn<ORDER, RW, false, true, NP>(b, I2, srel, acc);
+            else tile_mixed_xn<ORDER, RW, false, false, NP>(b, I2, srel, acc);
+        } else {
+            if (self_here) tile_mixed_xn<ORDER, RW, true, true, NP>(b, I2, srel, acc);
+            else tile_mixed_xn<ORDER, RW, true, false, NP>(b, I2, srel, acc);
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+            for (int pp = 0; pp < NP; ++pp) {
+                float2* s0 = &dsum[(c * NQ + 2 * pp) * FORCE_NT + tid];
+                float2* s1 = &dsum[(c * NQ + 2 * pp + 1) * FORCE_NT + tid];
+                float2 h0 = *s0, h1 = *s1;
+                ds_add(h0.x, h0.y, acc[pp][c].x);
+                ds_add(h1.x, h1.y, acc[pp][c].y);
+                *s0 = h0;
+                *s1 = h1;
+            }
+
+        __syncthreads();  // every thread is done with stage st
+        if (tid == 0 && k + NSTAGE < nt) {
+            mbar_expect_tx(&bars[st], TILE_BYTES);
+            bulk_g2s(buf + st * JT * RW, js + (size_t)(t0 + k + NSTAGE) * JT * RW, TILE_BYTES, &bars[st]);
+        }
+    }
+
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int p = pbase + q * FORCE_NT;
+        if (p < plim) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const float2 h = dsum[(c * NQ + q) * FORCE_NT + tid];
+                store_result<NC, pot_comp(ORDER)>(partial, split, ncol, p, c, (double)h.x + (double)h.y, ts);
+            }
+        }
+    }
+}
+
+template <int ORDER, int RW, bool PAIR, int NP>
+__global__ void __launch_bounds__(FORCE_NT) k_force_mixed_xs(const float4* __restrict__ js,
+                                                             const int32_t* __restrict__ idx, int n_act, int n,
+                                                             int ntiles, int jsplit, float eps2u, float eps2max,
+                                                             double* __restrict__ partial, DevScalars* sc, double* F)
+{
+    const int split = blockIdx.y;
+    const int t0 = (int)((long long)split * ntiles / jsplit);
+    const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
+    force_block_mixed_xs<ORDER, RW, PAIR, NP>(js, idx, blockIdx.x * (FORCE_NT * 2 * NP), n_act, n, t0, t1 - t0,
+                                              split, n_act, eps2u, eps2max, partial, sc, TileSum{F, jsplit});
 }
 
 // j-parallel form for small active sets: NI = FORCE_NT / JP i-particles per
@@ -779,7 +930,7 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_fp64(const double2* __restri
 // CTA (4, 32, 128); otherwise the two-per-thread variant (256).  The kernel
 // not matching the chosen variant returns at once.
 template <int ORDER, int RW, bool PAIR, bool SMALL>
-__global__ void __launch_bounds__(FORCE_NT, SMALL ? 5 : (ORDER >= 8 ? 3 : 4)) k_force_mixed_dyn(const float4* __restrict__ js,
+__global__ void __launch_bounds__(FORCE_NT, SMALL ? 5 : 4) k_force_mixed_dyn(const float4* __restrict__ js,
                                                               const int32_t* __restrict__ idx, int n, int ntiles,
                                                               float eps2u, float eps2max, double* __restrict__ partial,
                                                               DevScalars* sc, double* F)
@@ -794,8 +945,8 @@ __global__ void __launch_bounds__(FORCE_NT, SMALL ? 5 : (ORDER >= 8 ? 3 : 4)) k_
         const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
         const TileSum tsum{F, jsplit};
         if (!SMALL)
-            force_block_mixed<ORDER, RW, PAIR, 2>(js, idx, itile * ni, n_act, n, t0, t1 - t0, split, n_act, eps2u,
-                                                  eps2max, partial, sc, tsum);
+            force_block_mixed_xs<ORDER, RW, PAIR, 1>(js, idx, itile * ni, n_act, n, t0, t1 - t0, split, n_act,
+                                                     eps2u, eps2max, partial, sc, tsum);
         else if (ni == FORCE_NT)
             force_block_mixed<ORDER, RW, PAIR, 1>(js, idx, itile * ni, n_act, n, t0, t1 - t0, split, n_act, eps2u,
                                                   eps2max, partial, sc, tsum);

@@ -61,12 +61,36 @@ static cudaError_t run_mixed_jp(nb_ctx* c, const int32_t* idx, int n_act, int js
     return cudaGetLastError();
 }
 
+template <int ORDER, int RW, bool PAIR, int NP>
+static cudaError_t run_mixed_xs(nb_ctx* c, const int32_t* idx, int n_act, int jsplit, int itiles, int* occ_out)
+{
+    auto kern = k_force_mixed_xs<ORDER, RW, PAIR, NP>;
+    const size_t smem = xs_smem(ORDER, RW, NP);
+    static bool configured = false;
+    static int occ = 1;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        occ = occupancy_of(kern, smem);
+        configured = true;
+    }
+    if (occ_out) {
+        *occ_out = occ;
+        return cudaSuccess;
+    }
+    dim3 grid(itiles, jsplit);
+    kern<<<grid, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), idx, n_act, (int)c->n,
+                                              (int)(c->np / JT), jsplit, (float)(c->eps * c->eps),
+                                              (float)c->eps2_max, c->partial, c->sc, c->F);
+    return cudaGetLastError();
+}
+
 // Mixed path: the variant with ni i-particles per CTA (mixed_ni).
 template <int ORDER, int RW, bool PAIR>
 static cudaError_t run_mixed(nb_ctx* c, const int32_t* idx, int n_act, int jsplit, int itiles, int* occ_out, int ni)
 {
     switch (ni) {
-    case 2 * FORCE_NT: return run_mixed_ipt<ORDER, RW, PAIR, 2>(c, idx, n_act, jsplit, itiles, occ_out);
+    case 2 * FORCE_NT: return run_mixed_xs<ORDER, RW, PAIR, 1>(c, idx, n_act, jsplit, itiles, occ_out);
     case FORCE_NT: return run_mixed_ipt<ORDER, RW, PAIR, 1>(c, idx, n_act, jsplit, itiles, occ_out);
     case FORCE_NT / 4: return run_mixed_jp<ORDER, RW, PAIR, 4>(c, idx, n_act, jsplit, itiles, occ_out);
     case FORCE_NT / 32: return run_mixed_jp<ORDER, RW, PAIR, 32>(c, idx, n_act, jsplit, itiles, occ_out);
@@ -220,19 +244,19 @@ static cudaError_t force_dyn_o(nb_ctx* c, int* g_small, int* g_big, bool query_o
     const int ntiles = (int)(c->np / JT);
     if (c->prec == NB_MIXED) {
         constexpr int RW = mixed_rw(O);
-        const size_t smem = (size_t)NSTAGE * JT * RW * 16;
+        const size_t smem = (size_t)NSTAGE * JT * RW * 16, smem_big = xs_smem(O, RW, 1);
         auto k1 = pair ? k_force_mixed_dyn<O, RW, true, true> : k_force_mixed_dyn<O, RW, false, true>;
         auto k2 = pair ? k_force_mixed_dyn<O, RW, true, false> : k_force_mixed_dyn<O, RW, false, false>;
         if (query_only) {
             *g_small = dyn_slots(c, k1, smem);
-            *g_big = dyn_slots(c, k2, smem);
+            *g_big = dyn_slots(c, k2, smem_big);
             return cudaSuccess;
         }
         const float e2 = (float)(c->eps * c->eps), e2max = (float)c->eps2_max;
         k1<<<*g_small, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), c->act_idx,
                                                     (int)c->n, ntiles, e2, e2max, c->partial, c->sc, c->F);
-        k2<<<*g_big, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), c->act_idx,
-                                                  (int)c->n, ntiles, e2, e2max, c->partial, c->sc, c->F);
+        k2<<<*g_big, FORCE_NT, smem_big, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), c->act_idx,
+                                                      (int)c->n, ntiles, e2, e2max, c->partial, c->sc, c->F);
     } else {
         constexpr int RW = fp64_rw(O);
         const size_t smem = (size_t)NSTAGE * JT * RW * 16;
@@ -272,6 +296,27 @@ cudaError_t launch_force_reduce_dyn(nb_ctx* c)
     if (c->order == 4) k_force_reduce_dyn<ncomp(4), pot_comp(4)><<<nb, RED_NT, 0, c->stream>>>(c->partial, c->sc, c->F);
     else if (c->order == 6) k_force_reduce_dyn<ncomp(6), pot_comp(6)><<<nb, RED_NT, 0, c->stream>>>(c->partial, c->sc, c->F);
     else k_force_reduce_dyn<ncomp(8), pot_comp(8)><<<nb, RED_NT, 0, c->stream>>>(c->partial, c->sc, c->F);
+    return cudaGetLastError();
+}
+
+// Self-test of the bounded wait every kernel uses: one CTA waits on an
+// mbarrier that expects one arrival nobody makes, with the given limit; the
+// wait runs out, the kernel raises NB_ERR_TIMEOUT and returns.
+__global__ void k_wait_probe(long long limit_cycles, DevScalars* sc)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0, limit_cycles);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) raise_status(sc, NB_ERR_TIMEOUT);
+}
+
+cudaError_t launch_wait_probe(nb_ctx* c, long long limit_cycles)
+{
+    k_wait_probe<<<1, 32, 0, c->stream>>>(limit_cycles, c->sc);
     return cudaGetLastError();
 }
 

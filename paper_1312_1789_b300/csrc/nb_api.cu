@@ -615,6 +615,19 @@ int nb_get_tuning(nb_ctx* c, int* n_classes, int32_t* ni, int32_t* js, double* m
     return NB_OK;
 }
 
+int nb_selftest_wait(nb_ctx* c, double seconds)
+{
+    if (!c) return NB_ERR_ARG;
+    if (!(seconds > 0.0) || seconds > 5.0) return set_err(c, NB_ERR_ARG, "seconds must be in (0, 5]");
+    int khz = 0;
+    NB_CUDA(c, cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, c->dev));
+    const long long cycles = (long long)(seconds * 1e3 * (double)(khz > 0 ? khz : 2000000));
+    NB_CUDA(c, launch_wait_probe(c, cycles));
+    c->n_launch += 1;
+    NB_TRY(sync_scalars(c));
+    return set_err(c, NB_ERR_CUDA, "the probe's wait completed although nothing arrives");
+}
+
 int nb_set_jsplit(nb_ctx* c, int js)
 {
     if (!c) return NB_ERR_ARG;

@@ -670,10 +670,10 @@ int batch_force_dispatch(nb_batch* b, int order, const int32_t* list, int n_act,
     }
     BCASE(0)
     BCASE(4)
-    if (SO >= 6) {
+    if constexpr (SO >= 6) {
         BCASE(6)
     }
-    if (SO >= 8) {
+    if constexpr (SO >= 8) {
         BCASE(8)
     }
 #undef BCASE

@@ -195,12 +195,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
 }
 
 // Wait for phase `parity` of bar to complete, giving up after WAIT_LIMIT_CYCLES.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  long long limit_cycles = WAIT_LIMIT_CYCLES)
 {
     if (mbar_try_wait(bar, parity)) return true;
     long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > WAIT_LIMIT_CYCLES) return false;
+        if (clock64() - t0 > limit_cycles) return false;
     }
     return true;
 }
@@ -334,6 +335,7 @@ cudaError_t launch_correct(nb_ctx* c, const double* tfc = nullptr, const int32_t
 cudaError_t launch_cycle_gate(nb_ctx* c, const int* shape_slots);
 cudaError_t launch_force_dyn(nb_ctx* c, int* grid_small, int* grid_big, bool query_only);
 cudaError_t launch_force_reduce_dyn(nb_ctx* c);
+cudaError_t launch_wait_probe(nb_ctx* c, long long limit_cycles);
 cudaError_t launch_startup_store(nb_ctx* c, int order);
 cudaError_t launch_startup_dt(nb_ctx* c);
 cudaError_t launch_energy_sums(nb_ctx* c, int with_pot);

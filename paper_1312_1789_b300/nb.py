@@ -64,6 +64,7 @@ SIGNATURES = {
     "nb_get_noise_floor": (C.c_int, [_P, C.c_int, _D]),
     "nb_force_static": (C.c_int, [C.c_int, C.c_int, C.c_int64, _P, _P, _P, _P, _P, _P, _P, C.c_int64, _P, _P]),
     "nb_set_graph": (C.c_int, [_P, C.c_int]),
+    "nb_selftest_wait": (C.c_int, [_P, C.c_double]),
     "nb_autotune": (C.c_int, [_P, C.c_int]),
     "nb_get_tuning": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int32), C.POINTER(C.c_int32), _D]),
     "nb_set_tuning": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
@@ -205,6 +206,10 @@ class NBody:
         js = np.array([e[2] for e in table] or [0], dtype=np.int32)
         self._check(self._L.nb_set_tuning(self._h, len(table), ni.ctypes.data_as(C.POINTER(C.c_int32)),
                                           js.ctypes.data_as(C.POINTER(C.c_int32))))
+
+    def selftest_wait(self, seconds: float = 0.2) -> int:
+        """Run the bounded-wait probe; returns the code (NB_ERR_TIMEOUT when it works as designed)."""
+        return int(self._L.nb_selftest_wait(self._h, float(seconds)))
 
     def set_jsplit(self, js: int):
         self._check(self._L.nb_set_jsplit(self._h, int(js)))

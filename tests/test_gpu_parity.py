@@ -371,6 +371,33 @@ def test_energy_parity(prec):
     assert ep == pytest.approx(ep_o, rel=tol)
 
 
+# ----------------------------------------------------- 65536 Plummer, sampled
+def test_plummer_65536_sampled_blocks_parity():
+    # The 65536-particle Plummer sphere on the mixed path, stepped block by
+    # block through the C ABI; on sampled blocks (small ones, and the first
+    # large one) the force of up to 256 of the active particles against the
+    # oracle on the very store the kernel read.
+    wl = ics.standard_workload(1)
+    ctx = make_ctx(wl.m, wl.x, wl.v, wl.eps2, 6, nb.NB_MIXED)
+    rng = np.random.default_rng(65536)
+    checked, large = 0, False
+    for b in range(80):
+        tb, idx = ctx.next_block(want_idx=True)
+        ctx.predict(tb)
+        ctx.force()
+        if b % 16 == 0 or (len(idx) > 1024 and not large):
+            large = large or len(idx) > 1024
+            pos = np.arange(len(idx)) if len(idx) <= 256 else np.sort(rng.choice(len(idx), 256, replace=False))
+            G = ctx.get_force(len(idx))
+            O = oracle_force_on_predicted(ctx, wl.m, wl.eps2, idx[pos].astype(np.int32), 6)
+            Gs = {k: G[k][pos] for k in G}
+            assert_force_close(Gs, O, 6, nb.NB_MIXED, f"block {b} (t = {tb}, {len(idx)} active)")
+            checked += 1
+        ctx.correct()
+    assert checked >= 5 and large
+    ctx.close()
+
+
 # ------------------------------------------------------------ full-size sample
 def test_nucleus_2pow20_sampled_parity():
     # 2^20 stars + two holes, every particle active (the benchmarked block),
@@ -491,6 +518,27 @@ def test_errors_are_reported_not_faulted():
     with pytest.raises(nb.NBError) as e:
         c2.set_particles(m, x, v)
     assert e.value.code == nb.NB_ERR_DT_UNDERFLOW
+
+
+def test_bounded_wait_runs_out_and_reports_a_timeout():
+    # Failure detection without a fault: a kernel waits on a barrier nothing
+    # completes; its bounded wait gives up after the limit, the host reads
+    # NB_ERR_TIMEOUT, and the context computes correct forces afterwards.
+    import time
+    n = 300
+    m, x, v, eps2 = _system(n, 8, "plummer")
+    ctx = make_ctx(m, x, v, eps2, 6, nb.NB_MIXED)
+    t0 = time.perf_counter()
+    rc = ctx.selftest_wait(0.2)
+    el = time.perf_counter() - t0
+    assert rc == nb.NB_ERR_TIMEOUT
+    assert 0.15 < el < 3.0
+    ctx.predict(1.0 / 512)
+    idx = np.arange(n, dtype=np.int32)
+    ctx.force(idx)
+    O = oracle_force_on_predicted(ctx, m, eps2, idx, 6)
+    assert_force_close(ctx.get_force(n), O, 6, nb.NB_MIXED, "after a timeout")
+    ctx.close()
 
 
 def test_device_index_out_of_range_is_reported():
