@@ -535,7 +535,7 @@ int nb_autotune(nb_ctx* c, int reps)
                 if (na <= 16) cand[nv++] = 4;
                 if (na <= 512) cand[nv++] = 32;
                 if (na <= 16384) cand[nv++] = FORCE_NT;
-                if (na >= 256) cand[nv++] = 2 * FORCE_NT;
+                if (na >= 64) cand[nv++] = 2 * FORCE_NT;
             }
             float best = INFINITY;
             for (int v = 0; v < nv && rc == NB_OK; ++v) {

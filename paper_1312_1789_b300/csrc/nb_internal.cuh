@@ -25,11 +25,11 @@ constexpr int JT = 128;
 // threads per force CTA; each holds 1 or 2 i-particles (IPT).
 constexpr int FORCE_NT = 128;
 // the mixed force uses two i-particles per thread from this active-set size on
-constexpr int IPT2_MIN_NACT = 1024;
+constexpr int IPT2_MIN_NACT = 512;
 
 // Launch variant of the mixed force, named by its i-particles per CTA:
 //   256: two per thread (n_act >= IPT2_MIN_NACT);
-//   128: one per thread (n_act > 96);
+//   128: one per thread (96 < n_act < IPT2_MIN_NACT);
 //   32, 4: j-parallel -- 4 or 32 threads share an i-particle, each taking
 //          every 4th / 32nd record of a j tile, so that a few active
 //          particles still keep a CTA's threads busy (n_act <= 96: at most

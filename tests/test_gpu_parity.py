@@ -84,7 +84,7 @@ def test_force_parity(prec, order, kind):
 @pytest.mark.parametrize("order", [4, 6, 8])
 @pytest.mark.parametrize("kind", ["plummer", "holes"])
 def test_force_parity_two_particles_per_thread(order, kind):
-    # Active sets of >= 1024 run the mixed kernel with two i-particles per
+    # Active sets of >= 512 run the mixed kernel with two i-particles per
     # thread; ragged last i-tile, several split counts.
     n = 2 * 1024 + 77
     m, x, v, eps2 = _system(n, 50 + order, kind)
@@ -103,9 +103,9 @@ def test_force_parity_two_particles_per_thread(order, kind):
 
 
 # i-particles per CTA of the mixed force for an active-set size: 4 up to 4
-# active, 32 up to 96, 128 below 1024, then 256 (two per thread).
+# active, 32 up to 96, 128 below 512, then 256 (two per thread).
 def _expected_ni(n_act):
-    return 256 if n_act >= 1024 else 128 if n_act > 96 else 32 if n_act > 4 else 4
+    return 256 if n_act >= 512 else 128 if n_act > 96 else 32 if n_act > 4 else 4
 
 
 @pytest.mark.parametrize("order", [4, 6, 8])
