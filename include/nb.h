@@ -203,6 +203,14 @@ int nb_get_tuning(nb_ctx* ctx, int* n_classes, int32_t* ni, int32_t* js, double*
  * n_classes = 0 drops the table.                                           */
 int nb_set_tuning(nb_ctx* ctx, int n_classes, const int32_t* ni, const int32_t* js);
 
+/* Self-test of the bounded waits (failure detection without a fault): one
+ * CTA waits on an mbarrier that nothing completes, with a limit of `seconds`
+ * (0 < seconds <= 5) instead of the kernels' 2 s.  Returns NB_ERR_TIMEOUT --
+ * the wait ran out, the kernel reported it and returned, and the context
+ * stays usable -- or another error code if the probe misbehaved.
+ * Synchronises.                                                            */
+int nb_selftest_wait(nb_ctx* ctx, double seconds);
+
 /* Force the j-split count of later nb_force calls (0 = automatic).         */
 int nb_set_jsplit(nb_ctx* ctx, int j_splits);
 
@@ -227,7 +235,9 @@ int nb_get_noise_floor(nb_ctx* ctx, int precision, double* eps);
 /* ------------------------------------------------------------- profiling */
 
 /* Phases of the per-phase timers: scheduler, predictor, force kernel, j-split
- * reduction, corrector, everything else (start-up, energy, step reset).     */
+ * reduction, corrector, everything else (start-up, energy, step reset).
+ * Inside nb_block_step and nb_step_until the predictor runs fused into the
+ * scheduler's second pass, so its time counts as scheduler time there.     */
 #define NB_NPHASES 6
 #define NB_PHASE_SCHED 0
 #define NB_PHASE_PREDICT 1

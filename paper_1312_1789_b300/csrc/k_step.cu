@@ -96,11 +96,12 @@ __global__ void __launch_bounds__(SCHED_NT) k_sched_chunk(const double* __restri
     }
 }
 
-__global__ void __launch_bounds__(SCHED_NT) k_sched_compact(const double* __restrict__ t,
-                                                            const double* __restrict__ dt, int64_t n, int per,
-                                                            const double* __restrict__ cmin,
-                                                            const int32_t* __restrict__ ccnt, int nch,
-                                                            int32_t* __restrict__ idx, DevScalars* sc)
+// Second pass (every CTA): t_blk and this chunk's offset from the chunk table,
+// then the chunk's matches in index order.  Returns t_blk.
+__device__ __forceinline__ double sched_compact_body(const double* __restrict__ t, const double* __restrict__ dt,
+                                                     int64_t n, int per, const double* __restrict__ cmin,
+                                                     const int32_t* __restrict__ ccnt, int nch,
+                                                     int32_t* __restrict__ idx, DevScalars* sc)
 {
     __shared__ double wd[SCHED_NT / 32];
     __shared__ int wi[SCHED_NT / 32];
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(SCHED_NT) k_sched_compact(const double* __rest
         sc->t_blk = tb;
         sc->n_act = total;
     }
-    if (cmin[blockIdx.x] != tb) return;  // CTA-uniform
+    if (cmin[blockIdx.x] != tb) return tb;  // CTA-uniform: no match in this chunk
     const int64_t i0 = ((int64_t)blockIdx.x * SCHED_NT + threadIdx.x) * per;
     unsigned flags = 0;
 #pragma unroll
@@ -145,6 +146,16 @@ __global__ void __launch_bounds__(SCHED_NT) k_sched_compact(const double* __rest
         flags &= flags - 1;
         idx[pos++] = (int32_t)(i0 + k);
     }
+    return tb;
+}
+
+__global__ void __launch_bounds__(SCHED_NT) k_sched_compact(const double* __restrict__ t,
+                                                            const double* __restrict__ dt, int64_t n, int per,
+                                                            const double* __restrict__ cmin,
+                                                            const int32_t* __restrict__ ccnt, int nch,
+                                                            int32_t* __restrict__ idx, DevScalars* sc)
+{
+    sched_compact_body(t, dt, n, per, cmin, ccnt, nch, idx, sc);
 }
 
 // Particles per scheduler thread (about one wave of CTAs, at most
@@ -169,6 +180,7 @@ cudaError_t launch_sched(nb_ctx* c)
     return cudaGetLastError();
 }
 
+
 // ===================================================================== K1
 // Predictor: Taylor series of every particle from t_i to tp.
 //   orders 4, 6: x to the crackle term (dt^5), v to dt^4; order 6 also a to dt^3
@@ -184,19 +196,13 @@ cudaError_t launch_sched(nb_ctx* c)
 // scaled by h^2 -- far below the pair separations that need the
 // double-single position.
 template <int ORDER, bool MIXED>
-__global__ void __launch_bounds__(256) k_predict(const double* __restrict__ m, const double* __restrict__ eps2,
-                                                 const double* __restrict__ x, const double* __restrict__ v,
-                                                 const double* __restrict__ d, const double* __restrict__ t,
-                                                 int64_t n, int64_t np, double tp, void* __restrict__ jstore,
-                                                 const double* __restrict__ tpc, const int32_t* __restrict__ cid,
-                                                 const DevScalars* dyn)
+__device__ __forceinline__ void predict_one(const int64_t i, double tp, const double* __restrict__ m,
+                                            const double* __restrict__ eps2, const double* __restrict__ x,
+                                            const double* __restrict__ v, const double* __restrict__ d,
+                                            const double* __restrict__ t, int64_t n, int64_t np,
+                                            void* __restrict__ jstore, const double* __restrict__ tpc,
+                                            const int32_t* __restrict__ cid)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= np) return;
-    if (dyn) {
-        if (dyn->idle) return;
-        tp = dyn->t_blk;
-    }
     constexpr int RW = MIXED ? mixed_rw(ORDER) : fp64_rw(ORDER);
     double xp[3] = {0, 0, 0}, vp[3] = {0, 0, 0}, ap[3] = {0, 0, 0}, jp[3] = {0, 0, 0};
     float vf[3] = {0.f, 0.f, 0.f}, af[3] = {0.f, 0.f, 0.f}, jf[3] = {0.f, 0.f, 0.f};
@@ -307,6 +313,64 @@ __global__ void __launch_bounds__(256) k_predict(const double* __restrict__ m, c
             r[7] = make_double2(jp[2], 0.0);
         }
     }
+}
+
+template <int ORDER, bool MIXED>
+__global__ void __launch_bounds__(256) k_predict(const double* __restrict__ m, const double* __restrict__ eps2,
+                                                 const double* __restrict__ x, const double* __restrict__ v,
+                                                 const double* __restrict__ d, const double* __restrict__ t,
+                                                 int64_t n, int64_t np, double tp, void* __restrict__ jstore,
+                                                 const double* __restrict__ tpc, const int32_t* __restrict__ cid,
+                                                 const DevScalars* dyn)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    if (dyn) {
+        if (dyn->idle) return;
+        tp = dyn->t_blk;
+    }
+    predict_one<ORDER, MIXED>(i, tp, m, eps2, x, v, d, t, n, np, jstore, tpc, cid);
+}
+
+// Second pass fused with the predictor: once a CTA knows t_blk it predicts
+// its own chunk of particles to it (the last CTA also the padding records up
+// to np).  use_t_end: a device-driven cycle, which predicts nothing past
+// sc->t_end.
+template <int ORDER, bool MIXED>
+__global__ void __launch_bounds__(SCHED_NT) k_sched_compact_predict(
+    const double* __restrict__ t, const double* __restrict__ dt, int64_t n, int per, const double* __restrict__ cmin,
+    const int32_t* __restrict__ ccnt, int nch, int32_t* __restrict__ idx, DevScalars* sc, int use_t_end,
+    const double* __restrict__ m, const double* __restrict__ eps2, const double* __restrict__ x,
+    const double* __restrict__ v, const double* __restrict__ d, int64_t np, void* __restrict__ jstore)
+{
+    const double tb = sched_compact_body(t, dt, n, per, cmin, ccnt, nch, idx, sc);
+    if (use_t_end && !(tb <= sc->t_end)) return;
+    const int64_t c0 = (int64_t)blockIdx.x * SCHED_NT * per;
+    const int64_t c1 = blockIdx.x == nch - 1 ? np : min(c0 + (int64_t)SCHED_NT * per, np);
+    for (int64_t i = c0 + threadIdx.x; i < c1; i += SCHED_NT)
+        predict_one<ORDER, MIXED>(i, tb, m, eps2, x, v, d, t, n, np, jstore, nullptr, nullptr);
+}
+
+cudaError_t launch_sched_predict(nb_ctx* c, bool use_t_end)
+{
+    int per, nch;
+    sched_layout(c->n, c->sm_count, &per, &nch);
+    k_sched_chunk<<<nch, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, per, c->chunk_min, c->chunk_cnt, c->sc);
+    const bool mixed = c->prec == NB_MIXED;
+#define NB_SP(O, MX)                                                                                              \
+    k_sched_compact_predict<O, MX><<<nch, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, per, c->chunk_min,        \
+                                                                    c->chunk_cnt, nch, c->act_idx, c->sc,        \
+                                                                    use_t_end ? 1 : 0, c->m, c->eps2, c->x, c->v, \
+                                                                    c->d, c->np, c->jstore)
+    if (c->order == 4) {
+        if (mixed) NB_SP(4, true); else NB_SP(4, false);
+    } else if (c->order == 6) {
+        if (mixed) NB_SP(6, true); else NB_SP(6, false);
+    } else {
+        if (mixed) NB_SP(8, true); else NB_SP(8, false);
+    }
+#undef NB_SP
+    return cudaGetLastError();
 }
 
 cudaError_t launch_predict(nb_ctx* c, double t, const double* tpc, const int32_t* cid, const DevScalars* dyn)

@@ -242,9 +242,8 @@ int build_graph(nb_ctx* c)
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(c->graph_stream, cudaStreamCaptureModeThreadLocal);
     for (int r = 0; e == cudaSuccess && r < c->graph_cycles; ++r) {
-        if ((e = launch_sched(c)) != cudaSuccess) break;
+        if ((e = launch_sched_predict(c, true)) != cudaSuccess) break;
         if ((e = launch_cycle_gate(c, shape_slots)) != cudaSuccess) break;
-        if ((e = launch_predict(c, 0.0, nullptr, nullptr, c->sc)) != cudaSuccess) break;
         if ((e = launch_force_dyn(c, &s1, &s2, false)) != cudaSuccess) break;
         if ((e = launch_force_reduce_dyn(c)) != cudaSuccess) break;
         if ((e = launch_correct(c, nullptr, nullptr, c->sc)) != cudaSuccess) break;
@@ -273,9 +272,9 @@ int step_until_graph(nb_ctx* c, double t_end, int64_t* n_blocks, int64_t* n_inte
     h->blocks = 0;
     h->inter = 0;
     NB_CUDA(c, cudaMemcpy(c->sc, h, sizeof(DevScalars), cudaMemcpyHostToDevice));
-    // scheduler 2, gate, predictor, force (two persistent kernels on the
-    // mixed path), reduction, corrector
-    const long long per_cycle = 2 + 1 + 1 + (c->prec == NB_MIXED ? 2 : 1) + 1 + 1;
+    // scheduler 2 (the second predicts), gate, force (two persistent kernels
+    // on the mixed path), reduction, corrector
+    const long long per_cycle = 2 + 1 + (c->prec == NB_MIXED ? 2 : 1) + 1 + 1;
     for (;;) {
         NB_CUDA(c, cudaGraphLaunch(c->graph_exec, c->graph_stream));
         c->n_launch += per_cycle * c->graph_cycles;
@@ -781,12 +780,32 @@ int nb_correct(nb_ctx* c)
     return NB_OK;
 }
 
+// Scheduler with the predictor fused into its second pass: leaves the
+// scheduled block and the predicted store exactly as nb_next_block followed
+// by nb_predict(t_blk) would.
+static int next_block_predicted(nb_ctx* c, double* tb, int64_t* na)
+{
+    if (!c->have_particles) return set_err(c, NB_ERR_ARG, "block step before nb_set_particles");
+    NB_CUDA(c, timed(c, NB_PHASE_SCHED, 2, [&] { return launch_sched_predict(c, false); }));
+    NB_TRY(sync_scalars(c));
+    c->sched_t = c->h_sc->t_blk;
+    c->sched_n = c->h_sc->n_act;
+    c->have_sched = 1;
+    c->pred_prec = c->prec;
+    c->have_pred = 1;
+    c->t_pred = c->sched_t;
+    c->have_force = 0;
+    *tb = c->sched_t;
+    *na = c->sched_n;
+    return NB_OK;
+}
+
 int nb_block_step(nb_ctx* c, double* t_blk, int64_t* n_act)
 {
+    if (!c) return NB_ERR_ARG;
     double tb;
     int64_t na;
-    NB_TRY(nb_next_block(c, &tb, nullptr, &na));
-    NB_TRY(nb_predict(c, tb));
+    NB_TRY(next_block_predicted(c, &tb, &na));
     NB_TRY(nb_force(c, nullptr, na));
     NB_TRY(nb_correct(c));
     if (t_blk) *t_blk = tb;
@@ -804,9 +823,8 @@ int nb_step_until(nb_ctx* c, double t_end, int64_t* n_blocks, int64_t* n_inter)
     for (;;) {
         double tb;
         int64_t na;
-        NB_TRY(nb_next_block(c, &tb, nullptr, &na));
+        NB_TRY(next_block_predicted(c, &tb, &na));
         if (tb > t_end) break;
-        NB_TRY(nb_predict(c, tb));
         NB_TRY(nb_force(c, nullptr, na));
         NB_TRY(nb_correct(c));
         ++nb;

@@ -317,6 +317,9 @@ namespace nb {
 
 // Launchers (k_*.cu); each returns cudaGetLastError() of its launches.
 cudaError_t launch_sched(nb_ctx* c);
+// Scheduler whose second pass also predicts every particle to the new block
+// time (use_t_end: not past sc->t_end).
+cudaError_t launch_sched_predict(nb_ctx* c, bool use_t_end);
 // tpc, cid (ensembles): per-cluster prediction time and cluster of each slot; NULL for one system.
 // dyn (device-driven cycle): take the time from dyn->t_blk and do nothing when dyn->idle.
 cudaError_t launch_predict(nb_ctx* c, double t, const double* tpc = nullptr, const int32_t* cid = nullptr,
