@@ -261,6 +261,15 @@ def run_ours(args):
         "gpu_launches": int(launches1 - launches0),
         "clocks": clk,
     }
+    try:
+        fp32 = ctx.fma_peak(False)
+        fp64 = ctx.fma_peak(True)
+        out["measured_fma_peak"] = {"fp32_tflops": fp32, "fp64_tflops": fp64,
+                                    "force_frac_of_measured_fp32": achieved / fp32,
+                                    "note": "independent FFMA / DFMA chains on every SM (nb_fma_peak), best of 3, "
+                                            "at the clock of this run"}
+    except Exception as e:  # pragma: no cover
+        out["measured_fma_peak"] = {"error": repr(e)}
     if rank == 0 and not args.quick:
         extras(args, nb, ics, wl, ctx, stream, out, prec)
     ctx.close()
@@ -380,12 +389,12 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
         ctx.predict(float(S["t"][0]) + h)
         rng = np.random.default_rng(11)
         curve = {}
-        for k in range(0, 21, 2):
+        for k in range(0, 21):
             na = min(1 << k, n)
             blk = np.sort(rng.choice(n, na, replace=False)).astype(np.int32)
             ctx.force(blk)
             ctx.set_profiling(True)
-            reps = 3 if na >= 65536 else 10
+            reps = 2 if na >= 262144 else 3 if na >= 65536 else 10
             for _ in range(reps):
                 ctx.force(blk)
             prof, _ = ctx.get_profile()
@@ -437,6 +446,39 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
                                 "mixed_within_2x": abs(de["mixed"]["dE_E"]) <= 2 * abs(de["fp64"]["dE_E"])}
     except Exception as e:  # pragma: no cover
         out["energy_budget"] = {"error": repr(e)}
+    # ---- Plummer N = 1024 to t = 0.125 end to end: both GPU paths and the
+    #      oracle on the host cores; the FP64 path must take the oracle's blocks
+    try:
+        import oracle as orc
+        w0 = ics.standard_workload(0)
+        rec = {"workload": w0.name + f" to t={w0.t_end}"}
+        states = {}
+        for name, p in (("fp64", nb.NB_FP64), ("mixed", nb.NB_MIXED)):
+            c0 = nb.NBody(w0.n, w0.order, math.sqrt(w0.eps2[0]), p)
+            c0.set_stream(stream)
+            c0.set_params(w0.eta, w0.eta_s, w0.dt_max, 2.0 ** -40)
+            c0.set_particles(w0.m, w0.x, w0.v)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            nblk, ni = c0.step_until(w0.t_end)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            states[name] = c0.get_state()
+            rec[name] = {"blocks": nblk, "interactions": ni, "seconds": el, "interactions_per_s": ni / el}
+            c0.close()
+        st = orc.State(w0.m, w0.eps2, w0.x, w0.v)
+        nth = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        nblk_o = int(orc.integrate(st, order=w0.order, t_end=w0.t_end, eta=w0.eta, nthreads=nth))
+        el = time.perf_counter() - t0
+        rec["oracle"] = {"seconds": el, "cores": nth, "blocks": nblk_o,
+                         "interactions_per_s": rec["fp64"]["interactions"] / el}
+        rec["fp64_blocks_equal_oracle"] = rec["fp64"]["blocks"] == nblk_o
+        rec["fp64_steps_equal_oracle"] = bool(np.array_equal(states["fp64"]["dt"], st.dt))
+        rec["fp64_max_position_difference"] = float(np.max(np.abs(states["fp64"]["x"] - st.x)))
+        out["plummer_1k_end_to_end"] = rec
+    except Exception as e:  # pragma: no cover
+        out["plummer_1k_end_to_end"] = {"error": repr(e)}
     # ---- force kernel at N_act = N on each single-system workload (mixed),
     #      and the FP64 path on a 4096-particle block of each
     try:

@@ -166,7 +166,7 @@ int nb_get_predicted(nb_ctx* ctx, double* xp, double* vp, double* ap, double* jp
 /* Kernel launch shape of the last nb_force: CTAs along i, j-splits and
  * i-particles per CTA -- the launch variant: 256 (128 threads holding two
  * particles each), 128 (one each), 32 or 4 (j-parallel: 4 or 32 threads per
- * particle, for active sets of up to 96 or 4); any output may be NULL.      */
+ * particle, for active sets of up to 256 or 24); any output may be NULL.   */
 int nb_get_launch(nb_ctx* ctx, int* i_tiles, int* j_splits, int* i_per_cta);
 
 /* cycles > 0: nb_step_until replays a CUDA graph of that many device-driven
@@ -254,6 +254,12 @@ int nb_set_profiling(nb_ctx* ctx, int enable);
  * enabled (arrays of NB_NPHASES; either may be NULL), and the number of
  * kernel launches since nb_create (NULL to skip).  Synchronises.           */
 int nb_get_profile(nb_ctx* ctx, double* ms, int64_t* launches, int64_t* total_launches);
+
+/* FMA-throughput microbenchmark on the context's GPU (a measurement aid for
+ * roofline fractions, not part of the method): every SM runs independent
+ * multiply-add chains in FP32 (fp64 = 0) or FP64 (fp64 != 0); *tflops = the
+ * best of three timed launches, 2 flops per multiply-add.  Synchronises.   */
+int nb_fma_peak(nb_ctx* ctx, int fp64, double* tflops);
 
 /* Library version string.                                                  */
 const char* nb_version(void);

@@ -821,13 +821,13 @@ int batch_force_dyn(nb_batch* b, bool occ_only)
 }
 
 // Slots of the persistent force in the current precision and an item buffer
-// that holds every plan: items <= 4 slots + np/64 + 3K (each cluster's split
-// count rounds up by at most one, its i-tiles number at most cnt/128 + 3).
+// that holds every plan: items <= 4 slots + np/64 + 8K (each cluster's split
+// count rounds up by at most one, its i-tiles number at most cnt/128 + 8).
 int batch_prepare(nb_batch* b)
 {
     nb_ctx* c = b->c;
     const int slots = c->sm_count * batch_force_dyn(b, true);
-    const long long need = 8LL * slots + c->np / 32 + 4LL * b->K + 1024;
+    const long long need = 8LL * slots + c->np / 32 + 8LL * b->K + 1024;
     if (slots != b->force_slots || need > b->d_items_cap) {
         batch_destroy_graph(b);
         b->force_slots = slots;

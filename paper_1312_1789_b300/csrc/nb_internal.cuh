@@ -29,19 +29,18 @@ constexpr int IPT2_MIN_NACT = 512;
 
 // Launch variant of the mixed force, named by its i-particles per CTA:
 //   256: two per thread (n_act >= IPT2_MIN_NACT);
-//   128: one per thread (96 < n_act < IPT2_MIN_NACT);
+//   128: one per thread (256 < n_act < IPT2_MIN_NACT);
 //   32, 4: j-parallel -- 4 or 32 threads share an i-particle, each taking
 //          every 4th / 32nd record of a j tile, so that a few active
-//          particles still keep a CTA's threads busy (n_act <= 96: at most
-//          three i-tiles; n_act <= 4: one).
-// More i-tiles would each stream the whole j range again, so the smaller
-// variants stop where they would need more than three.  The FP64 force
-// always runs 128.
+//          particles still keep a CTA's threads busy (n_act <= 256: at most
+//          eight i-tiles of 32; n_act <= 24: at most six of 4).
+// The thresholds are where the autotuner's measurements switch variant on
+// the 65k and the 2^20 stores.  The FP64 force always runs 128.
 __host__ __device__ inline int mixed_ni(long long n_act)
 {
     if (n_act >= IPT2_MIN_NACT) return 2 * FORCE_NT;
-    if (n_act > 96) return FORCE_NT;
-    return n_act > 4 ? 32 : 4;
+    if (n_act > 256) return FORCE_NT;
+    return n_act > 24 ? 32 : 4;
 }
 // stages of the force kernel's shared-memory ring.
 constexpr int NSTAGE = 3;

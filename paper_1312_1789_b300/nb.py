@@ -64,6 +64,7 @@ SIGNATURES = {
     "nb_get_noise_floor": (C.c_int, [_P, C.c_int, _D]),
     "nb_force_static": (C.c_int, [C.c_int, C.c_int, C.c_int64, _P, _P, _P, _P, _P, _P, _P, C.c_int64, _P, _P]),
     "nb_set_graph": (C.c_int, [_P, C.c_int]),
+    "nb_fma_peak": (C.c_int, [_P, C.c_int, _D]),
     "nb_selftest_wait": (C.c_int, [_P, C.c_double]),
     "nb_autotune": (C.c_int, [_P, C.c_int]),
     "nb_get_tuning": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int32), C.POINTER(C.c_int32), _D]),
@@ -210,6 +211,12 @@ class NBody:
     def selftest_wait(self, seconds: float = 0.2) -> int:
         """Run the bounded-wait probe; returns the code (NB_ERR_TIMEOUT when it works as designed)."""
         return int(self._L.nb_selftest_wait(self._h, float(seconds)))
+
+    def fma_peak(self, fp64: bool = False) -> float:
+        """Measured FMA throughput of this GPU in TFLOP/s (FP32, or FP64 when fp64)."""
+        t = C.c_double()
+        self._check(self._L.nb_fma_peak(self._h, 1 if fp64 else 0, C.byref(t)))
+        return t.value
 
     def set_jsplit(self, js: int):
         self._check(self._L.nb_set_jsplit(self._h, int(js)))

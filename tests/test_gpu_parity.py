@@ -102,10 +102,10 @@ def test_force_parity_two_particles_per_thread(order, kind):
     ctx.close()
 
 
-# i-particles per CTA of the mixed force for an active-set size: 4 up to 4
-# active, 32 up to 96, 128 below 512, then 256 (two per thread).
+# i-particles per CTA of the mixed force for an active-set size: 4 up to 24
+# active, 32 up to 256, 128 below 512, then 256 (two per thread).
 def _expected_ni(n_act):
-    return 256 if n_act >= 512 else 128 if n_act > 96 else 32 if n_act > 4 else 4
+    return 256 if n_act >= 512 else 128 if n_act > 256 else 32 if n_act > 24 else 4
 
 
 @pytest.mark.parametrize("order", [4, 6, 8])
@@ -122,7 +122,7 @@ def test_force_parity_small_active_sets(order, kind):
     ctx.predict(tb)
     rng = np.random.default_rng(order + 11)
     seen = set()
-    for na in (1, 3, 4, 5, 9, 31, 32, 33, 100, 130, 600):
+    for na in (1, 3, 4, 5, 9, 24, 25, 32, 33, 100, 257, 300, 600):
         idx = np.sort(rng.choice(n, na, replace=False)).astype(np.int32)
         if kind == "holes" and na >= 2:
             idx[-1] = n - 1  # an unsoftened hole among the active particles
