@@ -614,17 +614,21 @@ __global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fid
     }
     // the floored criterion below would read a non-finite derivative as zero
     if (!finite_state) raise_status(sc, NB_ERR_NAN);
+    // all-zero channel precisions (the FP64 default): the floor is zero and
+    // the plain criterion applies -- skip its norms and polynomials
+    if (ne.e[0] != 0.0 || ne.e[1] != 0.0 || ne.e[2] != 0.0 || ne.e[3] != 0.0) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        nL[k] = norm3(L[k]);
-        nR[k] = k < MM ? nrm[k] : 0.0;
+        for (int k = 0; k < 4; ++k) {
+            nL[k] = norm3(L[k]);
+            nR[k] = k < MM ? nrm[k] : 0.0;
+        }
+        // rounding of a total scales with the terms it sums: kappa = B / |a| >= 1
+        const double kappa = nR[0] > 0.0 ? fmax(1.0, bacc / nR[0]) : 1.0;
+        const double ek[4] = {ne.e[0] * kappa, ne.e[1] * kappa, ne.e[2] * kappa, ne.e[3] * kappa};
+        noise_floor<ORDER>(nL, nR, h, ih, ek, N);
+#pragma unroll
+        for (int k = MM; k < 2 * MM; ++k) nrm[k] = fmax(nrm[k] - N[k], 0.0);
     }
-    // rounding of a total scales with the terms it sums: kappa = B / |a| >= 1
-    const double kappa = nR[0] > 0.0 ? fmax(1.0, bacc / nR[0]) : 1.0;
-    const double ek[4] = {ne.e[0] * kappa, ne.e[1] * kappa, ne.e[2] * kappa, ne.e[3] * kappa};
-    noise_floor<ORDER>(nL, nR, h, ih, ek, N);
-#pragma unroll
-    for (int k = MM; k < 2 * MM; ++k) nrm[k] = fmax(nrm[k] - N[k], 0.0);
     double lim = dt_criterion<ORDER>(eta, nrm);
     if (2.0 * h < lim) lim = 2.0 * h;
     const double dtn = quantise_dt(lim, tf, dt_max, dt_min, sc);
