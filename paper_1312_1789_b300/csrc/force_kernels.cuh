@@ -757,14 +757,15 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_mixed(const float4* __restri
                                             eps2u, eps2max, partial, sc, TileSum{F, jsplit});
 }
 
-template <int ORDER, int RW, bool PAIR, bool SELF>
+// records jl, jl + JP, ... of the tile (JP = 1: every record)
+template <int ORDER, int RW, bool PAIR, bool SELF, int JP = 1>
 __device__ __forceinline__ void tile_fp64(const double2* __restrict__ b, const double2 i0, const double2 i1,
                                           const double2 i2, const double2 i3, const double2 i4, const double2 i5,
                                           const double2 i6, const double2 i7, const double ei2, const double eps2u,
-                                          const int self_rel, double (&acc)[ncomp(ORDER)])
+                                          const int self_rel, double (&acc)[ncomp(ORDER)], const int jl = 0)
 {
     constexpr int NC = ncomp(ORDER);
-    for (int jj = 0; jj < JT; ++jj) {
+    for (int jj = jl; jj < JT; jj += JP) {
         const double2 w0 = b[jj * RW + 0], w1 = b[jj * RW + 1];
         const double dx = w0.x - i0.x, dy = w0.y - i0.y, dz = w1.x - i1.x;
         const double2 w3 = b[jj * RW + 3];
@@ -821,7 +822,10 @@ __device__ __forceinline__ void tile_fp64(const double2* __restrict__ b, const d
 // w2 = (v.x, v.y), w3 = (v.z, eps2), w4 = (a.x, a.y), w5 = (a.z, 0),
 // w6 = (jerk.x, jerk.y), w7 = (jerk.z, 0).
 // One CTA's work (one i-particle per thread), as force_block_mixed.
-template <int ORDER, int RW, bool PAIR>
+// JP > 1: the j-parallel form (NI = FORCE_NT / JP i-particles per CTA,
+// thread (tid % NI, tid / NI) takes every JP-th record of a tile; the JP
+// lane sums of a particle are added in lane order through the idle ring).
+template <int ORDER, int RW, bool PAIR, int JP = 1>
 __device__ __forceinline__ void force_block_fp64(const double2* __restrict__ js, const int32_t* __restrict__ idx,
                                                  const int pbase0, const int plim, const int n, const int t0,
                                                  const int nt, const int split, const int ncol, const double eps2u,
@@ -829,12 +833,14 @@ __device__ __forceinline__ void force_block_fp64(const double2* __restrict__ js,
                                                  const TileSum ts = TileSum{})
 {
     constexpr int NC = ncomp(ORDER);
+    constexpr int NI = FORCE_NT / JP;
+    static_assert(JP == 1 || NSTAGE * JT * RW * 16 >= NC * FORCE_NT * 8, "ring too small for the lane reduction");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     double2* buf = reinterpret_cast<double2*>(smem_raw);
     __shared__ __align__(8) uint64_t bars[NSTAGE];
 
-    const int tid = threadIdx.x;
-    const int p = pbase0 + tid;
+    const int tid = threadIdx.x, il = tid % NI, jl = tid / NI;
+    const int p = pbase0 + il;
     constexpr uint32_t TILE_BYTES = JT * RW * 16;
 
     if (tid == 0) {
@@ -887,9 +893,9 @@ __device__ __forceinline__ void force_block_fp64(const double2* __restrict__ js,
         for (int c = 0; c < NC; ++c) acc[c] = 0.0;
         const int self_rel = gi - (t0 + k) * JT;
         if (__any_sync(0xffffffffu, (unsigned)self_rel < (unsigned)JT))
-            tile_fp64<ORDER, RW, PAIR, true>(b, i0, i1, i2, i3, i4, i5, i6, i7, ei2, eps2u, self_rel, acc);
+            tile_fp64<ORDER, RW, PAIR, true, JP>(b, i0, i1, i2, i3, i4, i5, i6, i7, ei2, eps2u, self_rel, acc, jl);
         else
-            tile_fp64<ORDER, RW, PAIR, false>(b, i0, i1, i2, i3, i4, i5, i6, i7, ei2, eps2u, -1, acc);
+            tile_fp64<ORDER, RW, PAIR, false, JP>(b, i0, i1, i2, i3, i4, i5, i6, i7, ei2, eps2u, -1, acc, jl);
 #pragma unroll
         for (int c = 0; c < NC; ++c) sum[c] += acc[c];
 
@@ -900,14 +906,29 @@ __device__ __forceinline__ void force_block_fp64(const double2* __restrict__ js,
         }
     }
 
-    if (p < plim) {
+    if (JP == 1) {
+        if (p < plim) {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) store_result<NC, pot_comp(ORDER)>(partial, split, ncol, p, c, sum[c], ts);
+            for (int c = 0; c < NC; ++c) store_result<NC, pot_comp(ORDER)>(partial, split, ncol, p, c, sum[c], ts);
+        }
+        return;
+    }
+    // every copy has landed and been consumed: the ring holds the lane sums
+    double* lane = reinterpret_cast<double*>(smem_raw);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) lane[c * FORCE_NT + tid] = sum[c];
+    __syncthreads();
+    for (int o = tid; o < NI * NC; o += FORCE_NT) {
+        const int oi = o % NI, c = o / NI;
+        double s = 0.0;
+        for (int q = 0; q < JP; ++q) s += lane[c * FORCE_NT + q * NI + oi];
+        const int pp = pbase0 + oi;
+        if (pp < plim) store_result<NC, pot_comp(ORDER)>(partial, split, ncol, pp, c, s, ts);
     }
 }
 
 // F: result of a one-split launch (nullptr: partials only)
-template <int ORDER, int RW, bool PAIR>
+template <int ORDER, int RW, bool PAIR, int JP = 1>
 __global__ void __launch_bounds__(FORCE_NT) k_force_fp64(const double2* __restrict__ js, const int32_t* __restrict__ idx,
                                                          int n_act, int n, int ntiles, int jsplit, double eps2u,
                                                          double* __restrict__ partial, DevScalars* sc, double* F)
@@ -915,8 +936,8 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_fp64(const double2* __restri
     const int split = blockIdx.y;
     const int t0 = (int)((long long)split * ntiles / jsplit);
     const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
-    force_block_fp64<ORDER, RW, PAIR>(js, idx, blockIdx.x * FORCE_NT, n_act, n, t0, t1 - t0, split, n_act, eps2u,
-                                      partial, sc, TileSum{F, jsplit});
+    force_block_fp64<ORDER, RW, PAIR, JP>(js, idx, blockIdx.x * (FORCE_NT / JP), n_act, n, t0, t1 - t0, split, n_act,
+                                          eps2u, partial, sc, TileSum{F, jsplit});
 }
 
 // ------------------------------------------------------- device-driven cycle
@@ -974,8 +995,16 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_fp64_dyn(const double2* __re
         const int itile = w % it, split = w / it;
         const int t0 = (int)((long long)split * ntiles / jsplit);
         const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
-        force_block_fp64<ORDER, RW, PAIR>(js, idx, itile * FORCE_NT, n_act, n, t0, t1 - t0, split, n_act, eps2u,
-                                          partial, sc, TileSum{F, jsplit});
+        const int ni = sc->ni;
+        if (ni == FORCE_NT)
+            force_block_fp64<ORDER, RW, PAIR, 1>(js, idx, itile * ni, n_act, n, t0, t1 - t0, split, n_act, eps2u,
+                                                 partial, sc, TileSum{F, jsplit});
+        else if (ni == FORCE_NT / 4)
+            force_block_fp64<ORDER, RW, PAIR, 4>(js, idx, itile * ni, n_act, n, t0, t1 - t0, split, n_act, eps2u,
+                                                 partial, sc, TileSum{F, jsplit});
+        else
+            force_block_fp64<ORDER, RW, PAIR, 32>(js, idx, itile * ni, n_act, n, t0, t1 - t0, split, n_act, eps2u,
+                                                  partial, sc, TileSum{F, jsplit});
         if (__syncthreads_or(threadIdx.x == 0 && *(volatile int*)&sc->status != 0)) return;
     }
 }

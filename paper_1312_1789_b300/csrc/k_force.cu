@@ -98,11 +98,12 @@ static cudaError_t run_mixed(nb_ctx* c, const int32_t* idx, int n_act, int jspli
     }
 }
 
-// FP64 path: bound by the FP64 pipe, one i-particle per thread.
-template <int ORDER, int RW, bool PAIR>
-static cudaError_t run_fp64(nb_ctx* c, const int32_t* idx, int n_act, int jsplit, int itiles, int* occ_out, int)
+// FP64 path: bound by the FP64 pipe; one i-particle per thread (JP = 1) or
+// the j-parallel forms for small active sets.
+template <int ORDER, int RW, bool PAIR, int JP>
+static cudaError_t run_fp64_jp(nb_ctx* c, const int32_t* idx, int n_act, int jsplit, int itiles, int* occ_out)
 {
-    auto kern = k_force_fp64<ORDER, RW, PAIR>;
+    auto kern = k_force_fp64<ORDER, RW, PAIR, JP>;
     const size_t smem = (size_t)NSTAGE * JT * RW * 16;
     static bool configured = false;
     static int occ = 1;
@@ -121,6 +122,17 @@ static cudaError_t run_fp64(nb_ctx* c, const int32_t* idx, int n_act, int jsplit
                                               (int)(c->np / JT), jsplit, c->eps * c->eps, c->partial, c->sc,
                                               c->F);
     return cudaGetLastError();
+}
+
+template <int ORDER, int RW, bool PAIR>
+static cudaError_t run_fp64(nb_ctx* c, const int32_t* idx, int n_act, int jsplit, int itiles, int* occ_out, int ni)
+{
+    switch (ni) {
+    case FORCE_NT: return run_fp64_jp<ORDER, RW, PAIR, 1>(c, idx, n_act, jsplit, itiles, occ_out);
+    case FORCE_NT / 4: return run_fp64_jp<ORDER, RW, PAIR, 4>(c, idx, n_act, jsplit, itiles, occ_out);
+    case FORCE_NT / 32: return run_fp64_jp<ORDER, RW, PAIR, 32>(c, idx, n_act, jsplit, itiles, occ_out);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 // Dispatch on (computed order, stored record layout, softening mode, precision).
@@ -168,7 +180,7 @@ int force_occupancy(nb_ctx* c, int order, int ni)
 int force_ni(const nb_ctx* c, int64_t n_act)
 {
     const int prec = c->pred_prec >= 0 ? c->pred_prec : c->prec;
-    return prec == NB_MIXED ? mixed_ni(n_act) : FORCE_NT;
+    return prec == NB_MIXED ? mixed_ni(n_act) : fp64_ni(n_act);
 }
 
 cudaError_t launch_force(nb_ctx* c, int order, const int32_t* idx, int64_t n_act, int jsplit, int itiles, int ni)
@@ -213,7 +225,7 @@ __global__ void k_cycle_gate(DevScalars* sc, long long n, int ntiles, int4 slots
     const long long cap_splits = cap / ((long long)nc * na);
     int ni, it, js;
     if (js_force > 0 || !tuned_shape(tab, ntab, na, &ni, &it, &js)) {
-        ni = mixed ? mixed_ni(na) : FORCE_NT;
+        ni = mixed ? mixed_ni(na) : fp64_ni(na);
         const int sl = ni == 4 ? slots.x : ni == 32 ? slots.y : ni == FORCE_NT ? slots.z : slots.w;
         it = (int)((na + ni - 1) / ni);
         js = js_force > 0 ? js_force : makespan_split(it, ntiles, sl, cap_splits);

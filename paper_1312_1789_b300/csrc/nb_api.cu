@@ -234,8 +234,10 @@ int build_graph(nb_ctx* c)
     // gets the same shape (and the same summation order) in both modes
     int shape_slots[4];
     const int variants[4] = {4, 32, FORCE_NT, 2 * FORCE_NT};
-    for (int k = 0; k < 4; ++k)
-        shape_slots[k] = c->sm_count * force_occupancy(c, c->order, c->prec == NB_MIXED ? variants[k] : FORCE_NT);
+    for (int k = 0; k < 4; ++k) {
+        const int ni = c->prec == NB_MIXED || variants[k] <= FORCE_NT ? variants[k] : FORCE_NT;
+        shape_slots[k] = c->sm_count * force_occupancy(c, c->order, ni);
+    }
     if (!c->graph_stream) NB_CUDA(c, cudaStreamCreateWithFlags(&c->graph_stream, cudaStreamNonBlocking));
     cudaStream_t saved = c->stream;
     c->stream = c->graph_stream;
@@ -529,13 +531,10 @@ int nb_autotune(nb_ctx* c, int reps)
             const int64_t na = 1LL << k;
             const long long cap_splits = (long long)(c->partial_cap / ((size_t)nc * (size_t)na));
             int cand[4], nv = 0;
-            if (!mixed) cand[nv++] = FORCE_NT;
-            else {
-                if (na <= 16) cand[nv++] = 4;
-                if (na <= 512) cand[nv++] = 32;
-                if (na <= 16384) cand[nv++] = FORCE_NT;
-                if (na >= 64) cand[nv++] = 2 * FORCE_NT;
-            }
+            if (na <= 64) cand[nv++] = 4;
+            if (na <= 512) cand[nv++] = 32;
+            if (!mixed || na <= 16384) cand[nv++] = FORCE_NT;
+            if (mixed && na >= 64) cand[nv++] = 2 * FORCE_NT;
             float best = INFINITY;
             for (int v = 0; v < nv && rc == NB_OK; ++v) {
                 const int ni = cand[v];
@@ -581,8 +580,7 @@ int nb_set_tuning(nb_ctx* c, int n_classes, const int32_t* ni, const int32_t* js
         return set_err(c, NB_ERR_ARG, "need 0 <= n_classes <= %d and both arrays", TUNE_MAX);
     const bool mixed = c->prec == NB_MIXED;
     for (int k = 0; k < n_classes; ++k) {
-        const bool ok = ni[k] == 0 || ni[k] == FORCE_NT ||
-                        (mixed && (ni[k] == 4 || ni[k] == 32 || ni[k] == 2 * FORCE_NT));
+        const bool ok = ni[k] == 0 || ni[k] == 4 || ni[k] == 32 || ni[k] == FORCE_NT || (mixed && ni[k] == 2 * FORCE_NT);
         if (!ok || (ni[k] != 0 && js[k] < 1))
             return set_err(c, NB_ERR_ARG, "class %d: variant %d / split %d not valid here", k, ni[k], js[k]);
     }

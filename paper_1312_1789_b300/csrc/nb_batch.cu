@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(BNT) k_batch_plan(int K, const int32_t* __rest
     int smax = 1;
     for (int k = tid; k < K; k += BNT) {
         const int cnt = kcount[k];
-        const int ni = mixed ? min(mixed_ni(cnt), FORCE_NT) : FORCE_NT;
+        const int ni = mixed ? min(mixed_ni(cnt), FORCE_NT) : fp64_ni(cnt);
         const int jt = (int)(pk[k] / JT);
         int sk = 1;
         if (cnt > 0) {
@@ -439,8 +439,16 @@ __global__ void __launch_bounds__(FORCE_NT) k_batch_force_fp64_dyn(const double2
     const int n_items = sc->n_items, n_act = (int)sc->n_act;
     for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
         const BatchItem it = items[w];
-        force_block_fp64<ORDER, RW, true>(js, list, it.list_off, it.list_off + it.count, n, it.jt0, it.nt, it.split,
-                                          n_act, 0.0, partial, sc);
+        const int lim = it.list_off + it.count;
+        if (it.ni == FORCE_NT)
+            force_block_fp64<ORDER, RW, true, 1>(js, list, it.list_off, lim, n, it.jt0, it.nt, it.split, n_act, 0.0,
+                                                 partial, sc);
+        else if (it.ni == FORCE_NT / 4)
+            force_block_fp64<ORDER, RW, true, 4>(js, list, it.list_off, lim, n, it.jt0, it.nt, it.split, n_act, 0.0,
+                                                 partial, sc);
+        else
+            force_block_fp64<ORDER, RW, true, 32>(js, list, it.list_off, lim, n, it.jt0, it.nt, it.split, n_act, 0.0,
+                                                  partial, sc);
         if (__syncthreads_or(threadIdx.x == 0 && *(volatile int*)&sc->status != 0)) return;
     }
 }

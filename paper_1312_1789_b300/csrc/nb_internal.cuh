@@ -35,12 +35,20 @@ constexpr int IPT2_MIN_NACT = 512;
 //          particles still keep a CTA's threads busy (n_act <= 256: at most
 //          eight i-tiles of 32; n_act <= 24: at most six of 4).
 // The thresholds are where the autotuner's measurements switch variant on
-// the 65k and the 2^20 stores.  The FP64 force always runs 128.
+// the 65k and the 2^20 stores.
 __host__ __device__ inline int mixed_ni(long long n_act)
 {
     if (n_act >= IPT2_MIN_NACT) return 2 * FORCE_NT;
     if (n_act > 256) return FORCE_NT;
     return n_act > 24 ? 32 : 4;
+}
+
+// The FP64 force has the one-per-thread and the two j-parallel variants,
+// with the same thresholds.
+__host__ __device__ inline int fp64_ni(long long n_act)
+{
+    const int ni = mixed_ni(n_act);
+    return ni > FORCE_NT ? FORCE_NT : ni;
 }
 // stages of the force kernel's shared-memory ring.
 constexpr int NSTAGE = 3;

@@ -60,7 +60,7 @@ def test_autotune_fp64_table_is_per_precision():
     ctx = make_ctx(m, x, v, 1e-8, 6, nb.NB_FP64)
     ctx.autotune(1)
     t64 = ctx.get_tuning()
-    assert len(t64) == 10 and all(e[1] in (0, 128) for e in t64)
+    assert len(t64) == 10 and all(e[1] in (0, 4, 32, 128) for e in t64)
     ctx.set_precision(nb.NB_MIXED)
     assert ctx.get_tuning() == []  # the mixed table is separate and empty
     ctx.set_precision(nb.NB_FP64)
