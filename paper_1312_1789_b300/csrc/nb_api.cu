@@ -521,7 +521,7 @@ int nb_autotune(nb_ctx* c, int reps)
         int ncls = 0;
         while (ncls < TUNE_MAX && (1LL << ncls) <= c->n) ++ncls;
         // classes past this per-call time are left to the analytic rule
-        const float budget_ms = 25.f;
+        const float budget_ms = 60.f;
         int rc = NB_OK;
         float prev_best = 0.f;
         for (int k = 0; k < ncls && rc == NB_OK; ++k) {
@@ -540,9 +540,9 @@ int nb_autotune(nb_ctx* c, int reps)
                 const int ni = cand[v];
                 const int it = (int)((na + ni - 1) / ni);
                 const int base = makespan_split(it, ntiles, c->sm_count * force_occupancy(c, c->order, ni), cap_splits);
-                const int mult[6][2] = {{1, 4}, {1, 2}, {1, 1}, {2, 1}, {4, 1}, {0, 1}};
-                int tried[6], nt = 0;
-                for (int q = 0; q < 6 && rc == NB_OK; ++q) {
+                const int mult[8][2] = {{1, 4}, {1, 2}, {1, 1}, {2, 1}, {4, 1}, {8, 1}, {16, 1}, {0, 1}};
+                int tried[8], nt = 0;
+                for (int q = 0; q < 8 && rc == NB_OK; ++q) {
                     long long js = mult[q][0] == 0 ? 1 : (long long)base * mult[q][0] / mult[q][1];
                     if (js > ntiles) js = ntiles;
                     if (js > cap_splits) js = cap_splits;
