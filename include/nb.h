@@ -145,11 +145,16 @@ int nb_energy(nb_ctx* ctx, double* ekin, double* epot);
 
 /* Copy the state to host arrays (any may be NULL): x, v [n][3];
  * d [n][6][3] = acc, jerk, snap, crackle, a^(4), a^(5) (unused ones zero);
- * t, dt [n].  Synchronises.                                                */
+ * t, dt [n].  The reordering runs on the device (a staging buffer of 26 n
+ * doubles is allocated on first use); page-locked host arrays copy fastest.
+ * Synchronises.                                                            */
 int nb_get_state(nb_ctx* ctx, double* x, double* v, double* d, double* t, double* dt);
 
 /* Replace the state from host arrays with the nb_get_state layout (all
- * required; masses and softening are kept).  For checkpoint/restart.      */
+ * required; masses and softening are kept).  For checkpoint/restart.  The
+ * values are checked on the device first: NB_ERR_NAN for a non-finite one,
+ * NB_ERR_ARG for a dt <= 0, and then the old state is left unchanged.
+ * Synchronises.                                                            */
 int nb_set_state(nb_ctx* ctx, const double* x, const double* v, const double* d, const double* t,
                  const double* dt);
 

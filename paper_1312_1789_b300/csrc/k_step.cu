@@ -818,4 +818,69 @@ cudaError_t launch_energy_sums(nb_ctx* c, int with_pot)
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ state I/O
+// The caller's state in particle order (x[n][3], v[n][3], d[n][6][3], t[n],
+// dt[n]) sits in a staging buffer of 26 n doubles, segments in that order;
+// these kernels move it to and from the structure-of-arrays state.
+__global__ void k_state_check(const double* __restrict__ stage, int64_t n, DevScalars* sc)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double* x = stage;
+    const double* v = stage + 3 * n;
+    const double* d = stage + 6 * n;
+    const double* t = stage + 24 * n;
+    const double* dt = stage + 25 * n;
+    bool fin = isfinite(t[i]) && isfinite(dt[i]);
+    for (int k = 0; k < 3; ++k) fin = fin && isfinite(x[3 * i + k]) && isfinite(v[3 * i + k]);
+    for (int k = 0; k < 18; ++k) fin = fin && isfinite(d[18 * i + k]);
+    if (!fin) raise_status(sc, NB_ERR_NAN);
+    else if (!(dt[i] > 0.0)) raise_status(sc, NB_ERR_ARG);
+}
+
+__global__ void k_state_in(const double* __restrict__ stage, int64_t n, int64_t np, double* __restrict__ x,
+                           double* __restrict__ v, double* __restrict__ d, double* __restrict__ t,
+                           double* __restrict__ dt, const DevScalars* __restrict__ sc)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || sc->status != NB_OK) return;  // an invalid state leaves the old one in place
+    for (int k = 0; k < 3; ++k) {
+        x[k * np + i] = stage[3 * i + k];
+        v[k * np + i] = stage[3 * n + 3 * i + k];
+    }
+    for (int k = 0; k < 18; ++k) d[k * np + i] = stage[6 * n + 18 * i + k];
+    t[i] = stage[24 * n + i];
+    dt[i] = stage[25 * n + i];
+}
+
+__global__ void k_state_out(double* __restrict__ stage, int64_t n, int64_t np, const double* __restrict__ x,
+                            const double* __restrict__ v, const double* __restrict__ d,
+                            const double* __restrict__ t, const double* __restrict__ dt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int k = 0; k < 3; ++k) {
+        stage[3 * i + k] = x[k * np + i];
+        stage[3 * n + 3 * i + k] = v[k * np + i];
+    }
+    for (int k = 0; k < 18; ++k) stage[6 * n + 18 * i + k] = d[k * np + i];
+    stage[24 * n + i] = t[i];
+    stage[25 * n + i] = dt[i];
+}
+
+cudaError_t launch_state_in(nb_ctx* c)
+{
+    const int g = (int)((c->n + 255) / 256);
+    k_state_check<<<g, 256, 0, c->stream>>>(c->stage, c->n, c->sc);
+    k_state_in<<<g, 256, 0, c->stream>>>(c->stage, c->n, c->np, c->x, c->v, c->d, c->t, c->dt, c->sc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_out(nb_ctx* c)
+{
+    const int g = (int)((c->n + 255) / 256);
+    k_state_out<<<g, 256, 0, c->stream>>>(c->stage, c->n, c->np, c->x, c->v, c->d, c->t, c->dt);
+    return cudaGetLastError();
+}
+
 }  // namespace nb

@@ -329,7 +329,7 @@ void nb_destroy(nb_ctx* c)
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     void* ptrs[] = {c->m, c->eps2, c->x, c->v, c->d, c->t, c->dt, c->pot, c->jstore, c->act_idx, c->all_idx,
-                    c->chunk_cnt, c->chunk_min, c->d_tune, c->sc, c->red, c->f_idx, c->partial, c->F};
+                    c->chunk_cnt, c->chunk_min, c->d_tune, c->stage, c->sc, c->red, c->f_idx, c->partial, c->F};
     for (void* p : ptrs) dfree(c, p);
     if (c->h_sc) cudaFreeHost(c->h_sc);
     if (c->h_red) cudaFreeHost(c->h_red);
@@ -856,22 +856,26 @@ int nb_energy(nb_ctx* c, double* ekin, double* epot)
     return NB_OK;
 }
 
+// Device staging buffer for the state in the caller's particle order.
+static int ensure_stage(nb_ctx* c)
+{
+    if (!c->stage) NB_TRY(dalloc(c, &c->stage, (size_t)26 * (size_t)c->n));
+    return NB_OK;
+}
+
 int nb_get_state(nb_ctx* c, double* x, double* v, double* d, double* t, double* dt)
 {
     if (!c) return NB_ERR_ARG;
     NB_TRY(sync_scalars(c));
-    const size_t n = (size_t)c->n, np = (size_t)c->np;
-    if (x) NB_TRY(download_vec(c, x, c->x));
-    if (v) NB_TRY(download_vec(c, v, c->v));
-    if (d) {
-        std::vector<double> tmp(18 * np);
-        NB_CUDA(c, cudaMemcpyAsync(tmp.data(), c->d, tmp.size() * 8, cudaMemcpyDeviceToHost, c->stream));
-        NB_CUDA(c, cudaStreamSynchronize(c->stream));
-        for (size_t i = 0; i < n; ++i)
-            for (int q = 0; q < 18; ++q) d[18 * i + q] = tmp[(size_t)q * np + i];
-    }
-    if (t) NB_CUDA(c, cudaMemcpyAsync(t, c->t, n * 8, cudaMemcpyDeviceToHost, c->stream));
-    if (dt) NB_CUDA(c, cudaMemcpyAsync(dt, c->dt, n * 8, cudaMemcpyDeviceToHost, c->stream));
+    NB_TRY(ensure_stage(c));
+    const size_t n = (size_t)c->n;
+    NB_CUDA(c, launch_state_out(c));
+    const double* st = c->stage;
+    if (x) NB_CUDA(c, cudaMemcpyAsync(x, st, 3 * n * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (v) NB_CUDA(c, cudaMemcpyAsync(v, st + 3 * n, 3 * n * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (d) NB_CUDA(c, cudaMemcpyAsync(d, st + 6 * n, 18 * n * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (t) NB_CUDA(c, cudaMemcpyAsync(t, st + 24 * n, n * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (dt) NB_CUDA(c, cudaMemcpyAsync(dt, st + 25 * n, n * 8, cudaMemcpyDeviceToHost, c->stream));
     NB_CUDA(c, cudaStreamSynchronize(c->stream));
     return NB_OK;
 }
@@ -880,22 +884,21 @@ int nb_set_state(nb_ctx* c, const double* x, const double* v, const double* d, c
 {
     if (!c) return NB_ERR_ARG;
     if (!x || !v || !d || !t || !dt) return set_err(c, NB_ERR_ARG, "x, v, d, t and dt are required");
-    const size_t n = (size_t)c->n, np = (size_t)c->np;
-    if (!finite_all(x, 3 * n) || !finite_all(v, 3 * n) || !finite_all(d, 18 * n) || !finite_all(t, n) ||
-        !finite_all(dt, n))
-        return set_err(c, NB_ERR_NAN, "non-finite state");
-    for (size_t i = 0; i < n; ++i)
-        if (!(dt[i] > 0.0)) return set_err(c, NB_ERR_ARG, "dt[%zu] must be > 0", i);
-    NB_TRY(upload_vec(c, c->x, x));
-    NB_TRY(upload_vec(c, c->v, v));
-    std::vector<double> tmp(18 * np, 0.0);
-    for (size_t i = 0; i < n; ++i)
-        for (int q = 0; q < 18; ++q) tmp[(size_t)q * np + i] = d[18 * i + q];
-    NB_CUDA(c, cudaMemcpyAsync(c->d, tmp.data(), tmp.size() * 8, cudaMemcpyHostToDevice, c->stream));
-    NB_CUDA(c, cudaStreamSynchronize(c->stream));
-    NB_CUDA(c, cudaMemcpyAsync(c->t, t, n * 8, cudaMemcpyHostToDevice, c->stream));
-    NB_CUDA(c, cudaMemcpyAsync(c->dt, dt, n * 8, cudaMemcpyHostToDevice, c->stream));
-    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    NB_TRY(sync_scalars(c));
+    NB_TRY(ensure_stage(c));
+    const size_t n = (size_t)c->n;
+    double* st = c->stage;
+    NB_CUDA(c, cudaMemcpyAsync(st, x, 3 * n * 8, cudaMemcpyHostToDevice, c->stream));
+    NB_CUDA(c, cudaMemcpyAsync(st + 3 * n, v, 3 * n * 8, cudaMemcpyHostToDevice, c->stream));
+    NB_CUDA(c, cudaMemcpyAsync(st + 6 * n, d, 18 * n * 8, cudaMemcpyHostToDevice, c->stream));
+    NB_CUDA(c, cudaMemcpyAsync(st + 24 * n, t, n * 8, cudaMemcpyHostToDevice, c->stream));
+    NB_CUDA(c, cudaMemcpyAsync(st + 25 * n, dt, n * 8, cudaMemcpyHostToDevice, c->stream));
+    NB_CUDA(c, launch_state_in(c));
+    c->n_launch += 2;
+    const int st_code = sync_scalars(c);
+    if (st_code == NB_ERR_NAN) return set_err(c, NB_ERR_NAN, "non-finite state");
+    if (st_code == NB_ERR_ARG) return set_err(c, NB_ERR_ARG, "every dt must be > 0");
+    NB_TRY(st_code);
     c->have_particles = 1;
     c->have_pred = c->have_force = c->have_sched = 0;
     c->F_order = -1;

@@ -272,6 +272,7 @@ struct nb_ctx {
     int32_t* all_idx = nullptr;   // [n] 0..n-1
     int32_t* chunk_cnt = nullptr; // scheduler: per-chunk match counts
     double* chunk_min = nullptr;  // scheduler: per-chunk minima of t + dt
+    double* stage = nullptr;      // state I/O staging, 26 n doubles (allocated on first use)
     int n_chunks = 0;
     nb::DevScalars* sc = nullptr;
     nb::DevScalars* h_sc = nullptr;  // pinned
@@ -350,6 +351,10 @@ cudaError_t launch_startup_store(nb_ctx* c, int order);
 cudaError_t launch_startup_dt(nb_ctx* c);
 cudaError_t launch_energy_sums(nb_ctx* c, int with_pot);
 cudaError_t launch_set_dt(nb_ctx* c, double dt);
+// State I/O through c->stage: validate and scatter into the state (nothing
+// written if any value is invalid), or gather the state into it.
+cudaError_t launch_state_in(nb_ctx* c);
+cudaError_t launch_state_out(nb_ctx* c);
 int force_occupancy(nb_ctx* c, int order, int ni);
 int force_ni(const nb_ctx* c, int64_t n_act);
 void sched_layout(int64_t n, int sm_count, int* per, int* nch);

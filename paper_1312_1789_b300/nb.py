@@ -272,13 +272,19 @@ class NBody:
         return ek.value, ep.value
 
     # --------------------------------------------------------- state exchange
-    def get_state(self):
+    def get_state(self, out=None):
+        """State as {x, v, d, t, dt}; out: such a dict of C-contiguous float64 arrays to fill instead."""
         n = self.n
-        x, v = np.zeros((n, 3)), np.zeros((n, 3))
-        d = np.zeros((n, 6, 3))
-        t, dt = np.zeros(n), np.zeros(n)
-        self._check(self._L.nb_get_state(self._h, _d(x), _d(v), _d(d), _d(t), _d(dt)))
-        return {"x": x, "v": v, "d": d, "t": t, "dt": dt}
+        if out is None:
+            out = {"x": np.zeros((n, 3)), "v": np.zeros((n, 3)), "d": np.zeros((n, 6, 3)), "t": np.zeros(n),
+                   "dt": np.zeros(n)}
+        for k, shape in (("x", (n, 3)), ("v", (n, 3)), ("d", (n, 6, 3)), ("t", (n,)), ("dt", (n,))):
+            a = out[k]
+            if a.dtype != np.float64 or a.shape != shape or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError(f"out[{k!r}] must be a C-contiguous float64 array of shape {shape}")
+        self._check(self._L.nb_get_state(self._h, _d(out["x"]), _d(out["v"]), _d(out["d"]), _d(out["t"]),
+                                         _d(out["dt"])))
+        return out
 
     def set_state(self, x, v, d, t, dt):
         n = self.n

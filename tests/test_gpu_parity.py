@@ -512,6 +512,18 @@ def test_errors_are_reported_not_faulted():
     with pytest.raises(nb.NBError) as e:
         ctx.set_particles(m, bad, v)
     assert e.value.code == nb.NB_ERR_NAN
+    # an invalid state is rejected (checked on the device) and leaves the old one
+    S = ctx.get_state()
+    for key, idx, val, code in (("d", (5, 2, 1), np.inf, nb.NB_ERR_NAN), ("dt", (7,), 0.0, nb.NB_ERR_ARG),
+                                ("x", (n - 1, 0), np.nan, nb.NB_ERR_NAN)):
+        B = {k: a.copy() for k, a in S.items()}
+        B[key][idx] = val
+        with pytest.raises(nb.NBError) as e:
+            ctx.set_state(B["x"], B["v"], B["d"], B["t"], B["dt"])
+        assert e.value.code == code
+        after = ctx.get_state()
+        for k in S:
+            assert np.array_equal(after[k], S[k]), (key, k)
     # a minimum step larger than what the start-up criterion asks for
     c2 = nb.NBody(n, 6, 1e-4, nb.NB_FP64)
     c2.set_params(0.2, 0.01, 1.0 / 16, 1.0 / 32)
