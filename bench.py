@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--energy-t", type=float, default=1.0 / 16, help="end time of the energy-budget leg")
     p.add_argument("--cusp-fp64", action="store_true",
                    help="also run the full-size cusp on the FP64 path (about two minutes)")
+    p.add_argument("--nucleus-full", action="store_true",
+                   help="also run the 2^20 nucleus to t = 1/16 on the mixed path (about two minutes)")
     return p.parse_args()
 
 
@@ -312,6 +314,28 @@ def cusp_run(nb, w, p, stream, torch, t_end, dt_max=None):
             "interactions": ni, "seconds": el, "whole_run_interactions_per_s": ni / el}
 
 
+def nucleus_run(nb, w, p, stream, torch, t_end, graph=0):
+    c = nb.NBody(w.n, w.order, 0.0, p)
+    c.set_stream(stream)
+    c.set_softening(np.sqrt(w.eps2))
+    c.set_params(w.eta, w.eta_s, w.dt_max, 2.0 ** -40)
+    c.set_particles(w.m, w.x, w.v)
+    c.set_precision(nb.NB_FP64)
+    e0 = sum(c.energy())
+    c.set_precision(p)
+    c.set_graph(graph)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nblk, ni = c.step_until(t_end)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    c.set_precision(nb.NB_FP64)
+    e1 = sum(c.energy())
+    c.close()
+    return {"dE_E": (e1 - e0) / abs(e0), "blocks": nblk, "interactions": ni, "seconds": el,
+            "whole_run_interactions_per_s": ni / el}
+
+
 def cusp_leg(args, nb, ics, stream, torch):
     """Dehnen gamma=1 cusp with a central black-hole binary, 8th order.  The
     two-body elements are not conserved (the stellar mass inside the orbit
@@ -521,6 +545,23 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
                                      **table}
     except Exception as e:  # pragma: no cover
         out["per_workload_force"] = {"error": repr(e)}
+    # ---- galactic nucleus: energy error of both paths on the 2^16-star
+    #      version of the benchmark system to t = 1/16 (FP64 cannot finish the
+    #      2^20 one); the 2^20 mixed run with --nucleus-full
+    try:
+        nuc = {}
+        ws = ics.plummer_nucleus(1 << 16, 1002, 1e-5, 1.0 / 16)
+        nuc["reduced"] = {"workload": ws.name + " to t=1/16"}
+        for name, p in (("mixed", nb.NB_MIXED), ("fp64", nb.NB_FP64)):
+            nuc["reduced"][name] = nucleus_run(nb, ws, p, stream, torch, 1.0 / 16)
+        r = nuc["reduced"]
+        r["mixed_dE_within_2x_of_fp64"] = abs(r["mixed"]["dE_E"]) <= 2 * abs(r["fp64"]["dE_E"])
+        if args.nucleus_full:
+            nuc["full"] = {"workload": wl.name + " to t=1/16",
+                           "mixed": nucleus_run(nb, wl, nb.NB_MIXED, stream, torch, 1.0 / 16, graph=64)}
+        out["nucleus_energy"] = nuc
+    except Exception as e:  # pragma: no cover
+        out["nucleus_energy"] = {"error": repr(e)}
     # ---- cusp nucleus, order 8: energy and binary-element drift of both paths
     try:
         out["cusp8"] = cusp_leg(args, nb, ics, stream, torch)
