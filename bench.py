@@ -203,7 +203,11 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    build.build()
+    # one rank compiles (if the library is stale), the others wait and load it
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
     nb.lib()
     stream = torch.cuda.current_stream()
     prec = nb.NB_MIXED if args.precision == "mixed" else nb.NB_FP64
