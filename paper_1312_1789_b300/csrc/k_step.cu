@@ -195,6 +195,36 @@ cudaError_t launch_sched(nb_ctx* c)
 // position.  The tail's FP32 rounding is a few float ulps of its terms,
 // scaled by h^2 -- far below the pair separations that need the
 // double-single position.
+// IEEE format conversions in integer arithmetic: the FP64 pipe, which runs
+// f64 <-> f32 conversions here, is 1/64 of the FP32 rate.
+// double -> float rounded toward zero; a result below the normal float range
+// flushes to zero, one above it gives inf, NaN stays NaN.
+__device__ __forceinline__ float f64_to_f32_rz(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7FF);
+    const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+    if (e == 0x7FF) return __uint_as_float(sgn | 0x7F800000u | (mant ? 0x400000u : 0u));
+    const int ef = e - 1023 + 127;
+    if (ef >= 255) return __uint_as_float(sgn | 0x7F800000u);
+    if (ef <= 0) return __uint_as_float(sgn);
+    return __uint_as_float(sgn | ((unsigned)ef << 23) | (unsigned)(mant >> 29));
+}
+
+// float -> double, exact for every normal float (a subnormal one flushes to
+// zero)
+__device__ __forceinline__ double f32_to_f64(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
+    const int e = (int)((u >> 23) & 0xFF);
+    const unsigned long long mant = u & 0x7FFFFFu;
+    if (e == 0xFF) return __longlong_as_double((long long)(sgn | 0x7FF0000000000000ull | (mant << 29)));
+    if (e == 0) return __longlong_as_double((long long)sgn);
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)(e - 127 + 1023) << 52) | (mant << 29)));
+}
+
 template <int ORDER, bool MIXED>
 __device__ __forceinline__ void predict_one(const int64_t i, double tp, const double* __restrict__ m,
                                             const double* __restrict__ eps2, const double* __restrict__ x,
@@ -222,7 +252,7 @@ __device__ __forceinline__ void predict_one(const int64_t i, double tp, const do
         mi = m[i];
         ei = eps2[i];
         const double h = tp - t[i];
-        const float hf = (float)h;
+        const float hf = MIXED ? f64_to_f32_rz(h) : 0.0f;
         // Mixed: the FP32 tail needs every derivative within the float range
         // (interpolated high derivatives of a particle just out of a close
         // encounter can exceed it); such a particle takes the FP64 series.
@@ -231,31 +261,31 @@ __device__ __forceinline__ void predict_one(const int64_t i, double tp, const do
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const double x0 = x[c * np + i], v0 = v[c * np + i];
-                const float a0 = (float)d[(0 * 3 + c) * np + i], j0 = (float)d[(1 * 3 + c) * np + i];
-                const float s0 = (float)d[(2 * 3 + c) * np + i], c0 = (float)d[(3 * 3 + c) * np + i];
+                const float a0 = f64_to_f32_rz(d[(0 * 3 + c) * np + i]), j0 = f64_to_f32_rz(d[(1 * 3 + c) * np + i]);
+                const float s0 = f64_to_f32_rz(d[(2 * 3 + c) * np + i]), c0 = f64_to_f32_rz(d[(3 * 3 + c) * np + i]);
                 float T;
                 bool fin = isfinite(a0) && isfinite(j0) && isfinite(s0) && isfinite(c0);
                 if (ORDER == 8) {
-                    const float d4 = (float)d[(4 * 3 + c) * np + i], d5 = (float)d[(5 * 3 + c) * np + i];
+                    const float d4 = f64_to_f32_rz(d[(4 * 3 + c) * np + i]), d5 = f64_to_f32_rz(d[(5 * 3 + c) * np + i]);
                     fin = fin && isfinite(d4) && isfinite(d5);
                     T = fmaf(hf, fmaf(hf, fmaf(hf, fmaf(hf, fmaf(hf, d5 * (1.f / 5040), d4 * (1.f / 720)),
                                                          c0 * (1.f / 120)), s0 * (1.f / 24)), j0 * (1.f / 6)),
                              a0 * 0.5f);
                     vf[c] = fmaf(hf, fmaf(hf, fmaf(hf, fmaf(hf, fmaf(hf, fmaf(hf, d5 * (1.f / 720), d4 * (1.f / 120)),
                                                                      c0 * (1.f / 24)), s0 * (1.f / 6)), j0 * 0.5f), a0),
-                                 (float)v0);
+                                 f64_to_f32_rz(v0));
                     af[c] = fmaf(hf, fmaf(hf, fmaf(hf, fmaf(hf, fmaf(hf, d5 * (1.f / 120), d4 * (1.f / 24)),
                                                            c0 * (1.f / 6)), s0 * 0.5f), j0), a0);
                     jf[c] = fmaf(hf, fmaf(hf, fmaf(hf, fmaf(hf, d5 * (1.f / 24), d4 * (1.f / 6)), c0 * 0.5f), s0), j0);
                 } else {
                     T = fmaf(hf, fmaf(hf, fmaf(hf, c0 * (1.f / 120), s0 * (1.f / 24)), j0 * (1.f / 6)), a0 * 0.5f);
                     vf[c] = fmaf(hf, fmaf(hf, fmaf(hf, fmaf(hf, c0 * (1.f / 24), s0 * (1.f / 6)), j0 * 0.5f), a0),
-                                 (float)v0);
+                                 f64_to_f32_rz(v0));
                     af[c] = fmaf(hf, fmaf(hf, fmaf(hf, c0 * (1.f / 6), s0 * 0.5f), j0), a0);
                 }
                 fin = fin && isfinite(T) && isfinite(vf[c]) && isfinite(af[c]) && isfinite(jf[c]);
                 fp64_series = fp64_series || !fin;
-                xp[c] = fma(h, fma(h, (double)T, v0), x0);
+                xp[c] = fma(h, fma(h, f32_to_f64(T), v0), x0);
             }
         }
         if (fp64_series) {
@@ -290,11 +320,15 @@ __device__ __forceinline__ void predict_one(const int64_t i, double tp, const do
         float hx[3], lx[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            hx[c] = __double2float_rn(xp[c]);
-            lx[c] = __double2float_rn(xp[c] - (double)hx[c]);
+            // hi = the leading 24 bits (the double with its low 29 mantissa bits
+            // cleared, exact in float), lo = the rest (exact in double, then
+            // truncated to float): |hi + lo - x| <= 2^-47 |x|
+            const double dhi = __longlong_as_double(__double_as_longlong(xp[c]) & ~0x1FFFFFFFLL);
+            hx[c] = f64_to_f32_rz(dhi);
+            lx[c] = f64_to_f32_rz(xp[c] - dhi);
         }
-        r[0] = make_float4(hx[0], hx[1], hx[2], (float)mi);
-        r[1] = make_float4(lx[0], lx[1], lx[2], (float)ei);
+        r[0] = make_float4(hx[0], hx[1], hx[2], f64_to_f32_rz(mi));
+        r[1] = make_float4(lx[0], lx[1], lx[2], f64_to_f32_rz(ei));
         r[2] = make_float4(vf[0], vf[1], vf[2], 0.f);
         if (ORDER >= 6) r[3] = make_float4(af[0], af[1], af[2], 0.f);
         if (ORDER >= 8) r[4] = make_float4(jf[0], jf[1], jf[2], 0.f);
