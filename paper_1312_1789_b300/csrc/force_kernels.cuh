@@ -193,10 +193,9 @@ __device__ __forceinline__ void pair_mixed(const float4 w0, const float4 w1, con
     acc[NC - 1] = fmaf(mr, rinv, acc[NC - 1]);
 }
 
-// Two i-particles in the two lanes of packed FP32x2 arithmetic (FFMA2 and
-// kin on sm_100+), the j record broadcast to both: one instruction does the
-// work of two.  Same pair terms and operation order as pair_mixed.  The i
-// values are held negated (n*) so that every difference is an add.
+// i side of packed FP32x2 arithmetic: two i-particles (one per lane) or one
+// particle in both.  The values are held negated (n*) so that every
+// difference is an add.
 struct IMixed2 {
     float2 nxh[3], nxl[3], nv[3], na[3], nk[3];
     float2 e2;  // eps_i^2 (per-particle softening) or the uniform pair value
@@ -204,23 +203,65 @@ struct IMixed2 {
 
 __device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
 
-template <int ORDER, bool PAIR, bool SELF = false>
-__device__ __forceinline__ void pair_mixed_x2(const float4 w0, const float4 w1, const float4 w2, const float4 w3,
-                                              const float4 w4, const IMixed2& I, float2 (&acc)[ncomp(ORDER)],
-                                              const int2 srel = make_int2(-1, -1), const int jj = 0)
+// The j side of a packed pair: one record broadcast to both lanes, or one
+// record per lane.
+struct JMixed2 {
+    float2 xh[3], xl[3], v[3], a[3], k[3];
+    float2 m, e2;  // m_j, eps_j^2
+};
+
+template <int ORDER>
+__device__ __forceinline__ JMixed2 j_bcast(const float4 w0, const float4 w1, const float4 w2, const float4 w3,
+                                           const float4 w4)
+{
+    JMixed2 J;
+    J.xh[0] = bc2(w0.x), J.xh[1] = bc2(w0.y), J.xh[2] = bc2(w0.z), J.m = bc2(w0.w);
+    J.xl[0] = bc2(w1.x), J.xl[1] = bc2(w1.y), J.xl[2] = bc2(w1.z), J.e2 = bc2(w1.w);
+    J.v[0] = bc2(w2.x), J.v[1] = bc2(w2.y), J.v[2] = bc2(w2.z);
+    J.a[0] = bc2(w3.x), J.a[1] = bc2(w3.y), J.a[2] = bc2(w3.z);
+    J.k[0] = bc2(w4.x), J.k[1] = bc2(w4.y), J.k[2] = bc2(w4.z);
+    return J;
+}
+
+// records r (lane x) and s (lane y), RW float4 each
+template <int ORDER, int RW>
+__device__ __forceinline__ JMixed2 j_lanes(const float4* __restrict__ r, const float4* __restrict__ s)
+{
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 r0 = r[0], r1 = r[1], r2 = ORDER >= 4 ? r[2] : z, r3 = ORDER >= 6 ? r[3] : z,
+                 r4 = ORDER >= 8 ? r[4] : z;
+    const float4 s0 = s[0], s1 = s[1], s2 = ORDER >= 4 ? s[2] : z, s3 = ORDER >= 6 ? s[3] : z,
+                 s4 = ORDER >= 8 ? s[4] : z;
+    JMixed2 J;
+    J.xh[0] = make_float2(r0.x, s0.x), J.xh[1] = make_float2(r0.y, s0.y), J.xh[2] = make_float2(r0.z, s0.z);
+    J.m = make_float2(r0.w, s0.w);
+    J.xl[0] = make_float2(r1.x, s1.x), J.xl[1] = make_float2(r1.y, s1.y), J.xl[2] = make_float2(r1.z, s1.z);
+    J.e2 = make_float2(r1.w, s1.w);
+    J.v[0] = make_float2(r2.x, s2.x), J.v[1] = make_float2(r2.y, s2.y), J.v[2] = make_float2(r2.z, s2.z);
+    J.a[0] = make_float2(r3.x, s3.x), J.a[1] = make_float2(r3.y, s3.y), J.a[2] = make_float2(r3.z, s3.z);
+    J.k[0] = make_float2(r4.x, s4.x), J.k[1] = make_float2(r4.y, s4.y), J.k[2] = make_float2(r4.z, s4.z);
+    return J;
+}
+
+// The packed pair chain: lane x and lane y each take one (i, j) pair.  Same
+// pair terms and operation order as pair_mixed.  SELF: self_x / self_y mask
+// a lane whose pair is a particle with itself.
+template <int ORDER, bool PAIR, bool SELF>
+__device__ __forceinline__ void pair_mixed_x2j(const JMixed2& J, const IMixed2& I, float2 (&acc)[ncomp(ORDER)],
+                                               const bool self_x, const bool self_y)
 {
     constexpr int NC = ncomp(ORDER);
-    const float2 dx = __fadd2_rn(__fadd2_rn(bc2(w0.x), I.nxh[0]), __fadd2_rn(bc2(w1.x), I.nxl[0]));
-    const float2 dy = __fadd2_rn(__fadd2_rn(bc2(w0.y), I.nxh[1]), __fadd2_rn(bc2(w1.y), I.nxl[1]));
-    const float2 dz = __fadd2_rn(__fadd2_rn(bc2(w0.z), I.nxh[2]), __fadd2_rn(bc2(w1.z), I.nxl[2]));
-    const float2 e2 = PAIR ? make_float2(fmaxf(w1.w, I.e2.x), fmaxf(w1.w, I.e2.y)) : I.e2;
+    const float2 dx = __fadd2_rn(__fadd2_rn(J.xh[0], I.nxh[0]), __fadd2_rn(J.xl[0], I.nxl[0]));
+    const float2 dy = __fadd2_rn(__fadd2_rn(J.xh[1], I.nxh[1]), __fadd2_rn(J.xl[1], I.nxl[1]));
+    const float2 dz = __fadd2_rn(__fadd2_rn(J.xh[2], I.nxh[2]), __fadd2_rn(J.xl[2], I.nxl[2]));
+    const float2 e2 = PAIR ? make_float2(fmaxf(J.e2.x, I.e2.x), fmaxf(J.e2.y, I.e2.y)) : I.e2;
     const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
     float2 rinv = make_float2(guard_rinv<PAIR>(r2.x), guard_rinv<PAIR>(r2.y));
-    if (SELF) {  // a lane's own record: every term carries rinv
-        if (jj == srel.x) rinv.x = 0.0f;
-        if (jj == srel.y) rinv.y = 0.0f;
+    if (SELF) {  // every term carries rinv
+        if (self_x) rinv.x = 0.0f;
+        if (self_y) rinv.y = 0.0f;
     }
-    const float2 mr = __fmul2_rn(bc2(w0.w), rinv);
+    const float2 mr = __fmul2_rn(J.m, rinv);
     if (ORDER == 0) {
         acc[0] = __fadd2_rn(acc[0], mr);
         return;
@@ -228,8 +269,8 @@ __device__ __forceinline__ void pair_mixed_x2(const float4 w0, const float4 w1, 
     const float2 rinv2 = __fmul2_rn(rinv, rinv);
     const float2 q = __fmul2_rn(mr, rinv2);
     const float2 r3 = __fmul2_rn(bc2(-3.0f), rinv2);
-    const float2 dvx = __fadd2_rn(bc2(w2.x), I.nv[0]), dvy = __fadd2_rn(bc2(w2.y), I.nv[1]),
-                 dvz = __fadd2_rn(bc2(w2.z), I.nv[2]);
+    const float2 dvx = __fadd2_rn(J.v[0], I.nv[0]), dvy = __fadd2_rn(J.v[1], I.nv[1]),
+                 dvz = __fadd2_rn(J.v[2], I.nv[2]);
     acc[0] = __ffma2_rn(q, dx, acc[0]);
     acc[1] = __ffma2_rn(q, dy, acc[1]);
     acc[2] = __ffma2_rn(q, dz, acc[2]);
@@ -238,8 +279,8 @@ __device__ __forceinline__ void pair_mixed_x2(const float4 w0, const float4 w1, 
     acc[4] = __ffma2_rn(q, __ffma2_rn(a3, dy, dvy), acc[4]);
     acc[5] = __ffma2_rn(q, __ffma2_rn(a3, dz, dvz), acc[5]);
     if (ORDER >= 6) {
-        const float2 dax = __fadd2_rn(bc2(w3.x), I.na[0]), day = __fadd2_rn(bc2(w3.y), I.na[1]),
-                     daz = __fadd2_rn(bc2(w3.z), I.na[2]);
+        const float2 dax = __fadd2_rn(J.a[0], I.na[0]), day = __fadd2_rn(J.a[1], I.na[1]),
+                     daz = __fadd2_rn(J.a[2], I.na[2]);
         const float2 ww3 = __fmul2_rn(
             __ffma2_rn(dvx, dvx,
                        __ffma2_rn(dvy, dvy,
@@ -251,8 +292,8 @@ __device__ __forceinline__ void pair_mixed_x2(const float4 w0, const float4 w1, 
         acc[7] = __ffma2_rn(q, __ffma2_rn(c3, dy, __ffma2_rn(c2, dvy, day)), acc[7]);
         acc[8] = __ffma2_rn(q, __ffma2_rn(c3, dz, __ffma2_rn(c2, dvz, daz)), acc[8]);
         if (ORDER >= 8) {
-            const float2 dkx = __fadd2_rn(bc2(w4.x), I.nk[0]), dky = __fadd2_rn(bc2(w4.y), I.nk[1]),
-                         dkz = __fadd2_rn(bc2(w4.z), I.nk[2]);
+            const float2 dkx = __fadd2_rn(J.k[0], I.nk[0]), dky = __fadd2_rn(J.k[1], I.nk[1]),
+                         dkz = __fadd2_rn(J.k[2], I.nk[2]);
             const float2 u3 = __fmul2_rn(
                 __ffma2_rn(bc2(3.0f), __ffma2_rn(dvx, dax, __ffma2_rn(dvy, day, __fmul2_rn(dvz, daz))),
                            __ffma2_rn(dx, dkx, __ffma2_rn(dy, dky, __fmul2_rn(dz, dkz)))),
@@ -268,6 +309,18 @@ __device__ __forceinline__ void pair_mixed_x2(const float4 w0, const float4 w1, 
     }
     acc[NC - 2] = __fadd2_rn(acc[NC - 2], mr);
     acc[NC - 1] = __ffma2_rn(mr, rinv, acc[NC - 1]);
+}
+
+// Two i-particles in the two lanes (FFMA2 and kin on sm_100+), the j record
+// broadcast to both: one instruction does the work of two.  srel: the
+// lanes' own record in the tile (if any).
+template <int ORDER, bool PAIR, bool SELF = false>
+__device__ __forceinline__ void pair_mixed_x2(const float4 w0, const float4 w1, const float4 w2, const float4 w3,
+                                              const float4 w4, const IMixed2& I, float2 (&acc)[ncomp(ORDER)],
+                                              const int2 srel = make_int2(-1, -1), const int jj = 0)
+{
+    pair_mixed_x2j<ORDER, PAIR, SELF>(j_bcast<ORDER>(w0, w1, w2, w3, w4), I, acc, SELF && jj == srel.x,
+                                      SELF && jj == srel.y);
 }
 
 // One j tile for NP lane-pairs (2 NP i-particles) of a thread: every record
@@ -625,10 +678,31 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_mixed_xs(const float4* __res
 
 // j-parallel form for small active sets: NI = FORCE_NT / JP i-particles per
 // CTA; thread (il, jl) = (tid % NI, tid / NI) takes i-particle il and the
-// records jl, jl + JP, ... of every j tile.  Each thread keeps a
-// double-single sum (FP32 tile sums folded every FOLD tiles); at the end the
-// JP sums of an i-particle are added in jl order through the (then idle)
-// ring buffer, so the result depends on the launch shape only.
+// records jl, jl + JP, ... of every j tile, two at a time in the two lanes of
+// packed FP32x2 arithmetic (records jl + 2 JP m in lane x, jl + 2 JP m + JP in
+// lane y; the i-particle in both).  Each thread folds its two FP32 lane sums
+// into one double-single sum every 2 JP tiles (JT records per lane sum, as in
+// the two-per-thread form); at the end the JP sums of an i-particle are added
+// in jl order through the (then idle) ring buffer, so the result depends on
+// the launch shape only.
+template <int JP>
+__host__ __device__ constexpr int jx_unroll()
+{
+    return JT / (2 * JP) >= 4 ? 2 : JT / (2 * JP);
+}
+template <int ORDER, int RW, bool PAIR, bool SELF, int JP>
+__device__ __forceinline__ void tile_mixed_jx(const float4* __restrict__ b, const IMixed2& I, const int jl,
+                                              const int self_rel, float2 (&acc)[ncomp(ORDER)])
+{
+    static_assert(JT % (2 * JP) == 0, "a tile holds whole lane pairs");
+#pragma unroll jx_unroll<JP>()
+    for (int m = 0; m < JT / (2 * JP); ++m) {
+        const int ja = jl + 2 * JP * m, jb = ja + JP;
+        pair_mixed_x2j<ORDER, PAIR, SELF>(j_lanes<ORDER, RW>(b + ja * RW, b + jb * RW), I, acc,
+                                          SELF && ja == self_rel, SELF && jb == self_rel);
+    }
+}
+
 template <int ORDER, int RW, bool PAIR, int JP>
 __device__ __forceinline__ void force_block_mixed_jp(const float4* __restrict__ js, const int32_t* __restrict__ idx,
                                                      const int pbase0, const int plim, const int n, const int t0,
@@ -639,7 +713,7 @@ __device__ __forceinline__ void force_block_mixed_jp(const float4* __restrict__ 
 {
     constexpr int NC = ncomp(ORDER);
     constexpr int NI = FORCE_NT / JP;
-    constexpr int FOLD = JP >= 16 ? JP / 4 : 1;
+    constexpr int FOLD = 2 * JP;
     static_assert(NSTAGE * JT * RW * 16 >= NC * FORCE_NT * 8, "ring too small for the lane reduction");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float4* buf = reinterpret_cast<float4*>(smem_raw);
@@ -666,21 +740,26 @@ __device__ __forceinline__ void force_block_mixed_jp(const float4* __restrict__ 
         raise_status(sc, NB_ERR_ARG);
         gi = 0;
     }
-    IMixed I[1];
+    IMixed I;
     {
         const float4* ri = js + (size_t)gi * RW;
-        I[0].i0 = ri[0];
-        I[0].i1 = ri[1];
-        I[0].i2 = ri[2];
-        I[0].i3 = ORDER >= 6 ? ri[3] : make_float4(0.f, 0.f, 0.f, 0.f);
-        I[0].i4 = ORDER >= 8 ? ri[4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        I.i0 = ri[0];
+        I.i1 = ri[1];
+        I.i2 = ri[2];
+        I.i3 = ORDER >= 6 ? ri[3] : make_float4(0.f, 0.f, 0.f, 0.f);
+        I.i4 = ORDER >= 8 ? ri[4] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    const float ei2 = PAIR ? I[0].i1.w : eps2u;
+    const float ei2 = PAIR ? I.i1.w : eps2u;
     const bool dom = PAIR && __all_sync(0xffffffffu, ei2 >= eps2max && ei2 > 0.0f);
+    const IMixed2 I2 = pack_pair(I, I, ei2, ei2);
 
-    float hi[NC], lo[NC], acc[NC];
+    float hi[NC], lo[NC];
+    float2 acc[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) hi[c] = lo[c] = acc[c] = 0.f;
+    for (int c = 0; c < NC; ++c) {
+        hi[c] = lo[c] = 0.f;
+        acc[c] = make_float2(0.f, 0.f);
+    }
 
     for (int k = 0; k < nt; ++k) {
         const int st = k % NSTAGE;
@@ -695,23 +774,19 @@ __device__ __forceinline__ void force_block_mixed_jp(const float4* __restrict__ 
         const float4* b = buf + st * JT * RW;
         const int self_rel = gi - (t0 + k) * JT;
         const bool self_here = __any_sync(0xffffffffu, (unsigned)self_rel < (unsigned)JT);
-#define NB_JP_LOOP(PP, SS)                                                                                   \
-    for (int jj = jl; jj < JT; jj += JP)                                                                     \
-        pair_mixed<ORDER, PP, SS>(b[jj * RW + 0], b[jj * RW + 1], b[jj * RW + 2],                            \
-                                  ORDER >= 6 ? b[jj * RW + 3] : make_float4(0.f, 0.f, 0.f, 0.f),             \
-                                  ORDER >= 8 ? b[jj * RW + 4] : make_float4(0.f, 0.f, 0.f, 0.f), I[0], ei2, \
-                                  SS && jj == self_rel, acc);
         if (!PAIR || dom) {
-            if (self_here) { NB_JP_LOOP(false, true) } else { NB_JP_LOOP(false, false) }
+            if (self_here) tile_mixed_jx<ORDER, RW, false, true, JP>(b, I2, jl, self_rel, acc);
+            else tile_mixed_jx<ORDER, RW, false, false, JP>(b, I2, jl, self_rel, acc);
         } else {
-            if (self_here) { NB_JP_LOOP(true, true) } else { NB_JP_LOOP(true, false) }
+            if (self_here) tile_mixed_jx<ORDER, RW, true, true, JP>(b, I2, jl, self_rel, acc);
+            else tile_mixed_jx<ORDER, RW, true, false, JP>(b, I2, jl, self_rel, acc);
         }
-#undef NB_JP_LOOP
         if ((k + 1) % FOLD == 0 || k + 1 == nt) {
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                ds_add(hi[c], lo[c], acc[c]);
-                acc[c] = 0.f;
+                ds_add(hi[c], lo[c], acc[c].x);
+                ds_add(hi[c], lo[c], acc[c].y);
+                acc[c] = make_float2(0.f, 0.f);
             }
         }
         __syncthreads();  // every thread is done with stage st
@@ -740,7 +815,7 @@ __device__ __forceinline__ void force_block_mixed_jp(const float4* __restrict__ 
 // One system, j-parallel form: blockIdx.x = i-tile of FORCE_NT / JP active
 // particles, blockIdx.y = j-split of the whole store.
 template <int ORDER, int RW, bool PAIR, int JP>
-__global__ void __launch_bounds__(FORCE_NT) k_force_mixed_jp(const float4* __restrict__ js,
+__global__ void __launch_bounds__(FORCE_NT, 4) k_force_mixed_jp(const float4* __restrict__ js,
                                                              const int32_t* __restrict__ idx, int n_act, int n,
                                                              int ntiles, int jsplit, float eps2u, float eps2max,
                                                              double* __restrict__ partial, DevScalars* sc, double* F)
@@ -958,25 +1033,24 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_fp64(const double2* __restri
 // cycle idle.
 
 // Persistent force: a fixed grid walks the (i-tile, split) items of the
-// device-chosen shape.  SMALL: the variants of up to FORCE_NT i-particles per
-// CTA (4, 32, 128); otherwise the two-per-thread variant (256).  The kernel
-// not matching the chosen variant returns at once.
-template <int ORDER, int RW, bool PAIR, bool SMALL>
-__global__ void __launch_bounds__(FORCE_NT, SMALL ? 5 : 4) k_force_mixed_dyn(const float4* __restrict__ js,
-                                                              const int32_t* __restrict__ idx, int n, int ntiles,
-                                                              float eps2u, float eps2max, double* __restrict__ partial,
-                                                              DevScalars* sc, double* F)
+// device-chosen shape, in the chosen variant (4, 32, FORCE_NT or 2 FORCE_NT
+// i-particles per CTA); the dynamic shared memory fits the largest.
+template <int ORDER, int RW, bool PAIR>
+__global__ void __launch_bounds__(FORCE_NT, 4) k_force_mixed_dyn(const float4* __restrict__ js,
+                                                                 const int32_t* __restrict__ idx, int n, int ntiles,
+                                                                 float eps2u, float eps2max,
+                                                                 double* __restrict__ partial, DevScalars* sc,
+                                                                 double* F)
 {
     if (sc->idle) return;
     const int ni = sc->ni;
-    if (SMALL != (ni <= FORCE_NT)) return;
     const int n_act = (int)sc->n_act, it = sc->itiles, jsplit = sc->jsplit;
     for (int w = blockIdx.x; w < it * jsplit; w += gridDim.x) {
         const int itile = w % it, split = w / it;
         const int t0 = (int)((long long)split * ntiles / jsplit);
         const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
         const TileSum tsum{F, jsplit};
-        if (!SMALL)
+        if (ni == 2 * FORCE_NT)
             force_block_mixed_xs<ORDER, RW, PAIR, 1>(js, idx, itile * ni, n_act, n, t0, t1 - t0, split, n_act,
                                                      eps2u, eps2max, partial, sc, tsum);
         else if (ni == FORCE_NT)

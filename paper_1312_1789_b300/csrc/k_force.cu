@@ -207,38 +207,6 @@ cudaError_t launch_force_reduce(nb_ctx* c, int order, const int32_t* idx, int64_
 }
 
 // ------------------------------------------------------- device-driven cycle
-// One thread: close the cycle when the next block lies past t_end, otherwise
-// pick the force launch shape exactly as the host rule does for a block of
-// that size (the autotuned table if any, else the same variant rule, slot
-// counts and makespan split; a forced split).  slots = SMs x occupancy of the per-launch kernels with 4,
-// 32, 128 and 256 i-particles per CTA.
-__global__ void k_cycle_gate(DevScalars* sc, long long n, int ntiles, int4 slots, long long cap, int nc, int mixed,
-                             int js_force, const TuneEntry* tab, int ntab)
-{
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const long long na = sc->n_act;
-    if (!(sc->t_blk <= sc->t_end) || na <= 0) {
-        sc->idle = 1;
-        return;
-    }
-    sc->idle = 0;
-    const long long cap_splits = cap / ((long long)nc * na);
-    int ni, it, js;
-    if (js_force > 0 || !tuned_shape(tab, ntab, na, &ni, &it, &js)) {
-        ni = mixed ? mixed_ni(na) : fp64_ni(na);
-        const int sl = ni == 4 ? slots.x : ni == 32 ? slots.y : ni == FORCE_NT ? slots.z : slots.w;
-        it = (int)((na + ni - 1) / ni);
-        js = js_force > 0 ? js_force : makespan_split(it, ntiles, sl, cap_splits);
-    }
-    sc->ni = ni;
-    sc->itiles = it;
-    if (js > ntiles) js = ntiles;
-    if (js > cap_splits) js = (int)cap_splits;
-    sc->jsplit = js < 1 ? 1 : js;
-    sc->blocks += 1;
-    sc->inter += na * n;
-}
-
 template <typename K>
 static int dyn_slots(nb_ctx* c, K kern, size_t smem)
 {
@@ -246,61 +214,44 @@ static int dyn_slots(nb_ctx* c, K kern, size_t smem)
     return c->sm_count * occupancy_of(kern, smem);
 }
 
-// Launch (or, query_only, size) the persistent force kernels of the context's
-// order: on the mixed path one for the variants of up to FORCE_NT i-particles
-// per CTA and one for two per thread.
+// Launch (or, query_only, size) the persistent force kernel of the context's
+// order and precision.
 template <int O>
-static cudaError_t force_dyn_o(nb_ctx* c, int* g_small, int* g_big, bool query_only)
+static cudaError_t force_dyn_o(nb_ctx* c, int* grid, bool query_only)
 {
     const bool pair = c->pair_eps || !(c->eps > 0.0);
     const int ntiles = (int)(c->np / JT);
     if (c->prec == NB_MIXED) {
         constexpr int RW = mixed_rw(O);
-        const size_t smem = (size_t)NSTAGE * JT * RW * 16, smem_big = xs_smem(O, RW, 1);
-        auto k1 = pair ? k_force_mixed_dyn<O, RW, true, true> : k_force_mixed_dyn<O, RW, false, true>;
-        auto k2 = pair ? k_force_mixed_dyn<O, RW, true, false> : k_force_mixed_dyn<O, RW, false, false>;
+        const size_t smem = xs_smem(O, RW, 1);
+        auto k = pair ? k_force_mixed_dyn<O, RW, true> : k_force_mixed_dyn<O, RW, false>;
         if (query_only) {
-            *g_small = dyn_slots(c, k1, smem);
-            *g_big = dyn_slots(c, k2, smem_big);
+            *grid = dyn_slots(c, k, smem);
             return cudaSuccess;
         }
         const float e2 = (float)(c->eps * c->eps), e2max = (float)c->eps2_max;
-        k1<<<*g_small, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), c->act_idx,
-                                                    (int)c->n, ntiles, e2, e2max, c->partial, c->sc, c->F);
-        k2<<<*g_big, FORCE_NT, smem_big, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), c->act_idx,
-                                                      (int)c->n, ntiles, e2, e2max, c->partial, c->sc, c->F);
+        k<<<*grid, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), c->act_idx, (int)c->n,
+                                                ntiles, e2, e2max, c->partial, c->sc, c->F);
     } else {
         constexpr int RW = fp64_rw(O);
         const size_t smem = (size_t)NSTAGE * JT * RW * 16;
-        auto k1 = pair ? k_force_fp64_dyn<O, RW, true> : k_force_fp64_dyn<O, RW, false>;
+        auto k = pair ? k_force_fp64_dyn<O, RW, true> : k_force_fp64_dyn<O, RW, false>;
         if (query_only) {
-            *g_small = *g_big = dyn_slots(c, k1, smem);
+            *grid = dyn_slots(c, k, smem);
             return cudaSuccess;
         }
-        k1<<<*g_small, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const double2*>(c->jstore), c->act_idx,
-                                                    (int)c->n, ntiles, c->eps * c->eps, c->partial, c->sc,
-                                                    c->F);
+        k<<<*grid, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const double2*>(c->jstore), c->act_idx, (int)c->n,
+                                                ntiles, c->eps * c->eps, c->partial, c->sc, c->F);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_force_dyn(nb_ctx* c, int* g_small, int* g_big, bool query_only)
+cudaError_t launch_force_dyn(nb_ctx* c, int* grid, bool query_only)
 {
-    if (c->order == 4) return force_dyn_o<4>(c, g_small, g_big, query_only);
-    if (c->order == 6) return force_dyn_o<6>(c, g_small, g_big, query_only);
-    return force_dyn_o<8>(c, g_small, g_big, query_only);
+    if (c->order == 4) return force_dyn_o<4>(c, grid, query_only);
+    if (c->order == 6) return force_dyn_o<6>(c, grid, query_only);
+    return force_dyn_o<8>(c, grid, query_only);
 }
-
-cudaError_t launch_cycle_gate(nb_ctx* c, const int* shape_slots)
-{
-    const int4 sl = make_int4(shape_slots[0], shape_slots[1], shape_slots[2], shape_slots[3]);
-    const int pi = c->prec == NB_MIXED ? 1 : 0;
-    k_cycle_gate<<<1, 32, 0, c->stream>>>(c->sc, c->n, (int)(c->np / JT), sl, (long long)c->partial_cap,
-                                          ncomp(c->order), c->prec == NB_MIXED, c->jsplit_force,
-                                          c->d_tune + pi * TUNE_MAX, c->tune_n[pi]);
-    return cudaGetLastError();
-}
-
 
 cudaError_t launch_force_reduce_dyn(nb_ctx* c)
 {

@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(SCHED_NT) k_sched_chunk(const double* __restri
 __device__ __forceinline__ double sched_compact_body(const double* __restrict__ t, const double* __restrict__ dt,
                                                      int64_t n, int per, const double* __restrict__ cmin,
                                                      const int32_t* __restrict__ ccnt, int nch,
-                                                     int32_t* __restrict__ idx, DevScalars* sc)
+                                                     int32_t* __restrict__ idx, DevScalars* sc,
+                                                     const GateArgs* gate = nullptr)
 {
     __shared__ double wd[SCHED_NT / 32];
     __shared__ int wi[SCHED_NT / 32];
@@ -120,6 +121,7 @@ __device__ __forceinline__ double sched_compact_body(const double* __restrict__ 
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         sc->t_blk = tb;
         sc->n_act = total;
+        if (gate) cycle_gate_apply(sc, tb, total, *gate);
     }
     if (cmin[blockIdx.x] != tb) return tb;  // CTA-uniform: no match in this chunk
     const int64_t i0 = ((int64_t)blockIdx.x * SCHED_NT + threadIdx.x) * per;
@@ -369,15 +371,16 @@ __global__ void __launch_bounds__(256) k_predict(const double* __restrict__ m, c
 // Second pass fused with the predictor: once a CTA knows t_blk it predicts
 // its own chunk of particles to it (the last CTA also the padding records up
 // to np).  use_t_end: a device-driven cycle, which predicts nothing past
-// sc->t_end.
+// sc->t_end and whose force launch shape CTA 0 sets with the gate.
 template <int ORDER, bool MIXED>
 __global__ void __launch_bounds__(SCHED_NT) k_sched_compact_predict(
     const double* __restrict__ t, const double* __restrict__ dt, int64_t n, int per, const double* __restrict__ cmin,
     const int32_t* __restrict__ ccnt, int nch, int32_t* __restrict__ idx, DevScalars* sc, int use_t_end,
     const double* __restrict__ m, const double* __restrict__ eps2, const double* __restrict__ x,
-    const double* __restrict__ v, const double* __restrict__ d, int64_t np, void* __restrict__ jstore)
+    const double* __restrict__ v, const double* __restrict__ d, int64_t np, void* __restrict__ jstore,
+    GateArgs gate)
 {
-    const double tb = sched_compact_body(t, dt, n, per, cmin, ccnt, nch, idx, sc);
+    const double tb = sched_compact_body(t, dt, n, per, cmin, ccnt, nch, idx, sc, use_t_end ? &gate : nullptr);
     if (use_t_end && !(tb <= sc->t_end)) return;
     const int64_t c0 = (int64_t)blockIdx.x * SCHED_NT * per;
     const int64_t c1 = blockIdx.x == nch - 1 ? np : min(c0 + (int64_t)SCHED_NT * per, np);
@@ -385,17 +388,31 @@ __global__ void __launch_bounds__(SCHED_NT) k_sched_compact_predict(
         predict_one<ORDER, MIXED>(i, tb, m, eps2, x, v, d, t, n, np, jstore, nullptr, nullptr);
 }
 
-cudaError_t launch_sched_predict(nb_ctx* c, bool use_t_end)
+cudaError_t launch_sched_predict(nb_ctx* c, bool use_t_end, const int* shape_slots)
 {
     int per, nch;
     sched_layout(c->n, c->sm_count, &per, &nch);
+    GateArgs g{};
+    if (use_t_end) {
+        const int pi = c->prec == NB_MIXED ? 1 : 0;
+        g.n = c->n;
+        g.cap = (long long)c->partial_cap;
+        g.ntiles = (int)(c->np / JT);
+        g.nc = ncomp(c->order);
+        g.mixed = c->prec == NB_MIXED;
+        g.js_force = c->jsplit_force;
+        g.slots = shape_slots ? make_int4(shape_slots[0], shape_slots[1], shape_slots[2], shape_slots[3])
+                              : make_int4(1, 1, 1, 1);
+        g.tab = c->d_tune + pi * TUNE_MAX;
+        g.ntab = c->tune_n[pi];
+    }
     k_sched_chunk<<<nch, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, per, c->chunk_min, c->chunk_cnt, c->sc);
     const bool mixed = c->prec == NB_MIXED;
 #define NB_SP(O, MX)                                                                                              \
     k_sched_compact_predict<O, MX><<<nch, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, per, c->chunk_min,        \
                                                                     c->chunk_cnt, nch, c->act_idx, c->sc,        \
                                                                     use_t_end ? 1 : 0, c->m, c->eps2, c->x, c->v, \
-                                                                    c->d, c->np, c->jstore)
+                                                                    c->d, c->np, c->jstore, g)
     if (c->order == 4) {
         if (mixed) NB_SP(4, true); else NB_SP(4, false);
     } else if (c->order == 6) {
@@ -539,52 +556,18 @@ __device__ void noise_floor(const double* nL, const double* nR, double h, double
     }
 }
 
-// Corrector, interpolation and new step for the particles of the last force.
-// L = acc derivatives at t0 (held), R = new ones at t1 = tf (force); the
-// Hermite interpolant through L[0..mm-1], R[0..mm-1] (mm = p/2) gives the
-// higher derivatives at t1 in closed form (derived symbolically).
+// FP64 corrector of one particle: the Hermite interpolant through
+// L[0..mm-1] (acc derivatives at t0, held) and H[0..mm-1] (new ones at t1)
+// gives H[mm..2mm-1] in closed form (derived symbolically); then the
+// corrected x1, v1 and the step limit lim (criterion, capped at 2h).
+// Returns false if a value is not finite.
 template <int ORDER>
-__global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fidx, int fn, double tf,
-                                                 const double* __restrict__ F, int64_t n, int64_t np,
-                                                 double* __restrict__ x, double* __restrict__ v,
-                                                 double* __restrict__ d, double* __restrict__ t,
-                                                 double* __restrict__ dtv, double* __restrict__ pot, double eta,
-                                                 double dt_max, double dt_min, NoiseEps ne, DevScalars* sc,
-                                                 const double* __restrict__ tfc, const int32_t* __restrict__ cid,
-                                                 const DevScalars* dyn)
+__device__ __forceinline__ bool correct_fp64(const double (&L)[4][3], double (&H)[8][3], const double h,
+                                             const double ih, const double (&x0)[3], const double (&v0)[3],
+                                             const double bacc, const double eta, const NoiseEps& ne,
+                                             double (&x1)[3], double (&v1)[3], double& lim)
 {
     constexpr int MM = ORDER / 2;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (dyn) {  // device-driven cycle: the block of the scheduler, unless idle
-        if (dyn->idle) return;
-        fn = (int)dyn->n_act;
-        tf = dyn->t_blk;
-    }
-    if (p >= fn) return;
-    const int i = fidx[p];
-    if ((unsigned)i >= (unsigned)n) {
-        raise_status(sc, NB_ERR_ARG);
-        return;
-    }
-    if (tfc) tf = tfc[cid[i]];  // ensemble: the particle's cluster block time
-    const double h = tf - t[i];
-    if (!(h > 0.0)) {
-        raise_status(sc, NB_ERR_ARG);
-        return;
-    }
-    double L[4][3], H[8][3];
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) L[k][c] = d[(k * 3 + c) * np + i];
-#pragma unroll
-    for (int k = 0; k < MM; ++k)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) H[k][c] = F[(size_t)(3 * k + c) * fn + p];
-    const double potn = F[(size_t)(3 * MM) * fn + p];
-    const double bacc = F[(size_t)(3 * MM + 1) * fn + p];  // sum_j m_j / R_ij^2
-
-    const double ih = recip(h);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const double L0 = L[0][c], L1 = L[1][c], L2 = L[2][c], L3 = L[3][c];
@@ -618,25 +601,25 @@ __global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fid
     bool finite_state = true;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const double v0 = v[c * np + i], x0 = x[c * np + i];
-        double v1, x1;
+        const double vi = v0[c], xi = x0[c];
+        double vn, xn;
         if (ORDER == 4) {
-            v1 = v0 + h * 0.5 * (L[0][c] + H[0][c]) - h * h * (1.0 / 12) * (H[1][c] - L[1][c]);
-            x1 = x0 + h * 0.5 * (v0 + v1) - h * h * (1.0 / 12) * (H[0][c] - L[0][c]);
+            vn = vi + h * 0.5 * (L[0][c] + H[0][c]) - h * h * (1.0 / 12) * (H[1][c] - L[1][c]);
+            xn = xi + h * 0.5 * (vi + vn) - h * h * (1.0 / 12) * (H[0][c] - L[0][c]);
         } else if (ORDER == 6) {
-            v1 = v0 + h * 0.5 * (L[0][c] + H[0][c]) - h * h * 0.1 * (H[1][c] - L[1][c]) +
+            vn = vi + h * 0.5 * (L[0][c] + H[0][c]) - h * h * 0.1 * (H[1][c] - L[1][c]) +
                  h * h * h * (1.0 / 120) * (L[2][c] + H[2][c]);
-            x1 = x0 + h * 0.5 * (v0 + v1) - h * h * 0.1 * (H[0][c] - L[0][c]) +
+            xn = xi + h * 0.5 * (vi + vn) - h * h * 0.1 * (H[0][c] - L[0][c]) +
                  h * h * h * (1.0 / 120) * (L[1][c] + H[1][c]);
         } else {
-            v1 = v0 + h * 0.5 * (L[0][c] + H[0][c]) - h * h * (3.0 / 28) * (H[1][c] - L[1][c]) +
+            vn = vi + h * 0.5 * (L[0][c] + H[0][c]) - h * h * (3.0 / 28) * (H[1][c] - L[1][c]) +
                  h * h * h * (1.0 / 84) * (L[2][c] + H[2][c]) - h * h * h * h * (1.0 / 1680) * (H[3][c] - L[3][c]);
-            x1 = x0 + h * 0.5 * (v0 + v1) - h * h * (3.0 / 28) * (H[0][c] - L[0][c]) +
+            xn = xi + h * 0.5 * (vi + vn) - h * h * (3.0 / 28) * (H[0][c] - L[0][c]) +
                  h * h * h * (1.0 / 84) * (L[1][c] + H[1][c]) - h * h * h * h * (1.0 / 1680) * (H[2][c] - L[2][c]);
         }
-        v[c * np + i] = v1;
-        x[c * np + i] = x1;
-        finite_state = finite_state && fabs(v1) < INFINITY && fabs(x1) < INFINITY;
+        v1[c] = vn;
+        x1[c] = xn;
+        finite_state = finite_state && fabs(vn) < INFINITY && fabs(xn) < INFINITY;
     }
 
     // derivative norms at t1, the interpolated ones net of their noise floor
@@ -646,8 +629,6 @@ __global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fid
         nrm[k] = norm3(H[k]);
         finite_state = finite_state && nrm[k] < INFINITY;  // false for inf and NaN
     }
-    // the floored criterion below would read a non-finite derivative as zero
-    if (!finite_state) raise_status(sc, NB_ERR_NAN);
     // all-zero channel precisions (the FP64 default): the floor is zero and
     // the plain criterion applies -- skip its norms and polynomials
     if (ne.e[0] != 0.0 || ne.e[1] != 0.0 || ne.e[2] != 0.0 || ne.e[3] != 0.0) {
@@ -663,10 +644,246 @@ __global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fid
 #pragma unroll
         for (int k = MM; k < 2 * MM; ++k) nrm[k] = fmax(nrm[k] - N[k], 0.0);
     }
-    double lim = dt_criterion<ORDER>(eta, nrm);
+    lim = dt_criterion<ORDER>(eta, nrm);
     if (2.0 * h < lim) lim = 2.0 * h;
+    return finite_state;
+}
+
+// |(x, y, z)| in FP32; a sum of squares outside the normal float range is
+// redone on the vector scaled by a power of two.
+__device__ __forceinline__ float norm3f(const float (&p)[3])
+{
+    const float s = fmaf(p[0], p[0], fmaf(p[1], p[1], p[2] * p[2]));
+    if (s < 0x1p126f && (s > 0x1p-126f || s == 0.0f)) return sqrtf(s);
+    const float m = fmaxf(fabsf(p[0]), fmaxf(fabsf(p[1]), fabsf(p[2])));
+    if (!(m < INFINITY) || m == 0.0f) return m;  // inf / NaN propagate, 0 stays 0
+    // 2^-e with 2^e <= m < 2^(e+1), e within the normal range
+    const int e = (int)((__float_as_uint(m) >> 23) & 0xFF) - 127;
+    const float sc = __uint_as_float((unsigned)(127 - max(-126, min(e, 126))) << 23);
+    const float a = p[0] * sc, b = p[1] * sc, c = p[2] * sc;
+    return sqrtf(fmaf(a, a, fmaf(b, b, c * c))) / sc;
+}
+
+// Mixed-precision corrector (the mixed path, whose forces carry FP32-level
+// rounding): x1 and v1 keep their leading terms x0 + h/2 (v0 + v1) and
+// v0 + h/2 (a0 + a1) in FP64 and take the higher-order terms in FP32; the
+// interpolated derivatives, their noise floor and the step criterion run in
+// FP32 on h-scaled quantities a^(k) h^k (all of the size of the acceleration,
+// so that neither 1/h^k nor a high derivative's own range leaves the float
+// range) -- the same closed forms as correct_fp64 with h^k moved across, and
+// the criterion's ratio, which is h^(p-3) times the ratio of scaled norms.
+// The FP64 pipe (1/64 of the FP32 rate here) then does ~45 operations per
+// particle instead of ~500.  Returns false, with nothing usable written, if a
+// float value is not finite (a derivative beyond the float range); the
+// caller then takes correct_fp64.
+template <int ORDER>
+__device__ __forceinline__ bool correct_mixed(const double (&L)[4][3], double (&H)[8][3], const double h,
+                                              const double ih, const double (&x0)[3], const double (&v0)[3],
+                                              const double bacc, const double eta, const NoiseEps& ne,
+                                              double (&x1)[3], double (&v1)[3], double& lim)
+{
+    constexpr int MM = ORDER / 2;
+    const float u = f64_to_f32_rz(h);
+    if (!(u > 0.0f)) return false;  // h below the float range
+    // scaled inputs: ls[k] = L[k] h^k, rs[k] = H[k] h^k (k < MM), d0 = a1 - a0
+    float ls[4][3], rs[4][3], d0[3];
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        d0[c] = f64_to_f32_rz(H[0][c] - L[0][c]);
+        float uk = 1.0f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            ls[k][c] = f64_to_f32_rz(L[k][c]) * uk;
+            rs[k][c] = k < MM ? f64_to_f32_rz(H[k][c]) * uk : 0.0f;
+            ok = ok && isfinite(ls[k][c]) && isfinite(rs[k][c]);
+            uk *= u;
+        }
+        ok = ok && isfinite(d0[c]);
+    }
+    if (!ok) return false;
+    // T[k] = a^(k)(t1) h^k for k = MM .. 2MM-1 (closed forms as in correct_fp64)
+    float T[8][3], tv[3], tx[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float D = d0[c];
+        const float l1 = ls[1][c], r1 = rs[1][c], l2 = ls[2][c], r2 = rs[2][c], l3 = ls[3][c], r3 = rs[3][c];
+        if (ORDER == 4) {
+            T[2][c] = 2.0f * (-3.0f * D + (l1 + 2.0f * r1));
+            T[3][c] = 6.0f * (-2.0f * D + (l1 + r1));
+            tv[c] = -(1.0f / 12) * (r1 - l1);             // x h
+            tx[c] = -(1.0f / 12) * D;                     // x h^2
+        } else if (ORDER == 6) {
+            T[3][c] = 3.0f * (20.0f * D + (3.0f * r2 - l2) - 4.0f * (2.0f * l1 + 3.0f * r1));
+            T[4][c] = 12.0f * (30.0f * D + (3.0f * r2 - 2.0f * l2) - 2.0f * (7.0f * l1 + 8.0f * r1));
+            T[5][c] = 60.0f * (12.0f * D + (r2 - l2) - 6.0f * (l1 + r1));
+            tv[c] = -0.1f * (r1 - l1) + (1.0f / 120) * (l2 + r2);
+            tx[c] = -0.1f * D + (1.0f / 120) * (l1 + r1);
+        } else {
+            T[4][c] = 4.0f * (-210.0f * D + (l3 + 4.0f * r3) + 15.0f * (l2 - 2.0f * r2) + 30.0f * (3.0f * l1 + 4.0f * r1));
+            T[5][c] = 60.0f * (-168.0f * D + (l3 + 2.0f * r3) + 2.0f * (7.0f * l2 - 10.0f * r2) +
+                               6.0f * (13.0f * l1 + 15.0f * r1));
+            T[6][c] = 120.0f * (-420.0f * D + (3.0f * l3 + 4.0f * r3) + 3.0f * (13.0f * l2 - 15.0f * r2) +
+                                12.0f * (17.0f * l1 + 18.0f * r1));
+            T[7][c] = 840.0f * (-120.0f * D + (l3 + r3) + 12.0f * (l2 - r2) + 60.0f * (l1 + r1));
+            tv[c] = -(3.0f / 28) * (r1 - l1) + (1.0f / 84) * (l2 + r2) - (1.0f / 1680) * (r3 - l3);
+            tx[c] = -(3.0f / 28) * D + (1.0f / 84) * (l1 + r1) - (1.0f / 1680) * (r2 - l2);
+        }
+        tv[c] *= u;
+        tx[c] *= u * u;
+        ok = ok && isfinite(tv[c]) && isfinite(tx[c]);
+#pragma unroll
+        for (int k = MM; k < 2 * MM; ++k) ok = ok && isfinite(T[k][c]);
+    }
+    if (!ok) return false;
+    // scaled norms at t1: S[k] = |a^(k)| h^k, the interpolated ones net of
+    // their (scaled) noise floor
+    float S[8];
+#pragma unroll
+    for (int k = 0; k < 2 * MM; ++k) {
+        float q[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) q[c] = k < MM ? rs[k][c] : T[k][c];
+        S[k] = norm3f(q);
+    }
+    if (ne.e[0] != 0.0 || ne.e[1] != 0.0 || ne.e[2] != 0.0 || ne.e[3] != 0.0) {
+        float nl[4], nr[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            nl[k] = norm3f(ls[k]);
+            nr[k] = k < MM ? S[k] : 0.0f;
+        }
+        const float kappa = nr[0] > 0.0f ? fmaxf(1.0f, f64_to_f32_rz(bacc) / nr[0]) : 1.0f;
+        float e[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) e[k] = f64_to_f32_rz(ne.e[k]) * kappa;
+        const float A = e[0] * (nl[0] + nr[0]);
+        float N[8];
+        if (ORDER == 4) {
+            N[2] = 2.0f * (3.0f * A + e[1] * (nl[1] + 2.0f * nr[1]));
+            N[3] = 6.0f * (2.0f * A + e[1] * (nl[1] + nr[1]));
+        } else if (ORDER == 6) {
+            N[3] = 3.0f * (20.0f * A + e[2] * (nl[2] + 3.0f * nr[2]) + 4.0f * e[1] * (2.0f * nl[1] + 3.0f * nr[1]));
+            N[4] = 12.0f * (30.0f * A + e[2] * (2.0f * nl[2] + 3.0f * nr[2]) + 2.0f * e[1] * (7.0f * nl[1] + 8.0f * nr[1]));
+            N[5] = 60.0f * (12.0f * A + e[2] * (nl[2] + nr[2]) + 6.0f * e[1] * (nl[1] + nr[1]));
+        } else {
+            N[4] = 4.0f * (210.0f * A + e[3] * (nl[3] + 4.0f * nr[3]) + 15.0f * e[2] * (nl[2] + 2.0f * nr[2]) +
+                           30.0f * e[1] * (3.0f * nl[1] + 4.0f * nr[1]));
+            N[5] = 60.0f * (168.0f * A + e[3] * (nl[3] + 2.0f * nr[3]) + 2.0f * e[2] * (7.0f * nl[2] + 10.0f * nr[2]) +
+                            6.0f * e[1] * (13.0f * nl[1] + 15.0f * nr[1]));
+            N[6] = 120.0f * (420.0f * A + e[3] * (3.0f * nl[3] + 4.0f * nr[3]) + 3.0f * e[2] * (13.0f * nl[2] + 15.0f * nr[2]) +
+                             12.0f * e[1] * (17.0f * nl[1] + 18.0f * nr[1]));
+            N[7] = 840.0f * (120.0f * A + e[3] * (nl[3] + nr[3]) + 12.0f * e[2] * (nl[2] + nr[2]) +
+                             60.0f * e[1] * (nl[1] + nr[1]));
+        }
+#pragma unroll
+        for (int k = MM; k < 2 * MM; ++k) S[k] = fmaxf(S[k] - N[k], 0.0f);
+    }
+    // the criterion as a multiple f of h, capped at 2 (the step may at most double)
+    float f;
+    {
+        const float etaf = f64_to_f32_rz(eta);
+        if (ORDER == 4) {
+            const float num = S[0] * S[2] + S[1] * S[1], den = S[1] * S[3] + S[2] * S[2];
+            f = den > 0.0f ? sqrtf(etaf * (num / den)) : INFINITY;
+        } else {
+            const float num = sqrtf(S[0]) * sqrtf(S[2]) + S[1];
+            const float den = sqrtf(S[ORDER - 3]) * sqrtf(S[ORDER - 1]) + S[ORDER - 2];
+            const float r = num / den;
+            f = den > 0.0f ? etaf * (ORDER == 6 ? cbrtf(r) : exp2f(0.2f * log2f(r))) : INFINITY;
+        }
+        if (!(f <= 2.0f)) f = f == f ? 2.0f : f;  // inf -> 2; NaN stays
+    }
+    if (!(f == f)) return false;
+    lim = h * f32_to_f64(f);
+    // H[k] = T[k] / h^k, and the corrected state
+    double ihk = 1.0;
+#pragma unroll
+    for (int k = 1; k < 2 * MM; ++k) {
+        ihk *= ih;
+        if (k >= MM)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) H[k][c] = f32_to_f64(T[k][c]) * ihk;
+    }
+    const double hh = 0.5 * h;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        v1[c] = fma(hh, L[0][c] + H[0][c], v0[c]) + f32_to_f64(tv[c]);
+        x1[c] = fma(hh, v0[c] + v1[c], x0[c]) + f32_to_f64(tx[c]);
+    }
+    return true;
+}
+
+// Corrector, interpolation and new step for the particles of the last force
+// (MIXED: the mixed-precision form, FP64 for the particles it cannot take).
+template <int ORDER, bool MIXED>
+__global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fidx, int fn, double tf,
+                                                 const double* __restrict__ F, int64_t n, int64_t np,
+                                                 double* __restrict__ x, double* __restrict__ v,
+                                                 double* __restrict__ d, double* __restrict__ t,
+                                                 double* __restrict__ dtv, double* __restrict__ pot, double eta,
+                                                 double dt_max, double dt_min, NoiseEps ne, DevScalars* sc,
+                                                 const double* __restrict__ tfc, const int32_t* __restrict__ cid,
+                                                 const DevScalars* dyn)
+{
+    constexpr int MM = ORDER / 2;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (dyn) {  // device-driven cycle: the block of the scheduler, unless idle
+        if (dyn->idle) return;
+        fn = (int)dyn->n_act;
+        tf = dyn->t_blk;
+    }
+    if (p >= fn) return;
+    const int i = fidx[p];
+    if ((unsigned)i >= (unsigned)n) {
+        raise_status(sc, NB_ERR_ARG);
+        return;
+    }
+    if (tfc) tf = tfc[cid[i]];  // ensemble: the particle's cluster block time
+    const double h = tf - t[i];
+    if (!(h > 0.0)) {
+        raise_status(sc, NB_ERR_ARG);
+        return;
+    }
+    double L[4][3], H[8][3], x0[3], v0[3];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) L[k][c] = d[(k * 3 + c) * np + i];
+#pragma unroll
+    for (int k = 0; k < MM; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) H[k][c] = F[(size_t)(3 * k + c) * fn + p];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        x0[c] = x[c * np + i];
+        v0[c] = v[c * np + i];
+    }
+    const double potn = F[(size_t)(3 * MM) * fn + p];
+    const double bacc = F[(size_t)(3 * MM + 1) * fn + p];  // sum_j m_j / R_ij^2
+
+    const double ih = recip(h);
+    double x1[3], v1[3], lim;
+    bool finite_state;
+    if (MIXED && correct_mixed<ORDER>(L, H, h, ih, x0, v0, bacc, eta, ne, x1, v1, lim)) {
+        finite_state = true;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {  // exponent field not all ones
+            finite_state = finite_state && (~__double_as_longlong(x1[c]) & 0x7FF0000000000000LL) != 0 &&
+                           (~__double_as_longlong(v1[c]) & 0x7FF0000000000000LL) != 0;
+        }
+    } else {
+        finite_state = correct_fp64<ORDER>(L, H, h, ih, x0, v0, bacc, eta, ne, x1, v1, lim);
+    }
+    // the floored criterion would read a non-finite derivative as zero
+    if (!finite_state) raise_status(sc, NB_ERR_NAN);
     const double dtn = quantise_dt(lim, tf, dt_max, dt_min, sc);
 
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        v[c * np + i] = v1[c];
+        x[c * np + i] = x1[c];
+    }
 #pragma unroll
     for (int k = 0; k < 6; ++k)
 #pragma unroll
@@ -680,17 +897,17 @@ cudaError_t launch_correct(nb_ctx* c, const double* tfc, const int32_t* cid, con
 {
     const int nt = 128;
     const int nb = (int)(((dyn ? c->n : c->f_n) + nt - 1) / nt);
-#define NB_CORR(O)                                                                                          \
-    k_correct<O><<<nb, nt, 0, c->stream>>>(dyn ? c->act_idx : c->f_idx, (int)c->f_n, c->f_t, c->F, c->n, c->np, \
-                                           c->x, c->v,                                                      \
-                                           c->d, c->t, c->dt, c->pot, c->eta, c->dt_max, c->dt_min,        \
-                                           c->noise[c->pred_prec == NB_MIXED ? 1 : 0], c->sc, tfc, cid, dyn);
+    const bool mixed = c->pred_prec == NB_MIXED;
+#define NB_CORR(O, MX)                                                                                           \
+    k_correct<O, MX><<<nb, nt, 0, c->stream>>>(dyn ? c->act_idx : c->f_idx, (int)c->f_n, c->f_t, c->F, c->n,   \
+                                               c->np, c->x, c->v, c->d, c->t, c->dt, c->pot, c->eta, c->dt_max, \
+                                               c->dt_min, c->noise[mixed ? 1 : 0], c->sc, tfc, cid, dyn)
     if (c->order == 4) {
-        NB_CORR(4)
+        if (mixed) NB_CORR(4, true); else NB_CORR(4, false);
     } else if (c->order == 6) {
-        NB_CORR(6)
+        if (mixed) NB_CORR(6, true); else NB_CORR(6, false);
     } else {
-        NB_CORR(8)
+        if (mixed) NB_CORR(8, true); else NB_CORR(8, false);
     }
 #undef NB_CORR
     return cudaGetLastError();

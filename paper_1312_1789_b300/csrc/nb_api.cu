@@ -220,16 +220,17 @@ void destroy_graph(nb_ctx* c)
     }
 }
 
-// Capture graph_cycles device-driven block cycles (scheduler, shape gate,
-// predictor, persistent force, reduction, corrector) into one CUDA graph.
+// Capture graph_cycles device-driven block cycles (scheduler with the
+// predictor and the shape gate, persistent force, reduction, corrector) into
+// one CUDA graph.
 // Every kernel reads n_act / t_blk / the launch shape from the device
 // scalars, so the graph replays with no host round trip.
 int build_graph(nb_ctx* c)
 {
     destroy_graph(c);
-    int s1 = 0, s2 = 0;
+    int grid = 0;
     c->pred_prec = c->prec;
-    NB_CUDA(c, launch_force_dyn(c, &s1, &s2, true));
+    NB_CUDA(c, launch_force_dyn(c, &grid, true));
     // the split rule sees the per-launch kernels' slot counts, so a block
     // gets the same shape (and the same summation order) in both modes
     int shape_slots[4];
@@ -244,9 +245,8 @@ int build_graph(nb_ctx* c)
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(c->graph_stream, cudaStreamCaptureModeThreadLocal);
     for (int r = 0; e == cudaSuccess && r < c->graph_cycles; ++r) {
-        if ((e = launch_sched_predict(c, true)) != cudaSuccess) break;
-        if ((e = launch_cycle_gate(c, shape_slots)) != cudaSuccess) break;
-        if ((e = launch_force_dyn(c, &s1, &s2, false)) != cudaSuccess) break;
+        if ((e = launch_sched_predict(c, true, shape_slots)) != cudaSuccess) break;
+        if ((e = launch_force_dyn(c, &grid, false)) != cudaSuccess) break;
         if ((e = launch_force_reduce_dyn(c)) != cudaSuccess) break;
         if ((e = launch_correct(c, nullptr, nullptr, c->sc)) != cudaSuccess) break;
     }
@@ -274,9 +274,9 @@ int step_until_graph(nb_ctx* c, double t_end, int64_t* n_blocks, int64_t* n_inte
     h->blocks = 0;
     h->inter = 0;
     NB_CUDA(c, cudaMemcpy(c->sc, h, sizeof(DevScalars), cudaMemcpyHostToDevice));
-    // scheduler 2 (the second predicts), gate, force (two persistent kernels
-    // on the mixed path), reduction, corrector
-    const long long per_cycle = 2 + 1 + (c->prec == NB_MIXED ? 2 : 1) + 1 + 1;
+    // scheduler 2 (the second predicts and sets the launch shape), persistent
+    // force, reduction, corrector
+    const long long per_cycle = 2 + 1 + 1 + 1;
     for (;;) {
         NB_CUDA(c, cudaGraphLaunch(c->graph_exec, c->graph_stream));
         c->n_launch += per_cycle * c->graph_cycles;
@@ -654,16 +654,6 @@ static int upload_vec(nb_ctx* c, double* dst, const double* src)
     return NB_OK;
 }
 
-static int download_vec(nb_ctx* c, double* dst, const double* src)
-{
-    std::vector<double> tmp((size_t)3 * c->np);
-    NB_CUDA(c, cudaMemcpyAsync(tmp.data(), src, tmp.size() * 8, cudaMemcpyDeviceToHost, c->stream));
-    NB_CUDA(c, cudaStreamSynchronize(c->stream));
-    for (int64_t i = 0; i < c->n; ++i)
-        for (int k = 0; k < 3; ++k) dst[3 * i + k] = tmp[(size_t)k * c->np + i];
-    return NB_OK;
-}
-
 int nb_set_particles(nb_ctx* c, const double* m, const double* x, const double* v)
 {
     if (!c || !m || !x || !v) return c ? set_err(c, NB_ERR_ARG, "m, x and v are required") : NB_ERR_ARG;
@@ -801,8 +791,8 @@ static int next_block_predicted(nb_ctx* c, double* tb, int64_t* na)
 int nb_block_step(nb_ctx* c, double* t_blk, int64_t* n_act)
 {
     if (!c) return NB_ERR_ARG;
-    double tb;
-    int64_t na;
+    double tb = 0.0;
+    int64_t na = 0;
     NB_TRY(next_block_predicted(c, &tb, &na));
     NB_TRY(nb_force(c, nullptr, na));
     NB_TRY(nb_correct(c));
@@ -819,8 +809,8 @@ int nb_step_until(nb_ctx* c, double t_end, int64_t* n_blocks, int64_t* n_inter)
     if (c->graph_cycles > 0) return step_until_graph(c, t_end, n_blocks, n_inter);
     int64_t nb = 0, ni = 0;
     for (;;) {
-        double tb;
-        int64_t na;
+        double tb = 0.0;
+        int64_t na = 0;
         NB_TRY(next_block_predicted(c, &tb, &na));
         if (tb > t_end) break;
         NB_TRY(nb_force(c, nullptr, na));

@@ -33,7 +33,7 @@ struct BatchItem {
     int jt0;       // first j tile (global)
     int nt;        // j tiles
     int split;     // row of the partial sums
-    int ni;        // mixed launch variant: 4, 32 or FORCE_NT i-particles per CTA
+    int ni;        // launch variant: 4, 32, FORCE_NT or (mixed) 2 FORCE_NT i-particles per CTA
     int pad[2];
 };
 
@@ -202,17 +202,6 @@ __global__ void k_batch_scatter(const double* __restrict__ t, const double* __re
     }
 }
 
-// Segment of each cluster in the (cluster-major, ascending) active list.
-__global__ void k_batch_bounds(const int32_t* __restrict__ list, int n_act, const int32_t* __restrict__ cid,
-                               int32_t* __restrict__ kstart, int32_t* __restrict__ kcount)
-{
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n_act) return;
-    const int k = cid[list[p]];
-    if (p == 0 || cid[list[p - 1]] != k) kstart[k] = p;
-    if (p == n_act - 1 || cid[list[p + 1]] != k) kcount[k] = p + 1;  // end, turned into a count below
-}
-
 __global__ void k_batch_counts(int K, const int32_t* __restrict__ kstart, int32_t* __restrict__ kcount)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -220,18 +209,21 @@ __global__ void k_batch_counts(int K, const int32_t* __restrict__ kstart, int32_
 }
 
 // One item per CTA, in the item's launch variant (the cluster's active-set
-// size picks it with the rule of a single system, mixed_ni, capped at one
-// i-particle per thread).
+// size picks it with the rule of a single system, mixed_ni: two i-particles
+// per thread in packed FP32x2 lanes from 512 active on).
 template <int ORDER, int RW>
-__global__ void __launch_bounds__(FORCE_NT) k_batch_force_mixed(const float4* __restrict__ js,
-                                                                const int32_t* __restrict__ list,
-                                                                const BatchItem* __restrict__ items, int n_act, int n,
-                                                                float eps2max, double* __restrict__ partial,
-                                                                DevScalars* sc)
+__global__ void __launch_bounds__(FORCE_NT, 4) k_batch_force_mixed(const float4* __restrict__ js,
+                                                                   const int32_t* __restrict__ list,
+                                                                   const BatchItem* __restrict__ items, int n_act,
+                                                                   int n, float eps2max, double* __restrict__ partial,
+                                                                   DevScalars* sc)
 {
     const BatchItem it = items[blockIdx.x];
     const int lim = it.list_off + it.count;
-    if (it.ni == FORCE_NT)
+    if (it.ni == 2 * FORCE_NT)
+        force_block_mixed_xs<ORDER, RW, true, 1>(js, list, it.list_off, lim, n, it.jt0, it.nt, it.split, n_act, 0.0f,
+                                                 eps2max, partial, sc);
+    else if (it.ni == FORCE_NT)
         force_block_mixed<ORDER, RW, true, 1>(js, list, it.list_off, lim, n, it.jt0, it.nt, it.split, n_act, 0.0f,
                                               eps2max, partial, sc);
     else if (it.ni == FORCE_NT / 4)
@@ -243,7 +235,8 @@ __global__ void __launch_bounds__(FORCE_NT) k_batch_force_mixed(const float4* __
 }
 
 // ------------------------------------------------ device-driven cycle
-// The cycle's active-set size lives in sc->n_act; a fixed grid strides.
+// Segment of each cluster in the (cluster-major, ascending) active list; the
+// cycle's active-set size lives in sc->n_act, a fixed grid strides.
 __global__ void k_batch_bounds_dyn(const int32_t* __restrict__ list, const DevScalars* __restrict__ sc,
                                    const int32_t* __restrict__ cid, int32_t* __restrict__ kstart,
                                    int32_t* __restrict__ kcount)
@@ -257,13 +250,17 @@ __global__ void k_batch_bounds_dyn(const int32_t* __restrict__ list, const DevSc
 }
 
 // Plan of the cycle's force (one CTA): each cluster with cnt active takes the
-// launch variant ni = mixed_ni(cnt) (at most one i-particle per thread) and
+// launch variant ni = mixed_ni(cnt) (fp64_ni(cnt) in FP64) and
 // s j-splits, s = ceil(min(cnt, ni) * pk / target) in [1, pk / JT], with
 // target = max(work / (4 slots), FORCE_NT * JT) and work = sum cnt * pk: items
 // of about equal work, about four waves of them.  The largest split is then
-// capped by the partial-sum buffer.  Writes ksplit, kni, koff (exclusive
-// item offsets, cluster order), n_items, the clusters stepped and the
-// interactions of the cycle.
+// capped by the partial-sum buffer.  The force kernel hands items out in
+// table order, so the table lists the heavy items first: clusters whose item
+// work min(cnt, ni) pk / s is at least target / 2, then at least target / 8,
+// then the rest (cluster order within a class), and the short items fill the
+// gaps at the end.  Writes ksplit, kni, koff (first item of each cluster),
+// n_items, the item counter, the clusters stepped and the interactions of
+// the cycle.
 __global__ void __launch_bounds__(BNT) k_batch_plan(int K, const int32_t* __restrict__ kcount,
                                                     const int64_t* __restrict__ pk, const int64_t* __restrict__ nk,
                                                     int slots, long long cap, int nc, int mixed, int items_cap,
@@ -278,6 +275,7 @@ __global__ void __launch_bounds__(BNT) k_batch_plan(int K, const int32_t* __rest
     if (sc->idle) {
         if (tid == 0) {
             sc->n_items = 0;
+            sc->next_item = 0;
             sc->stepped = 0;
         }
         return;
@@ -309,7 +307,7 @@ __global__ void __launch_bounds__(BNT) k_batch_plan(int K, const int32_t* __rest
     int smax = 1;
     for (int k = tid; k < K; k += BNT) {
         const int cnt = kcount[k];
-        const int ni = mixed ? min(mixed_ni(cnt), FORCE_NT) : fp64_ni(cnt);
+        const int ni = mixed ? mixed_ni(cnt) : fp64_ni(cnt);
         const int jt = (int)(pk[k] / JT);
         int sk = 1;
         if (cnt > 0) {
@@ -333,42 +331,46 @@ __global__ void __launch_bounds__(BNT) k_batch_plan(int K, const int32_t* __rest
     }
     __syncthreads();
     const int scap = s_smax;
-    // items per cluster and their exclusive scan, BNT clusters at a time
+    for (int k = tid; k < K; k += BNT) ksplit[k] = min(ksplit[k], scap);
+    // items per cluster and their exclusive scan, one class after another,
+    // BNT clusters at a time (thread tid keeps clusters tid + BNT m)
+    auto item_class = [&](int k) {
+        const long long cnt = kcount[k];
+        const double w = (double)min(cnt, (long long)kni[k]) * (double)pk[k] / ksplit[k];
+        return w >= 0.5 * target ? 0 : w >= 0.125 * target ? 1 : 2;
+    };
     int running = 0;
-    for (int base = 0; base < K; base += BNT) {
-        const int k = base + tid;
-        int items = 0;
-        if (k < K) {
-            const int cnt = kcount[k];
-            int sk = ksplit[k];
-            if (sk > scap) {
-                sk = scap;
-                ksplit[k] = sk;
+    for (int cls = 0; cls < 3; ++cls)
+        for (int base = 0; base < K; base += BNT) {
+            const int k = base + tid;
+            int items = 0;
+            if (k < K) {
+                const int cnt = kcount[k];
+                if (cnt > 0 && item_class(k) == cls) items = (cnt + kni[k] - 1) / kni[k] * ksplit[k];
             }
-            if (cnt > 0) items = (cnt + kni[k] - 1) / kni[k] * sk;
+            int incl = items;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            __syncthreads();
+            if (lane == 31) s_i[warp] = incl;
+            __syncthreads();
+            int wbase = 0, tot = 0;
+            for (int w = 0; w < BNT / 32; ++w) {
+                if (w < warp) wbase += s_i[w];
+                tot += s_i[w];
+            }
+            if (items > 0) koff[k] = running + wbase + incl - items;
+            running += tot;
         }
-        int incl = items;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        __syncthreads();
-        if (lane == 31) s_i[warp] = incl;
-        __syncthreads();
-        int wbase = 0, tot = 0;
-        for (int w = 0; w < BNT / 32; ++w) {
-            if (w < warp) wbase += s_i[w];
-            tot += s_i[w];
-        }
-        if (k < K) koff[k] = running + wbase + incl - items;
-        running += tot;
-    }
     if (tid == 0) {
         if (running > items_cap) {
             raise_status(sc, NB_ERR_ARG);
             running = items_cap;
         }
         sc->n_items = running;
+        sc->next_item = 0;
         sc->stepped = (int)stepped;
         sc->blocks += stepped > 0 ? 1 : 0;
         sc->inter += inter;
@@ -403,20 +405,28 @@ __global__ void __launch_bounds__(BNT) k_batch_items(const int32_t* __restrict__
     }
 }
 
-// Persistent force over the cycle's items (count in sc->n_items).
+// Persistent force over the cycle's items (count in sc->n_items): each CTA
+// takes the next item from a counter, so that CTAs that drew short items take
+// more of them.
 template <int ORDER, int RW>
-__global__ void __launch_bounds__(FORCE_NT) k_batch_force_mixed_dyn(const float4* __restrict__ js,
-                                                                    const int32_t* __restrict__ list,
-                                                                    const BatchItem* __restrict__ items, int n,
-                                                                    float eps2max, double* __restrict__ partial,
-                                                                    DevScalars* sc)
+__global__ void __launch_bounds__(FORCE_NT, 4) k_batch_force_mixed_dyn(const float4* __restrict__ js,
+                                                                       const int32_t* __restrict__ list,
+                                                                       const BatchItem* __restrict__ items, int n,
+                                                                       float eps2max, double* __restrict__ partial,
+                                                                       DevScalars* sc)
 {
     if (sc->idle) return;
     const int n_items = sc->n_items, n_act = (int)sc->n_act;
-    for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+    __shared__ int s_w;
+    if (threadIdx.x == 0) s_w = atomicAdd(&sc->next_item, 1);
+    __syncthreads();
+    for (int w = s_w; w < n_items; w = s_w) {
         const BatchItem it = items[w];
         const int lim = it.list_off + it.count;
-        if (it.ni == FORCE_NT)
+        if (it.ni == 2 * FORCE_NT)
+            force_block_mixed_xs<ORDER, RW, true, 1>(js, list, it.list_off, lim, n, it.jt0, it.nt, it.split, n_act,
+                                                     0.0f, eps2max, partial, sc);
+        else if (it.ni == FORCE_NT)
             force_block_mixed<ORDER, RW, true, 1>(js, list, it.list_off, lim, n, it.jt0, it.nt, it.split, n_act, 0.0f,
                                                   eps2max, partial, sc);
         else if (it.ni == FORCE_NT / 4)
@@ -425,6 +435,9 @@ __global__ void __launch_bounds__(FORCE_NT) k_batch_force_mixed_dyn(const float4
         else
             force_block_mixed_jp<ORDER, RW, true, 32>(js, list, it.list_off, lim, n, it.jt0, it.nt, it.split, n_act,
                                                       0.0f, eps2max, partial, sc);
+        // the next item: taken after every thread has read w (the item's own
+        // barriers lie between), published by the barrier below
+        if (threadIdx.x == 0) s_w = atomicAdd(&sc->next_item, 1);
         if (__syncthreads_or(threadIdx.x == 0 && *(volatile int*)&sc->status != 0)) return;
     }
 }
@@ -437,7 +450,10 @@ __global__ void __launch_bounds__(FORCE_NT) k_batch_force_fp64_dyn(const double2
 {
     if (sc->idle) return;
     const int n_items = sc->n_items, n_act = (int)sc->n_act;
-    for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+    __shared__ int s_w;
+    if (threadIdx.x == 0) s_w = atomicAdd(&sc->next_item, 1);
+    __syncthreads();
+    for (int w = s_w; w < n_items; w = s_w) {
         const BatchItem it = items[w];
         const int lim = it.list_off + it.count;
         if (it.ni == FORCE_NT)
@@ -449,6 +465,9 @@ __global__ void __launch_bounds__(FORCE_NT) k_batch_force_fp64_dyn(const double2
         else
             force_block_fp64<ORDER, RW, true, 32>(js, list, it.list_off, lim, n, it.jt0, it.nt, it.split, n_act, 0.0,
                                                   partial, sc);
+        // the next item: taken after every thread has read w (the item's own
+        // barriers lie between), published by the barrier below
+        if (threadIdx.x == 0) s_w = atomicAdd(&sc->next_item, 1);
         if (__syncthreads_or(threadIdx.x == 0 && *(volatile int*)&sc->status != 0)) return;
     }
 }
@@ -658,7 +677,7 @@ int batch_force_dispatch(nb_batch* b, int order, const int32_t* list, int n_act,
     if (order == O) {                                                                                             \
         if (mixed) {                                                                                              \
             constexpr int RW = mixed_rw(SO);                                                                      \
-            const size_t smem = (size_t)NSTAGE * JT * RW * 16;                                                    \
+            const size_t smem = xs_smem(O, RW, 1);                                                                \
             auto kern = k_batch_force_mixed<O, RW>;                                                            \
             const int occ = occ_of(kern, smem);                                                                   \
             if (occ_only) return occ;                                                                             \
@@ -727,7 +746,7 @@ int batch_force(nb_batch* b, int order, const int32_t* list, int n_act, const in
     int smax = 1;
     size_t nitems = 0;
     const bool mixed = c->pred_prec == NB_MIXED;  // the kernel batch_force_call launches
-    auto variant = [&](int count) { return mixed ? std::min(mixed_ni(count), FORCE_NT) : FORCE_NT; };
+    auto variant = [&](int count) { return mixed ? mixed_ni(count) : FORCE_NT; };
     for (int k = 0; k < b->K; ++k) {
         b->h_ksplit[k] = 1;
         if (h_count[k] <= 0) continue;
@@ -802,7 +821,7 @@ int batch_force_dyn_o(nb_batch* b, bool occ_only)
     nb_ctx* c = b->c;
     if (c->prec == NB_MIXED) {
         constexpr int RW = mixed_rw(SO);
-        const size_t smem = (size_t)NSTAGE * JT * RW * 16;
+        const size_t smem = xs_smem(SO, RW, 1);
         auto kern = k_batch_force_mixed_dyn<SO, RW>;
         if (occ_only) return occ_of(kern, smem);
         kern<<<b->force_slots, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), c->act_idx,

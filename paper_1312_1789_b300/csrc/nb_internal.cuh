@@ -141,8 +141,52 @@ struct DevScalars {
     int itiles, jsplit, ni;        // device-driven cycle: force launch shape
     int n_items;                   // ensemble cycle: force work items
     long long blocks, inter;       // device-driven cycle: blocks (cycles) taken, interactions
-    int stepped, pad3;             // ensemble cycle: clusters stepped in the last cycle
+    int stepped;                   // ensemble cycle: clusters stepped in the last cycle
+    int next_item;                 // ensemble cycle: next force item to hand out
 };
+
+// Launch-shape gate of a device-driven cycle, applied by the thread that
+// publishes the cycle's t_blk and n_act: close the cycle when the block lies
+// past t_end, otherwise pick the force launch shape exactly as the host rule
+// does for a block of that size (the autotuned table if any, else the same
+// variant rule, slot counts and makespan split; a forced split).  slots = SMs
+// x occupancy of the per-launch kernels with 4, 32, FORCE_NT and 2 FORCE_NT
+// i-particles per CTA.
+struct GateArgs {
+    long long n;     // particles (interactions per active particle)
+    long long cap;   // partial-sum buffer, doubles
+    int ntiles;      // j tiles of the store
+    int nc;          // force components
+    int mixed;       // precision of the force
+    int js_force;    // forced split (0: none)
+    int4 slots;
+    const TuneEntry* tab;
+    int ntab;
+};
+
+__device__ __forceinline__ void cycle_gate_apply(DevScalars* sc, double tb, long long na, const GateArgs& g)
+{
+    if (!(tb <= sc->t_end) || na <= 0) {
+        sc->idle = 1;
+        return;
+    }
+    sc->idle = 0;
+    const long long cap_splits = g.cap / ((long long)g.nc * na);
+    int ni, it, js;
+    if (g.js_force > 0 || !tuned_shape(g.tab, g.ntab, na, &ni, &it, &js)) {
+        ni = g.mixed ? mixed_ni(na) : fp64_ni(na);
+        const int sl = ni == 4 ? g.slots.x : ni == 32 ? g.slots.y : ni == FORCE_NT ? g.slots.z : g.slots.w;
+        it = (int)((na + ni - 1) / ni);
+        js = g.js_force > 0 ? g.js_force : makespan_split(it, g.ntiles, sl, cap_splits);
+    }
+    sc->ni = ni;
+    sc->itiles = it;
+    if (js > g.ntiles) js = g.ntiles;
+    if (js > cap_splits) js = (int)cap_splits;
+    sc->jsplit = js < 1 ? 1 : js;
+    sc->blocks += 1;
+    sc->inter += na * g.n;
+}
 
 // Relative precision of the force components (acc, jerk, snap, crackle) that
 // sets the noise floor of interpolated derivatives in the time-step criterion.
@@ -327,7 +371,7 @@ namespace nb {
 cudaError_t launch_sched(nb_ctx* c);
 // Scheduler whose second pass also predicts every particle to the new block
 // time (use_t_end: not past sc->t_end).
-cudaError_t launch_sched_predict(nb_ctx* c, bool use_t_end);
+cudaError_t launch_sched_predict(nb_ctx* c, bool use_t_end, const int* shape_slots = nullptr);
 // tpc, cid (ensembles): per-cluster prediction time and cluster of each slot; NULL for one system.
 // dyn (device-driven cycle): take the time from dyn->t_blk and do nothing when dyn->idle.
 cudaError_t launch_predict(nb_ctx* c, double t, const double* tpc = nullptr, const int32_t* cid = nullptr,
@@ -343,8 +387,7 @@ cudaError_t launch_correct(nb_ctx* c, const double* tfc = nullptr, const int32_t
 // force over device-chosen items, split reduction; all read n_act / t_blk on
 // the device.
 // shape_slots[4]: SMs x occupancy of the per-launch kernels with 4, 32, 128, 256 i-particles per CTA
-cudaError_t launch_cycle_gate(nb_ctx* c, const int* shape_slots);
-cudaError_t launch_force_dyn(nb_ctx* c, int* grid_small, int* grid_big, bool query_only);
+cudaError_t launch_force_dyn(nb_ctx* c, int* grid, bool query_only);
 cudaError_t launch_force_reduce_dyn(nb_ctx* c);
 cudaError_t launch_wait_probe(nb_ctx* c, long long limit_cycles);
 cudaError_t launch_startup_store(nb_ctx* c, int order);
