@@ -69,7 +69,7 @@ static __device__ void drain_after_timeout(uint64_t* bars, int k, int nt)
 //   by warp   : lane l adds splits l, l+32, ... in turn, then the 32 lane
 //               sums meet in a butterfly (every lane ends with the same bits,
 //               as a + b == b + a exactly);
-//   sequential: one thread adds the splits in turn.
+//   sequential: one thread per (component, particle) adds the splits in turn.
 // The warp form serves many splits over few particles, where a thread per
 // particle would leave the GPU idle behind one long chain of loads.
 constexpr int RED_WARP_MIN_SPLIT = 9;
@@ -83,19 +83,21 @@ __host__ __device__ __forceinline__ bool reduce_by_warp(int jsplit, int n_act)
 __host__ __forceinline__ int reduce_grid(int jsplit, int n_act, int nc)
 {
     return reduce_by_warp(jsplit, n_act) ? (n_act * nc + RED_NT / 32 - 1) / (RED_NT / 32)
-                                         : (n_act + RED_NT - 1) / RED_NT;
+                                         : (n_act * nc + RED_NT - 1) / RED_NT;
 }
 
+// q = c * n_act + p
 template <int NC, int PC>
-__device__ __forceinline__ void reduce_seq(const double* __restrict__ partial, int jsplit, int n_act, int p,
+__device__ __forceinline__ void reduce_seq(const double* __restrict__ partial, int jsplit, int n_act, int q,
                                            double* __restrict__ F)
 {
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        double s = 0.0;
-        for (int sp = 0; sp < jsplit; ++sp) s += partial[((size_t)sp * NC + c) * n_act + p];
-        F[(size_t)c * n_act + p] = c == PC ? -s : s;
-    }
+    const int c = q / n_act;
+    const double* src = partial + q;
+    const size_t stride = (size_t)NC * n_act;
+    double s = 0.0;
+#pragma unroll 8
+    for (int sp = 0; sp < jsplit; ++sp) s += src[(size_t)sp * stride];
+    F[q] = c == PC ? -s : s;
 }
 
 // q = p * NC + c; called by a whole warp
@@ -1108,7 +1110,7 @@ __global__ void __launch_bounds__(RED_NT) k_force_reduce_dyn(const double* __res
         for (int q = g >> 5; q < n_act * NC; q += stride >> 5)
             reduce_warp<NC, PC>(partial, jsplit, n_act, q, threadIdx.x & 31, F);
     } else {
-        for (int p = g; p < n_act; p += stride) reduce_seq<NC, PC>(partial, jsplit, n_act, p, F);
+        for (int q = g; q < n_act * NC; q += stride) reduce_seq<NC, PC>(partial, jsplit, n_act, q, F);
     }
 }
 
@@ -1120,7 +1122,7 @@ __global__ void __launch_bounds__(RED_NT) k_force_reduce(const double* __restric
     if (reduce_by_warp(jsplit, n_act)) {
         const int q = g >> 5;  // warp-uniform
         if (q < n_act * NC) reduce_warp<NC, PC>(partial, jsplit, n_act, q, threadIdx.x & 31, F);
-    } else if (g < n_act) {
+    } else if (g < n_act * NC) {
         reduce_seq<NC, PC>(partial, jsplit, n_act, g, F);
     }
 }

@@ -49,6 +49,7 @@ struct nb_batch {
     int64_t* d_off = nullptr;     // [K]
     int64_t* d_nk = nullptr;      // [K]
     double* tblk = nullptr;       // [K] block time of each cluster (+inf: idle)
+    unsigned long long* kmin = nullptr;  // [K] its first-pass key (all ones between cycles)
     int32_t* kstart = nullptr;    // [K] first position of the cluster in the active list
     int32_t* kcount = nullptr;    // [K] active particles of the cluster
     int32_t* ksplit = nullptr;    // [K] j-splits of the cluster this cycle
@@ -102,41 +103,97 @@ int berr(nb_batch* b, int code, const char* fmt, ...)
 // ------------------------------------------------------------------ kernels
 constexpr int BNT = 256;
 
-// Block time of each cluster (one CTA per cluster); past t_end -> idle (+inf).
-__global__ void k_batch_min(const double* __restrict__ t, const double* __restrict__ dt,
-                            const int64_t* __restrict__ off, const int64_t* __restrict__ nk,
-                            double* __restrict__ tblk, DevScalars* sc)
+constexpr int BPER = 8;
+constexpr int BCHUNK = BNT * BPER;
+
+// Order-preserving key of a non-NaN double (k(a) < k(b) <=> a < b), and back.
+constexpr unsigned long long KEY_EMPTY = ~0ull;
+__device__ __forceinline__ unsigned long long time_key(double x)
 {
-    const double t_end = sc->t_end;
-    __shared__ double ws[BNT / 32];
-    const int k = blockIdx.x;
-    double mn = INFINITY;
-    bool bad = false;
-    for (int64_t i = off[k] + threadIdx.x; i < off[k] + nk[k]; i += BNT) {
-        const double tn = t[i] + dt[i];
-        bad |= !(tn == tn);
-        mn = fmin(mn, tn);
-    }
-    if (bad) raise_status(sc, NB_ERR_NAN);
-    for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = mn;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double b = ws[0];
-        for (int w = 1; w < BNT / 32; ++w) b = fmin(b, ws[w]);
-        tblk[k] = b <= t_end ? b : INFINITY;
-    }
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double key_time(unsigned long long k)
+{
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k));
 }
 
+// Block time of each cluster, first pass: min_i (t_i + dt_i) over the
+// cluster's particles, as keys into kmin[k] (atomicMin).  CTA = BCHUNK slots,
+// warp w = 256 consecutive slots as 8 groups of 32; clusters start on
+// multiples of JT (a multiple of 32), so a group's real slots share one
+// cluster and a warp meets at most a few clusters, flushing its running
+// minimum when the cluster changes.  The only FP64 operation is the sum
+// t + dt (the FP64 pipe runs at 1/64 of the FP32 rate here); comparisons run
+// on the keys.
+__global__ void __launch_bounds__(BNT) k_batch_tmin(const double* __restrict__ t, const double* __restrict__ dt,
+                                                    const int32_t* __restrict__ cid, int64_t n,
+                                                    unsigned long long* __restrict__ kmin, DevScalars* sc)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t s0 = (int64_t)blockIdx.x * BCHUNK + (int64_t)warp * 256;
+    int cur = -1;
+    unsigned long long cmin = KEY_EMPTY;
+    bool bad = false;
+    auto flush = [&]() {
+        if (lane == 0 && cur >= 0 && cmin != KEY_EMPTY) atomicMin(&kmin[cur], cmin);
+    };
+    // all eight groups' loads first, then the reductions and flushes
+    int kg[8];
+    unsigned long long kv[8];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+        const int64_t i = s0 + g * 32 + lane;
+        kg[g] = i < n ? cid[i] : -1;
+        kv[g] = KEY_EMPTY;
+        if (kg[g] >= 0) {
+            const double tn = t[i] + dt[i];
+            if (tn == tn) kv[g] = time_key(tn);
+            else bad = true;
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+        const int k = kg[g];
+        unsigned long long key = kv[g];
+        const int gk = __reduce_max_sync(0xffffffffu, k);
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(0xffffffffu, key, o);
+            key = y < key ? y : key;
+        }
+        if (gk < 0) continue;
+        if (gk != cur) {
+            flush();
+            cur = gk;
+            cmin = key;
+        } else if (key < cmin) {
+            cmin = key;
+        }
+    }
+    flush();
+    if (bad) raise_status(sc, NB_ERR_NAN);
+}
+
+// Second pass: tblk[k] from the key, +inf past t_end (the cluster idles);
+// the key is reset for the next cycle.
+__global__ void k_batch_tfinal(int K, unsigned long long* __restrict__ kmin, double* __restrict__ tblk,
+                               const DevScalars* __restrict__ sc)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const unsigned long long key = kmin[k];
+    kmin[k] = KEY_EMPTY;
+    const double b = key == KEY_EMPTY ? INFINITY : key_time(key);
+    tblk[k] = b <= sc->t_end ? b : INFINITY;
+}
+
+// t_i + dt_i == tblk[k] as bits (both sides exact dyadic sums; no FP64 compare)
 __device__ __forceinline__ bool batch_active(const double* t, const double* dt, const int32_t* cid,
                                              const double* tblk, int64_t i)
 {
     const int k = cid[i];
-    return k >= 0 && t[i] + dt[i] == tblk[k];
+    return k >= 0 && __double_as_longlong(t[i] + dt[i]) == __double_as_longlong(tblk[k]);
 }
-
-constexpr int BPER = 8;
-constexpr int BCHUNK = BNT * BPER;
 
 __global__ void k_batch_count(const double* __restrict__ t, const double* __restrict__ dt,
                               const int32_t* __restrict__ cid, const double* __restrict__ tblk, int64_t n,
@@ -473,7 +530,9 @@ __global__ void __launch_bounds__(FORCE_NT) k_batch_force_fp64_dyn(const double2
 }
 
 // F[c][p] = sum over the particle's cluster splits (fixed order); a fixed
-// grid strides over the cycle's active list.
+// grid strides over the (component, particle) pairs of the cycle, one sum
+// per thread (eleven times the parallelism of a thread per particle, which
+// left the many-split sums waiting on memory).
 template <int NC, int PC>
 __global__ void k_batch_reduce_dyn(const double* __restrict__ partial, const int32_t* __restrict__ list,
                                    const int32_t* __restrict__ cid, const int32_t* __restrict__ ksplit,
@@ -481,14 +540,17 @@ __global__ void k_batch_reduce_dyn(const double* __restrict__ partial, const int
 {
     if (sc->idle) return;
     const int n_act = (int)sc->n_act;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_act; p += gridDim.x * blockDim.x) {
+    const long long total = (long long)NC * n_act;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(q / n_act), p = (int)(q - (long long)c * n_act);
         const int S = ksplit[cid[list[p]]];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            double s = 0.0;
-            for (int sp = 0; sp < S; ++sp) s += partial[((size_t)sp * NC + c) * n_act + p];
-            F[(size_t)c * n_act + p] = c == PC ? -s : s;
-        }
+        const double* src = partial + (size_t)c * n_act + p;
+        const size_t stride = (size_t)NC * n_act;
+        double s = 0.0;
+#pragma unroll 8
+        for (int sp = 0; sp < S; ++sp) s += src[(size_t)sp * stride];
+        F[(size_t)c * n_act + p] = c == PC ? -s : s;
     }
 }
 
@@ -804,8 +866,9 @@ int batch_force(nb_batch* b, int order, const int32_t* list, int n_act, const in
 }
 
 // ------------------------------------------------ device-driven cycle (host)
-// scheduler 3, bounds 2, plan, items, predictor, force, reduction, corrector
-constexpr int BATCH_CYCLE_LAUNCHES = 11;
+// scheduler 4 (block times 2, count, scatter), bounds 2, plan, items,
+// predictor, force, reduction, corrector
+constexpr int BATCH_CYCLE_LAUNCHES = 12;
 
 void batch_destroy_graph(nb_batch* b)
 {
@@ -896,7 +959,8 @@ cudaError_t batch_cycle_launches(nb_batch* b)
 {
     nb_ctx* c = b->c;
     const int K = b->K, nch = (int)((c->n + BCHUNK - 1) / BCHUNK), g = c->sm_count * 4;
-    k_batch_min<<<K, BNT, 0, c->stream>>>(c->t, c->dt, b->d_off, b->d_nk, b->tblk, c->sc);
+    k_batch_tmin<<<nch, BNT, 0, c->stream>>>(c->t, c->dt, b->cid, c->n, b->kmin, c->sc);
+    k_batch_tfinal<<<(K + 255) / 256, 256, 0, c->stream>>>(K, b->kmin, b->tblk, c->sc);
     k_batch_count<<<nch, BNT, 0, c->stream>>>(c->t, c->dt, b->cid, b->tblk, c->n, b->chunk_cnt);
     k_batch_scatter<<<nch, BNT, 0, c->stream>>>(c->t, c->dt, b->cid, b->tblk, c->n, b->chunk_cnt, nch, c->act_idx,
                                                 c->sc);
@@ -912,8 +976,8 @@ cudaError_t batch_cycle_launches(nb_batch* b)
     if ((e = launch_predict(c, 0.0, b->tblk, b->cid, c->sc)) != cudaSuccess) return e;
     if (batch_force_dyn(b, false) != NB_OK) return cudaGetLastError();
 #define BRED(O)                                                                                                   \
-    k_batch_reduce_dyn<ncomp(O), pot_comp(O)><<<g, 256, 0, c->stream>>>(c->partial, c->act_idx, b->cid, b->ksplit, \
-                                                                        c->sc, c->F)
+    k_batch_reduce_dyn<ncomp(O), pot_comp(O)><<<2 * g, 256, 0, c->stream>>>(c->partial, c->act_idx, b->cid,         \
+                                                                            b->ksplit, c->sc, c->F)
     if (c->order == 4) BRED(4);
     else if (c->order == 6) BRED(6);
     else BRED(8);
@@ -960,8 +1024,8 @@ void nb_batch_destroy(nb_batch* b)
     if (b->c) cudaStreamSynchronize(b->c->stream);
     batch_destroy_graph(b);
     if (b->graph_stream) cudaStreamDestroy(b->graph_stream);
-    void* d[] = {b->cid, b->real_idx, b->d_off, b->d_nk, b->tblk, b->kstart, b->kcount, b->ksplit, b->chunk_cnt,
-                 b->items, b->esum, b->d_pk, b->kni, b->koff, b->d_items};
+    void* d[] = {b->cid,    b->real_idx, b->d_off, b->d_nk,    b->tblk, b->kmin, b->kstart, b->kcount,
+                 b->ksplit, b->chunk_cnt, b->items, b->esum, b->d_pk, b->kni,  b->koff,   b->d_items};
     for (void* p : d)
         if (p) cudaFree(p);
     void* h[] = {b->h_tblk, b->h_kstart, b->h_kcount, b->h_ksplit, b->h_items, b->h_esum};
@@ -1001,6 +1065,7 @@ int nb_batch_create(nb_batch** out, int n_clusters, const int64_t* n_per_cluster
     const int K = n_clusters;
     if ((rc = balloc(b, &b->cid, (size_t)b->c->np)) || (rc = balloc(b, &b->real_idx, (size_t)b->n_real)) ||
         (rc = balloc(b, &b->d_off, K)) || (rc = balloc(b, &b->d_nk, K)) || (rc = balloc(b, &b->tblk, K)) ||
+        (rc = balloc(b, &b->kmin, K)) ||
         (rc = balloc(b, &b->kstart, K)) || (rc = balloc(b, &b->kcount, K)) || (rc = balloc(b, &b->ksplit, K)) ||
         (rc = balloc(b, &b->kni, K)) || (rc = balloc(b, &b->koff, K)) || (rc = balloc(b, &b->d_pk, K)) ||
         (rc = balloc(b, &b->chunk_cnt, (size_t)((slots + BCHUNK - 1) / BCHUNK))) ||
@@ -1026,7 +1091,8 @@ int nb_batch_create(nb_batch** out, int n_clusters, const int64_t* n_per_cluster
         cudaMemcpy(b->real_idx, real.data(), real.size() * 4, cudaMemcpyHostToDevice) ||
         cudaMemcpy(b->d_off, b->off.data(), K * 8, cudaMemcpyHostToDevice) ||
         cudaMemcpy(b->d_nk, b->nk.data(), K * 8, cudaMemcpyHostToDevice) ||
-        cudaMemcpy(b->d_pk, b->pk.data(), K * 8, cudaMemcpyHostToDevice)) {
+        cudaMemcpy(b->d_pk, b->pk.data(), K * 8, cudaMemcpyHostToDevice) ||
+        cudaMemset(b->kmin, 0xFF, K * sizeof(unsigned long long))) {
         cudaGetLastError();
         nb_batch_destroy(b);
         return NB_ERR_CUDA;
