@@ -13,15 +13,33 @@ namespace nb {
 // ===================================================================== K5
 // Block scheduler (abstract: individual hierarchical block time-steps):
 // t_blk = min_i (t_i + dt_i), active = {i : t_i + dt_i == t_blk} ascending.
-// Two passes, no atomics, deterministic.  Chunk b = SCHED_NT threads x `per`
-// consecutive particles each (per from sched_layout).
+// Two passes, no atomics, deterministic.  Chunk b = SCHED_NT threads x PER
+// consecutive particles each (PER from sched_layout, a power of two).
 //   1. chunk b publishes m_b = its minimum of t_i + dt_i and c_b = how many of
 //      its particles reach m_b;
 //   2. every chunk reads the table: t_blk = min_b m_b, its offset = sum of c_b'
 //      over earlier chunks with m_b' == t_blk; a chunk with m_b == t_blk
 //      writes its matches in index order (one block-wide exclusive scan).
+// Times are compared as order-preserving integer keys of the (exact, dyadic)
+// sums t_i + dt_i: the only FP64 operation is the sum itself (the FP64 pipe
+// runs at 1/64 of the FP32 rate here).  A NaN sum raises NB_ERR_NAN and is
+// left out.
 constexpr int SCHED_NT = 256;
 constexpr int SCHED_PER_MAX = 16;
+constexpr unsigned long long KEY_NONE = ~0ull;
+
+// k(a) < k(b) <=> a < b for non-NaN doubles; NaN -> KEY_NONE
+__device__ __forceinline__ unsigned long long time_key(double x)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    if ((u & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull) return KEY_NONE;
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double key_time(unsigned long long k)
+{
+    if (k == KEY_NONE) return INFINITY;
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k));
+}
 
 __device__ __forceinline__ double warp_min(double v)
 {
@@ -41,15 +59,18 @@ __device__ __forceinline__ int warp_isum(int v)
     return v;
 }
 
-// minimum over the CTA; every thread gets it
-__device__ __forceinline__ double block_min(double v, double* ws)
+// minimum key over the CTA; every thread gets it
+__device__ __forceinline__ unsigned long long block_kmin(unsigned long long v, unsigned long long* ws)
 {
-    v = warp_min(v);
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, v, o);
+        v = y < v ? y : v;
+    }
     __syncthreads();  // ws reuse
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
     __syncthreads();
-    double b = ws[0];
-    for (int w = 1; w < SCHED_NT / 32; ++w) b = fmin(b, ws[w]);
+    unsigned long long b = ws[0];
+    for (int w = 1; w < SCHED_NT / 32; ++w) b = ws[w] < b ? ws[w] : b;
     return b;
 }
 
@@ -65,30 +86,31 @@ __device__ __forceinline__ int block_isum(int v, int* ws)
     return s;
 }
 
+template <int PER>
 __global__ void __launch_bounds__(SCHED_NT) k_sched_chunk(const double* __restrict__ t, const double* __restrict__ dt,
-                                                          int64_t n, int per, double* __restrict__ cmin,
+                                                          int64_t n, unsigned long long* __restrict__ cmin,
                                                           int32_t* __restrict__ ccnt, DevScalars* sc)
 {
-    __shared__ double wd[SCHED_NT / 32];
+    __shared__ unsigned long long wk[SCHED_NT / 32];
     __shared__ int wi[SCHED_NT / 32];
-    const int64_t i0 = ((int64_t)blockIdx.x * SCHED_NT + threadIdx.x) * per;
-    double tn[SCHED_PER_MAX];
-    double mn = INFINITY;
+    const int64_t i0 = ((int64_t)blockIdx.x * SCHED_NT + threadIdx.x) * PER;
+    unsigned long long key[PER];
+    unsigned long long mn = KEY_NONE;
     bool bad = false;
 #pragma unroll
-    for (int k = 0; k < SCHED_PER_MAX; ++k) {
-        tn[k] = INFINITY;
-        if (k < per && i0 + k < n) {
-            tn[k] = t[i0 + k] + dt[i0 + k];
-            bad |= !(tn[k] == tn[k]);
-            mn = fmin(mn, tn[k]);
+    for (int k = 0; k < PER; ++k) {
+        key[k] = KEY_NONE;
+        if (i0 + k < n) {
+            key[k] = time_key(t[i0 + k] + dt[i0 + k]);
+            bad |= key[k] == KEY_NONE;
+            mn = key[k] < mn ? key[k] : mn;
         }
     }
     if (bad) raise_status(sc, NB_ERR_NAN);
-    const double m_b = block_min(mn, wd);
+    const unsigned long long m_b = block_kmin(mn, wk);
     int c = 0;
 #pragma unroll
-    for (int k = 0; k < SCHED_PER_MAX; ++k) c += (k < per && i0 + k < n && tn[k] == m_b) ? 1 : 0;
+    for (int k = 0; k < PER; ++k) c += (key[k] == m_b && m_b != KEY_NONE) ? 1 : 0;
     c = block_isum(c, wi);
     if (threadIdx.x == 0) {
         cmin[blockIdx.x] = m_b;
@@ -97,22 +119,26 @@ __global__ void __launch_bounds__(SCHED_NT) k_sched_chunk(const double* __restri
 }
 
 // Second pass (every CTA): t_blk and this chunk's offset from the chunk table,
-// then the chunk's matches in index order.  Returns t_blk.
+// then the chunk's matches in index order.  CTA 0 publishes t_blk and n_act
+// (and, in a device-driven cycle, applies the launch-shape gate).  Returns
+// t_blk.
+template <int PER>
 __device__ __forceinline__ double sched_compact_body(const double* __restrict__ t, const double* __restrict__ dt,
-                                                     int64_t n, int per, const double* __restrict__ cmin,
+                                                     int64_t n, const unsigned long long* __restrict__ cmin,
                                                      const int32_t* __restrict__ ccnt, int nch,
                                                      int32_t* __restrict__ idx, DevScalars* sc,
                                                      const GateArgs* gate = nullptr)
 {
-    __shared__ double wd[SCHED_NT / 32];
+    __shared__ unsigned long long wk[SCHED_NT / 32];
     __shared__ int wi[SCHED_NT / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double mn = INFINITY;
-    for (int k = threadIdx.x; k < nch; k += SCHED_NT) mn = fmin(mn, cmin[k]);
-    const double tb = block_min(mn, wd);
+    unsigned long long mn = KEY_NONE;
+    for (int k = threadIdx.x; k < nch; k += SCHED_NT) mn = cmin[k] < mn ? cmin[k] : mn;
+    const unsigned long long tbk = block_kmin(mn, wk);
+    const double tb = key_time(tbk);
     int before = 0, total = 0;
     for (int k = threadIdx.x; k < nch; k += SCHED_NT) {
-        const int ck = cmin[k] == tb ? ccnt[k] : 0;
+        const int ck = cmin[k] == tbk ? ccnt[k] : 0;
         total += ck;
         if (k < (int)blockIdx.x) before += ck;
     }
@@ -123,12 +149,12 @@ __device__ __forceinline__ double sched_compact_body(const double* __restrict__ 
         sc->n_act = total;
         if (gate) cycle_gate_apply(sc, tb, total, *gate);
     }
-    if (cmin[blockIdx.x] != tb) return tb;  // CTA-uniform: no match in this chunk
-    const int64_t i0 = ((int64_t)blockIdx.x * SCHED_NT + threadIdx.x) * per;
+    if (cmin[blockIdx.x] != tbk || tbk == KEY_NONE) return tb;  // CTA-uniform: no match in this chunk
+    const int64_t i0 = ((int64_t)blockIdx.x * SCHED_NT + threadIdx.x) * PER;
     unsigned flags = 0;
 #pragma unroll
-    for (int k = 0; k < SCHED_PER_MAX; ++k)
-        if (k < per && i0 + k < n && t[i0 + k] + dt[i0 + k] == tb) flags |= 1u << k;
+    for (int k = 0; k < PER; ++k)
+        if (i0 + k < n && time_key(t[i0 + k] + dt[i0 + k]) == tbk) flags |= 1u << k;
     // exclusive scan of the per-thread match counts over the CTA
     const int mine = __popc(flags);
     int incl = mine;
@@ -151,34 +177,47 @@ __device__ __forceinline__ double sched_compact_body(const double* __restrict__ 
     return tb;
 }
 
+template <int PER>
 __global__ void __launch_bounds__(SCHED_NT) k_sched_compact(const double* __restrict__ t,
-                                                            const double* __restrict__ dt, int64_t n, int per,
-                                                            const double* __restrict__ cmin,
+                                                            const double* __restrict__ dt, int64_t n,
+                                                            const unsigned long long* __restrict__ cmin,
                                                             const int32_t* __restrict__ ccnt, int nch,
                                                             int32_t* __restrict__ idx, DevScalars* sc)
 {
-    sched_compact_body(t, dt, n, per, cmin, ccnt, nch, idx, sc);
+    sched_compact_body<PER>(t, dt, n, cmin, ccnt, nch, idx, sc);
 }
 
-// Particles per scheduler thread (about one wave of CTAs, at most
-// SCHED_PER_MAX) and the number of chunks.
+// Particles per scheduler thread: the smallest power of two that covers n
+// with one chunk per SM, at most SCHED_PER_MAX (more chunks beyond that).
 void sched_layout(int64_t n, int sm_count, int* per, int* nch)
 {
     const int64_t lanes = (int64_t)SCHED_NT * (sm_count > 0 ? sm_count : 1);
-    int64_t p = (n + lanes - 1) / lanes;
-    if (p < 1) p = 1;
-    if (p > SCHED_PER_MAX) p = SCHED_PER_MAX;
-    *per = (int)p;
+    int p = 1;
+    while (p < SCHED_PER_MAX && (int64_t)p * lanes < n) p *= 2;
+    *per = p;
     *nch = (int)((n + (int64_t)SCHED_NT * p - 1) / ((int64_t)SCHED_NT * p));
 }
+
+// dispatch on the layout's PER
+#define NB_SCHED_PER(per, F) \
+    switch (per) {           \
+    case 1: F(1); break;     \
+    case 2: F(2); break;     \
+    case 4: F(4); break;     \
+    case 8: F(8); break;     \
+    default: F(16); break;   \
+    }
 
 cudaError_t launch_sched(nb_ctx* c)
 {
     int per, nch;
     sched_layout(c->n, c->sm_count, &per, &nch);
-    k_sched_chunk<<<nch, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, per, c->chunk_min, c->chunk_cnt, c->sc);
-    k_sched_compact<<<nch, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, per, c->chunk_min, c->chunk_cnt, nch,
-                                                     c->act_idx, c->sc);
+#define NB_S(P)                                                                                                      \
+    k_sched_chunk<P><<<nch, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, c->chunk_min, c->chunk_cnt, c->sc);       \
+    k_sched_compact<P><<<nch, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, c->chunk_min, c->chunk_cnt, nch,         \
+                                                        c->act_idx, c->sc)
+    NB_SCHED_PER(per, NB_S)
+#undef NB_S
     return cudaGetLastError();
 }
 
@@ -372,18 +411,18 @@ __global__ void __launch_bounds__(256) k_predict(const double* __restrict__ m, c
 // its own chunk of particles to it (the last CTA also the padding records up
 // to np).  use_t_end: a device-driven cycle, which predicts nothing past
 // sc->t_end and whose force launch shape CTA 0 sets with the gate.
-template <int ORDER, bool MIXED>
+template <int ORDER, bool MIXED, int PER>
 __global__ void __launch_bounds__(SCHED_NT) k_sched_compact_predict(
-    const double* __restrict__ t, const double* __restrict__ dt, int64_t n, int per, const double* __restrict__ cmin,
-    const int32_t* __restrict__ ccnt, int nch, int32_t* __restrict__ idx, DevScalars* sc, int use_t_end,
-    const double* __restrict__ m, const double* __restrict__ eps2, const double* __restrict__ x,
-    const double* __restrict__ v, const double* __restrict__ d, int64_t np, void* __restrict__ jstore,
-    GateArgs gate)
+    const double* __restrict__ t, const double* __restrict__ dt, int64_t n,
+    const unsigned long long* __restrict__ cmin, const int32_t* __restrict__ ccnt, int nch,
+    int32_t* __restrict__ idx, DevScalars* sc, int use_t_end, const double* __restrict__ m,
+    const double* __restrict__ eps2, const double* __restrict__ x, const double* __restrict__ v,
+    const double* __restrict__ d, int64_t np, void* __restrict__ jstore, GateArgs gate)
 {
-    const double tb = sched_compact_body(t, dt, n, per, cmin, ccnt, nch, idx, sc, use_t_end ? &gate : nullptr);
+    const double tb = sched_compact_body<PER>(t, dt, n, cmin, ccnt, nch, idx, sc, use_t_end ? &gate : nullptr);
     if (use_t_end && !(tb <= sc->t_end)) return;
-    const int64_t c0 = (int64_t)blockIdx.x * SCHED_NT * per;
-    const int64_t c1 = blockIdx.x == nch - 1 ? np : min(c0 + (int64_t)SCHED_NT * per, np);
+    const int64_t c0 = (int64_t)blockIdx.x * SCHED_NT * PER;
+    const int64_t c1 = blockIdx.x == nch - 1 ? np : min(c0 + (int64_t)SCHED_NT * PER, np);
     for (int64_t i = c0 + threadIdx.x; i < c1; i += SCHED_NT)
         predict_one<ORDER, MIXED>(i, tb, m, eps2, x, v, d, t, n, np, jstore, nullptr, nullptr);
 }
@@ -406,20 +445,23 @@ cudaError_t launch_sched_predict(nb_ctx* c, bool use_t_end, const int* shape_slo
         g.tab = c->d_tune + pi * TUNE_MAX;
         g.ntab = c->tune_n[pi];
     }
-    k_sched_chunk<<<nch, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, per, c->chunk_min, c->chunk_cnt, c->sc);
     const bool mixed = c->prec == NB_MIXED;
-#define NB_SP(O, MX)                                                                                              \
-    k_sched_compact_predict<O, MX><<<nch, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, per, c->chunk_min,        \
-                                                                    c->chunk_cnt, nch, c->act_idx, c->sc,        \
-                                                                    use_t_end ? 1 : 0, c->m, c->eps2, c->x, c->v, \
-                                                                    c->d, c->np, c->jstore, g)
-    if (c->order == 4) {
-        if (mixed) NB_SP(4, true); else NB_SP(4, false);
-    } else if (c->order == 6) {
-        if (mixed) NB_SP(6, true); else NB_SP(6, false);
-    } else {
-        if (mixed) NB_SP(8, true); else NB_SP(8, false);
+#define NB_SP(O, MX, P)                                                                                             \
+    k_sched_compact_predict<O, MX, P><<<nch, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, c->chunk_min,           \
+                                                                       c->chunk_cnt, nch, c->act_idx, c->sc,       \
+                                                                       use_t_end ? 1 : 0, c->m, c->eps2, c->x,     \
+                                                                       c->v, c->d, c->np, c->jstore, g)
+#define NB_S(P)                                                                                                     \
+    k_sched_chunk<P><<<nch, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, c->chunk_min, c->chunk_cnt, c->sc);      \
+    if (c->order == 4) {                                                                                            \
+        if (mixed) NB_SP(4, true, P); else NB_SP(4, false, P);                                                      \
+    } else if (c->order == 6) {                                                                                     \
+        if (mixed) NB_SP(6, true, P); else NB_SP(6, false, P);                                                      \
+    } else {                                                                                                        \
+        if (mixed) NB_SP(8, true, P); else NB_SP(8, false, P);                                                      \
     }
+    NB_SCHED_PER(per, NB_S)
+#undef NB_S
 #undef NB_SP
     return cudaGetLastError();
 }

@@ -315,7 +315,7 @@ struct nb_ctx {
     int32_t* act_idx = nullptr;   // [n] active list
     int32_t* all_idx = nullptr;   // [n] 0..n-1
     int32_t* chunk_cnt = nullptr; // scheduler: per-chunk match counts
-    double* chunk_min = nullptr;  // scheduler: per-chunk minima of t + dt
+    unsigned long long* chunk_min = nullptr;  // scheduler: per-chunk minima of t + dt (order keys)
     double* stage = nullptr;      // state I/O staging, 26 n doubles (allocated on first use)
     int n_chunks = 0;
     nb::DevScalars* sc = nullptr;
