@@ -1034,27 +1034,46 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_fp64(const double2* __restri
 // capped by the partial-sum buffer); an active set past t_end makes the
 // cycle idle.
 
+// Resident CTAs per SM that the kernels holding several mixed variants are
+// compiled for: 4 at orders <= 6, 3 at order 8 (whose larger chain then gets
+// the registers instead of spilling).
+__host__ __device__ constexpr int dyn_min_ctas(int order) { return order >= 8 ? 3 : 4; }
+
 // Persistent force: a fixed grid walks the (i-tile, split) items of the
-// device-chosen shape, in the chosen variant (4, 32, FORCE_NT or 2 FORCE_NT
-// i-particles per CTA); the dynamic shared memory fits the largest.
+// device-chosen shape.  SMALL: the variants of up to FORCE_NT i-particles per
+// CTA (4, 32, FORCE_NT), compiled for dyn_min_ctas resident CTAs; otherwise
+// the two-per-thread variant (2 FORCE_NT), whose block is an out-of-line
+// call (xs_item).  The kernel not matching the chosen variant returns at
+// once.
+// The two-per-thread block as a call of its own: compiled apart from a
+// persistent caller's item loop it keeps the code of its per-launch kernel
+// (inlined into the loop it ran 12-20 % slower at order 8, 5 % at order 6).
 template <int ORDER, int RW, bool PAIR>
-__global__ void __launch_bounds__(FORCE_NT, 4) k_force_mixed_dyn(const float4* __restrict__ js,
-                                                                 const int32_t* __restrict__ idx, int n, int ntiles,
-                                                                 float eps2u, float eps2max,
-                                                                 double* __restrict__ partial, DevScalars* sc,
-                                                                 double* F)
+__device__ __noinline__ void xs_item(const float4* __restrict__ js, const int32_t* __restrict__ idx, int pbase0,
+                                     int plim, int n, int t0, int nt, int split, int ncol, float eps2u, float eps2max,
+                                     double* __restrict__ partial, DevScalars* sc, TileSum ts)
+{
+    force_block_mixed_xs<ORDER, RW, PAIR, 1>(js, idx, pbase0, plim, n, t0, nt, split, ncol, eps2u, eps2max, partial,
+                                             sc, ts);
+}
+
+template <int ORDER, int RW, bool PAIR, bool SMALL>
+__global__ void __launch_bounds__(FORCE_NT, SMALL ? dyn_min_ctas(ORDER) : 1)
+    k_force_mixed_dyn(const float4* __restrict__ js, const int32_t* __restrict__ idx, int n, int ntiles, float eps2u,
+                      float eps2max, double* __restrict__ partial, DevScalars* sc, double* F)
 {
     if (sc->idle) return;
     const int ni = sc->ni;
+    if (SMALL != (ni <= FORCE_NT)) return;
     const int n_act = (int)sc->n_act, it = sc->itiles, jsplit = sc->jsplit;
     for (int w = blockIdx.x; w < it * jsplit; w += gridDim.x) {
         const int itile = w % it, split = w / it;
         const int t0 = (int)((long long)split * ntiles / jsplit);
         const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
         const TileSum tsum{F, jsplit};
-        if (ni == 2 * FORCE_NT)
-            force_block_mixed_xs<ORDER, RW, PAIR, 1>(js, idx, itile * ni, n_act, n, t0, t1 - t0, split, n_act,
-                                                     eps2u, eps2max, partial, sc, tsum);
+        if (!SMALL)
+            xs_item<ORDER, RW, PAIR>(js, idx, itile * ni, n_act, n, t0, t1 - t0, split, n_act, eps2u, eps2max, partial,
+                                     sc, tsum);
         else if (ni == FORCE_NT)
             force_block_mixed<ORDER, RW, PAIR, 1>(js, idx, itile * ni, n_act, n, t0, t1 - t0, split, n_act, eps2u,
                                                   eps2max, partial, sc, tsum);

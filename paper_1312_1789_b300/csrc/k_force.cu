@@ -214,43 +214,74 @@ static int dyn_slots(nb_ctx* c, K kern, size_t smem)
     return c->sm_count * occupancy_of(kern, smem);
 }
 
-// Launch (or, query_only, size) the persistent force kernel of the context's
-// order and precision.
+// Launch (or, query_only, size) the persistent force kernels of the context's
+// order in the given precision: on the mixed path one for the variants of up
+// to FORCE_NT i-particles per CTA (grid[0]) and one for two per thread
+// (grid[1]); FP64 one kernel (both entries).
 template <int O>
-static cudaError_t force_dyn_o(nb_ctx* c, int* grid, bool query_only)
+static cudaError_t force_dyn_o(nb_ctx* c, int* grid, bool query_only, bool mixed)
 {
     const bool pair = c->pair_eps || !(c->eps > 0.0);
     const int ntiles = (int)(c->np / JT);
-    if (c->prec == NB_MIXED) {
+    if (mixed) {
         constexpr int RW = mixed_rw(O);
-        const size_t smem = xs_smem(O, RW, 1);
-        auto k = pair ? k_force_mixed_dyn<O, RW, true> : k_force_mixed_dyn<O, RW, false>;
+        const size_t smem = (size_t)NSTAGE * JT * RW * 16, smem_big = xs_smem(O, RW, 1);
+        auto k1 = pair ? k_force_mixed_dyn<O, RW, true, true> : k_force_mixed_dyn<O, RW, false, true>;
+        auto k2 = pair ? k_force_mixed_dyn<O, RW, true, false> : k_force_mixed_dyn<O, RW, false, false>;
+        static int occ[2][2] = {{0, 0}, {0, 0}};  // [pair][big]
+        int* o = occ[pair ? 1 : 0];
+        if (!o[0]) o[0] = dyn_slots(c, k1, smem) / c->sm_count;
+        if (!o[1]) o[1] = dyn_slots(c, k2, smem_big) / c->sm_count;
         if (query_only) {
-            *grid = dyn_slots(c, k, smem);
+            grid[0] = c->sm_count * o[0];
+            grid[1] = c->sm_count * o[1];
             return cudaSuccess;
         }
         const float e2 = (float)(c->eps * c->eps), e2max = (float)c->eps2_max;
-        k<<<*grid, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), c->act_idx, (int)c->n,
-                                                ntiles, e2, e2max, c->partial, c->sc, c->F);
+        k1<<<grid[0], FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), c->act_idx,
+                                                   (int)c->n, ntiles, e2, e2max, c->partial, c->sc, c->F);
+        k2<<<grid[1], FORCE_NT, smem_big, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), c->act_idx,
+                                                       (int)c->n, ntiles, e2, e2max, c->partial, c->sc, c->F);
     } else {
         constexpr int RW = fp64_rw(O);
         const size_t smem = (size_t)NSTAGE * JT * RW * 16;
         auto k = pair ? k_force_fp64_dyn<O, RW, true> : k_force_fp64_dyn<O, RW, false>;
+        static int occ[2] = {0, 0};
+        int& o = occ[pair ? 1 : 0];
+        if (!o) o = dyn_slots(c, k, smem) / c->sm_count;
         if (query_only) {
-            *grid = dyn_slots(c, k, smem);
+            grid[0] = grid[1] = c->sm_count * o;
             return cudaSuccess;
         }
-        k<<<*grid, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const double2*>(c->jstore), c->act_idx, (int)c->n,
-                                                ntiles, c->eps * c->eps, c->partial, c->sc, c->F);
+        k<<<grid[0], FORCE_NT, smem, c->stream>>>(reinterpret_cast<const double2*>(c->jstore), c->act_idx,
+                                                  (int)c->n, ntiles, c->eps * c->eps, c->partial, c->sc, c->F);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_force_dyn(nb_ctx* c, int* grid, bool query_only)
 {
-    if (c->order == 4) return force_dyn_o<4>(c, grid, query_only);
-    if (c->order == 6) return force_dyn_o<6>(c, grid, query_only);
-    return force_dyn_o<8>(c, grid, query_only);
+    const bool mixed = c->prec == NB_MIXED;
+    if (c->order == 4) return force_dyn_o<4>(c, grid, query_only, mixed);
+    if (c->order == 6) return force_dyn_o<6>(c, grid, query_only, mixed);
+    return force_dyn_o<8>(c, grid, query_only, mixed);
+}
+
+// Resident CTAs the split rule plans for.  At the context's own order, those
+// of the persistent kernel that runs the variant: a block then gets the same
+// shape in host-driven and device-driven cycles, and a device-driven cycle
+// never runs more waves than were planned (a per-launch kernel with more
+// resident CTAs just finishes its waves sooner).  At other orders (start-up
+// passes, energy) the per-launch kernel's.
+int shape_slots(nb_ctx* c, int order, int ni, bool mixed)
+{
+    if (order != c->order) return c->sm_count * force_occupancy(c, order, ni);
+    int g[2] = {0, 0};
+    if (order == 4) force_dyn_o<4>(c, g, true, mixed);
+    else if (order == 6) force_dyn_o<6>(c, g, true, mixed);
+    else force_dyn_o<8>(c, g, true, mixed);
+    const int s = g[mixed && ni > FORCE_NT ? 1 : 0];
+    return s > 0 ? s : c->sm_count;
 }
 
 cudaError_t launch_force_reduce_dyn(nb_ctx* c)

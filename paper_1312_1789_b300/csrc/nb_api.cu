@@ -186,7 +186,7 @@ void choose_shape(nb_ctx* c, int order, int64_t n_act, int* itiles, int* jsplit,
         it = (int)((n_act + ni - 1) / ni);
         js = c->jsplit_force > 0
                  ? c->jsplit_force
-                 : makespan_split(it, ntiles, c->sm_count * force_occupancy(c, order, ni), cap_splits);
+                 : makespan_split(it, ntiles, shape_slots(c, order, ni, pi == 1), cap_splits);
     }
     if (js > ntiles) js = ntiles;
     if (js > cap_splits) js = (int)cap_splits;
@@ -228,25 +228,22 @@ void destroy_graph(nb_ctx* c)
 int build_graph(nb_ctx* c)
 {
     destroy_graph(c);
-    int grid = 0;
+    int grid[2] = {0, 0};
     c->pred_prec = c->prec;
-    NB_CUDA(c, launch_force_dyn(c, &grid, true));
-    // the split rule sees the per-launch kernels' slot counts, so a block
-    // gets the same shape (and the same summation order) in both modes
-    int shape_slots[4];
+    NB_CUDA(c, launch_force_dyn(c, grid, true));
+    // the split rule sees the same slot counts as in host-driven cycles, so
+    // a block gets the same shape (and the same summation order) in both
+    int slots[4];
     const int variants[4] = {4, 32, FORCE_NT, 2 * FORCE_NT};
-    for (int k = 0; k < 4; ++k) {
-        const int ni = c->prec == NB_MIXED || variants[k] <= FORCE_NT ? variants[k] : FORCE_NT;
-        shape_slots[k] = c->sm_count * force_occupancy(c, c->order, ni);
-    }
+    for (int k = 0; k < 4; ++k) slots[k] = shape_slots(c, c->order, variants[k], c->prec == NB_MIXED);
     if (!c->graph_stream) NB_CUDA(c, cudaStreamCreateWithFlags(&c->graph_stream, cudaStreamNonBlocking));
     cudaStream_t saved = c->stream;
     c->stream = c->graph_stream;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(c->graph_stream, cudaStreamCaptureModeThreadLocal);
     for (int r = 0; e == cudaSuccess && r < c->graph_cycles; ++r) {
-        if ((e = launch_sched_predict(c, true, shape_slots)) != cudaSuccess) break;
-        if ((e = launch_force_dyn(c, &grid, false)) != cudaSuccess) break;
+        if ((e = launch_sched_predict(c, true, slots)) != cudaSuccess) break;
+        if ((e = launch_force_dyn(c, grid, false)) != cudaSuccess) break;
         if ((e = launch_force_reduce_dyn(c)) != cudaSuccess) break;
         if ((e = launch_correct(c, nullptr, nullptr, c->sc)) != cudaSuccess) break;
     }
@@ -275,8 +272,8 @@ int step_until_graph(nb_ctx* c, double t_end, int64_t* n_blocks, int64_t* n_inte
     h->inter = 0;
     NB_CUDA(c, cudaMemcpy(c->sc, h, sizeof(DevScalars), cudaMemcpyHostToDevice));
     // scheduler 2 (the second predicts and sets the launch shape), persistent
-    // force, reduction, corrector
-    const long long per_cycle = 2 + 1 + 1 + 1;
+    // force (two kernels on the mixed path), reduction, corrector
+    const long long per_cycle = 2 + (c->prec == NB_MIXED ? 2 : 1) + 1 + 1;
     for (;;) {
         NB_CUDA(c, cudaGraphLaunch(c->graph_exec, c->graph_stream));
         c->n_launch += per_cycle * c->graph_cycles;
@@ -539,7 +536,7 @@ int nb_autotune(nb_ctx* c, int reps)
             for (int v = 0; v < nv && rc == NB_OK; ++v) {
                 const int ni = cand[v];
                 const int it = (int)((na + ni - 1) / ni);
-                const int base = makespan_split(it, ntiles, c->sm_count * force_occupancy(c, c->order, ni), cap_splits);
+                const int base = makespan_split(it, ntiles, shape_slots(c, c->order, ni, mixed), cap_splits);
                 const int mult[8][2] = {{1, 4}, {1, 2}, {1, 1}, {2, 1}, {4, 1}, {8, 1}, {16, 1}, {0, 1}};
                 int tried[8], nt = 0;
                 for (int q = 0; q < 8 && rc == NB_OK; ++q) {

@@ -269,7 +269,7 @@ __global__ void k_batch_counts(int K, const int32_t* __restrict__ kstart, int32_
 // size picks it with the rule of a single system, mixed_ni: two i-particles
 // per thread in packed FP32x2 lanes from 512 active on).
 template <int ORDER, int RW>
-__global__ void __launch_bounds__(FORCE_NT, 4) k_batch_force_mixed(const float4* __restrict__ js,
+__global__ void __launch_bounds__(FORCE_NT, dyn_min_ctas(ORDER)) k_batch_force_mixed(const float4* __restrict__ js,
                                                                    const int32_t* __restrict__ list,
                                                                    const BatchItem* __restrict__ items, int n_act,
                                                                    int n, float eps2max, double* __restrict__ partial,
@@ -278,8 +278,8 @@ __global__ void __launch_bounds__(FORCE_NT, 4) k_batch_force_mixed(const float4*
     const BatchItem it = items[blockIdx.x];
     const int lim = it.list_off + it.count;
     if (it.ni == 2 * FORCE_NT)
-        force_block_mixed_xs<ORDER, RW, true, 1>(js, list, it.list_off, lim, n, it.jt0, it.nt, it.split, n_act, 0.0f,
-                                                 eps2max, partial, sc);
+        xs_item<ORDER, RW, true>(js, list, it.list_off, lim, n, it.jt0, it.nt, it.split, n_act, 0.0f, eps2max, partial,
+                                 sc, TileSum{});
     else if (it.ni == FORCE_NT)
         force_block_mixed<ORDER, RW, true, 1>(js, list, it.list_off, lim, n, it.jt0, it.nt, it.split, n_act, 0.0f,
                                               eps2max, partial, sc);
@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(BNT) k_batch_items(const int32_t* __restrict__
 // takes the next item from a counter, so that CTAs that drew short items take
 // more of them.
 template <int ORDER, int RW>
-__global__ void __launch_bounds__(FORCE_NT, 4) k_batch_force_mixed_dyn(const float4* __restrict__ js,
+__global__ void __launch_bounds__(FORCE_NT, dyn_min_ctas(ORDER)) k_batch_force_mixed_dyn(const float4* __restrict__ js,
                                                                        const int32_t* __restrict__ list,
                                                                        const BatchItem* __restrict__ items, int n,
                                                                        float eps2max, double* __restrict__ partial,
@@ -481,8 +481,8 @@ __global__ void __launch_bounds__(FORCE_NT, 4) k_batch_force_mixed_dyn(const flo
         const BatchItem it = items[w];
         const int lim = it.list_off + it.count;
         if (it.ni == 2 * FORCE_NT)
-            force_block_mixed_xs<ORDER, RW, true, 1>(js, list, it.list_off, lim, n, it.jt0, it.nt, it.split, n_act,
-                                                     0.0f, eps2max, partial, sc);
+            xs_item<ORDER, RW, true>(js, list, it.list_off, lim, n, it.jt0, it.nt, it.split, n_act, 0.0f, eps2max,
+                                     partial, sc, TileSum{});
         else if (it.ni == FORCE_NT)
             force_block_mixed<ORDER, RW, true, 1>(js, list, it.list_off, lim, n, it.jt0, it.nt, it.split, n_act, 0.0f,
                                                   eps2max, partial, sc);

@@ -149,9 +149,9 @@ struct DevScalars {
 // publishes the cycle's t_blk and n_act: close the cycle when the block lies
 // past t_end, otherwise pick the force launch shape exactly as the host rule
 // does for a block of that size (the autotuned table if any, else the same
-// variant rule, slot counts and makespan split; a forced split).  slots = SMs
-// x occupancy of the per-launch kernels with 4, 32, FORCE_NT and 2 FORCE_NT
-// i-particles per CTA.
+// variant rule, slot counts and makespan split; a forced split).  slots = the
+// resident CTAs the split rule plans for with 4, 32, FORCE_NT and 2 FORCE_NT
+// i-particles per CTA (shape_slots).
 struct GateArgs {
     long long n;     // particles (interactions per active particle)
     long long cap;   // partial-sum buffer, doubles
@@ -387,7 +387,7 @@ cudaError_t launch_correct(nb_ctx* c, const double* tfc = nullptr, const int32_t
 // force over device-chosen items, split reduction; all read n_act / t_blk on
 // the device.
 // shape_slots[4]: SMs x occupancy of the per-launch kernels with 4, 32, 128, 256 i-particles per CTA
-cudaError_t launch_force_dyn(nb_ctx* c, int* grid, bool query_only);
+cudaError_t launch_force_dyn(nb_ctx* c, int* grid /*[2]*/, bool query_only);
 cudaError_t launch_force_reduce_dyn(nb_ctx* c);
 cudaError_t launch_wait_probe(nb_ctx* c, long long limit_cycles);
 cudaError_t launch_startup_store(nb_ctx* c, int order);
@@ -399,6 +399,7 @@ cudaError_t launch_set_dt(nb_ctx* c, double dt);
 cudaError_t launch_state_in(nb_ctx* c);
 cudaError_t launch_state_out(nb_ctx* c);
 int force_occupancy(nb_ctx* c, int order, int ni);
+int shape_slots(nb_ctx* c, int order, int ni, bool mixed);
 int force_ni(const nb_ctx* c, int64_t n_act);
 void sched_layout(int64_t n, int sm_count, int* per, int* nch);
 int energy_grid(const nb_ctx* c);
