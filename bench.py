@@ -42,6 +42,11 @@ FLOPS_PER_INTERACTION = {4: 60, 6: 97, 8: 144}   # direct N-body flop convention
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 148, 128, 2032.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 76.96, FMA = 2 flops
 FP64_PEAK_TFLOPS = 1.25                                                     # nominal dense FP64
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one mixed force
+# launch over the whole nucleus system (N_act = N = 2^20 + 2, one j-split), from
+# a one-pass ncu capture of that launch; the capture's command and figures are
+# in profiles/force_mixed_order6_nucleus_n1048578.md.
+FORCE_TRAFFIC_BYTES = {("nucleus_plummer_n1048576_2bh", "mixed"): 1.17e9 + 98.72e6}
 
 
 def parse():
@@ -260,7 +265,9 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "tflops_convention": value * flop_pi / world / 1e12 if world else None,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved / FP32_PEAK_TFLOPS,
+                     "traffic": FORCE_TRAFFIC_BYTES.get((wl.name, args.precision)),
+                     "traffic_unit": "DRAM bytes per force launch (ncu)",
                      "note": f"force kernel, {flop_pi} flops per interaction (direct N-body convention); peak "
                              "= 148 SMs x 128 FP32 lanes x 2 x 2032 MHz"},
         "phases_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},

@@ -33,7 +33,7 @@ static cudaError_t run_mixed_ipt(nb_ctx* c, const int32_t* idx, int n_act, int j
     dim3 grid(itiles, jsplit);
     kern<<<grid, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), idx, n_act, (int)c->n,
                                               (int)(c->np / JT), jsplit, (float)(c->eps * c->eps),
-                                              (float)c->eps2_max, c->partial, c->sc, c->F);
+                                              eps2_threshold(c->eps2_max), c->partial, c->sc, c->F);
     return cudaGetLastError();
 }
 
@@ -57,7 +57,7 @@ static cudaError_t run_mixed_jp(nb_ctx* c, const int32_t* idx, int n_act, int js
     dim3 grid(itiles, jsplit);
     kern<<<grid, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), idx, n_act, (int)c->n,
                                               (int)(c->np / JT), jsplit, (float)(c->eps * c->eps),
-                                              (float)c->eps2_max, c->partial, c->sc, c->F);
+                                              eps2_threshold(c->eps2_max), c->partial, c->sc, c->F);
     return cudaGetLastError();
 }
 
@@ -81,7 +81,7 @@ static cudaError_t run_mixed_xs(nb_ctx* c, const int32_t* idx, int n_act, int js
     dim3 grid(itiles, jsplit);
     kern<<<grid, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), idx, n_act, (int)c->n,
                                               (int)(c->np / JT), jsplit, (float)(c->eps * c->eps),
-                                              (float)c->eps2_max, c->partial, c->sc, c->F);
+                                              eps2_threshold(c->eps2_max), c->partial, c->sc, c->F);
     return cudaGetLastError();
 }
 
@@ -237,7 +237,7 @@ static cudaError_t force_dyn_o(nb_ctx* c, int* grid, bool query_only, bool mixed
             grid[1] = c->sm_count * o[1];
             return cudaSuccess;
         }
-        const float e2 = (float)(c->eps * c->eps), e2max = (float)c->eps2_max;
+        const float e2 = (float)(c->eps * c->eps), e2max = eps2_threshold(c->eps2_max);
         k1<<<grid[0], FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), c->act_idx,
                                                    (int)c->n, ntiles, e2, e2max, c->partial, c->sc, c->F);
         k2<<<grid[1], FORCE_NT, smem_big, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), c->act_idx,

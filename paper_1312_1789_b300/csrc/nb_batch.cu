@@ -744,7 +744,8 @@ int batch_force_dispatch(nb_batch* b, int order, const int32_t* list, int n_act,
             const int occ = occ_of(kern, smem);                                                                   \
             if (occ_only) return occ;                                                                             \
             kern<<<nitems, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), list,         \
-                                                        b->items, n_act, (int)c->n, (float)c->eps2_max,          \
+                                                        b->items, n_act, (int)c->n,                               \
+                                                        eps2_threshold(c->eps2_max),                              \
                                                         c->partial, c->sc);                                       \
         } else {                                                                                                  \
             constexpr int RW = fp64_rw(SO);                                                                       \
@@ -888,8 +889,8 @@ int batch_force_dyn_o(nb_batch* b, bool occ_only)
         auto kern = k_batch_force_mixed_dyn<SO, RW>;
         if (occ_only) return occ_of(kern, smem);
         kern<<<b->force_slots, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), c->act_idx,
-                                                             b->d_items, (int)c->n, (float)c->eps2_max, c->partial,
-                                                             c->sc);
+                                                             b->d_items, (int)c->n, eps2_threshold(c->eps2_max),
+                                                             c->partial, c->sc);
     } else {
         constexpr int RW = fp64_rw(SO);
         const size_t smem = (size_t)NSTAGE * JT * RW * 16;

@@ -12,6 +12,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cmath>
 #include <stdint.h>
 
 #include <vector>
@@ -144,6 +145,19 @@ struct DevScalars {
     int stepped;                   // ensemble cycle: clusters stepped in the last cycle
     int next_item;                 // ensemble cycle: next force item to hand out
 };
+
+// Threshold of the dominant-softening test.  A warp whose i-particles all
+// have the system's largest eps^2 takes the pair value eps_i^2 without a
+// per-pair max.  The test compares the float eps^2 of the j-store, which the
+// predictor converts toward zero, so the threshold takes the same
+// conversion: rounded to nearest it can lie above every stored value, and no
+// warp would take the uniform path.
+inline float eps2_threshold(double e2max)
+{
+    float f = (float)e2max;
+    if (std::fabs((double)f) > std::fabs(e2max)) f = std::nextafter(f, 0.0f);
+    return f;
+}
 
 // Launch-shape gate of a device-driven cycle, applied by the thread that
 // publishes the cycle's t_blk and n_act: close the cycle when the block lies
