@@ -407,10 +407,14 @@ __global__ void __launch_bounds__(256) k_predict(const double* __restrict__ m, c
     predict_one<ORDER, MIXED>(i, tp, m, eps2, x, v, d, t, n, np, jstore, tpc, cid);
 }
 
-// Second pass fused with the predictor: once a CTA knows t_blk it predicts
-// its own chunk of particles to it (the last CTA also the padding records up
-// to np).  use_t_end: a device-driven cycle, which predicts nothing past
-// sc->t_end and whose force launch shape CTA 0 sets with the gate.
+// Second pass fused with the predictor.  The grid has one CTA per chunk or
+// per SCHED_NT records, whichever is more: the first nch CTAs compact their
+// chunks, the others only read t_blk from the chunk table; then every CTA
+// predicts SCHED_NT records to t_blk, one per thread (the predictor is
+// bound by memory latency, so it gets a thread per particle rather than the
+// scheduler's PER).  use_t_end: a device-driven cycle, which predicts
+// nothing past sc->t_end and whose force launch shape CTA 0 sets with the
+// gate.
 template <int ORDER, bool MIXED, int PER>
 __global__ void __launch_bounds__(SCHED_NT) k_sched_compact_predict(
     const double* __restrict__ t, const double* __restrict__ dt, int64_t n,
@@ -419,12 +423,25 @@ __global__ void __launch_bounds__(SCHED_NT) k_sched_compact_predict(
     const double* __restrict__ eps2, const double* __restrict__ x, const double* __restrict__ v,
     const double* __restrict__ d, int64_t np, void* __restrict__ jstore, GateArgs gate)
 {
-    const double tb = sched_compact_body<PER>(t, dt, n, cmin, ccnt, nch, idx, sc, use_t_end ? &gate : nullptr);
+    double tb;
+    if ((int)blockIdx.x < nch) {
+        tb = sched_compact_body<PER>(t, dt, n, cmin, ccnt, nch, idx, sc, use_t_end ? &gate : nullptr);
+    } else {
+        __shared__ unsigned long long wk[SCHED_NT / 32];
+        unsigned long long mn = KEY_NONE;
+        for (int k = threadIdx.x; k < nch; k += SCHED_NT) mn = cmin[k] < mn ? cmin[k] : mn;
+        tb = key_time(block_kmin(mn, wk));
+    }
     if (use_t_end && !(tb <= sc->t_end)) return;
-    const int64_t c0 = (int64_t)blockIdx.x * SCHED_NT * PER;
-    const int64_t c1 = blockIdx.x == nch - 1 ? np : min(c0 + (int64_t)SCHED_NT * PER, np);
-    for (int64_t i = c0 + threadIdx.x; i < c1; i += SCHED_NT)
-        predict_one<ORDER, MIXED>(i, tb, m, eps2, x, v, d, t, n, np, jstore, nullptr, nullptr);
+    const int64_t i = (int64_t)blockIdx.x * SCHED_NT + threadIdx.x;
+    if (i < np) predict_one<ORDER, MIXED>(i, tb, m, eps2, x, v, d, t, n, np, jstore, nullptr, nullptr);
+}
+
+// CTAs of the fused second pass: every chunk, and SCHED_NT records per CTA
+static int sched_predict_grid(int nch, int64_t np)
+{
+    const int64_t g = (np + SCHED_NT - 1) / SCHED_NT;
+    return g > nch ? (int)g : nch;
 }
 
 cudaError_t launch_sched_predict(nb_ctx* c, bool use_t_end, const int* shape_slots)
@@ -446,8 +463,9 @@ cudaError_t launch_sched_predict(nb_ctx* c, bool use_t_end, const int* shape_slo
         g.ntab = c->tune_n[pi];
     }
     const bool mixed = c->prec == NB_MIXED;
+    const int gsp = sched_predict_grid(nch, c->np);
 #define NB_SP(O, MX, P)                                                                                             \
-    k_sched_compact_predict<O, MX, P><<<nch, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, c->chunk_min,           \
+    k_sched_compact_predict<O, MX, P><<<gsp, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, c->chunk_min,           \
                                                                        c->chunk_cnt, nch, c->act_idx, c->sc,       \
                                                                        use_t_end ? 1 : 0, c->m, c->eps2, c->x,     \
                                                                        c->v, c->d, c->np, c->jstore, g)
