@@ -46,7 +46,7 @@ FP64_PEAK_TFLOPS = 1.25                                                     # no
 # launch over the whole nucleus system (N_act = N = 2^20 + 2, one j-split), from
 # a one-pass ncu capture of that launch; the capture's command and figures are
 # in profiles/force_mixed_order6_nucleus_n1048578.md.
-FORCE_TRAFFIC_BYTES = {("nucleus_plummer_n1048576_2bh", "mixed"): 1.17e9 + 98.72e6}
+FORCE_TRAFFIC_BYTES = {("nucleus_plummer_n1048576_2bh", "mixed"): 1.18e9 + 99.65e6}
 
 
 def parse():
@@ -635,6 +635,15 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
         out["cpu_baseline"] = {"value": n_s * n / el, "unit": "interactions/s", "cores": nth, "kind": "oracle",
                                "sample": f"force of {n_s} of {n} particles on all {n} (long-double direct sum), "
                                          f"{el:.1f} s"}
+        # the same oracle on one host thread
+        n_1, _ = oracle_rate(wl, n_target_s=4.0, nthreads=1)
+        idx = np.sort(np.random.default_rng(4).choice(n, n_1, replace=False)).astype(np.int32)
+        t0 = time.perf_counter()
+        orc.force(wl.m, wl.eps2, wl.x, wl.v, np.zeros_like(wl.x), None, order=wl.order, idx=idx, nthreads=1)
+        el = time.perf_counter() - t0
+        out["cpu_baseline"]["one_thread"] = {
+            "value": n_1 * n / el, "unit": "interactions/s", "cores": 1,
+            "sample": f"force of {n_1} of {n} particles on all {n}, {el:.1f} s"}
     except Exception as e:  # pragma: no cover
         out["cpu_baseline"] = {"error": repr(e)}
     torch.cuda.synchronize()

@@ -377,6 +377,16 @@ __device__ __forceinline__ IMixed2 pack_pair(const IMixed& a, const IMixed& z, f
     return r;
 }
 
+// Resident CTAs per SM that the persistent kernels holding several mixed
+// variants are compiled for: 4 at orders <= 6, 3 at order 8 -- the CTAs that
+// the shared memory of the two-per-thread variant admits.
+__host__ __device__ constexpr int dyn_min_ctas(int order) { return order >= 8 ? 3 : 4; }
+// The per-launch two-per-thread kernel: at orders <= 6 the same hint lets
+// ptxas use the registers that occupancy leaves free (116 instead of 96 at
+// order 6: 3 % faster); at order 8 it is left to ptxas (compiled for 3 CTAs
+// it ran 0.6 % slower).
+__host__ __device__ constexpr int xs_min_ctas(int order) { return order >= 8 ? 1 : dyn_min_ctas(order); }
+
 // Dynamic shared memory of the force variants that keep their double-single
 // sums in shared memory (NP lane-pairs per thread): the TMA ring, then
 // (hi, lo) float2 [NC][2 NP][FORCE_NT].
@@ -666,7 +676,7 @@ __device__ __forceinline__ void force_block_mixed_xs(const float4* __restrict__ 
 }
 
 template <int ORDER, int RW, bool PAIR, int NP>
-__global__ void __launch_bounds__(FORCE_NT) k_force_mixed_xs(const float4* __restrict__ js,
+__global__ void __launch_bounds__(FORCE_NT, xs_min_ctas(ORDER)) k_force_mixed_xs(const float4* __restrict__ js,
                                                              const int32_t* __restrict__ idx, int n_act, int n,
                                                              int ntiles, int jsplit, float eps2u, float eps2max,
                                                              double* __restrict__ partial, DevScalars* sc, double* F)
@@ -1034,11 +1044,6 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_fp64(const double2* __restri
 // capped by the partial-sum buffer); an active set past t_end makes the
 // cycle idle.
 
-// Resident CTAs per SM that the kernels holding several mixed variants are
-// compiled for: 4 at orders <= 6, 3 at order 8 (whose larger chain then gets
-// the registers instead of spilling).
-__host__ __device__ constexpr int dyn_min_ctas(int order) { return order >= 8 ? 3 : 4; }
-
 // Persistent force: a fixed grid walks the (i-tile, split) items of the
 // device-chosen shape.  SMALL: the variants of up to FORCE_NT i-particles per
 // CTA (4, 32, FORCE_NT), compiled for dyn_min_ctas resident CTAs; otherwise
@@ -1058,7 +1063,7 @@ __device__ __noinline__ void xs_item(const float4* __restrict__ js, const int32_
 }
 
 template <int ORDER, int RW, bool PAIR, bool SMALL>
-__global__ void __launch_bounds__(FORCE_NT, SMALL ? dyn_min_ctas(ORDER) : 1)
+__global__ void __launch_bounds__(FORCE_NT, dyn_min_ctas(ORDER))
     k_force_mixed_dyn(const float4* __restrict__ js, const int32_t* __restrict__ idx, int n, int ntiles, float eps2u,
                       float eps2max, double* __restrict__ partial, DevScalars* sc, double* F)
 {

@@ -1,9 +1,11 @@
 """Small, self-contained force case for profilers (ncu) and quick timing.
 
     python -m paper_1312_1789_b300.profile_case [--n-act 4096] [--precision mixed|fp64] [--repeat 2]
+                                                [--workload nucleus|cusp]
 
-Builds the galactic-nucleus system (2^20 Plummer stars + two black holes),
-runs the start-up (two force launches over every particle), predicts, then
+Builds the galactic-nucleus system (2^20 Plummer stars + two black holes,
+6th order) or the cusp (2^18 Dehnen stars + a black-hole binary, 8th order),
+runs the start-up (force launches over every particle), predicts, then
 launches the force kernel --repeat times on one block of --n-act particles.
 With ncu, `-k regex:k_force -s 2 -c 1` captures the first block launch.
 """
@@ -21,8 +23,9 @@ def main():
     p.add_argument("--n-act", type=int, default=4096)
     p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     p.add_argument("--repeat", type=int, default=2)
+    p.add_argument("--workload", choices=["nucleus", "cusp"], default="nucleus")
     a = p.parse_args()
-    wl = ics.standard_workload(2)
+    wl = ics.standard_workload(2 if a.workload == "nucleus" else 3)
     prec = nb.NB_MIXED if a.precision == "mixed" else nb.NB_FP64
     ctx = nb.NBody(wl.n, wl.order, 0.0, prec)
     ctx.set_softening(np.sqrt(wl.eps2))
