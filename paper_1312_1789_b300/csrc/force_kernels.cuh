@@ -1067,6 +1067,8 @@ __global__ void __launch_bounds__(FORCE_NT, dyn_min_ctas(ORDER))
     k_force_mixed_dyn(const float4* __restrict__ js, const int32_t* __restrict__ idx, int n, int ntiles, float eps2u,
                       float eps2max, double* __restrict__ partial, DevScalars* sc, double* F)
 {
+    pdl_wait();
+    pdl_release();
     if (sc->idle) return;
     const int ni = sc->ni;
     if (SMALL != (ni <= FORCE_NT)) return;
@@ -1100,6 +1102,8 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_fp64_dyn(const double2* __re
                                                              double eps2u, double* __restrict__ partial,
                                                              DevScalars* sc, double* F)
 {
+    pdl_wait();
+    pdl_release();
     if (sc->idle) return;
     const int n_act = (int)sc->n_act, it = sc->itiles, jsplit = sc->jsplit;
     for (int w = blockIdx.x; w < it * jsplit; w += gridDim.x) {
@@ -1127,6 +1131,8 @@ __global__ void __launch_bounds__(RED_NT) k_force_reduce_dyn(const double* __res
                                                              const DevScalars* __restrict__ sc,
                                                              double* __restrict__ F)
 {
+    pdl_wait();
+    pdl_release();
     if (sc->idle || sc->jsplit == 1) return;
     const int n_act = (int)sc->n_act, jsplit = sc->jsplit;
     const int g = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;

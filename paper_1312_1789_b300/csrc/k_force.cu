@@ -238,10 +238,12 @@ static cudaError_t force_dyn_o(nb_ctx* c, int* grid, bool query_only, bool mixed
             return cudaSuccess;
         }
         const float e2 = (float)(c->eps * c->eps), e2max = eps2_threshold(c->eps2_max);
-        k1<<<grid[0], FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), c->act_idx,
-                                                   (int)c->n, ntiles, e2, e2max, c->partial, c->sc, c->F);
-        k2<<<grid[1], FORCE_NT, smem_big, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), c->act_idx,
-                                                       (int)c->n, ntiles, e2, e2max, c->partial, c->sc, c->F);
+        const float4* js = reinterpret_cast<const float4*>(c->jstore);
+        cudaError_t e = launch_k(k1, dim3(grid[0]), dim3(FORCE_NT), smem, c->stream, c->pdl != 0, js, c->act_idx,
+                                 (int)c->n, ntiles, e2, e2max, c->partial, c->sc, c->F);
+        if (e != cudaSuccess) return e;
+        return launch_k(k2, dim3(grid[1]), dim3(FORCE_NT), smem_big, c->stream, c->pdl != 0, js, c->act_idx,
+                        (int)c->n, ntiles, e2, e2max, c->partial, c->sc, c->F);
     } else {
         constexpr int RW = fp64_rw(O);
         const size_t smem = (size_t)NSTAGE * JT * RW * 16;
@@ -253,8 +255,9 @@ static cudaError_t force_dyn_o(nb_ctx* c, int* grid, bool query_only, bool mixed
             grid[0] = grid[1] = c->sm_count * o;
             return cudaSuccess;
         }
-        k<<<grid[0], FORCE_NT, smem, c->stream>>>(reinterpret_cast<const double2*>(c->jstore), c->act_idx,
-                                                  (int)c->n, ntiles, c->eps * c->eps, c->partial, c->sc, c->F);
+        return launch_k(k, dim3(grid[0]), dim3(FORCE_NT), smem, c->stream, c->pdl != 0,
+                        reinterpret_cast<const double2*>(c->jstore), c->act_idx, (int)c->n, ntiles,
+                        c->eps * c->eps, c->partial, c->sc, c->F);
     }
     return cudaGetLastError();
 }
@@ -287,10 +290,11 @@ int shape_slots(nb_ctx* c, int order, int ni, bool mixed)
 cudaError_t launch_force_reduce_dyn(nb_ctx* c)
 {
     const int nb = c->sm_count * 8;
-    if (c->order == 4) k_force_reduce_dyn<ncomp(4), pot_comp(4)><<<nb, RED_NT, 0, c->stream>>>(c->partial, c->sc, c->F);
-    else if (c->order == 6) k_force_reduce_dyn<ncomp(6), pot_comp(6)><<<nb, RED_NT, 0, c->stream>>>(c->partial, c->sc, c->F);
-    else k_force_reduce_dyn<ncomp(8), pot_comp(8)><<<nb, RED_NT, 0, c->stream>>>(c->partial, c->sc, c->F);
-    return cudaGetLastError();
+    const DevScalars* sc = c->sc;
+    auto k = c->order == 4   ? k_force_reduce_dyn<ncomp(4), pot_comp(4)>
+             : c->order == 6 ? k_force_reduce_dyn<ncomp(6), pot_comp(6)>
+                             : k_force_reduce_dyn<ncomp(8), pot_comp(8)>;
+    return launch_k(k, dim3(nb), dim3(RED_NT), 0, c->stream, c->pdl != 0, (const double*)c->partial, sc, c->F);
 }
 
 // Self-test of the bounded wait every kernel uses: one CTA waits on an

@@ -91,6 +91,8 @@ __global__ void __launch_bounds__(SCHED_NT) k_sched_chunk(const double* __restri
                                                           int64_t n, unsigned long long* __restrict__ cmin,
                                                           int32_t* __restrict__ ccnt, DevScalars* sc)
 {
+    pdl_wait();
+    pdl_release();
     __shared__ unsigned long long wk[SCHED_NT / 32];
     __shared__ int wi[SCHED_NT / 32];
     const int64_t i0 = ((int64_t)blockIdx.x * SCHED_NT + threadIdx.x) * PER;
@@ -423,6 +425,8 @@ __global__ void __launch_bounds__(SCHED_NT) k_sched_compact_predict(
     const double* __restrict__ eps2, const double* __restrict__ x, const double* __restrict__ v,
     const double* __restrict__ d, int64_t np, void* __restrict__ jstore, GateArgs gate)
 {
+    pdl_wait();
+    pdl_release();
     double tb;
     if ((int)blockIdx.x < nch) {
         tb = sched_compact_body<PER>(t, dt, n, cmin, ccnt, nch, idx, sc, use_t_end ? &gate : nullptr);
@@ -462,15 +466,17 @@ cudaError_t launch_sched_predict(nb_ctx* c, bool use_t_end, const int* shape_slo
         g.tab = c->d_tune + pi * TUNE_MAX;
         g.ntab = c->tune_n[pi];
     }
-    const bool mixed = c->prec == NB_MIXED;
+    const bool mixed = c->prec == NB_MIXED, pdl = c->pdl != 0;
     const int gsp = sched_predict_grid(nch, c->np);
+    cudaError_t e = cudaSuccess;
 #define NB_SP(O, MX, P)                                                                                             \
-    k_sched_compact_predict<O, MX, P><<<gsp, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, c->chunk_min,           \
-                                                                       c->chunk_cnt, nch, c->act_idx, c->sc,       \
-                                                                       use_t_end ? 1 : 0, c->m, c->eps2, c->x,     \
-                                                                       c->v, c->d, c->np, c->jstore, g)
+    e = launch_k(k_sched_compact_predict<O, MX, P>, dim3(gsp), dim3(SCHED_NT), 0, c->stream, pdl, c->t, c->dt,     \
+                 c->n, c->chunk_min, c->chunk_cnt, nch, c->act_idx, c->sc, use_t_end ? 1 : 0, c->m, c->eps2, c->x, \
+                 c->v, c->d, c->np, c->jstore, g)
 #define NB_S(P)                                                                                                     \
-    k_sched_chunk<P><<<nch, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, c->chunk_min, c->chunk_cnt, c->sc);      \
+    e = launch_k(k_sched_chunk<P>, dim3(nch), dim3(SCHED_NT), 0, c->stream, pdl, c->t, c->dt, c->n, c->chunk_min,  \
+                 c->chunk_cnt, c->sc);                                                                              \
+    if (e != cudaSuccess) return e;                                                                                 \
     if (c->order == 4) {                                                                                            \
         if (mixed) NB_SP(4, true, P); else NB_SP(4, false, P);                                                      \
     } else if (c->order == 6) {                                                                                     \
@@ -481,7 +487,7 @@ cudaError_t launch_sched_predict(nb_ctx* c, bool use_t_end, const int* shape_slo
     NB_SCHED_PER(per, NB_S)
 #undef NB_S
 #undef NB_SP
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_predict(nb_ctx* c, double t, const double* tpc, const int32_t* cid, const DevScalars* dyn)
@@ -886,6 +892,8 @@ __global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fid
                                                  const double* __restrict__ tfc, const int32_t* __restrict__ cid,
                                                  const DevScalars* dyn)
 {
+    pdl_wait();
+    pdl_release();
     constexpr int MM = ORDER / 2;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (dyn) {  // device-driven cycle: the block of the scheduler, unless idle
@@ -958,10 +966,12 @@ cudaError_t launch_correct(nb_ctx* c, const double* tfc, const int32_t* cid, con
     const int nt = 128;
     const int nb = (int)(((dyn ? c->n : c->f_n) + nt - 1) / nt);
     const bool mixed = c->pred_prec == NB_MIXED;
+    const bool pdl = c->pdl != 0;
+    cudaError_t e;
 #define NB_CORR(O, MX)                                                                                           \
-    k_correct<O, MX><<<nb, nt, 0, c->stream>>>(dyn ? c->act_idx : c->f_idx, (int)c->f_n, c->f_t, c->F, c->n,   \
-                                               c->np, c->x, c->v, c->d, c->t, c->dt, c->pot, c->eta, c->dt_max, \
-                                               c->dt_min, c->noise[mixed ? 1 : 0], c->sc, tfc, cid, dyn)
+    e = launch_k(k_correct<O, MX>, dim3(nb), dim3(nt), 0, c->stream, pdl, dyn ? c->act_idx : c->f_idx,         \
+                 (int)c->f_n, c->f_t, c->F, c->n, c->np, c->x, c->v, c->d, c->t, c->dt, c->pot, c->eta,         \
+                 c->dt_max, c->dt_min, c->noise[mixed ? 1 : 0], c->sc, tfc, cid, dyn)
     if (c->order == 4) {
         if (mixed) NB_CORR(4, true); else NB_CORR(4, false);
     } else if (c->order == 6) {
@@ -970,7 +980,7 @@ cudaError_t launch_correct(nb_ctx* c, const double* tfc, const int32_t* cid, con
         if (mixed) NB_CORR(8, true); else NB_CORR(8, false);
     }
 #undef NB_CORR
-    return cudaGetLastError();
+    return e;
 }
 
 // ============================================================== start-up

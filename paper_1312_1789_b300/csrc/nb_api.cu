@@ -241,12 +241,16 @@ int build_graph(nb_ctx* c)
     c->stream = c->graph_stream;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(c->graph_stream, cudaStreamCaptureModeThreadLocal);
+    // every kernel of the cycle may be scheduled while its predecessor runs
+    // (programmatic dependent launch; each waits for it before reading)
+    c->pdl = 1;
     for (int r = 0; e == cudaSuccess && r < c->graph_cycles; ++r) {
         if ((e = launch_sched_predict(c, true, slots)) != cudaSuccess) break;
         if ((e = launch_force_dyn(c, grid, false)) != cudaSuccess) break;
         if ((e = launch_force_reduce_dyn(c)) != cudaSuccess) break;
         if ((e = launch_correct(c, nullptr, nullptr, c->sc)) != cudaSuccess) break;
     }
+    c->pdl = 0;
     const cudaError_t e2 = cudaStreamEndCapture(c->graph_stream, &g);
     c->stream = saved;
     if (e == cudaSuccess) e = e2;

@@ -213,6 +213,17 @@ __device__ __forceinline__ void raise_status(DevScalars* sc, int code)
     atomicCAS(&sc->status, NB_OK, code);
 }
 
+// ------------------------------------------- programmatic dependent launch
+// The kernels of a block cycle start with pdl_wait() then pdl_release().
+// Launched with programmatic stream serialization (launch_k, pdl = true), a
+// kernel's CTAs may become resident while its predecessor in the stream still
+// runs: pdl_wait() holds them until that grid has completed and its writes are
+// visible, so nothing is read early.  pdl_release() lets the next kernel's
+// CTAs be scheduled once every CTA of this grid has started.  Launched
+// without the attribute, both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ------------------------------------------------------------ bulk copies
 __device__ __forceinline__ uint32_t smem_addr(const void* p)
 {
@@ -369,6 +380,7 @@ struct nb_ctx {
     int tune_n[2] = {0, 0};
     nb::TuneEntry* d_tune = nullptr;  // [2][TUNE_MAX]
     // device-driven cycles captured in a CUDA graph (nb_set_graph)
+    int pdl = 0;  // launch the cycle's kernels with programmatic stream serialization
     int graph_cycles = 0;
     cudaGraphExec_t graph_exec = nullptr;
     cudaStream_t graph_stream = nullptr;
@@ -420,4 +432,23 @@ int energy_grid(const nb_ctx* c);
 // Message returned by nb_last_error(NULL) (calls made without a context).
 void set_global_error(const char* msg);
 
+
+// Launch kern<<<grid, block, smem, st>>>(args...), with programmatic stream
+// serialization when pdl is set (the kernel must start with pdl_wait()).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool pdl,
+                     Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
 }  // namespace nb
