@@ -12,7 +12,8 @@ Printed JSON line (rank 0): value = interactions/s over the timed steps with
 the state resident in HBM; e2e = the same through the C ABI with host state
 copied in and out every step; roofline of the force kernel (CUDA events on its
 stream); the FP64 path on a 4096-particle block of the same system; the force
-rate of both paths on each single-system workload; energy error and
+rate of both paths on each single-system workload and on the nucleus at 4th
+order; energy error and
 whole-run throughput of both paths on the 65536-particle Plummer sphere
 (host-driven, CUDA-graph and autotuned cycles); energy and binary-element
 drift of both paths on the 8th-order cusp nucleus; the 256-cluster ensemble;
@@ -46,7 +47,7 @@ FP64_PEAK_TFLOPS = 1.25                                                     # no
 # launch over the whole nucleus system (N_act = N = 2^20 + 2, one j-split), from
 # a one-pass ncu capture of that launch; the capture's command and figures are
 # in profiles/force_mixed_order6_nucleus_n1048578.md.
-FORCE_TRAFFIC_BYTES = {("nucleus_plummer_n1048576_2bh", "mixed"): 1.18e9 + 99.65e6}
+FORCE_TRAFFIC_BYTES = {("nucleus_plummer_n1048576_2bh", "mixed"): 1.18e9 + 99.99e6}
 
 
 def parse():
@@ -522,11 +523,15 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
     except Exception as e:  # pragma: no cover
         out["plummer_1k_end_to_end"] = {"error": repr(e)}
     # ---- force kernel at N_act = N on each single-system workload (mixed),
-    #      and the FP64 path on a 4096-particle block of each
+    #      and the FP64 path on a 4096-particle block of each; last, the
+    #      nucleus at 4th order (acc and jerk only, 60 flops per interaction)
     try:
+        import dataclasses
         table = {}
-        for k in range(4):
-            w = ics.standard_workload(k) if k != 2 else wl
+        for k in range(5):
+            w = ics.standard_workload(k) if k not in (2, 4) else wl
+            if k == 4:
+                w = dataclasses.replace(wl, order=4, name=wl.name + "_order4")
             fl = FLOPS_PER_INTERACTION[w.order]
             row = {"n": w.n, "order": w.order}
             for name, p, na in (("mixed", nb.NB_MIXED, w.n), ("fp64", nb.NB_FP64, min(4096, w.n))):

@@ -174,6 +174,17 @@ int nb_get_predicted(nb_ctx* ctx, double* xp, double* vp, double* ap, double* jp
  * particle, for active sets of up to 256 or 24); any output may be NULL.   */
 int nb_get_launch(nb_ctx* ctx, int* i_tiles, int* j_splits, int* i_per_cta);
 
+/* Test hook with no counterpart in the paper: warps of the mixed force
+ * kernels that took the per-pair softening form since nb_create or the
+ * previous call, which resets the count; n_warps must not be NULL.  With
+ * per-particle softening the pair value is max(eps_i^2, eps_j^2) (this
+ * library's reading; the paper gives only the star and hole values).  A warp
+ * whose i-particles all carry the system's largest eps^2 has that maximum in
+ * eps_i^2 and takes it without a per-pair max; only the other warps take the
+ * per-pair form.  Synchronises; NB_ERR_ARG on a NULL argument, NB_ERR_CUDA
+ * on a CUDA failure.                                                       */
+int nb_get_pair_warps(nb_ctx* ctx, int64_t* n_warps);
+
 /* cycles > 0: nb_step_until replays a CUDA graph of that many device-driven
  * block cycles (scheduler, predictor, force, corrector with the active-set
  * size, block time and force launch shape decided on the device), checking

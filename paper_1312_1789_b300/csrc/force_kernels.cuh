@@ -54,6 +54,14 @@ __device__ __forceinline__ double guard_rinv_d(double r2)
     return ri;
 }
 
+// Per-particle softening: a warp whose i-particles all carry the system's
+// largest eps^2 takes eps_i^2 as the pair value (no per-pair max or R^2 = 0
+// guard); the others take the per-pair form, and lane 0 counts them.
+__device__ __forceinline__ void count_pair_warp(DevScalars* sc, bool pair_form)
+{
+    if (pair_form && (threadIdx.x & 31) == 0) atomicAdd(&sc->pair_warps, 1ull);
+}
+
 // Wait for the copies still in flight after a timeout (bounded again), then
 // the caller returns.  Called by thread 0 only.
 static __device__ void drain_after_timeout(uint64_t* bars, int k, int nt)
@@ -475,6 +483,7 @@ __device__ __forceinline__ void force_block_mixed(const float4* __restrict__ js,
     // particle pairs with the constant eps_i^2: the per-pair max and the
     // R^2 = 0 guard drop out (same results, fewer instructions).
     const bool dom = PAIR && __all_sync(0xffffffffu, dom_lane);
+    count_pair_warp(sc, PAIR && !dom);
 
     float hi[IPT][NC], lo[IPT][NC];
 #pragma unroll
@@ -606,6 +615,7 @@ __device__ __forceinline__ void force_block_mixed_xs(const float4* __restrict__ 
         I2[pp] = pack_pair(I[0], I[1], e[0], e[1]);
     }
     const bool dom = PAIR && __all_sync(0xffffffffu, dom_lane);
+    count_pair_warp(sc, PAIR && !dom);
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
@@ -763,6 +773,7 @@ __device__ __forceinline__ void force_block_mixed_jp(const float4* __restrict__ 
     }
     const float ei2 = PAIR ? I.i1.w : eps2u;
     const bool dom = PAIR && __all_sync(0xffffffffu, ei2 >= eps2max && ei2 > 0.0f);
+    count_pair_warp(sc, PAIR && !dom);
     const IMixed2 I2 = pack_pair(I, I, ei2, ei2);
 
     float hi[NC], lo[NC];

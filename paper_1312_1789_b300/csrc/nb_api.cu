@@ -917,6 +917,17 @@ int nb_get_force(nb_ctx* c, double* acc, double* jerk, double* snap, double* cra
     return NB_OK;
 }
 
+int nb_get_pair_warps(nb_ctx* c, int64_t* n_warps)
+{
+    if (!c || !n_warps) return NB_ERR_ARG;
+    unsigned long long v = 0;
+    NB_CUDA(c, cudaMemcpyAsync(&v, &c->sc->pair_warps, sizeof v, cudaMemcpyDeviceToHost, c->stream));
+    NB_CUDA(c, cudaMemsetAsync(&c->sc->pair_warps, 0, sizeof v, c->stream));
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    *n_warps = (int64_t)v;
+    return NB_OK;
+}
+
 int nb_get_predicted(nb_ctx* c, double* xp, double* vp, double* ap, double* jp)
 {
     if (!c) return NB_ERR_ARG;

@@ -144,6 +144,7 @@ struct DevScalars {
     long long blocks, inter;       // device-driven cycle: blocks (cycles) taken, interactions
     int stepped;                   // ensemble cycle: clusters stepped in the last cycle
     int next_item;                 // ensemble cycle: next force item to hand out
+    unsigned long long pair_warps; // mixed force: warps that took the per-pair softening form
 };
 
 // Threshold of the dominant-softening test.  A warp whose i-particles all

@@ -55,6 +55,7 @@ SIGNATURES = {
     "nb_get_force": (C.c_int, [_P, _D, _D, _D, _D, _D]),
     "nb_get_predicted": (C.c_int, [_P, _D, _D, _D, _D]),
     "nb_get_launch": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "nb_get_pair_warps": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "nb_set_jsplit": (C.c_int, [_P, C.c_int]),
     "nb_version": (C.c_char_p, []),
     "nb_set_block_step": (C.c_int, [_P, C.c_double]),
@@ -328,6 +329,12 @@ class NBody:
         tot = C.c_int64()
         self._check(self._L.nb_get_profile(self._h, _d(ms), nl.ctypes.data_as(_I64), C.byref(tot)))
         return {p: (float(ms[k]), int(nl[k])) for k, p in enumerate(PHASES)}, tot.value
+
+    def get_pair_warps(self) -> int:
+        """Warps of the mixed force that took the per-pair softening form since the last call."""
+        n = C.c_int64()
+        self._check(self._L.nb_get_pair_warps(self._h, C.byref(n)))
+        return n.value
 
     def get_launch(self):
         a, b, c = C.c_int(), C.c_int(), C.c_int()

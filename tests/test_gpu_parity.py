@@ -102,6 +102,34 @@ def test_force_parity_two_particles_per_thread(order, kind):
     ctx.close()
 
 
+def test_uniform_softening_form_on_star_warps():
+    # Per-particle softening: a warp whose i-particles all carry the largest
+    # eps^2 takes it as the pair value, the others take the per-pair max.
+    # Both forms give the same bits, so only the kernel's warp count shows
+    # which ran.  Stars at 1e-5 (eps^2 = 1e-10 lies below its nearest float,
+    # so a threshold rounded to nearest misses the stored, truncated value),
+    # two unsoftened holes listed first: exactly warp 0 of the first i-tile
+    # per j-split takes the per-pair form; without the holes none does.
+    n = 2 * 1024 + 77
+    m, x, v, _ = _system(n, 91, "holes")
+    for holes in (True, False):
+        eps2 = np.full(n, 1e-10)
+        if holes:
+            eps2[-2:] = 0.0
+        ctx = make_ctx(m, x, v, eps2, 6, nb.NB_MIXED, pair=True)
+        tb, _ = ctx.next_block()
+        ctx.predict(tb)
+        idx = np.concatenate([[n - 2, n - 1], np.arange(n - 2)]).astype(np.int32)
+        ctx.get_pair_warps()
+        for js in (0, 1, 5):
+            ctx.set_jsplit(js)
+            ctx.force(idx)
+            _, jsplit, ni = ctx.get_launch()
+            assert ni == 256
+            assert ctx.get_pair_warps() == (jsplit if holes else 0), (holes, js, jsplit)
+        ctx.close()
+
+
 # i-particles per CTA of the mixed force for an active-set size: 4 up to 24
 # active, 32 up to 256, 128 below 512, then 256 (two per thread).
 def _expected_ni(n_act):
