@@ -465,12 +465,12 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
             e0 = sum(c2.energy())
             c2.set_precision(p)
             tune_s = None
-            if tune:
+            c2.set_graph(cyc)
+            if tune:  # after set_graph: tuned with the kernels graph cycles run
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 c2.autotune(tune)
                 tune_s = time.perf_counter() - t0
-            c2.set_graph(cyc)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             nblk, ni = c2.step_until(t_end)

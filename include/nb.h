@@ -196,7 +196,11 @@ int nb_set_graph(nb_ctx* ctx, int cycles);
 /* Autotuner of the force launch shape.  For active-set sizes 1, 2, 4, ...
  * up to N it times candidate launch variants (i-particles per CTA) and
  * j-split counts on the context's own store (CUDA events on its stream, best
- * of `reps` runs each) and keeps the fastest per size class; later forces of
+ * of `reps` runs each) and keeps the fastest per size class.  It times the
+ * kernels of the context's current mode: after nb_set_graph(cycles > 0) the
+ * persistent kernels of device-driven cycles, otherwise the per-launch
+ * kernels of host-driven ones (call nb_set_graph first to tune graph
+ * replays).  Later forces of
  * the context in the current precision (host- and device-driven alike) take
  * their shape from that table: class floor(log2(n_act)), the tuned variant,
  * the split count scaled to keep the tuned number of CTAs.  reps <= 0 drops

@@ -501,6 +501,38 @@ static int time_shape(nb_ctx* c, int64_t na, int ni, int js, int reps, cudaEvent
     return sync_scalars(c);
 }
 
+// The same for a device-driven cycle: the shape written into the device
+// scalars, the persistent force kernels and the split reduction, as a
+// replayed cycle runs them (the active list must hold particles 0..na-1).
+static int time_shape_dyn(nb_ctx* c, int64_t na, int ni, int js, int reps, cudaEvent_t e0, cudaEvent_t e1,
+                          float* best)
+{
+    DevScalars* h = c->h_sc;
+    NB_CUDA(c, cudaMemcpyAsync(h, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    h->idle = 0;
+    h->n_act = na;
+    h->ni = ni;
+    h->itiles = (int)((na + ni - 1) / ni);
+    h->jsplit = js;
+    NB_CUDA(c, cudaMemcpyAsync(c->sc, h, sizeof(DevScalars), cudaMemcpyHostToDevice, c->stream));
+    int grid[2] = {0, 0};
+    NB_CUDA(c, launch_force_dyn(c, grid, true));
+    *best = INFINITY;
+    for (int r = -1; r < reps; ++r) {  // r = -1: untimed warm-up
+        NB_CUDA(c, cudaEventRecord(e0, c->stream));
+        NB_CUDA(c, launch_force_dyn(c, grid, false));
+        NB_CUDA(c, launch_force_reduce_dyn(c));
+        NB_CUDA(c, cudaEventRecord(e1, c->stream));
+        NB_CUDA(c, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        NB_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+        if (r >= 0 && ms < *best) *best = ms;
+    }
+    c->n_launch += (int64_t)(reps + 1) * (c->prec == NB_MIXED ? 3 : 2);
+    return sync_scalars(c);
+}
+
 int nb_autotune(nb_ctx* c, int reps)
 {
     if (!c) return NB_ERR_ARG;
@@ -514,6 +546,12 @@ int nb_autotune(nb_ctx* c, int reps)
         int64_t na0;
         NB_TRY(nb_next_block(c, &tb, nullptr, &na0));
         NB_TRY(do_predict(c, tb));
+        // graph mode set: time the persistent kernels its cycles run, on the
+        // active list 0..n-1
+        const bool dyn = c->graph_cycles > 0;
+        if (dyn)
+            NB_CUDA(c, cudaMemcpyAsync(c->act_idx, c->all_idx, (size_t)c->n * sizeof(int32_t),
+                                       cudaMemcpyDeviceToDevice, c->stream));
         cudaEvent_t e0, e1;
         NB_CUDA(c, cudaEventCreate(&e0));
         NB_CUDA(c, cudaEventCreate(&e1));
@@ -553,7 +591,8 @@ int nb_autotune(nb_ctx* c, int reps)
                     if (dup) continue;
                     tried[nt++] = (int)js;
                     float ms;
-                    rc = time_shape(c, na, ni, (int)js, reps, e0, e1, &ms);
+                    rc = dyn ? time_shape_dyn(c, na, ni, (int)js, reps, e0, e1, &ms)
+                             : time_shape(c, na, ni, (int)js, reps, e0, e1, &ms);
                     if (rc == NB_OK && ms < best) {
                         best = ms;
                         e = TuneEntry{ni, (int)js, it, ms};

@@ -68,14 +68,19 @@ def test_autotune_fp64_table_is_per_precision():
     ctx.close()
 
 
-def test_autotuned_graph_cycles_match_host_cycles_bitwise():
+@pytest.mark.parametrize("tune_graph", [False, True])
+def test_autotuned_graph_cycles_match_host_cycles_bitwise(tune_graph):
     # One measured table, installed in both contexts (a second measurement
-    # could pick other shapes, whose rounding differs).
+    # could pick other shapes, whose rounding differs).  tune_graph: measured
+    # with the persistent kernels of graph cycles (nb_set_graph first).
     n = 1800
     m, x, v = ics.plummer(n, 23)
     ctx = make_ctx(m, x, v, 1e-8, 6, nb.NB_MIXED)
+    if tune_graph:
+        ctx.set_graph(6)
     ctx.autotune(1)
     table = ctx.get_tuning()
+    assert len(table) == 11 and all(e[1] in (4, 32, 128, 256) for e in table)
     ctx.close()
     states = []
     for cycles in (0, 6):
