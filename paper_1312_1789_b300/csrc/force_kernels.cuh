@@ -836,9 +836,12 @@ __device__ __forceinline__ void force_block_mixed_jp(const float4* __restrict__ 
 }
 
 // One system, j-parallel form: blockIdx.x = i-tile of FORCE_NT / JP active
-// particles, blockIdx.y = j-split of the whole store.
+// particles, blockIdx.y = j-split of the whole store.  Compiled for the
+// resident CTAs of the persistent kernels (dyn_min_ctas): at order 8, 3 CTAs
+// give the chain 156-161 registers without spills (4 CTAs: 128 registers and
+// spills, 3 % slower on 64-200 active particles of the cusp).
 template <int ORDER, int RW, bool PAIR, int JP>
-__global__ void __launch_bounds__(FORCE_NT, 4) k_force_mixed_jp(const float4* __restrict__ js,
+__global__ void __launch_bounds__(FORCE_NT, dyn_min_ctas(ORDER)) k_force_mixed_jp(const float4* __restrict__ js,
                                                              const int32_t* __restrict__ idx, int n_act, int n,
                                                              int ntiles, int jsplit, float eps2u, float eps2max,
                                                              double* __restrict__ partial, DevScalars* sc, double* F)
