@@ -196,7 +196,9 @@ int nb_set_graph(nb_ctx* ctx, int cycles);
 /* Autotuner of the force launch shape.  For active-set sizes 1, 2, 4, ...
  * up to N it times candidate launch variants (i-particles per CTA) and
  * j-split counts on the context's own store (CUDA events on its stream, best
- * of `reps` runs each) and keeps the fastest per size class.  It times the
+ * of `reps` runs each) and keeps per size class the fastest, if it beat the
+ * analytic rule's own shape by 3 % at that size (else the class keeps the
+ * rule: variant 0 in nb_get_tuning, with the rule's time).  It times the
  * kernels of the context's current mode: after nb_set_graph(cycles > 0) the
  * persistent kernels of device-driven cycles, otherwise the per-launch
  * kernels of host-driven ones (call nb_set_graph first to tune graph

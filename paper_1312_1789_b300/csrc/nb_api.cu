@@ -533,6 +533,9 @@ static int time_shape_dyn(nb_ctx* c, int64_t na, int ni, int js, int reps, cudaE
     return sync_scalars(c);
 }
 
+// A tuned shape must be this much faster than the analytic rule's to be kept.
+constexpr float TUNE_MARGIN = 0.97f;
+
 int nb_autotune(nb_ctx* c, int reps)
 {
     if (!c) return NB_ERR_ARG;
@@ -574,11 +577,15 @@ int nb_autotune(nb_ctx* c, int reps)
             if (na <= 512) cand[nv++] = 32;
             if (!mixed || na <= 16384) cand[nv++] = FORCE_NT;
             if (mixed && na >= 64) cand[nv++] = 2 * FORCE_NT;
-            float best = INFINITY;
+            // the analytic rule's own shape for this size (one of the candidates)
+            const int r16_ni = force_ni(c, na);
+            float best = INFINITY, r16_ms = INFINITY;
             for (int v = 0; v < nv && rc == NB_OK; ++v) {
                 const int ni = cand[v];
                 const int it = (int)((na + ni - 1) / ni);
                 const int base = makespan_split(it, ntiles, shape_slots(c, c->order, ni, mixed), cap_splits);
+                const long long js_rule = std::max(1LL, std::min<long long>(std::min<long long>(base, ntiles),
+                                                                            cap_splits));
                 const int mult[8][2] = {{1, 4}, {1, 2}, {1, 1}, {2, 1}, {4, 1}, {8, 1}, {16, 1}, {0, 1}};
                 int tried[8], nt = 0;
                 for (int q = 0; q < 8 && rc == NB_OK; ++q) {
@@ -593,12 +600,17 @@ int nb_autotune(nb_ctx* c, int reps)
                     float ms;
                     rc = dyn ? time_shape_dyn(c, na, ni, (int)js, reps, e0, e1, &ms)
                              : time_shape(c, na, ni, (int)js, reps, e0, e1, &ms);
+                    if (rc == NB_OK && ni == r16_ni && js == js_rule) r16_ms = ms;
                     if (rc == NB_OK && ms < best) {
                         best = ms;
                         e = TuneEntry{ni, (int)js, it, ms};
                     }
                 }
             }
+            // a class keeps a tuned shape only if it beat the analytic rule's
+            // by TUNE_MARGIN at the class's size: the rule adapts the split to
+            // every size of the class, a tuned shape only scales it
+            if (!(best < TUNE_MARGIN * r16_ms)) e = TuneEntry{0, 0, 0, r16_ms};
             prev_best = best;
         }
         cudaEventDestroy(e0);
