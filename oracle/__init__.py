@@ -6,8 +6,7 @@ no code with the CUDA library.  See oracle.c for the formulas and their sources.
 
 Parity status per function:
   force, energy, predict, correct, interp, dt_criterion, dt_quantise,
-  next_block, integrate: pinned (tests/test_oracle_pins.py).
-  dt_startup: parity unpinned (a start-up reading, no closed form to check it
-  against; it is exercised only through the integrator pins).
+  dt_startup, next_block, integrate: pinned (tests/test_oracle_pins.py; the
+  start-up step against the closed form eta_s / w on a circular binary).
 """
 from .oracle import *  # noqa: F401,F403

@@ -294,6 +294,27 @@ def test_timestep_criterion_circular_orbit(orc, order):
     assert dt == pytest.approx(want, rel=1e-14)
 
 
+@pytest.mark.parametrize("eta_s", [0.01, 0.05])
+def test_startup_step_circular_binary(orc, eta_s):
+    # Start-up (the integrator's first pass): acc and jerk from the force at
+    # t = 0, step eta_s |a| / |j|, quantised.  On a circular unsoftened binary
+    # (total mass M, separation r) each body's acc rotates at the orbital rate
+    # w = sqrt(M / r^3), so |j| = w |a| and the limit is eta_s / w; the step is
+    # the largest power of two not above it.  A swapped ratio, a squared eta_s
+    # or a missing quantisation fails this.
+    M, r = 1.0, 0.3
+    w = math.sqrt(M / r ** 3)
+    x = np.array([[-r / 2, 0, 0], [r / 2, 0, 0]])
+    v = np.array([[0, -w * r / 2, 0], [0, w * r / 2, 0]])
+    st = orc.State(np.full(2, M / 2), np.zeros(2), x, v)
+    assert orc.integrate(st, order=6, t_end=0.0, eta_s=eta_s) == 0  # start-up only
+    for i in range(2):
+        lim = orc.dt_startup(eta_s, st.d[i, 0], st.d[i, 1])
+        assert lim == pytest.approx(eta_s / w, rel=1e-13)
+        assert st.dt[i] == 2.0 ** math.floor(math.log2(eta_s / w))
+        assert st.t[i] == 0.0
+
+
 def test_timestep_quantiser_brute_force(orc):
     dt_max, dt_min = 1.0 / 16, 2.0 ** -40
     rng = np.random.default_rng(5)
