@@ -60,11 +60,27 @@ def parse():
     p.add_argument("--block-step", type=float, default=2.0 ** -12)
     p.add_argument("--quick", action="store_true", help="skip the FP64, energy, ensemble and CPU legs")
     p.add_argument("--ensemble-t", type=float, default=1.0 / 64, help="end time of the ensemble leg")
-    p.add_argument("--energy-t", type=float, default=1.0 / 16, help="end time of the energy-budget leg")
+    p.add_argument("--energy-t", type=float, default=1.0, help="end time of the energy-budget legs")
+    p.add_argument("--energy-n", type=int, default=16384,
+                   help="Plummer sphere of the both-paths energy-budget leg (FP64 to --energy-t)")
     p.add_argument("--cusp-fp64", action="store_true",
                    help="also run the full-size cusp on the FP64 path (about two minutes)")
     p.add_argument("--nucleus-full", action="store_true",
                    help="also run the 2^20 nucleus to t = 1/16 on the mixed path (about two minutes)")
+    p.add_argument("--nucleus-fp64", type=float, default=0.0, metavar="T",
+                   help="also run the 2^20 nucleus to t = T with dt_max = T on both paths (T = 2^-10: about "
+                        "ten minutes, most of it the FP64 start-up and energies)")
+    p.add_argument("--nucleus-trend", action="store_true",
+                   help="also run the nucleus recipe with 2^14 and 2^17 stars to t = 1/16 on both paths (about "
+                        "two minutes)")
+    p.add_argument("--profile-force", action="store_true",
+                   help="instead of the benchmark: a small force case for profilers (see profile_force)")
+    p.add_argument("--profile-step", action="store_true",
+                   help="instead of the benchmark: block steps of one small active set (see profile_step)")
+    p.add_argument("--n-act", type=int, default=4096, help="active particles of the profiling cases")
+    p.add_argument("--repeat", type=int, default=2, help="force launches / block steps of the profiling cases")
+    p.add_argument("--workload", choices=["nucleus", "cusp", "plummer65k"], default="nucleus",
+                   help="system of the profiling cases")
     return p.parse_args()
 
 
@@ -326,11 +342,11 @@ def cusp_run(nb, w, p, stream, torch, t_end, dt_max=None):
             "interactions": ni, "seconds": el, "whole_run_interactions_per_s": ni / el}
 
 
-def nucleus_run(nb, w, p, stream, torch, t_end, graph=0):
+def nucleus_run(nb, w, p, stream, torch, t_end, graph=0, dt_max=None):
     c = nb.NBody(w.n, w.order, 0.0, p)
     c.set_stream(stream)
     c.set_softening(np.sqrt(w.eps2))
-    c.set_params(w.eta, w.eta_s, w.dt_max, 2.0 ** -40)
+    c.set_params(w.eta, w.eta_s, dt_max or w.dt_max, 2.0 ** -40)
     c.set_particles(w.m, w.x, w.v)
     c.set_precision(nb.NB_FP64)
     e0 = sum(c.energy())
@@ -447,46 +463,56 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
         out["nact_curve_interactions_per_s"] = curve
     except Exception as e:  # pragma: no cover
         out["nact_curve_interactions_per_s"] = {"error": repr(e)}
-    # ---- energy error of both paths, Plummer N = 65536 to t = 1/16
+    # ---- energy error of both paths after one time unit: a Plummer sphere of
+    #      --energy-n particles (the FP64 path finishes it in well under a
+    #      minute) on both paths; then the 65536-particle sphere to the same
+    #      time on the mixed path as host-driven cycles, CUDA-graph replays of 64
+    #      device-driven cycles, and graph replays with autotuned shapes
     try:
-        pw = ics.standard_workload(1)
         t_end = args.energy_t
-        de, final = {}, {}
-        # host-driven cycles for both precisions, then the mixed run again as
-        # CUDA-graph replays of 64 device-driven cycles, untuned and autotuned
-        legs = (("fp64", nb.NB_FP64, 0, 0), ("mixed", nb.NB_MIXED, 0, 0), ("mixed_graph", nb.NB_MIXED, 64, 0),
-                ("mixed_graph_tuned", nb.NB_MIXED, 64, 3))
-        for name, p, cyc, tune in legs:
-            c2 = nb.NBody(pw.n, 6, math.sqrt(pw.eps2[0]), p)
+
+        def energy_run(w, p, cyc, tune=0):
+            c2 = nb.NBody(w.n, 6, math.sqrt(w.eps2[0]), p)
             c2.set_stream(stream)
-            c2.set_params(pw.eta, pw.eta_s, pw.dt_max, 2.0 ** -40)
-            c2.set_particles(pw.m, pw.x, pw.v)
+            c2.set_params(w.eta, w.eta_s, w.dt_max, 2.0 ** -40)
+            c2.set_particles(w.m, w.x, w.v)
             c2.set_precision(nb.NB_FP64)
             e0 = sum(c2.energy())
             c2.set_precision(p)
-            tune_s = None
             c2.set_graph(cyc)
+            rec = {}
             if tune:  # after set_graph: tuned with the kernels graph cycles run
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 c2.autotune(tune)
-                tune_s = time.perf_counter() - t0
+                rec["autotune_seconds"] = time.perf_counter() - t0
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             nblk, ni = c2.step_until(t_end)
             torch.cuda.synchronize()
             el = time.perf_counter() - t0
-            final[name] = c2.get_state()["x"]
+            xf = c2.get_state()["x"]
             c2.set_precision(nb.NB_FP64)
             e1 = sum(c2.energy())
-            de[name] = {"dE_E": (e1 - e0) / abs(e0), "blocks": nblk, "interactions": ni,
-                        "whole_run_interactions_per_s": ni / el, "seconds": el}
-            if tune_s is not None:
-                de[name]["autotune_seconds"] = tune_s
             c2.close()
-        de["mixed_graph"]["same_state_as_host_driven"] = bool(np.array_equal(final["mixed"], final["mixed_graph"]))
-        out["energy_budget"] = {"workload": pw.name + f" to t={t_end}", **de,
-                                "mixed_within_2x": abs(de["mixed"]["dE_E"]) <= 2 * abs(de["fp64"]["dE_E"])}
+            rec.update({"dE_E": (e1 - e0) / abs(e0), "blocks": nblk, "interactions": ni,
+                        "whole_run_interactions_per_s": ni / el, "seconds": el})
+            return rec, xf
+
+        ws = ics.plummer_cluster(args.energy_n, 1001, 1e-4, 6, t_end)
+        both = {}
+        for name, p in (("fp64", nb.NB_FP64), ("mixed", nb.NB_MIXED)):
+            both[name], _ = energy_run(ws, p, 64)
+        both["mixed_within_2x"] = abs(both["mixed"]["dE_E"]) <= 2 * abs(both["fp64"]["dE_E"])
+        both["time_to_solution_ratio"] = both["fp64"]["seconds"] / both["mixed"]["seconds"]
+        pw = ics.standard_workload(1)
+        de, final = {}, {}
+        for name, cyc, tune in (("mixed_host", 0, 0), ("mixed_graph", 64, 0), ("mixed_graph_tuned", 64, 3)):
+            de[name], final[name] = energy_run(pw, nb.NB_MIXED, cyc, tune)
+        de["mixed_graph"]["same_state_as_host_driven"] = bool(np.array_equal(final["mixed_host"],
+                                                                              final["mixed_graph"]))
+        out["energy_budget"] = {"workload": ws.name + f" to t={t_end}, graph replays, both paths", **both,
+                                "plummer65k": {"workload": pw.name + f" to t={t_end}, mixed", **de}}
     except Exception as e:  # pragma: no cover
         out["energy_budget"] = {"error": repr(e)}
     # ---- Plummer N = 1024 to t = 0.125 end to end: both GPU paths and the
@@ -572,9 +598,27 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
             nuc["reduced"][name] = nucleus_run(nb, ws, p, stream, torch, 1.0 / 16)
         r = nuc["reduced"]
         r["mixed_dE_within_2x_of_fp64"] = abs(r["mixed"]["dE_E"]) <= 2 * abs(r["fp64"]["dE_E"])
+        if args.nucleus_trend:
+            for k in (14, 17):
+                wk = ics.plummer_nucleus(1 << k, 1002, 1e-5, 1.0 / 16)
+                rk = {"workload": wk.name + " to t=1/16"}
+                for name, p in (("mixed", nb.NB_MIXED), ("fp64", nb.NB_FP64)):
+                    rk[name] = nucleus_run(nb, wk, p, stream, torch, 1.0 / 16, graph=64)
+                rk["mixed_dE_within_2x_of_fp64"] = abs(rk["mixed"]["dE_E"]) <= 2 * abs(rk["fp64"]["dE_E"])
+                nuc[f"stars_2p{k}"] = rk
         if args.nucleus_full:
             nuc["full"] = {"workload": wl.name + " to t=1/16",
                            "mixed": nucleus_run(nb, wl, nb.NB_MIXED, stream, torch, 1.0 / 16, graph=64)}
+        if args.nucleus_fp64 > 0:
+            T = args.nucleus_fp64
+            r = {"workload": wl.name + f" to t={T} with dt_max={T}, every path started and measured in its own "
+                             "precision (energies in FP64)"}
+            for name, p in (("mixed", nb.NB_MIXED), ("fp64", nb.NB_FP64)):
+                r[name] = nucleus_run(nb, wl, p, stream, torch, T, graph=64, dt_max=T)
+            r["mixed_dE_within_2x_of_fp64"] = abs(r["mixed"]["dE_E"]) <= 2 * abs(r["fp64"]["dE_E"])
+            r["whole_run_rate_ratio"] = (r["mixed"]["whole_run_interactions_per_s"] /
+                                         r["fp64"]["whole_run_interactions_per_s"])
+            nuc["full_short_both"] = r
         out["nucleus_energy"] = nuc
     except Exception as e:  # pragma: no cover
         out["nucleus_energy"] = {"error": repr(e)}
@@ -654,8 +698,83 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
     torch.cuda.synchronize()
 
 
+# ------------------------------------------------------------ profiling cases
+def _profile_workload(args):
+    from paper_1312_1789_b300 import ics
+    return ics.standard_workload({"nucleus": 2, "cusp": 3, "plummer65k": 1}[args.workload])
+
+
+def profile_force(args):
+    """Small, self-contained force case for ncu.
+
+    Builds the workload (default: the 2^20-star nucleus, order 6; cusp: 2^18
+    stars and a binary, order 8), runs the start-up in mixed precision (mixed
+    force launches over every particle: 2 at order 6, 3 at order 8), predicts
+    in --precision, then launches the force --repeat times on one block of
+    --n-act particles.  With ncu, `-k regex:k_force_mixed -s 2 -c 1` (order 6;
+    -s 3 at order 8) or `-k regex:k_force_fp64 -s 0 -c 1` captures the first
+    block launch."""
+    from paper_1312_1789_b300 import build, nb
+    build.build()
+    wl = _profile_workload(args)
+    prec = nb.NB_MIXED if args.precision == "mixed" else nb.NB_FP64
+    # start-up in mixed precision (an FP64 start-up of 2^20 particles takes
+    # minutes), then the block in the requested precision
+    ctx = nb.NBody(wl.n, wl.order, 0.0, nb.NB_MIXED)
+    ctx.set_softening(np.sqrt(wl.eps2))
+    ctx.set_particles(wl.m, wl.x, wl.v)
+    ctx.set_precision(prec)
+    ctx.predict(2.0 ** -12)
+    blk = np.sort(np.random.default_rng(7).choice(wl.n, min(args.n_act, wl.n), replace=False)).astype(np.int32)
+    ctx.set_profiling(True)
+    for _ in range(args.repeat):
+        ctx.force(blk)
+    prof, _ = ctx.get_profile()
+    ms = prof["force"][0] / max(prof["force"][1], 1)
+    print(f"{wl.name} {args.precision}: block {len(blk)}, launch {ctx.get_launch()}, force kernel {ms:.3f} ms, "
+          f"{len(blk) * wl.n / (ms * 1e-3):.3e} interactions/s")
+    ctx.close()
+
+
+def profile_step(args):
+    """Block steps whose active set is the first --n-act particles, for ncu
+    captures of the scheduler, predictor and corrector: after the start-up
+    (mixed), every particle gets the step 2^-12, then those of the first n-act
+    particles are halved; each of the --repeat block steps then runs the
+    scheduler's two passes (the second with the predictor), the force and the
+    corrector on those n-act particles (whose new steps are reset before the
+    next one)."""
+    from paper_1312_1789_b300 import build, nb
+    build.build()
+    wl = _profile_workload(args)
+    prec = nb.NB_MIXED if args.precision == "mixed" else nb.NB_FP64
+    ctx = nb.NBody(wl.n, wl.order, 0.0, nb.NB_MIXED)
+    ctx.set_softening(np.sqrt(wl.eps2))
+    ctx.set_particles(wl.m, wl.x, wl.v)
+    ctx.set_precision(prec)
+    S = ctx.get_state()
+    na = min(args.n_act, wl.n)
+    ctx.set_profiling(True)
+    for _ in range(args.repeat):
+        dt = np.full(wl.n, 2.0 ** -12)
+        dt[:na] = 2.0 ** -13
+        ctx.set_state(S["x"], S["v"], S["d"], S["t"], dt)
+        tb, n_act = ctx.block_step()
+        assert n_act == na, (n_act, na)
+    prof, launches = ctx.get_profile()
+    print(f"{wl.name} {args.precision}: {args.repeat} block steps of {na} active; per step (ms): " +
+          ", ".join(f"{k} {v[0] / args.repeat:.4f}" for k, v in prof.items()) + f"; launches {launches}")
+    ctx.close()
+
+
 def main():
     args = parse()
+    if args.profile_force:
+        profile_force(args)
+        return
+    if args.profile_step:
+        profile_step(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -67,7 +67,9 @@ int nb_create(nb_ctx** out, int64_t n, int order, double eps);
 /* Free every device and host resource of ctx.  NULL is ignored.            */
 void nb_destroy(nb_ctx* ctx);
 
-/* Message for the last failed call on ctx (or on nb_create when ctx is NULL). */
+/* Message for the last failed call on ctx; with ctx NULL, the last failed
+ * context-free call (nb_create, nb_force_static, ...) of the calling host
+ * thread.                                                                  */
 const char* nb_last_error(const nb_ctx* ctx);
 
 /* Order later device work on this CUDA stream (a cudaStream_t); NULL = the
@@ -236,6 +238,39 @@ int nb_selftest_wait(nb_ctx* ctx, double seconds);
 /* Force the j-split count of later nb_force calls (0 = automatic).         */
 int nb_set_jsplit(nb_ctx* ctx, int j_splits);
 
+/* ------------------------------------------- j decomposition across ranks */
+
+/* The paper's multi-GPU scheme ("Codes description": MPI between the GPUs,
+ * each GPU computing forces; the log(N_GPU) communication term of the
+ * performance model): every rank holds all particles and the same active
+ * set, sums the force over its own contiguous share of the j particles, the
+ * partial results are exchanged once per block, and every rank adds them in
+ * the same order and runs the same corrector, so the states stay identical.
+ *
+ * nb_set_jrange: later nb_force calls sum over the j particles
+ * [j_begin, j_end) only; j_begin and j_end multiples of NB_JTILE (j_end may
+ * also be n).  (0, 0) or (0, n) restores the whole range.  The start-up
+ * passes and nb_energy always use every particle.  While a range is set,
+ * nb_block_step, nb_step_until and graph cycles fail with NB_ERR_ARG: step
+ * with nb_next_block, nb_predict, nb_force, the exchange, nb_reduce_force and
+ * nb_correct.  With the ranges [r T / G, (r + 1) T / G) tiles (T = tiles of
+ * the store, G ranks) and one j-split per rank, the reduced force is bit for
+ * bit the single-rank force with G j-splits.                                */
+#define NB_JTILE 128
+int nb_set_jrange(nb_ctx* ctx, int64_t j_begin, int64_t j_end);
+
+/* Copy the last nb_force result, ncomp x n_act doubles component-major
+ * (acc xyz, jerk xyz[, snap xyz[, crackle xyz]], potential, sum_j m_j/R_ij^2),
+ * to dst (device or host memory), ordered on the context's stream (the
+ * caller synchronises, or orders its exchange on that stream).  Optional
+ * outputs: ncomp and n_act.                                                 */
+int nb_copy_force(nb_ctx* ctx, double* dst, int64_t* ncomp, int64_t* n_act);
+
+/* Replace the last nb_force result by the sum of n_parts results in device
+ * memory, parts[n_parts][ncomp][n_act] (each laid out as nb_copy_force
+ * writes it), added in part order; nb_correct then uses it.               */
+int nb_reduce_force(nb_ctx* ctx, const double* parts, int n_parts);
+
 /* Give every particle the step dt, so that the next block is the whole
  * system -- the synchronised block that occurs at every multiple of dt_max of
  * a hierarchical block-step run (abstract).  All particles must be at one
@@ -344,7 +379,10 @@ int nb_batch_get_state(nb_batch* b, double* x, double* v, double* t, double* dt)
  * its own allocator, or a loop that must not allocate once it has started.
  *
  * Force of the n_act particles idx[] (device int32, in [0, n)) from all n
- * particles given at one instant, with the same kernels as nb_force.  Every
+ * particles given at one instant, with the pair arithmetic of nb_force (its
+ * one-particle-per-thread kernels, not the autotuned or two-per-thread
+ * launch shapes), so results agree with nb_force's within the parity
+ * tolerances, not bit for bit.  Every
  * pointer is device memory owned by the caller: m, eps2 [n]; x, v [n][3];
  * a [n][3] (order >= 6, else may be NULL); jerk [n][3] (order 8, else NULL);
  * out [ncomp][n_act], component-major: acc xyz, jerk xyz, snap xyz (order
@@ -355,13 +393,14 @@ int nb_batch_get_state(nb_batch* b, double* x, double* v, double* t, double* dt)
  * status word live in one fixed array of NB_STATIC_SCRATCH_BYTES that every
  * GPU loading this part of the library holds until the process exits; n is
  * limited to NB_STATIC_MAX_N (larger n fails with NB_ERR_ARG).  The first call
- * on a device looks up the array's device address (cudaGetSymbolAddress), so
- * make that first call before any stream capture.  All calls share the array
- * and it keeps the last call's contents: calls that overlap on the GPU race,
- * so order them (one stream, or synchronise).  Work runs on `stream` (a
- * cudaStream_t, NULL = legacy default) and the call returns after it has
- * finished, reporting device-side errors (an index out of range gives
- * NB_ERR_ARG).  Messages: nb_last_error(NULL).                              */
+ * on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current.  All calls share the array and it keeps the last
+ * call's contents: calls that overlap on the GPU race, so order them (one
+ * stream, or synchronise).  Work runs on `stream` (a cudaStream_t, NULL =
+ * legacy default) and the call synchronises with it before returning, to
+ * report device-side errors (an index out of range gives NB_ERR_ARG); so it
+ * must not be called while that stream is being captured into a graph.
+ * Messages: nb_last_error(NULL), kept per host thread.                       */
 #define NB_STATIC_MAX_N 16384
 #define NB_STATIC_SCRATCH_BYTES (16384 * 128 + (1 << 20) * 8 + 256)
 int nb_force_static(int order, int precision, int64_t n, const double* m, const double* eps2, const double* x,

@@ -36,12 +36,25 @@
 
 namespace nb {
 
+// Inverse distance of a pair: the hardware reciprocal square root (MUFU)
+// with subnormal inputs flushed to zero.  rsqrtf without the flush adds a
+// compare and two multiplies per pair to rescale subnormal inputs; R^2 is
+// never subnormal here (at least eps^2 for softened pairs, and a subnormal
+// unsoftened R^2 would put the pair force beyond the float range anyway).
+// Measured: 5 % more interactions/s at N = 2^20, identical results.
+__device__ __forceinline__ float rsqrt_ftz(float r2)
+{
+    float ri;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(ri) : "f"(r2));
+    return ri;
+}
+
 // self-term guard: with per-particle softening a pair can have R^2 = 0 (an
 // unsoftened particle meeting itself); its contribution is zero by definition.
 template <bool PAIR>
 __device__ __forceinline__ float guard_rinv(float r2)
 {
-    float ri = rsqrtf(r2);
+    float ri = rsqrt_ftz(r2);
     if (PAIR) ri = (r2 > 0.0f) ? ri : 0.0f;
     return ri;
 }
@@ -688,12 +701,12 @@ __device__ __forceinline__ void force_block_mixed_xs(const float4* __restrict__ 
 template <int ORDER, int RW, bool PAIR, int NP>
 __global__ void __launch_bounds__(FORCE_NT, xs_min_ctas(ORDER)) k_force_mixed_xs(const float4* __restrict__ js,
                                                              const int32_t* __restrict__ idx, int n_act, int n,
-                                                             int ntiles, int jsplit, float eps2u, float eps2max,
+                                                             int ntiles, int jt0, int jsplit, float eps2u, float eps2max,
                                                              double* __restrict__ partial, DevScalars* sc, double* F)
 {
     const int split = blockIdx.y;
-    const int t0 = (int)((long long)split * ntiles / jsplit);
-    const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
+    const int t0 = jt0 + (int)((long long)split * ntiles / jsplit);
+    const int t1 = jt0 + (int)((long long)(split + 1) * ntiles / jsplit);
     force_block_mixed_xs<ORDER, RW, PAIR, NP>(js, idx, blockIdx.x * (FORCE_NT * 2 * NP), n_act, n, t0, t1 - t0,
                                               split, n_act, eps2u, eps2max, partial, sc, TileSum{F, jsplit});
 }
@@ -843,12 +856,12 @@ __device__ __forceinline__ void force_block_mixed_jp(const float4* __restrict__ 
 template <int ORDER, int RW, bool PAIR, int JP>
 __global__ void __launch_bounds__(FORCE_NT, dyn_min_ctas(ORDER)) k_force_mixed_jp(const float4* __restrict__ js,
                                                              const int32_t* __restrict__ idx, int n_act, int n,
-                                                             int ntiles, int jsplit, float eps2u, float eps2max,
+                                                             int ntiles, int jt0, int jsplit, float eps2u, float eps2max,
                                                              double* __restrict__ partial, DevScalars* sc, double* F)
 {
     const int split = blockIdx.y;
-    const int t0 = (int)((long long)split * ntiles / jsplit);
-    const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
+    const int t0 = jt0 + (int)((long long)split * ntiles / jsplit);
+    const int t1 = jt0 + (int)((long long)(split + 1) * ntiles / jsplit);
     force_block_mixed_jp<ORDER, RW, PAIR, JP>(js, idx, blockIdx.x * (FORCE_NT / JP), n_act, n, t0, t1 - t0, split,
                                               n_act, eps2u, eps2max, partial, sc,
                                               TileSum{F, jsplit});
@@ -858,13 +871,13 @@ __global__ void __launch_bounds__(FORCE_NT, dyn_min_ctas(ORDER)) k_force_mixed_j
 // blockIdx.y = j-split of the whole store.
 template <int ORDER, int RW, bool PAIR, int IPT>
 __global__ void __launch_bounds__(FORCE_NT) k_force_mixed(const float4* __restrict__ js, const int32_t* __restrict__ idx,
-                                                          int n_act, int n, int ntiles, int jsplit, float eps2u,
+                                                          int n_act, int n, int ntiles, int jt0, int jsplit, float eps2u,
                                                           float eps2max, double* __restrict__ partial, DevScalars* sc,
                                                           double* F)
 {
     const int split = blockIdx.y;
-    const int t0 = (int)((long long)split * ntiles / jsplit);
-    const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
+    const int t0 = jt0 + (int)((long long)split * ntiles / jsplit);
+    const int t1 = jt0 + (int)((long long)(split + 1) * ntiles / jsplit);
     force_block_mixed<ORDER, RW, PAIR, IPT>(js, idx, blockIdx.x * (FORCE_NT * IPT), n_act, n, t0, t1 - t0, split, n_act,
                                             eps2u, eps2max, partial, sc, TileSum{F, jsplit});
 }
@@ -1042,12 +1055,12 @@ __device__ __forceinline__ void force_block_fp64(const double2* __restrict__ js,
 // F: result of a one-split launch (nullptr: partials only)
 template <int ORDER, int RW, bool PAIR, int JP = 1>
 __global__ void __launch_bounds__(FORCE_NT) k_force_fp64(const double2* __restrict__ js, const int32_t* __restrict__ idx,
-                                                         int n_act, int n, int ntiles, int jsplit, double eps2u,
+                                                         int n_act, int n, int ntiles, int jt0, int jsplit, double eps2u,
                                                          double* __restrict__ partial, DevScalars* sc, double* F)
 {
     const int split = blockIdx.y;
-    const int t0 = (int)((long long)split * ntiles / jsplit);
-    const int t1 = (int)((long long)(split + 1) * ntiles / jsplit);
+    const int t0 = jt0 + (int)((long long)split * ntiles / jsplit);
+    const int t1 = jt0 + (int)((long long)(split + 1) * ntiles / jsplit);
     force_block_fp64<ORDER, RW, PAIR, JP>(js, idx, blockIdx.x * (FORCE_NT / JP), n_act, n, t0, t1 - t0, split, n_act,
                                           eps2u, partial, sc, TileSum{F, jsplit});
 }

@@ -32,7 +32,7 @@ static cudaError_t run_mixed_ipt(nb_ctx* c, const int32_t* idx, int n_act, int j
     }
     dim3 grid(itiles, jsplit);
     kern<<<grid, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), idx, n_act, (int)c->n,
-                                              (int)(c->np / JT), jsplit, (float)(c->eps * c->eps),
+                                              c->ltn, c->lt0, jsplit, (float)(c->eps * c->eps),
                                               eps2_threshold(c->eps2_max), c->partial, c->sc, c->F);
     return cudaGetLastError();
 }
@@ -56,7 +56,7 @@ static cudaError_t run_mixed_jp(nb_ctx* c, const int32_t* idx, int n_act, int js
     }
     dim3 grid(itiles, jsplit);
     kern<<<grid, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), idx, n_act, (int)c->n,
-                                              (int)(c->np / JT), jsplit, (float)(c->eps * c->eps),
+                                              c->ltn, c->lt0, jsplit, (float)(c->eps * c->eps),
                                               eps2_threshold(c->eps2_max), c->partial, c->sc, c->F);
     return cudaGetLastError();
 }
@@ -80,7 +80,7 @@ static cudaError_t run_mixed_xs(nb_ctx* c, const int32_t* idx, int n_act, int js
     }
     dim3 grid(itiles, jsplit);
     kern<<<grid, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const float4*>(c->jstore), idx, n_act, (int)c->n,
-                                              (int)(c->np / JT), jsplit, (float)(c->eps * c->eps),
+                                              c->ltn, c->lt0, jsplit, (float)(c->eps * c->eps),
                                               eps2_threshold(c->eps2_max), c->partial, c->sc, c->F);
     return cudaGetLastError();
 }
@@ -119,7 +119,7 @@ static cudaError_t run_fp64_jp(nb_ctx* c, const int32_t* idx, int n_act, int jsp
     }
     dim3 grid(itiles, jsplit);
     kern<<<grid, FORCE_NT, smem, c->stream>>>(reinterpret_cast<const double2*>(c->jstore), idx, n_act, (int)c->n,
-                                              (int)(c->np / JT), jsplit, c->eps * c->eps, c->partial, c->sc,
+                                              c->ltn, c->lt0, jsplit, c->eps * c->eps, c->partial, c->sc,
                                               c->F);
     return cudaGetLastError();
 }
@@ -197,6 +197,22 @@ cudaError_t launch_force_reduce(nb_ctx* c, int order, const int32_t* idx, int64_
                                                                                                       jsplit, na, c->F)
     switch (order) {
     case 0: NB_RED(0); break;
+    case 4: NB_RED(4); break;
+    case 6: NB_RED(6); break;
+    case 8: NB_RED(8); break;
+    default: return cudaErrorInvalidValue;
+    }
+#undef NB_RED
+    return cudaGetLastError();
+}
+
+cudaError_t launch_parts_reduce(nb_ctx* c, int order, const double* parts, int64_t n_act, int n_parts)
+{
+    const int na = (int)n_act;
+#define NB_RED(O)                                                                                               \
+    k_force_reduce<ncomp(O), -1><<<reduce_grid(n_parts, na, ncomp(O)), RED_NT, 0, c->stream>>>(parts, n_parts, na, \
+                                                                                             c->F)
+    switch (order) {
     case 4: NB_RED(4); break;
     case 6: NB_RED(6); break;
     case 8: NB_RED(8); break;

@@ -20,7 +20,8 @@ namespace {
 void* (*g_alloc)(size_t, void*) = nullptr;
 void (*g_free)(void*, void*) = nullptr;
 void* g_user = nullptr;
-char g_err[512] = "";
+// per host thread, like errno: concurrent context-free calls keep their own message
+thread_local char g_err[512] = "";
 
 int set_err(nb_ctx* c, int code, const char* fmt, ...)
 {
@@ -173,9 +174,22 @@ int sync_scalars(nb_ctx* c)
 // Launch shape of the force: FORCE_NT i-particles per CTA; the j range is
 // split so that small active sets still fill every SM (j-split), capped by the
 // partial-sum buffer.
+// j tiles of later force launches: the nb_force range when `ranged` and a
+// range is set, else the whole store.
+void set_launch_tiles(nb_ctx* c, bool ranged)
+{
+    if (ranged && c->jr_end > 0) {
+        c->lt0 = (int)(c->jr_begin / JT);
+        c->ltn = (int)((c->jr_end + JT - 1) / JT) - c->lt0;
+    } else {
+        c->lt0 = 0;
+        c->ltn = (int)(c->np / JT);
+    }
+}
+
 void choose_shape(nb_ctx* c, int order, int64_t n_act, int* itiles, int* jsplit, int* ni_out)
 {
-    const int ntiles = (int)(c->np / JT);
+    const int ntiles = c->ltn;
     const long long cap_splits = (long long)(c->partial_cap / ((size_t)ncomp(order) * (size_t)n_act));
     const int pi = (c->pred_prec >= 0 ? c->pred_prec : c->prec) == NB_MIXED ? 1 : 0;
     int ni, it, js;
@@ -196,9 +210,12 @@ void choose_shape(nb_ctx* c, int order, int64_t n_act, int* itiles, int* jsplit,
     *jsplit = js;
 }
 
-int run_force(nb_ctx* c, int order, const int32_t* idx_dev, int64_t n_act)
+// ranged: sum over the nb_force j range only (nb_set_jrange); the start-up
+// and energy passes always sum over every particle.
+int run_force(nb_ctx* c, int order, const int32_t* idx_dev, int64_t n_act, bool ranged = false)
 {
     int it, js, ni;
+    set_launch_tiles(c, ranged);
     choose_shape(c, order, n_act, &it, &js, &ni);
     NB_CUDA(c, timed(c, NB_PHASE_FORCE, 1, [&] { return launch_force(c, order, idx_dev, n_act, js, it, ni); }));
     if (js > 1)
@@ -476,6 +493,7 @@ int nb_set_graph(nb_ctx* c, int cycles)
 {
     if (!c) return NB_ERR_ARG;
     if (cycles < 0 || cycles > 4096) return set_err(c, NB_ERR_ARG, "cycles must be in [0, 4096]");
+    if (cycles > 0 && c->jr_end > 0) return set_err(c, NB_ERR_ARG, "graph cycles need the whole j range");
     destroy_graph(c);
     c->graph_cycles = cycles;
     return NB_OK;
@@ -558,6 +576,7 @@ int nb_autotune(nb_ctx* c, int reps)
         cudaEvent_t e0, e1;
         NB_CUDA(c, cudaEventCreate(&e0));
         NB_CUDA(c, cudaEventCreate(&e1));
+        set_launch_tiles(c, false);
         const int ntiles = (int)(c->np / JT), nc = ncomp(c->order);
         const bool mixed = c->prec == NB_MIXED;
         int ncls = 0;
@@ -686,6 +705,42 @@ int nb_set_jsplit(nb_ctx* c, int js)
     return NB_OK;
 }
 
+int nb_set_jrange(nb_ctx* c, int64_t j_begin, int64_t j_end)
+{
+    if (!c) return NB_ERR_ARG;
+    if (j_begin == 0 && (j_end == 0 || j_end == c->n)) {
+        c->jr_begin = c->jr_end = 0;
+        return NB_OK;
+    }
+    if (j_begin < 0 || j_end <= j_begin || j_end > c->n || j_begin % JT != 0 || (j_end % JT != 0 && j_end != c->n))
+        return set_err(c, NB_ERR_ARG, "j range [%lld, %lld) must lie in [0, %lld) and start and end on multiples of %d "
+                       "(or end at n)", (long long)j_begin, (long long)j_end, (long long)c->n, JT);
+    if (c->graph_cycles > 0) return set_err(c, NB_ERR_ARG, "a j range cannot be combined with graph cycles");
+    c->jr_begin = j_begin;
+    c->jr_end = j_end;
+    return NB_OK;
+}
+
+int nb_copy_force(nb_ctx* c, double* dst, int64_t* ncomp_out, int64_t* n_act_out)
+{
+    if (!c || !dst) return NB_ERR_ARG;
+    if (!c->have_force || c->F_order != c->order) return set_err(c, NB_ERR_ARG, "no force result held (call nb_force first)");
+    const size_t cnt = (size_t)ncomp(c->order) * (size_t)c->F_n;
+    NB_CUDA(c, cudaMemcpyAsync(dst, c->F, cnt * sizeof(double), cudaMemcpyDefault, c->stream));
+    if (ncomp_out) *ncomp_out = ncomp(c->order);
+    if (n_act_out) *n_act_out = c->F_n;
+    return NB_OK;
+}
+
+int nb_reduce_force(nb_ctx* c, const double* parts, int n_parts)
+{
+    if (!c || !parts || n_parts < 1) return set_err(c, NB_ERR_ARG, "parts must be non-NULL and n_parts >= 1");
+    if (!c->have_force || c->F_order != c->order)
+        return set_err(c, NB_ERR_ARG, "nb_reduce_force needs a preceding nb_force");
+    NB_CUDA(c, timed(c, NB_PHASE_REDUCE, 1, [&] { return launch_parts_reduce(c, c->order, parts, c->F_n, n_parts); }));
+    return NB_OK;
+}
+
 int nb_get_launch(nb_ctx* c, int* it, int* js, int* nt)
 {
     if (!c) return NB_ERR_ARG;
@@ -799,7 +854,7 @@ int nb_force(nb_ctx* c, const int32_t* idx, int64_t n_act)
                                        c->stream));
         }
     }
-    NB_TRY(run_force(c, c->order, c->f_idx, n_act));
+    NB_TRY(run_force(c, c->order, c->f_idx, n_act, true));
     c->f_n = n_act;
     c->f_t = c->t_pred;
     c->f_order = c->order;
@@ -840,9 +895,19 @@ static int next_block_predicted(nb_ctx* c, double* tb, int64_t* na)
     return NB_OK;
 }
 
+// A block step corrects with the force it computed, so it needs the whole
+// j range; with a range set, step with nb_force, the exchange of the partial
+// sums and nb_reduce_force.
+static int need_whole_range(nb_ctx* c)
+{
+    if (c->jr_end > 0) return set_err(c, NB_ERR_ARG, "block steps need the whole j range (nb_set_jrange(0, 0))");
+    return NB_OK;
+}
+
 int nb_block_step(nb_ctx* c, double* t_blk, int64_t* n_act)
 {
     if (!c) return NB_ERR_ARG;
+    NB_TRY(need_whole_range(c));
     double tb = 0.0;
     int64_t na = 0;
     NB_TRY(next_block_predicted(c, &tb, &na));
@@ -856,6 +921,7 @@ int nb_block_step(nb_ctx* c, double* t_blk, int64_t* n_act)
 int nb_step_until(nb_ctx* c, double t_end, int64_t* n_blocks, int64_t* n_inter)
 {
     if (!c) return NB_ERR_ARG;
+    NB_TRY(need_whole_range(c));
     if (!std::isfinite(t_end)) return set_err(c, NB_ERR_ARG, "t_end must be finite");
     if (!c->have_particles) return set_err(c, NB_ERR_ARG, "nb_step_until before nb_set_particles");
     if (c->graph_cycles > 0) return step_until_graph(c, t_end, n_blocks, n_inter);

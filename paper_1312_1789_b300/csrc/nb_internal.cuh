@@ -357,6 +357,10 @@ struct nb_ctx {
     double* partial = nullptr;  // j-split partial sums
     size_t partial_cap = 0;     // doubles
     double* F = nullptr;        // [ncomp][n] reduced force, list order
+    // j range of nb_force (nb_set_jrange): particles [jr_begin, jr_end); jr_end = 0: all
+    int64_t jr_begin = 0, jr_end = 0;
+    // j tiles of the force launch in progress: [lt0, lt0 + ltn) (run_force sets them)
+    int lt0 = 0, ltn = 0;
     int have_particles = 0, have_pred = 0, have_force = 0;
     double t_pred = 0.0;
     int F_order = -1;           // order of the result held in F (-1: none)
@@ -408,6 +412,9 @@ cudaError_t launch_predict(nb_ctx* c, double t, const double* tpc = nullptr, con
 // adds the split partials into c->F.
 cudaError_t launch_force(nb_ctx* c, int order, const int32_t* idx, int64_t n_act, int jsplit, int itiles, int ni);
 cudaError_t launch_force_reduce(nb_ctx* c, int order, const int32_t* idx, int64_t n_act, int jsplit);
+// c->F = the n_parts force results parts[n_parts][ncomp][n_act] added in part
+// order (no sign change: each part is already a finished result).
+cudaError_t launch_parts_reduce(nb_ctx* c, int order, const double* parts, int64_t n_act, int n_parts);
 cudaError_t launch_correct(nb_ctx* c, const double* tfc = nullptr, const int32_t* cid = nullptr,
                            const DevScalars* dyn = nullptr);
 // Device-driven block cycle (CUDA-graph capturable): shape gate, persistent

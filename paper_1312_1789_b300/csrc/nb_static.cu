@@ -16,6 +16,7 @@
 // or different host threads) race on it; callers must order their calls.
 #include <algorithm>
 #include <cmath>
+#include <cstdarg>
 #include <cstdio>
 #include <mutex>
 
@@ -41,28 +42,31 @@ static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 void* g_addr[MAX_DEVICES] = {nullptr};
-char g_err[256] = "";
 
-int fail(int code)
+// The message is formatted in the caller's own buffer and stored as the
+// calling thread's nb_last_error(NULL) text, so concurrent callers do not
+// overwrite each other's message.
+int fail(int code, const char* fmt, ...)
 {
-    nb::set_global_error(g_err);
+    char buf[256];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    nb::set_global_error(buf);
     return code;
 }
 
 int scratch_address(int dev, unsigned char** out)
 {
+    if (dev < 0 || dev >= MAX_DEVICES) return fail(NB_ERR_ARG, "device %d beyond the supported %d", dev, MAX_DEVICES);
     std::lock_guard<std::mutex> lock(g_mu);
-    if (dev < 0 || dev >= MAX_DEVICES) {
-        snprintf(g_err, sizeof g_err, "device %d beyond the supported %d", dev, MAX_DEVICES);
-        return NB_ERR_ARG;
-    }
     if (!g_addr[dev]) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
-            snprintf(g_err, sizeof g_err, "cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-            return NB_ERR_CUDA;
+            return fail(NB_ERR_CUDA, "cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
         }
         g_addr[dev] = p;
     }
@@ -161,14 +165,14 @@ int run_static(const double* m, const double* eps2, const double* x, const doubl
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return NB_ERR_CUDA;
         js = choose_split(it, np / JT, NC, n_act, slots_of(kern, smem, sm_count));
-        kern<<<dim3(it, js), FORCE_NT, smem, st>>>(reinterpret_cast<const float4*>(rec), idx, n_act, n, np / JT, js,
+        kern<<<dim3(it, js), FORCE_NT, smem, st>>>(reinterpret_cast<const float4*>(rec), idx, n_act, n, np / JT, 0, js,
                                                    0.0f, INFINITY, partial, sc, nullptr);
     } else {
         auto kern = k_force_fp64<ORDER, RW, true>;
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return NB_ERR_CUDA;
         js = choose_split(it, np / JT, NC, n_act, slots_of(kern, smem, sm_count));
-        kern<<<dim3(it, js), FORCE_NT, smem, st>>>(reinterpret_cast<const double2*>(rec), idx, n_act, n, np / JT, js,
+        kern<<<dim3(it, js), FORCE_NT, smem, st>>>(reinterpret_cast<const double2*>(rec), idx, n_act, n, np / JT, 0, js,
                                                    0.0, partial, sc, nullptr);
     }
     k_force_reduce<NC, pot_comp(ORDER)><<<reduce_grid(js, n_act, NC), RED_NT, 0, st>>>(partial, js, n_act, out);
@@ -186,32 +190,22 @@ extern "C" int nb_force_static(int order, int precision, int64_t n, const double
                                const double* x, const double* v, const double* a, const double* jerk,
                                const int32_t* idx, int64_t n_act, double* out, void* stream)
 {
-    if (!(order == 4 || order == 6 || order == 8) || (precision != NB_FP64 && precision != NB_MIXED)) {
-        snprintf(g_err, sizeof g_err, "order must be 4, 6 or 8 and precision NB_FP64 or NB_MIXED");
-        return fail(NB_ERR_ARG);
-    }
-    if (n < 1 || n > STATIC_MAX_N) {
-        snprintf(g_err, sizeof g_err, "n = %lld outside [1, %lld]: the fixed scratch holds at most %lld particles",
-                 (long long)n, (long long)STATIC_MAX_N, (long long)STATIC_MAX_N);
-        return fail(NB_ERR_ARG);
-    }
-    if (n_act < 1 || n_act > n) {
-        snprintf(g_err, sizeof g_err, "n_act = %lld outside [1, n]", (long long)n_act);
-        return fail(NB_ERR_ARG);
-    }
-    if (!m || !eps2 || !x || !v || !idx || !out || (order >= 6 && !a) || (order >= 8 && !jerk)) {
-        snprintf(g_err, sizeof g_err, "a required pointer is NULL");
-        return fail(NB_ERR_ARG);
-    }
+    if (!(order == 4 || order == 6 || order == 8) || (precision != NB_FP64 && precision != NB_MIXED))
+        return fail(NB_ERR_ARG, "order must be 4, 6 or 8 and precision NB_FP64 or NB_MIXED");
+    if (n < 1 || n > STATIC_MAX_N)
+        return fail(NB_ERR_ARG, "n = %lld outside [1, %lld]: the fixed scratch holds at most %lld particles",
+                    (long long)n, (long long)STATIC_MAX_N, (long long)STATIC_MAX_N);
+    if (n_act < 1 || n_act > n) return fail(NB_ERR_ARG, "n_act = %lld outside [1, n]", (long long)n_act);
+    if (!m || !eps2 || !x || !v || !idx || !out || (order >= 6 && !a) || (order >= 8 && !jerk))
+        return fail(NB_ERR_ARG, "a required pointer is NULL");
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
-        snprintf(g_err, sizeof g_err, "no usable CUDA device");
-        return fail(NB_ERR_CUDA);
+        return fail(NB_ERR_CUDA, "no usable CUDA device");
     }
     unsigned char* scratch = nullptr;
     int rc = scratch_address(dev, &scratch);
-    if (rc != NB_OK) return fail(rc);
+    if (rc != NB_OK) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int nn = (int)n, na = (int)n_act;
     if (precision == NB_MIXED) {
@@ -223,8 +217,7 @@ extern "C" int nb_force_static(int order, int precision, int64_t n, const double
         else if (order == 6) rc = run_static<6, false>(m, eps2, x, v, a, jerk, nn, idx, na, out, st, scratch, sms);
         else rc = run_static<8, false>(m, eps2, x, v, a, jerk, nn, idx, na, out, st, scratch, sms);
     }
-    if (rc == NB_ERR_CUDA) snprintf(g_err, sizeof g_err, "a CUDA call or launch failed");
-    else if (rc != NB_OK) snprintf(g_err, sizeof g_err, "a device kernel reported error %d (index out of range?)", rc);
-    return rc == NB_OK ? rc : fail(rc);
+    if (rc == NB_ERR_CUDA) return fail(rc, "a CUDA call or launch failed");
+    if (rc != NB_OK) return fail(rc, "a device kernel reported error %d (index out of range?)", rc);
+    return NB_OK;
 }
-

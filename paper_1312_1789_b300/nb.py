@@ -57,6 +57,9 @@ SIGNATURES = {
     "nb_get_launch": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "nb_get_pair_warps": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "nb_set_jsplit": (C.c_int, [_P, C.c_int]),
+    "nb_set_jrange": (C.c_int, [_P, C.c_int64, C.c_int64]),
+    "nb_copy_force": (C.c_int, [_P, _P, _I64, _I64]),
+    "nb_reduce_force": (C.c_int, [_P, _P, C.c_int]),
     "nb_version": (C.c_char_p, []),
     "nb_set_block_step": (C.c_int, [_P, C.c_double]),
     "nb_set_profiling": (C.c_int, [_P, C.c_int]),
@@ -84,6 +87,7 @@ SIGNATURES = {
     "nb_batch_get_state": (C.c_int, [_P, _D, _D, _D, _D]),
 }
 NB_STATIC_MAX_N = 16384
+NB_JTILE = 128
 NB_NPHASES = 6
 NB_TUNE_MAX = 32
 PHASES = ("sched", "predict", "force", "reduce", "correct", "other")
@@ -221,6 +225,23 @@ class NBody:
 
     def set_jsplit(self, js: int):
         self._check(self._L.nb_set_jsplit(self._h, int(js)))
+
+    # ------------------------------------------- j decomposition across ranks
+    def set_jrange(self, j_begin: int, j_end: int):
+        self._check(self._L.nb_set_jrange(self._h, int(j_begin), int(j_end)))
+
+    def copy_force(self, dst):
+        """Copy the last force result into dst (a CUDA float64 tensor or a numpy
+        array of ncomp x n_act); returns (ncomp, n_act).  Ordered on the
+        context's stream."""
+        nc, na = C.c_int64(), C.c_int64()
+        ptr = dst.data_ptr() if hasattr(dst, "data_ptr") else np.ascontiguousarray(dst).ctypes.data
+        self._check(self._L.nb_copy_force(self._h, _P(ptr), C.byref(nc), C.byref(na)))
+        return nc.value, na.value
+
+    def reduce_force(self, parts, n_parts: int):
+        """parts: CUDA float64 tensor [n_parts][ncomp][n_act] of force results."""
+        self._check(self._L.nb_reduce_force(self._h, _P(parts.data_ptr()), int(n_parts)))
 
     # ------------------------------------------------------------- the method
     def set_particles(self, m, x, v):

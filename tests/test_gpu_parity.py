@@ -440,30 +440,66 @@ def test_energy_parity(prec):
 
 
 # ----------------------------------------------------- 65536 Plummer, sampled
-def test_plummer_65536_sampled_blocks_parity():
-    # The 65536-particle Plummer sphere on the mixed path, stepped block by
-    # block through the C ABI; on sampled blocks (small ones, and the first
-    # large one) the force of up to 256 of the active particles against the
-    # oracle on the very store the kernel read.
+def test_plummer_65536_sampled_blocks_parity_to_t1():
+    # The 65536-particle Plummer sphere on the mixed path, integrated to
+    # t = 1 as CUDA-graph replays of device-driven block cycles.  At 16
+    # times spread over the run, one block is stepped through the C ABI and
+    # the force of up to 256 of its active particles is compared with the
+    # oracle on the very store the kernel read: alternately the synchronised
+    # block at t = k/16 (every particle active) and the first block after
+    # it (the particles on the shortest steps), so that early and late
+    # blocks (after the core has evolved), large and small, are all checked.
     wl = ics.standard_workload(1)
     ctx = make_ctx(wl.m, wl.x, wl.v, wl.eps2, 6, nb.NB_MIXED)
+    ctx.set_graph(64)
     rng = np.random.default_rng(65536)
-    checked, large = 0, False
-    for b in range(80):
+    checks, sizes, strict = [], [], {}
+    for k in range(1, 17):
+        t_k = k / 16.0
+        ctx.step_until(t_k - 2.0 ** -30 if k % 2 else t_k)
         tb, idx = ctx.next_block(want_idx=True)
+        assert (tb == t_k) == bool(k % 2), (k, tb)
         ctx.predict(tb)
         ctx.force()
-        if b % 16 == 0 or (len(idx) > 1024 and not large):
-            large = large or len(idx) > 1024
-            pos = np.arange(len(idx)) if len(idx) <= 256 else np.sort(rng.choice(len(idx), 256, replace=False))
-            G = ctx.get_force(len(idx))
-            O = oracle_force_on_predicted(ctx, wl.m, wl.eps2, idx[pos].astype(np.int32), 6)
-            Gs = {k: G[k][pos] for k in G}
-            assert_force_close(Gs, O, 6, nb.NB_MIXED, f"block {b} (t = {tb}, {len(idx)} active)")
-            checked += 1
+        pos = np.arange(len(idx)) if len(idx) <= 256 else np.sort(rng.choice(len(idx), 256, replace=False))
+        G = ctx.get_force(len(idx))
+        O = oracle_force_on_predicted(ctx, wl.m, wl.eps2, idx[pos].astype(np.int32), 6)
+        v = assert_force_close({key: G[key][pos] for key in G}, O, 6, nb.NB_MIXED,
+                               f"t = {tb} ({len(idx)} active)")
+        for key, r in v.items():
+            strict.setdefault(key, []).append(r["strict_pass"] * r["n"])
         ctx.correct()
-    assert checked >= 5 and large
+        checks.append(tb)
+        sizes.append(len(idx))
+    n_checked = sum(min(s, 256) for s in sizes)
+    print("65536 Plummer to t = 1: %d blocks checked (t = %.4f .. %.4f, %d .. %d active); strict pass: %s"
+          % (len(checks), checks[0], checks[-1], min(sizes), max(sizes),
+             ", ".join(f"{k} {sum(v) / n_checked:.4f}" for k, v in strict.items())))
+    assert len(checks) == 16 and checks[-1] > 1.0 and max(sizes) == wl.n and min(sizes) < 1024
     ctx.close()
+
+
+def test_mixed_energy_error_within_twice_fp64_after_one_time_unit():
+    # The spec energy target: a 4096-particle Plummer sphere integrated
+    # for one time unit on both paths; |dE/E| of the mixed path within twice
+    # the FP64 path's (energies measured in FP64 at t = 0 and t = 1).
+    wl = ics.plummer_cluster(4096, 1001, 1e-4, 6, 1.0)
+    out = {}
+    for prec in PRECS:
+        ctx = make_ctx(wl.m, wl.x, wl.v, wl.eps2, 6, prec)
+        ctx.set_precision(nb.NB_FP64)
+        e0 = sum(ctx.energy())
+        ctx.set_precision(prec)
+        ctx.set_graph(64)
+        nblk, _ = ctx.step_until(1.0)
+        ctx.set_precision(nb.NB_FP64)
+        assert np.all(ctx.get_state()["t"] == 1.0)
+        out[prec] = ((sum(ctx.energy()) - e0) / abs(e0), nblk)
+        ctx.close()
+    print("4096 Plummer to t = 1: dE/E fp64 %.4e (%d blocks), mixed %.4e (%d blocks)"
+          % (out[nb.NB_FP64][0], out[nb.NB_FP64][1], out[nb.NB_MIXED][0], out[nb.NB_MIXED][1]))
+    assert abs(out[nb.NB_MIXED][0]) <= 2.0 * abs(out[nb.NB_FP64][0])
+    assert abs(out[nb.NB_FP64][0]) < 1e-3
 
 
 # ------------------------------------------------------------ full-size sample

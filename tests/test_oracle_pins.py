@@ -202,10 +202,8 @@ def test_predictor_exact_on_polynomials(orc, order):
     assert np.allclose(xp, _eval(coef, t), rtol=1e-14, atol=1e-14)
     assert np.allclose(vp, _eval(coef, t, 1), rtol=1e-14, atol=1e-14)
     if order >= 6:
-        # order 6 predicts a to the crackle term: exact for a of degree <= 3
-        if order == 6:
-            coef3 = coef.copy()
-            coef3[:, :, 6:] = 0
+        # a is predicted to the crackle term (order 6) or to a^(5) (order 8):
+        # exact, since a of this x is a polynomial of degree deg - 2
         assert np.allclose(ap, _eval(coef, t, 2), rtol=1e-13, atol=1e-13)
     if order == 8:
         assert np.allclose(jp, _eval(coef, t, 3), rtol=1e-13, atol=1e-13)
@@ -292,6 +290,128 @@ def test_timestep_criterion_circular_orbit(orc, order):
     dt = orc.dt_criterion(order, eta, D)
     want = math.sqrt(eta) / w if order == 4 else eta / w
     assert dt == pytest.approx(want, rel=1e-14)
+
+
+def _fg_series(kmax):
+    """Lagrange f and g series of the Kepler problem: the k-th time derivative
+    of the relative position is F_k r + G_k v, with F_k, G_k polynomials in
+    u = M/r^3, p = r.v/r^2, q = v.v/r^2 - u.  They follow from r'' = -u r by
+    differentiating along the orbit, with du/dt = -3up, dp/dt = q - 2p^2,
+    dq/dt = -p(u + 2q) (textbook celestial mechanics).  This route uses the
+    equation of motion only, none of the oracle's pair formulas."""
+    import sympy as sp
+    u, p, q = sp.symbols("u p q")
+
+    def ddt(e):
+        return sp.diff(e, u) * (-3 * u * p) + sp.diff(e, p) * (q - 2 * p ** 2) + sp.diff(e, q) * (-p * (u + 2 * q))
+
+    F, G = [sp.Integer(1)], [sp.Integer(0)]
+    for _ in range(kmax):
+        F, G = F + [sp.expand(ddt(F[-1]) - u * G[-1])], G + [sp.expand(F[-1] + ddt(G[-1]))]
+    return [sp.lambdify((u, p, q), f) for f in F], [sp.lambdify((u, p, q), g) for g in G]
+
+
+_FG = {}
+
+
+def _kepler_derivatives(r, v, M, kmax=9):
+    """d^k r / dt^k for k = 0..kmax of the relative orbit at (r, v)."""
+    if kmax not in _FG:
+        _FG[kmax] = _fg_series(kmax)
+    F, G = _FG[kmax]
+    rr = float(r @ r)
+    u = M / rr ** 1.5
+    p, q = float(r @ v) / rr, float(v @ v) / rr - u
+    return np.array([F[k](u, p, q) * r + G[k](u, p, q) * v for k in range(kmax + 1)])
+
+
+def _kepler_state(e, t, a=1.0, M=1.0):
+    """Relative position and velocity at time t after apocentre (Kepler's equation)."""
+    n = math.sqrt(M / a ** 3)
+    mean = math.pi + n * t
+    E = mean
+    for _ in range(100):
+        E -= (E - e * math.sin(E) - mean) / (1 - e * math.cos(E))
+    Ed = n / (1 - e * math.cos(E))
+    b = a * math.sqrt(1 - e * e)
+    return (np.array([a * (math.cos(E) - e), b * math.sin(E), 0.0]),
+            np.array([-a * math.sin(E) * Ed, b * math.cos(E) * Ed, 0.0]))
+
+
+@pytest.mark.parametrize("t", [math.pi, 2.9, 0.7])
+def test_force_derivatives_on_an_eccentric_orbit(orc, t):
+    # Unsoftened pair (0.3 + 0.7) on an e = 0.9 orbit, at pericentre (t = pi
+    # after apocentre, where r.v = 0), just before it (where alpha, beta and
+    # gamma are all large and non-zero) and far out.  Body i's acceleration is
+    # (m_j / M) times the relative one, so its acc, jerk, snap and crackle are
+    # (m_j / M) r^(2..5), taken from the f and g series.  Each pair term of
+    # the force derivatives (the 3 alpha A of J, the 6 alpha J + 3 beta A of S,
+    # the 9 alpha S + 9 beta J + 3 gamma A of C) is large here, so a dropped
+    # term, a wrong coefficient or a wrong sign fails.
+    M, m = 1.0, np.array([0.3, 0.7])
+    r, v = _kepler_state(0.9, t, M=M)
+    D = _kepler_derivatives(r, v, M, 5)
+    sgn = np.array([1.0, -1.0])  # x0 - x1 = r
+    frac = np.array([m[1] / M, m[0] / M])
+    x = np.array([sgn[i] * frac[i] * D[0] for i in range(2)])
+    vv = np.array([sgn[i] * frac[i] * D[1] for i in range(2)])
+    aa = np.array([sgn[i] * frac[i] * D[2] for i in range(2)])
+    jj = np.array([sgn[i] * frac[i] * D[3] for i in range(2)])
+    out = orc.force(m, np.zeros(2), x, vv, aa, jj, order=8)
+    for k, key in enumerate(("acc", "jerk", "snap", "crackle")):
+        for i in range(2):
+            want = sgn[i] * frac[i] * D[k + 2]
+            assert np.max(np.abs(out[key][i] - want)) <= 1e-12 * np.linalg.norm(want), (key, i)
+
+
+@pytest.mark.parametrize("order", [6, 8])
+@pytest.mark.parametrize("t", [math.pi, 2.9, 0.0])
+def test_timestep_criterion_off_the_circle(orc, order, t):
+    # On an e = 0.9 Kepler orbit the derivative norms |a^(k)| are far from
+    # the geometric sequence w^k |a| of the circle, so the criterion's
+    # pairing (sqrt(|a||a^(2)|) with |a^(1)|, sqrt(|a^(p-3)||a^(p-1)|) with
+    # |a^(p-2)|), its plain (not squared) norms and its 1/(p-3) power are all
+    # visible.  Derivatives from the f and g series, at pericentre, near it
+    # and at apocentre.
+    eta = 0.2
+    r, v = _kepler_state(0.9, t)
+    D = _kepler_derivatives(r, v, 1.0, order + 1)[2:2 + order]
+    n = [float(np.linalg.norm(d)) for d in D]
+    p = order
+
+    def crit(top, bottom, power):
+        return eta * (top / bottom) ** power
+
+    want = crit(math.sqrt(n[0] * n[2]) + n[1], math.sqrt(n[p - 3] * n[p - 1]) + n[p - 2], 1.0 / (p - 3))
+    got = orc.dt_criterion(order, eta, D)
+    assert got == pytest.approx(want, rel=1e-12)
+    # the readings this pin tells apart differ by far more than its tolerance
+    squared = crit(n[0] * n[2] + n[1] ** 2, n[p - 3] * n[p - 1] + n[p - 2] ** 2, 0.5 / (p - 3))
+    swapped = crit(math.sqrt(n[0] * n[1]) + n[2], math.sqrt(n[p - 3] * n[p - 2]) + n[p - 1], 1.0 / (p - 3))
+    assert abs(squared / want - 1) > 1e-3 and abs(swapped / want - 1) > 1e-2
+
+
+@pytest.mark.parametrize("order", [6, 8])
+def test_steps_per_orbit_on_an_eccentric_orbit(orc, order):
+    # Integrate two e = 0.9 orbits (no step cap: dt_max = 1) at eta and eta/2.
+    # With eta used linearly the step count doubles when eta halves (a root
+    # of eta, as in the order-4 form, would give sqrt(2)).  Each step is a
+    # power of two within a factor 2 below the criterion, so the count per
+    # orbit lies between I and 2I, I = the integral over one orbit of
+    # dt / dt_crit(t) with the criterion evaluated on the exact orbit.
+    T = 2 * math.pi
+    ts = np.linspace(0.0, T, 12001)
+    counts = {}
+    for eta in (0.2, 0.1):
+        inv = [1.0 / orc.dt_criterion(order, eta, _kepler_derivatives(*_kepler_state(0.9, t), 1.0,
+                                                                       order + 1)[2:2 + order]) for t in ts]
+        integral = float(np.trapezoid(inv, ts))
+        r, v = _kepler_state(0.9, 0.0)
+        m = np.array([0.5, 0.5])
+        st = orc.State(m, 0.0, np.array([0.5 * r, -0.5 * r]), np.array([0.5 * v, -0.5 * v]))
+        counts[eta] = orc.integrate(st, order=order, t_end=2 * T, eta=eta, dt_max=1.0) / 2
+        assert integral <= counts[eta] <= 2 * integral, (eta, counts[eta], integral)
+    assert counts[0.1] / counts[0.2] == pytest.approx(2.0, rel=0.05)
 
 
 @pytest.mark.parametrize("eta_s", [0.01, 0.05])

@@ -1,9 +1,9 @@
 """nb_force_static: the force call for callers that cannot allocate device memory
 (for example code inside another framework's memory pool or a loop that must not
-allocate once running).  Checked through the C ABI against nb_force on the same
-instant, with the parity tolerances of the other GPU tests, on two calls in a
-row (the fixed scratch keeps the first call's contents).  This file is named to
-be collected last."""
+allocate once running).  Checked through the C ABI against the oracle's direct
+sum on the same state, with the parity gate of the other GPU tests, on two calls
+in a row (the fixed scratch keeps the first call's contents), and against
+nb_force on the same instant.  This file is named to be collected last."""
 import ctypes as C
 
 import numpy as np
@@ -11,6 +11,7 @@ import pytest
 
 import oracle as orc
 from gpu_common import assert_force_close
+from oracle import parity
 
 pytestmark = pytest.mark.gpu
 
@@ -19,7 +20,7 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
-def test_static_force_matches_nb_force_on_two_calls():
+def test_static_force_matches_oracle_and_nb_force_on_two_calls():
     torch = pytest.importorskip("torch")
     from paper_1312_1789_b300 import build, ics, nb
     build.build()
@@ -41,11 +42,11 @@ def test_static_force_matches_nb_force_on_two_calls():
             S = ctx.get_state()
             ctx.predict(0.0)
             ctx.force(idx)
-            ref = ctx.get_force(len(idx))
-            xp, vp, ap, jp = ctx.get_predicted()
-            ref["absum"] = orc.force(m, eps2, xp, vp, ap, jp if order == 8 else None, order=order, idx=idx,
-                                     nthreads=16)["absum"]
+            via_ctx = ctx.get_force(len(idx))
             ctx.close()
+            # the oracle on the very state handed to the static call (no prediction)
+            ref = orc.force(m, eps2, S["x"], S["v"], S["d"][:, 0], S["d"][:, 1] if order == 8 else None,
+                            order=order, idx=idx, nthreads=16)
             dev = {k: torch.from_numpy(np.ascontiguousarray(a)).cuda()
                    for k, a in (("m", m), ("eps2", eps2), ("x", S["x"]), ("v", S["v"]),
                                 ("a", S["d"][:, 0]), ("j", S["d"][:, 1]))}
@@ -65,6 +66,10 @@ def test_static_force_matches_nb_force_on_two_calls():
                 if order >= 8:
                     G["crackle"] = got[9:12].T
                 assert_force_close(G, ref, order, prec, f"static call {call}, precision {prec}, order {order}")
+                # nb_force on the same instant: both lie within the gate of the
+                # oracle, so they differ by at most twice its bound
+                st = parity.force_parity(G, dict(via_ctx, absum=ref["absum"]), order, prec)
+                assert all(r["worst"] <= 2.0 for r in st.values()), (call, prec, order, st)
 
 
 def test_static_force_rejects_sizes_beyond_its_scratch():
