@@ -382,7 +382,14 @@ def cusp_leg(args, nb, ics, stream, torch):
         w = {"workload": full.name + " to t=1/256 with dt_max=1/256"}
         for name, p in (("mixed", nb.NB_MIXED), ("fp64", nb.NB_FP64)):
             w[name] = cusp_run(nb, full, p, stream, torch, 1.0 / 256, dt_max=1.0 / 256)
+        # the drift of the holes' two-body elements that the precision causes:
+        # mixed minus FP64 at the same time (the elements themselves are not
+        # conserved, the stars inside the orbit outweigh the binary)
+        w["binary_a_mixed_minus_fp64"] = w["mixed"]["binary_a"][1] - w["fp64"]["binary_a"][1]
+        w["binary_e_mixed_minus_fp64"] = w["mixed"]["binary_e"][1] - w["fp64"]["binary_e"][1]
         res["full_short"] = w
+    r["binary_a_mixed_minus_fp64"] = r["mixed"]["binary_a"][1] - r["fp64"]["binary_a"][1]
+    r["binary_e_mixed_minus_fp64"] = r["mixed"]["binary_e"][1] - r["fp64"]["binary_e"][1]
     return res
 
 
@@ -442,6 +449,31 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
         out["mixed_vs_fp64"] = res["mixed"] / res["fp64"]
     except Exception as e:  # pragma: no cover
         out["fp64"] = {"error": repr(e)}
+    # ---- parity at the benchmarked size: 2048 sampled particles (both holes
+    #      among them) of the nucleus, every particle active, against the
+    #      oracle on the very store the kernel read; the force gate of the
+    #      test suite and the fraction within the plain relative bound
+    try:
+        import oracle as orc
+        from oracle import parity
+        ctx.set_state(S["x"], S["v"], S["d"], S["t"], S["dt"])
+        ctx.predict(float(S["t"][0]) + h)
+        rng = np.random.default_rng(2048)
+        blk = np.unique(np.concatenate([rng.choice(n - 2, 2046, replace=False), [n - 2, n - 1]])).astype(np.int32)
+        allidx = np.arange(n, dtype=np.int32)
+        ctx.force(allidx)
+        G = ctx.get_force(n)
+        xp, vp, ap, _ = ctx.get_predicted()
+        t0 = time.perf_counter()
+        O = orc.force(wl.m, wl.eps2, xp, vp, ap, None, order=wl.order, idx=blk, nthreads=os.cpu_count() or 1)
+        st = parity.force_parity({k: G[k][blk] for k in G}, O, wl.order, prec)
+        out["parity"] = {"sample": f"{len(blk)} of {n} particles (both holes), N_act = N, oracle on the same "
+                                   f"predicted store ({time.perf_counter() - t0:.1f} s)",
+                         "within_gate": all(r["worst"] <= 1.0 for r in st.values()),
+                         **{k: {"strict_pass": r["strict_pass"], "worst_over_gate": r["worst"],
+                                "worst_rel_err": r["rel_err"], "worst_cond": r["cond"]} for k, r in st.items()}}
+    except Exception as e:  # pragma: no cover
+        out["parity"] = {"error": repr(e)}
     # ---- per-N_act curve of the mixed force on the 2^20 store (powers of two)
     try:
         ctx.set_state(S["x"], S["v"], S["d"], S["t"], S["dt"])

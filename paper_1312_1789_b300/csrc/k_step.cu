@@ -26,6 +26,14 @@ namespace nb {
 // left out.
 constexpr int SCHED_NT = 256;
 constexpr int SCHED_PER_MAX = 16;
+// The predictor takes two consecutive particles per thread (16-byte loads,
+// twice the bytes in flight) on stores large enough that the scheduler
+// gives each thread SCHED_PER_MAX particles (n > 8 SCHED_NT SMs); below
+// that the grid has too few CTAs to fill the SMs twice over and one particle
+// per thread is faster (measured at N = 65536: 28 against 33 us per block
+// for scheduler and predictor; at 2^20 the two-particle form moves the
+// predictor from 51 % to 64 % of the HBM bandwidth).
+__host__ __device__ constexpr bool pred_two(int per) { return per >= SCHED_PER_MAX; }
 constexpr unsigned long long KEY_NONE = ~0ull;
 
 // k(a) < k(b) <=> a < b for non-NaN doubles; NaN -> KEY_NONE
@@ -86,15 +94,45 @@ __device__ __forceinline__ int block_isum(int v, int* ws)
     return s;
 }
 
+// exclusive scan over the CTA; every thread gets its prefix and the total
+__device__ __forceinline__ int block_exscan(int v, int* ws, int* total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    __syncthreads();  // ws reuse
+    if (lane == 31) ws[warp] = incl;
+    __syncthreads();
+    int base = 0, all = 0;
+    for (int w = 0; w < SCHED_NT / 32; ++w) {
+        if (w < warp) base += ws[w];
+        all += ws[w];
+    }
+    *total = all;
+    return base + incl - v;
+}
+
+// First pass: chunk b publishes its minimum of t + dt and how many of its
+// particles reach it.  The last CTA to finish (a ticket in the device
+// scalars) then reduces the chunk table in chunk order: the block time's key
+// (the minimum), the number of matches, and each chunk's offset in the
+// active list, so that the second pass reads them instead of the table.
+// The order of that reduction does not depend on which CTA is last.
 template <int PER>
 __global__ void __launch_bounds__(SCHED_NT) k_sched_chunk(const double* __restrict__ t, const double* __restrict__ dt,
                                                           int64_t n, unsigned long long* __restrict__ cmin,
-                                                          int32_t* __restrict__ ccnt, DevScalars* sc)
+                                                          int32_t* __restrict__ ccnt, int32_t* __restrict__ coff,
+                                                          DevScalars* sc)
 {
     pdl_wait();
     pdl_release();
     __shared__ unsigned long long wk[SCHED_NT / 32];
     __shared__ int wi[SCHED_NT / 32];
+    __shared__ bool last;
     const int64_t i0 = ((int64_t)blockIdx.x * SCHED_NT + threadIdx.x) * PER;
     unsigned long long key[PER];
     unsigned long long mn = KEY_NONE;
@@ -117,41 +155,60 @@ __global__ void __launch_bounds__(SCHED_NT) k_sched_chunk(const double* __restri
     if (threadIdx.x == 0) {
         cmin[blockIdx.x] = m_b;
         ccnt[blockIdx.x] = c;
+        __threadfence();  // the table entry is visible before the ticket is taken
+        last = atomicAdd(&sc->sched_ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int nch = (int)gridDim.x;
+    unsigned long long tm = KEY_NONE;
+    for (int k = threadIdx.x; k < nch; k += SCHED_NT) {
+        const unsigned long long v = __ldcg(cmin + k);
+        tm = v < tm ? v : tm;
+    }
+    const unsigned long long tbk = block_kmin(tm, wk);
+    // chunks [k0, k1) per thread, in order
+    const int seg = (nch + SCHED_NT - 1) / SCHED_NT;
+    const int k0 = min((int)threadIdx.x * seg, nch), k1 = min(k0 + seg, nch);
+    int mine = 0;
+    for (int k = k0; k < k1; ++k) mine += (__ldcg(cmin + k) == tbk && tbk != KEY_NONE) ? __ldcg(ccnt + k) : 0;
+    int total;
+    int off = block_exscan(mine, wi, &total);
+    for (int k = k0; k < k1; ++k) {
+        coff[k] = off;
+        off += (__ldcg(cmin + k) == tbk && tbk != KEY_NONE) ? __ldcg(ccnt + k) : 0;
+    }
+    if (threadIdx.x == 0) {
+        sc->tb_key = tbk;
+        sc->n_match = total;
+        sc->sched_ticket = 0;  // ready for the next block
     }
 }
 
-// Second pass (every CTA): t_blk and this chunk's offset from the chunk table,
-// then the chunk's matches in index order.  CTA 0 publishes t_blk and n_act
-// (and, in a device-driven cycle, applies the launch-shape gate).  Returns
-// t_blk.
+// Second pass (every CTA): t_blk, the match count and this chunk's offset as
+// the first pass's last CTA left them, then the chunk's matches in index
+// order.  CTA 0 publishes t_blk and n_act (and, in a device-driven cycle,
+// applies the launch-shape gate).  Returns t_blk.
 template <int PER>
 __device__ __forceinline__ double sched_compact_body(const double* __restrict__ t, const double* __restrict__ dt,
                                                      int64_t n, const unsigned long long* __restrict__ cmin,
-                                                     const int32_t* __restrict__ ccnt, int nch,
+                                                     const int32_t* __restrict__ coff, int nch,
                                                      int32_t* __restrict__ idx, DevScalars* sc,
                                                      const GateArgs* gate = nullptr)
 {
-    __shared__ unsigned long long wk[SCHED_NT / 32];
     __shared__ int wi[SCHED_NT / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long mn = KEY_NONE;
-    for (int k = threadIdx.x; k < nch; k += SCHED_NT) mn = cmin[k] < mn ? cmin[k] : mn;
-    const unsigned long long tbk = block_kmin(mn, wk);
+    const unsigned long long tbk = sc->tb_key;
     const double tb = key_time(tbk);
-    int before = 0, total = 0;
-    for (int k = threadIdx.x; k < nch; k += SCHED_NT) {
-        const int ck = cmin[k] == tbk ? ccnt[k] : 0;
-        total += ck;
-        if (k < (int)blockIdx.x) before += ck;
-    }
-    total = block_isum(total, wi);
-    const int off = block_isum(before, wi);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int total = sc->n_match;
         sc->t_blk = tb;
         sc->n_act = total;
         if (gate) cycle_gate_apply(sc, tb, total, *gate);
     }
     if (cmin[blockIdx.x] != tbk || tbk == KEY_NONE) return tb;  // CTA-uniform: no match in this chunk
+    const int off = coff[blockIdx.x];
     const int64_t i0 = ((int64_t)blockIdx.x * SCHED_NT + threadIdx.x) * PER;
     unsigned flags = 0;
 #pragma unroll
@@ -165,7 +222,6 @@ __device__ __forceinline__ double sched_compact_body(const double* __restrict__ 
         const int y = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += y;
     }
-    __syncthreads();  // wi reuse
     if (lane == 31) wi[warp] = incl;
     __syncthreads();
     int wbase = 0;
@@ -183,10 +239,10 @@ template <int PER>
 __global__ void __launch_bounds__(SCHED_NT) k_sched_compact(const double* __restrict__ t,
                                                             const double* __restrict__ dt, int64_t n,
                                                             const unsigned long long* __restrict__ cmin,
-                                                            const int32_t* __restrict__ ccnt, int nch,
+                                                            const int32_t* __restrict__ coff, int nch,
                                                             int32_t* __restrict__ idx, DevScalars* sc)
 {
-    sched_compact_body<PER>(t, dt, n, cmin, ccnt, nch, idx, sc);
+    sched_compact_body<PER>(t, dt, n, cmin, coff, nch, idx, sc);
 }
 
 // Particles per scheduler thread: the smallest power of two that covers n
@@ -215,8 +271,9 @@ cudaError_t launch_sched(nb_ctx* c)
     int per, nch;
     sched_layout(c->n, c->sm_count, &per, &nch);
 #define NB_S(P)                                                                                                      \
-    k_sched_chunk<P><<<nch, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, c->chunk_min, c->chunk_cnt, c->sc);       \
-    k_sched_compact<P><<<nch, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, c->chunk_min, c->chunk_cnt, nch,         \
+    k_sched_chunk<P><<<nch, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, c->chunk_min, c->chunk_cnt,               \
+                                                      c->chunk_off, c->sc);                                          \
+    k_sched_compact<P><<<nch, SCHED_NT, 0, c->stream>>>(c->t, c->dt, c->n, c->chunk_min, c->chunk_off, nch,         \
                                                         c->act_idx, c->sc)
     NB_SCHED_PER(per, NB_S)
 #undef NB_S
@@ -268,33 +325,75 @@ __device__ __forceinline__ double f32_to_f64(float f)
     return __longlong_as_double((long long)(sgn | ((unsigned long long)(e - 127 + 1023) << 52) | (mant << 29)));
 }
 
+// The state a particle's prediction reads: x, v, the derivatives it holds
+// (a, j, s, c; order 8 also a^(4), a^(5)), t, m, eps^2.
+template <int ORDER>
+struct PredIn {
+    static constexpr int ND = ORDER == 8 ? 6 : 4;
+    double x[3], v[3], d[ND][3];
+    double t, m, e;
+};
+
+template <int ORDER>
+__device__ __forceinline__ void pred_load(PredIn<ORDER>& s, int64_t i, const double* __restrict__ m,
+                                          const double* __restrict__ eps2, const double* __restrict__ x,
+                                          const double* __restrict__ v, const double* __restrict__ d,
+                                          const double* __restrict__ t, int64_t np)
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        s.x[c] = x[c * np + i];
+        s.v[c] = v[c * np + i];
+#pragma unroll
+        for (int k = 0; k < PredIn<ORDER>::ND; ++k) s.d[k][c] = d[(k * 3 + c) * np + i];
+    }
+    s.t = t[i];
+    s.m = m[i];
+    s.e = eps2[i];
+}
+
+// Two consecutive particles i, i + 1 (i even: the SoA rows are 16-byte
+// aligned) with one 16-byte load per array: half the load instructions and
+// twice the bytes in flight per thread of the one-particle form.
+template <int ORDER>
+__device__ __forceinline__ void pred_load2(PredIn<ORDER>& s0, PredIn<ORDER>& s1, int64_t i,
+                                           const double* __restrict__ m, const double* __restrict__ eps2,
+                                           const double* __restrict__ x, const double* __restrict__ v,
+                                           const double* __restrict__ d, const double* __restrict__ t, int64_t np)
+{
+    auto ld2 = [](const double* p) { return *reinterpret_cast<const double2*>(p); };
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double2 xx = ld2(x + c * np + i), vv = ld2(v + c * np + i);
+        s0.x[c] = xx.x, s1.x[c] = xx.y;
+        s0.v[c] = vv.x, s1.v[c] = vv.y;
+#pragma unroll
+        for (int k = 0; k < PredIn<ORDER>::ND; ++k) {
+            const double2 dd = ld2(d + (k * 3 + c) * np + i);
+            s0.d[k][c] = dd.x, s1.d[k][c] = dd.y;
+        }
+    }
+    const double2 tt = ld2(t + i), mm = ld2(m + i), ee = ld2(eps2 + i);
+    s0.t = tt.x, s1.t = tt.y;
+    s0.m = mm.x, s1.m = mm.y;
+    s0.e = ee.x, s1.e = ee.y;
+}
+
+// Prediction of one particle from its loaded state to tp, written as record i
+// of the j-particle store; real = false writes a padding record (m = 0,
+// eps2 = 1).
 template <int ORDER, bool MIXED>
-__device__ __forceinline__ void predict_one(const int64_t i, double tp, const double* __restrict__ m,
-                                            const double* __restrict__ eps2, const double* __restrict__ x,
-                                            const double* __restrict__ v, const double* __restrict__ d,
-                                            const double* __restrict__ t, int64_t n, int64_t np,
-                                            void* __restrict__ jstore, const double* __restrict__ tpc,
-                                            const int32_t* __restrict__ cid)
+__device__ __forceinline__ void pred_store(const PredIn<ORDER>& s, bool real, double tp, int64_t i,
+                                           void* __restrict__ jstore)
 {
     constexpr int RW = MIXED ? mixed_rw(ORDER) : fp64_rw(ORDER);
     double xp[3] = {0, 0, 0}, vp[3] = {0, 0, 0}, ap[3] = {0, 0, 0}, jp[3] = {0, 0, 0};
     float vf[3] = {0.f, 0.f, 0.f}, af[3] = {0.f, 0.f, 0.f}, jf[3] = {0.f, 0.f, 0.f};
     double mi = 0.0, ei = 1.0;
-    bool real = i < n;
-    if (real && tpc) {
-        // ensemble: each particle to its own cluster's block time; cid < 0 marks
-        // padding between clusters, an infinite time an idle cluster
-        const int k = cid[i];
-        if (k < 0) real = false;
-        else {
-            tp = tpc[k];
-            if (!(tp < INFINITY)) return;
-        }
-    }
     if (real) {
-        mi = m[i];
-        ei = eps2[i];
-        const double h = tp - t[i];
+        mi = s.m;
+        ei = s.e;
+        const double h = tp - s.t;
         const float hf = MIXED ? f64_to_f32_rz(h) : 0.0f;
         // Mixed: the FP32 tail needs every derivative within the float range
         // (interpolated high derivatives of a particle just out of a close
@@ -303,13 +402,14 @@ __device__ __forceinline__ void predict_one(const int64_t i, double tp, const do
         if (MIXED) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const double x0 = x[c * np + i], v0 = v[c * np + i];
-                const float a0 = f64_to_f32_rz(d[(0 * 3 + c) * np + i]), j0 = f64_to_f32_rz(d[(1 * 3 + c) * np + i]);
-                const float s0 = f64_to_f32_rz(d[(2 * 3 + c) * np + i]), c0 = f64_to_f32_rz(d[(3 * 3 + c) * np + i]);
+                const double x0 = s.x[c], v0 = s.v[c];
+                const float a0 = f64_to_f32_rz(s.d[0][c]), j0 = f64_to_f32_rz(s.d[1][c]);
+                const float s0 = f64_to_f32_rz(s.d[2][c]), c0 = f64_to_f32_rz(s.d[3][c]);
                 float T;
                 bool fin = isfinite(a0) && isfinite(j0) && isfinite(s0) && isfinite(c0);
                 if (ORDER == 8) {
-                    const float d4 = f64_to_f32_rz(d[(4 * 3 + c) * np + i]), d5 = f64_to_f32_rz(d[(5 * 3 + c) * np + i]);
+                    const float d4 = f64_to_f32_rz(s.d[4 % PredIn<ORDER>::ND][c]);
+                    const float d5 = f64_to_f32_rz(s.d[5 % PredIn<ORDER>::ND][c]);
                     fin = fin && isfinite(d4) && isfinite(d5);
                     T = fmaf(hf, fmaf(hf, fmaf(hf, fmaf(hf, fmaf(hf, d5 * (1.f / 5040), d4 * (1.f / 720)),
                                                          c0 * (1.f / 120)), s0 * (1.f / 24)), j0 * (1.f / 6)),
@@ -334,11 +434,11 @@ __device__ __forceinline__ void predict_one(const int64_t i, double tp, const do
         if (fp64_series) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const double x0 = x[c * np + i], v0 = v[c * np + i];
-                const double a0 = d[(0 * 3 + c) * np + i], j0 = d[(1 * 3 + c) * np + i];
-                const double s0 = d[(2 * 3 + c) * np + i], c0 = d[(3 * 3 + c) * np + i];
+                const double x0 = s.x[c], v0 = s.v[c];
+                const double a0 = s.d[0][c], j0 = s.d[1][c];
+                const double s0 = s.d[2][c], c0 = s.d[3][c];
                 if (ORDER == 8) {
-                    const double d4 = d[(4 * 3 + c) * np + i], d5 = d[(5 * 3 + c) * np + i];
+                    const double d4 = s.d[4 % PredIn<ORDER>::ND][c], d5 = s.d[5 % PredIn<ORDER>::ND][c];
                     xp[c] = x0 + h * (v0 + h * (a0 * (1.0 / 2) + h * (j0 * (1.0 / 6) + h * (s0 * (1.0 / 24) +
                             h * (c0 * (1.0 / 120) + h * (d4 * (1.0 / 720) + h * d5 * (1.0 / 5040)))))));
                     vp[c] = v0 + h * (a0 + h * (j0 * (1.0 / 2) + h * (s0 * (1.0 / 6) + h * (c0 * (1.0 / 24) +
@@ -393,6 +493,46 @@ __device__ __forceinline__ void predict_one(const int64_t i, double tp, const do
 }
 
 template <int ORDER, bool MIXED>
+__device__ __forceinline__ void predict_one(const int64_t i, double tp, const double* __restrict__ m,
+                                            const double* __restrict__ eps2, const double* __restrict__ x,
+                                            const double* __restrict__ v, const double* __restrict__ d,
+                                            const double* __restrict__ t, int64_t n, int64_t np,
+                                            void* __restrict__ jstore, const double* __restrict__ tpc,
+                                            const int32_t* __restrict__ cid)
+{
+    bool real = i < n;
+    if (real && tpc) {
+        // ensemble: each particle to its own cluster's block time; cid < 0 marks
+        // padding between clusters, an infinite time an idle cluster
+        const int k = cid[i];
+        if (k < 0) real = false;
+        else {
+            tp = tpc[k];
+            if (!(tp < INFINITY)) return;
+        }
+    }
+    PredIn<ORDER> s;
+    if (real) pred_load<ORDER>(s, i, m, eps2, x, v, d, t, np);
+    pred_store<ORDER, MIXED>(s, real, tp, i, jstore);
+}
+
+// Particles i and i + 1 of one system (i even, i + 1 < np).
+template <int ORDER, bool MIXED>
+__device__ __forceinline__ void predict_two(const int64_t i, double tp, const double* __restrict__ m,
+                                            const double* __restrict__ eps2, const double* __restrict__ x,
+                                            const double* __restrict__ v, const double* __restrict__ d,
+                                            const double* __restrict__ t, int64_t n, int64_t np,
+                                            void* __restrict__ jstore)
+{
+    PredIn<ORDER> s0, s1;
+    pred_load2<ORDER>(s0, s1, i, m, eps2, x, v, d, t, np);
+    pred_store<ORDER, MIXED>(s0, i < n, tp, i, jstore);
+    pred_store<ORDER, MIXED>(s1, i + 1 < n, tp, i + 1, jstore);
+}
+
+// TWO: one system (tpc == nullptr), two consecutive particles per thread;
+// else one particle per thread (ensembles).
+template <int ORDER, bool MIXED, bool TWO>
 __global__ void __launch_bounds__(256) k_predict(const double* __restrict__ m, const double* __restrict__ eps2,
                                                  const double* __restrict__ x, const double* __restrict__ v,
                                                  const double* __restrict__ d, const double* __restrict__ t,
@@ -400,51 +540,53 @@ __global__ void __launch_bounds__(256) k_predict(const double* __restrict__ m, c
                                                  const double* __restrict__ tpc, const int32_t* __restrict__ cid,
                                                  const DevScalars* dyn)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = TWO ? 2 * g : g;
     if (i >= np) return;
     if (dyn) {
         if (dyn->idle) return;
         tp = dyn->t_blk;
     }
-    predict_one<ORDER, MIXED>(i, tp, m, eps2, x, v, d, t, n, np, jstore, tpc, cid);
+    if (TWO) predict_two<ORDER, MIXED>(i, tp, m, eps2, x, v, d, t, n, np, jstore);
+    else predict_one<ORDER, MIXED>(i, tp, m, eps2, x, v, d, t, n, np, jstore, tpc, cid);
 }
 
 // Second pass fused with the predictor.  The grid has one CTA per chunk or
-// per SCHED_NT records, whichever is more: the first nch CTAs compact their
-// chunks, the others only read t_blk from the chunk table; then every CTA
-// predicts SCHED_NT records to t_blk, one per thread (the predictor is
-// bound by memory latency, so it gets a thread per particle rather than the
-// scheduler's PER).  use_t_end: a device-driven cycle, which predicts
-// nothing past sc->t_end and whose force launch shape CTA 0 sets with the
-// gate.
+// per 2 SCHED_NT records, whichever is more: the first nch CTAs compact their
+// chunks, the others only read the block time the first pass published; then
+// every CTA predicts 2 SCHED_NT records to t_blk, two consecutive ones per
+// thread with 16-byte loads (the predictor is bound by memory traffic, so it
+// gets far more threads than the scheduler's PER particles each).
+// use_t_end: a device-driven cycle, which predicts nothing past sc->t_end and
+// whose force launch shape CTA 0 sets with the gate.
 template <int ORDER, bool MIXED, int PER>
 __global__ void __launch_bounds__(SCHED_NT) k_sched_compact_predict(
     const double* __restrict__ t, const double* __restrict__ dt, int64_t n,
-    const unsigned long long* __restrict__ cmin, const int32_t* __restrict__ ccnt, int nch,
+    const unsigned long long* __restrict__ cmin, const int32_t* __restrict__ coff, int nch,
     int32_t* __restrict__ idx, DevScalars* sc, int use_t_end, const double* __restrict__ m,
     const double* __restrict__ eps2, const double* __restrict__ x, const double* __restrict__ v,
     const double* __restrict__ d, int64_t np, void* __restrict__ jstore, GateArgs gate)
 {
     pdl_wait();
     pdl_release();
-    double tb;
-    if ((int)blockIdx.x < nch) {
-        tb = sched_compact_body<PER>(t, dt, n, cmin, ccnt, nch, idx, sc, use_t_end ? &gate : nullptr);
-    } else {
-        __shared__ unsigned long long wk[SCHED_NT / 32];
-        unsigned long long mn = KEY_NONE;
-        for (int k = threadIdx.x; k < nch; k += SCHED_NT) mn = cmin[k] < mn ? cmin[k] : mn;
-        tb = key_time(block_kmin(mn, wk));
-    }
+    const double tb = (int)blockIdx.x < nch
+                          ? sched_compact_body<PER>(t, dt, n, cmin, coff, nch, idx, sc, use_t_end ? &gate : nullptr)
+                          : key_time(sc->tb_key);
     if (use_t_end && !(tb <= sc->t_end)) return;
-    const int64_t i = (int64_t)blockIdx.x * SCHED_NT + threadIdx.x;
-    if (i < np) predict_one<ORDER, MIXED>(i, tb, m, eps2, x, v, d, t, n, np, jstore, nullptr, nullptr);
+    const int64_t g = (int64_t)blockIdx.x * SCHED_NT + threadIdx.x;
+    if (pred_two(PER)) {
+        if (2 * g < np) predict_two<ORDER, MIXED>(2 * g, tb, m, eps2, x, v, d, t, n, np, jstore);
+    } else if (g < np) {
+        predict_one<ORDER, MIXED>(g, tb, m, eps2, x, v, d, t, n, np, jstore, nullptr, nullptr);
+    }
 }
 
-// CTAs of the fused second pass: every chunk, and SCHED_NT records per CTA
-static int sched_predict_grid(int nch, int64_t np)
+// CTAs of the fused second pass: every chunk, and SCHED_NT or 2 SCHED_NT
+// records per CTA
+static int sched_predict_grid(int nch, int64_t np, int per)
 {
-    const int64_t g = (np + SCHED_NT - 1) / SCHED_NT;
+    const int64_t rec = pred_two(per) ? 2 * SCHED_NT : SCHED_NT;
+    const int64_t g = (np + rec - 1) / rec;
     return g > nch ? (int)g : nch;
 }
 
@@ -467,15 +609,15 @@ cudaError_t launch_sched_predict(nb_ctx* c, bool use_t_end, const int* shape_slo
         g.ntab = c->tune_n[pi];
     }
     const bool mixed = c->prec == NB_MIXED, pdl = c->pdl != 0;
-    const int gsp = sched_predict_grid(nch, c->np);
+    const int gsp = sched_predict_grid(nch, c->np, per);
     cudaError_t e = cudaSuccess;
 #define NB_SP(O, MX, P)                                                                                             \
     e = launch_k(k_sched_compact_predict<O, MX, P>, dim3(gsp), dim3(SCHED_NT), 0, c->stream, pdl, c->t, c->dt,     \
-                 c->n, c->chunk_min, c->chunk_cnt, nch, c->act_idx, c->sc, use_t_end ? 1 : 0, c->m, c->eps2, c->x, \
+                 c->n, c->chunk_min, c->chunk_off, nch, c->act_idx, c->sc, use_t_end ? 1 : 0, c->m, c->eps2, c->x, \
                  c->v, c->d, c->np, c->jstore, g)
 #define NB_S(P)                                                                                                     \
     e = launch_k(k_sched_chunk<P>, dim3(nch), dim3(SCHED_NT), 0, c->stream, pdl, c->t, c->dt, c->n, c->chunk_min,  \
-                 c->chunk_cnt, c->sc);                                                                              \
+                 c->chunk_cnt, c->chunk_off, c->sc);                                                                \
     if (e != cudaSuccess) return e;                                                                                 \
     if (c->order == 4) {                                                                                            \
         if (mixed) NB_SP(4, true, P); else NB_SP(4, false, P);                                                      \
@@ -493,15 +635,25 @@ cudaError_t launch_sched_predict(nb_ctx* c, bool use_t_end, const int* shape_slo
 cudaError_t launch_predict(nb_ctx* c, double t, const double* tpc, const int32_t* cid, const DevScalars* dyn)
 {
     const int nt = 256;
-    const int nb = (int)((c->np + nt - 1) / nt);
+    int per, nch;
+    sched_layout(c->n, c->sm_count, &per, &nch);
+    const bool two = tpc == nullptr && pred_two(per);  // one large system: two particles per thread
+    const int64_t per_cta = two ? 2 * nt : nt;
+    const int nb = (int)((c->np + per_cta - 1) / per_cta);
     const bool mixed = c->prec == NB_MIXED;
-#define NB_PRED(O)                                                                                       \
-    if (mixed)                                                                                           \
-        k_predict<O, true><<<nb, nt, 0, c->stream>>>(c->m, c->eps2, c->x, c->v, c->d, c->t, c->n, c->np, \
-                                                     t, c->jstore, tpc, cid, dyn);                       \
-    else                                                                                                 \
-        k_predict<O, false><<<nb, nt, 0, c->stream>>>(c->m, c->eps2, c->x, c->v, c->d, c->t, c->n,      \
-                                                      c->np, t, c->jstore, tpc, cid, dyn);
+#define NB_PRED_K(O, MX)                                                                                      \
+    if (two)                                                                                                  \
+        k_predict<O, MX, true><<<nb, nt, 0, c->stream>>>(c->m, c->eps2, c->x, c->v, c->d, c->t, c->n, c->np, \
+                                                         t, c->jstore, tpc, cid, dyn);                        \
+    else                                                                                                      \
+        k_predict<O, MX, false><<<nb, nt, 0, c->stream>>>(c->m, c->eps2, c->x, c->v, c->d, c->t, c->n,       \
+                                                          c->np, t, c->jstore, tpc, cid, dyn);
+#define NB_PRED(O)            \
+    if (mixed) {              \
+        NB_PRED_K(O, true)    \
+    } else {                  \
+        NB_PRED_K(O, false)   \
+    }
     if (c->order == 4) {
         NB_PRED(4)
     } else if (c->order == 6) {
@@ -510,6 +662,7 @@ cudaError_t launch_predict(nb_ctx* c, double t, const double* tpc, const int32_t
         NB_PRED(8)
     }
 #undef NB_PRED
+#undef NB_PRED_K
     return cudaGetLastError();
 }
 

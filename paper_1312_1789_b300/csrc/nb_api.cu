@@ -347,7 +347,7 @@ void nb_destroy(nb_ctx* c)
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     void* ptrs[] = {c->m, c->eps2, c->x, c->v, c->d, c->t, c->dt, c->pot, c->jstore, c->act_idx, c->all_idx,
-                    c->chunk_cnt, c->chunk_min, c->d_tune, c->stage, c->sc, c->red, c->f_idx, c->partial, c->F};
+                    c->chunk_cnt, c->chunk_min, c->chunk_off, c->d_tune, c->stage, c->sc, c->red, c->f_idx, c->partial, c->F};
     for (void* p : ptrs) dfree(c, p);
     if (c->h_sc) cudaFreeHost(c->h_sc);
     if (c->h_red) cudaFreeHost(c->h_red);
@@ -404,7 +404,7 @@ int nb_create(nb_ctx** out, int64_t n, int order, double eps)
         (rc = dalloc(c, reinterpret_cast<unsigned char**>(&c->jstore), np * rec)) ||
         (rc = dalloc(c, &c->act_idx, (size_t)n)) || (rc = dalloc(c, &c->all_idx, (size_t)n)) ||
         (rc = dalloc(c, &c->f_idx, (size_t)n)) || (rc = dalloc(c, &c->chunk_cnt, (size_t)c->n_chunks)) ||
-        (rc = dalloc(c, &c->chunk_min, (size_t)c->n_chunks)) ||
+        (rc = dalloc(c, &c->chunk_min, (size_t)c->n_chunks)) || (rc = dalloc(c, &c->chunk_off, (size_t)c->n_chunks)) ||
         (rc = dalloc(c, &c->d_tune, (size_t)2 * TUNE_MAX)) ||
         (rc = dalloc(c, &c->sc, 1)) || (rc = dalloc(c, &c->red, (size_t)c->red_len)) ||
         (rc = dalloc(c, &c->partial, c->partial_cap)) || (rc = dalloc(c, &c->F, (size_t)nc * (size_t)n)))

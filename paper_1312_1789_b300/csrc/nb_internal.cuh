@@ -145,6 +145,11 @@ struct DevScalars {
     int stepped;                   // ensemble cycle: clusters stepped in the last cycle
     int next_item;                 // ensemble cycle: next force item to hand out
     unsigned long long pair_warps; // mixed force: warps that took the per-pair softening form
+    // scheduler: the first pass's last CTA publishes the block time's order
+    // key and the number of matches (sched_ticket counts the CTAs done)
+    unsigned long long tb_key;
+    int n_match;
+    unsigned int sched_ticket;
 };
 
 // Threshold of the dominant-softening test.  A warp whose i-particles all
@@ -342,6 +347,7 @@ struct nb_ctx {
     int32_t* all_idx = nullptr;   // [n] 0..n-1
     int32_t* chunk_cnt = nullptr; // scheduler: per-chunk match counts
     unsigned long long* chunk_min = nullptr;  // scheduler: per-chunk minima of t + dt (order keys)
+    int32_t* chunk_off = nullptr; // scheduler: per-chunk offsets of the matches in the active list
     double* stage = nullptr;      // state I/O staging, 26 n doubles (allocated on first use)
     int n_chunks = 0;
     nb::DevScalars* sc = nullptr;
