@@ -47,7 +47,7 @@ FP64_PEAK_TFLOPS = 1.25                                                     # no
 # launch over the whole nucleus system (N_act = N = 2^20 + 2, one j-split), from
 # a one-pass ncu capture of that launch; the capture's command and figures are
 # in profiles/force_mixed_order6_nucleus_n1048578.md.
-FORCE_TRAFFIC_BYTES = {("nucleus_plummer_n1048576_2bh", "mixed"): 1.18e9 + 99.99e6}
+FORCE_TRAFFIC_BYTES = {("nucleus_plummer_n1048576_2bh", "mixed"): 1.049e9 + 99.93e6}
 
 
 def parse():
