@@ -647,7 +647,9 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
                              "precision (energies in FP64)"}
             for name, p in (("mixed", nb.NB_MIXED), ("fp64", nb.NB_FP64)):
                 r[name] = nucleus_run(nb, wl, p, stream, torch, T, graph=64, dt_max=T)
-            r["mixed_dE_within_2x_of_fp64"] = abs(r["mixed"]["dE_E"]) <= 2 * abs(r["fp64"]["dE_E"])
+            # over so short a horizon neither path has a truncation error above the rounding of the energy
+            # sum: the FP64 figure is that rounding, the mixed one the floor of its FP32 pair terms
+            r["note"] = "short horizon: energy errors are rounding floors, not truncation errors"
             r["whole_run_rate_ratio"] = (r["mixed"]["whole_run_interactions_per_s"] /
                                          r["fp64"]["whole_run_interactions_per_s"])
             nuc["full_short_both"] = r
@@ -667,12 +669,23 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
         m = np.concatenate([c.m for c in clusters])
         x = np.concatenate([c.x for c in clusters])
         v = np.concatenate([c.v for c in clusters])
+        # the plan's wave count, autotuned on a copy of the ensemble (the
+        # tuning cycles advance the state they run on)
+        bt = nb.Batch(sizes, 6, math.sqrt(clusters[0].eps2[0]), nb.NB_MIXED)
+        bt.set_stream(stream)
+        bt.set_params(0.2, 0.01, 1.0 / 16, 2.0 ** -40)
+        bt.set_particles(m, x, v)
+        t0 = time.perf_counter()
+        tuned_waves, tune_ms = bt.autotune(cycles=48, reps=2)
+        tune_s = time.perf_counter() - t0
+        bt.close()
         runs = {}
-        for name, cyc in (("host", 0), ("graph", 32)):
+        for name, cyc, waves in (("host", 0, 4), ("graph", 32, 4), ("graph_tuned", 32, tuned_waves)):
             bt = nb.Batch(sizes, 6, math.sqrt(clusters[0].eps2[0]), nb.NB_MIXED)
             bt.set_stream(stream)
             bt.set_params(0.2, 0.01, 1.0 / 16, 2.0 ** -40)
             bt.set_graph(cyc)
+            bt.set_waves(waves)
             bt.set_particles(m, x, v)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -699,6 +712,9 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
                            "batched_interactions_per_s": ni_b / el_b, "batched_cycles": ncyc,
                            "batched_seconds": el_b, "batched": "CUDA-graph replays of 32 device-planned cycles",
                            "batched_host_cycles_interactions_per_s": runs["host"][1] / runs["host"][2],
+                           "batched_autotuned": {"waves": tuned_waves, "tune_ms_per_wave_count": tune_ms,
+                                                 "tune_seconds": tune_s,
+                                                 "interactions_per_s": runs["graph_tuned"][1] / runs["graph_tuned"][2]},
                            "graph_state_equals_host_cycles": same,
                            "per_cluster_interactions_per_s": ni_s / el_s,
                            "per_cluster_seconds": el_s, "interactions": ni_b,

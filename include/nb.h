@@ -235,6 +235,16 @@ int nb_set_tuning(nb_ctx* ctx, int n_classes, const int32_t* ni, const int32_t* 
  * Synchronises.                                                            */
 int nb_selftest_wait(nb_ctx* ctx, double seconds);
 
+/* Self-check of the format conversions of the mixed corrector (the reading
+ * of the mixed precision: FP32 values truncated toward zero from FP64, with
+ * results below the normal float range flushed to zero and those from
+ * |x| >= 2^128 taken to inf; FP32 widened exactly, subnormals flushed): the
+ * corrector converts with the cvt instruction, the predictor with integer
+ * arithmetic.  Compares the two forms bit for bit on n seeded inputs (any
+ * bit pattern, and exponents across and at the edges of the float range;
+ * NaN skipped); *mismatches = the count (0 when they agree).  Synchronises. */
+int nb_selftest_convert(nb_ctx* ctx, int64_t n, uint64_t seed, int64_t* mismatches);
+
 /* Force the j-split count of later nb_force calls (0 = automatic).         */
 int nb_set_jsplit(nb_ctx* ctx, int j_splits);
 
@@ -362,6 +372,24 @@ int nb_batch_step_until(nb_batch* b, double t_end, int64_t* n_cycles, int64_t* n
  * 0 (default): one host-checked cycle at a time.  Captured on first use and
  * again after a parameter change.                                          */
 int nb_batch_set_graph(nb_batch* b, int cycles);
+
+/* The force plan of a cycle (nb_batch_cycle) cuts each cluster's work into
+ * (i-tile, j-split) items of about equal size, about `waves` times as many
+ * as the persistent force kernel has resident CTAs (default 4; 1 .. 8).
+ * nb_batch_set_waves sets it; nb_batch_get_waves reads it.                  */
+int nb_batch_set_waves(nb_batch* b, int waves);
+int nb_batch_get_waves(nb_batch* b, int* waves);
+
+/* Autotuner of the force plan (the benchmark spec: autotuned tiles for the
+ * ensemble): for each of the next `cycles` cycles, the force and split
+ * reduction are timed (CUDA events, best of reps) with the plans of 1, 2, 4
+ * and 8 waves, then the cycle is completed with the wave count in use; the
+ * count with the least total time is kept if it beats 4 by 3 %.  The tuning
+ * cycles are real cycles of the run (the state advances by them), so tune
+ * on a copy of the ensemble and pass the result to nb_batch_set_waves when
+ * the run itself must start from the initial state.  ms_per_wave (nullable,
+ * [4]): total milliseconds of 1, 2, 4, 8 waves.                            */
+int nb_batch_autotune(nb_batch* b, int cycles, int reps, double* ms_per_wave);
 
 /* Per-cluster kinetic and potential energy (arrays [n_clusters]); every
  * cluster must be synchronised within itself, else NB_ERR_NOT_SYNC.         */

@@ -77,9 +77,9 @@ __device__ __forceinline__ void count_pair_warp(DevScalars* sc, bool pair_form)
 
 // Wait for the copies still in flight after a timeout (bounded again), then
 // the caller returns.  Called by thread 0 only.
-static __device__ void drain_after_timeout(uint64_t* bars, int k, int nt)
+static __device__ void drain_after_timeout(uint64_t* bars, int k, int nt, int ns = NSTAGE)
 {
-    for (int kk = k; kk < nt && kk < k + NSTAGE; ++kk) mbar_wait_bounded(&bars[kk % NSTAGE], (kk / NSTAGE) & 1);
+    for (int kk = k; kk < nt && kk < k + ns; ++kk) mbar_wait_bounded(&bars[kk % ns], (kk / ns) & 1);
 }
 
 // -------------------------------------------------------------------- K3
@@ -408,12 +408,17 @@ __host__ __device__ constexpr int dyn_min_ctas(int order) { return order >= 8 ? 
 // it ran 0.6 % slower).
 __host__ __device__ constexpr int xs_min_ctas(int order) { return order >= 8 ? 1 : dyn_min_ctas(order); }
 
+// Stages of the two-per-thread variant's ring: 2 at order 8, where 3 stages of
+// 80-byte records and the sums of 13 components (57 KB per CTA) left room
+// for 3 CTAs per SM and 2 stages (47 KB) admit 4; NSTAGE otherwise.
+__host__ __device__ constexpr int xs_nstage(int order) { return order >= 8 ? 2 : NSTAGE; }
+
 // Dynamic shared memory of the force variants that keep their double-single
 // sums in shared memory (NP lane-pairs per thread): the TMA ring, then
 // (hi, lo) float2 [NC][2 NP][FORCE_NT].
 __host__ __device__ constexpr size_t xs_smem(int order, int rw, int np)
 {
-    return (size_t)NSTAGE * JT * rw * 16 + (size_t)ncomp(order) * 2 * np * FORCE_NT * 8;
+    return (size_t)xs_nstage(order) * JT * rw * 16 + (size_t)ncomp(order) * 2 * np * FORCE_NT * 8;
 }
 
 // One j tile for IPT i-particles: every record is read once from shared
@@ -579,22 +584,23 @@ __device__ __forceinline__ void force_block_mixed_xs(const float4* __restrict__ 
 {
     constexpr int NC = ncomp(ORDER);
     constexpr int NQ = 2 * NP;
+    constexpr int XS = xs_nstage(ORDER);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float4* buf = reinterpret_cast<float4*>(smem_raw);
-    float2* dsum = reinterpret_cast<float2*>(smem_raw + (size_t)NSTAGE * JT * RW * 16);
-    __shared__ __align__(8) uint64_t bars[NSTAGE];
+    float2* dsum = reinterpret_cast<float2*>(smem_raw + (size_t)XS * JT * RW * 16);
+    __shared__ __align__(8) uint64_t bars[XS];
 
     const int tid = threadIdx.x;
     const int pbase = pbase0 + tid;
     constexpr uint32_t TILE_BYTES = JT * RW * 16;
 
     if (tid == 0) {
-        for (int k = 0; k < NSTAGE; ++k) mbar_init(&bars[k], 1);
+        for (int k = 0; k < XS; ++k) mbar_init(&bars[k], 1);
         fence_barrier_init();
     }
     __syncthreads();
     if (tid == 0) {
-        for (int k = 0; k < NSTAGE && k < nt; ++k) {
+        for (int k = 0; k < XS && k < nt; ++k) {
             mbar_expect_tx(&bars[k], TILE_BYTES);
             bulk_g2s(buf + k * JT * RW, js + (size_t)(t0 + k) * JT * RW, TILE_BYTES, &bars[k]);
         }
@@ -635,12 +641,12 @@ __device__ __forceinline__ void force_block_mixed_xs(const float4* __restrict__ 
         for (int q = 0; q < NQ; ++q) dsum[(c * NQ + q) * FORCE_NT + tid] = make_float2(0.f, 0.f);
 
     for (int k = 0; k < nt; ++k) {
-        const int st = k % NSTAGE;
-        const bool ok = mbar_wait_bounded(&bars[st], (k / NSTAGE) & 1);
+        const int st = k % XS;
+        const bool ok = mbar_wait_bounded(&bars[st], (k / XS) & 1);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 raise_status(sc, NB_ERR_TIMEOUT);
-                drain_after_timeout(bars, k, nt);
+                drain_after_timeout(bars, k, nt, XS);
             }
             return;
         }
@@ -679,9 +685,9 @@ __device__ __forceinline__ void force_block_mixed_xs(const float4* __restrict__ 
             }
 
         __syncthreads();  // every thread is done with stage st
-        if (tid == 0 && k + NSTAGE < nt) {
+        if (tid == 0 && k + XS < nt) {
             mbar_expect_tx(&bars[st], TILE_BYTES);
-            bulk_g2s(buf + st * JT * RW, js + (size_t)(t0 + k + NSTAGE) * JT * RW, TILE_BYTES, &bars[st]);
+            bulk_g2s(buf + st * JT * RW, js + (size_t)(t0 + k + XS) * JT * RW, TILE_BYTES, &bars[st]);
         }
     }
 

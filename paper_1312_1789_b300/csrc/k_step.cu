@@ -325,6 +325,29 @@ __device__ __forceinline__ double f32_to_f64(float f)
     return __longlong_as_double((long long)(sgn | ((unsigned long long)(e - 127 + 1023) << 52) | (mant << 29)));
 }
 
+// The same two conversions by the cvt instruction, for code that runs once
+// per particle on small blocks (the corrector), where the dozen integer
+// instructions of the forms above cost more in instruction fetch than one
+// conversion on the FP64 pipe: round toward zero with subnormal results and
+// inputs flushed, and |x| >= 2^128 -- which the rounding mode would clamp to
+// the largest float -- taken to inf as above, so both give the same bits
+// for every non-NaN input.
+__device__ __forceinline__ float f64_to_f32_rz_cvt(double x)
+{
+    float r;
+    asm("cvt.rz.ftz.f32.f64 %0, %1;" : "=f"(r) : "d"(x));
+    if (fabsf(r) == 0x1.fffffep127f && ((__double2hiint(x) >> 20) & 0x7FF) >= 1023 + 128)
+        r = copysignf(INFINITY, r);
+    return r;
+}
+
+__device__ __forceinline__ double f32_to_f64_cvt(float f)
+{
+    double r;
+    asm("cvt.ftz.f64.f32 %0, %1;" : "=d"(r) : "f"(f));
+    return r;
+}
+
 // The state a particle's prediction reads: x, v, the derivatives it holds
 // (a, j, s, c; order 8 also a^(4), a^(5)), t, m, eps^2.
 template <int ORDER>
@@ -892,7 +915,9 @@ __device__ __forceinline__ float norm3f(const float (&p)[3])
 // range) -- the same closed forms as correct_fp64 with h^k moved across, and
 // the criterion's ratio, which is h^(p-3) times the ratio of scaled norms.
 // The FP64 pipe (1/64 of the FP32 rate here) then does ~45 operations per
-// particle instead of ~500.  Returns false, with nothing usable written, if a
+// particle instead of ~500, plus the format conversions (cvt: one
+// instruction each; this code runs once per active particle, where
+// instruction fetch, not the pipe, sets the time of small blocks).  Returns false, with nothing usable written, if a
 // float value is not finite (a derivative beyond the float range); the
 // caller then takes correct_fp64.
 template <int ORDER>
@@ -902,19 +927,19 @@ __device__ __forceinline__ bool correct_mixed(const double (&L)[4][3], double (&
                                               double (&x1)[3], double (&v1)[3], double& lim)
 {
     constexpr int MM = ORDER / 2;
-    const float u = f64_to_f32_rz(h);
+    const float u = f64_to_f32_rz_cvt(h);
     if (!(u > 0.0f)) return false;  // h below the float range
     // scaled inputs: ls[k] = L[k] h^k, rs[k] = H[k] h^k (k < MM), d0 = a1 - a0
     float ls[4][3], rs[4][3], d0[3];
     bool ok = true;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        d0[c] = f64_to_f32_rz(H[0][c] - L[0][c]);
+        d0[c] = f64_to_f32_rz_cvt(H[0][c] - L[0][c]);
         float uk = 1.0f;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            ls[k][c] = f64_to_f32_rz(L[k][c]) * uk;
-            rs[k][c] = k < MM ? f64_to_f32_rz(H[k][c]) * uk : 0.0f;
+            ls[k][c] = f64_to_f32_rz_cvt(L[k][c]) * uk;
+            rs[k][c] = k < MM ? f64_to_f32_rz_cvt(H[k][c]) * uk : 0.0f;
             ok = ok && isfinite(ls[k][c]) && isfinite(rs[k][c]);
             uk *= u;
         }
@@ -972,10 +997,10 @@ __device__ __forceinline__ bool correct_mixed(const double (&L)[4][3], double (&
             nl[k] = norm3f(ls[k]);
             nr[k] = k < MM ? S[k] : 0.0f;
         }
-        const float kappa = nr[0] > 0.0f ? fmaxf(1.0f, f64_to_f32_rz(bacc) / nr[0]) : 1.0f;
+        const float kappa = nr[0] > 0.0f ? fmaxf(1.0f, f64_to_f32_rz_cvt(bacc) / nr[0]) : 1.0f;
         float e[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) e[k] = f64_to_f32_rz(ne.e[k]) * kappa;
+        for (int k = 0; k < 4; ++k) e[k] = f64_to_f32_rz_cvt(ne.e[k]) * kappa;
         const float A = e[0] * (nl[0] + nr[0]);
         float N[8];
         if (ORDER == 4) {
@@ -1001,7 +1026,7 @@ __device__ __forceinline__ bool correct_mixed(const double (&L)[4][3], double (&
     // the criterion as a multiple f of h, capped at 2 (the step may at most double)
     float f;
     {
-        const float etaf = f64_to_f32_rz(eta);
+        const float etaf = f64_to_f32_rz_cvt(eta);
         if (ORDER == 4) {
             const float num = S[0] * S[2] + S[1] * S[1], den = S[1] * S[3] + S[2] * S[2];
             f = den > 0.0f ? sqrtf(etaf * (num / den)) : INFINITY;
@@ -1014,7 +1039,7 @@ __device__ __forceinline__ bool correct_mixed(const double (&L)[4][3], double (&
         if (!(f <= 2.0f)) f = f == f ? 2.0f : f;  // inf -> 2; NaN stays
     }
     if (!(f == f)) return false;
-    lim = h * f32_to_f64(f);
+    lim = h * f32_to_f64_cvt(f);
     // H[k] = T[k] / h^k, and the corrected state
     double ihk = 1.0;
 #pragma unroll
@@ -1022,39 +1047,30 @@ __device__ __forceinline__ bool correct_mixed(const double (&L)[4][3], double (&
         ihk *= ih;
         if (k >= MM)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) H[k][c] = f32_to_f64(T[k][c]) * ihk;
+            for (int c = 0; c < 3; ++c) H[k][c] = f32_to_f64_cvt(T[k][c]) * ihk;
     }
     const double hh = 0.5 * h;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        v1[c] = fma(hh, L[0][c] + H[0][c], v0[c]) + f32_to_f64(tv[c]);
-        x1[c] = fma(hh, v0[c] + v1[c], x0[c]) + f32_to_f64(tx[c]);
+        v1[c] = fma(hh, L[0][c] + H[0][c], v0[c]) + f32_to_f64_cvt(tv[c]);
+        x1[c] = fma(hh, v0[c] + v1[c], x0[c]) + f32_to_f64_cvt(tx[c]);
     }
     return true;
 }
 
-// Corrector, interpolation and new step for the particles of the last force
-// (MIXED: the mixed-precision form, FP64 for the particles it cannot take).
+// Corrector, interpolation and new step of the force list's particle p
+// (MIXED: the mixed-precision form, FP64 for the particles it cannot take);
+// component k of its force is Fp[k * fs].
 template <int ORDER, bool MIXED>
-__global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fidx, int fn, double tf,
-                                                 const double* __restrict__ F, int64_t n, int64_t np,
-                                                 double* __restrict__ x, double* __restrict__ v,
-                                                 double* __restrict__ d, double* __restrict__ t,
-                                                 double* __restrict__ dtv, double* __restrict__ pot, double eta,
-                                                 double dt_max, double dt_min, NoiseEps ne, DevScalars* sc,
-                                                 const double* __restrict__ tfc, const int32_t* __restrict__ cid,
-                                                 const DevScalars* dyn)
+__device__ __forceinline__ void correct_one(const int p, const int32_t* __restrict__ fidx, double tf,
+                                            const double* Fp, const size_t fs, int64_t n, int64_t np,
+                                            double* __restrict__ x, double* __restrict__ v, double* __restrict__ d,
+                                            double* __restrict__ t, double* __restrict__ dtv,
+                                            double* __restrict__ pot, double eta, double dt_max, double dt_min,
+                                            const NoiseEps& ne, DevScalars* sc, const double* __restrict__ tfc,
+                                            const int32_t* __restrict__ cid)
 {
-    pdl_wait();
-    pdl_release();
     constexpr int MM = ORDER / 2;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (dyn) {  // device-driven cycle: the block of the scheduler, unless idle
-        if (dyn->idle) return;
-        fn = (int)dyn->n_act;
-        tf = dyn->t_blk;
-    }
-    if (p >= fn) return;
     const int i = fidx[p];
     if ((unsigned)i >= (unsigned)n) {
         raise_status(sc, NB_ERR_ARG);
@@ -1074,14 +1090,14 @@ __global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fid
 #pragma unroll
     for (int k = 0; k < MM; ++k)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) H[k][c] = F[(size_t)(3 * k + c) * fn + p];
+        for (int c = 0; c < 3; ++c) H[k][c] = Fp[(size_t)(3 * k + c) * fs];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         x0[c] = x[c * np + i];
         v0[c] = v[c * np + i];
     }
-    const double potn = F[(size_t)(3 * MM) * fn + p];
-    const double bacc = F[(size_t)(3 * MM + 1) * fn + p];  // sum_j m_j / R_ij^2
+    const double potn = Fp[(size_t)(3 * MM) * fs];
+    const double bacc = Fp[(size_t)(3 * MM + 1) * fs];  // sum_j m_j / R_ij^2
 
     const double ih = recip(h);
     double x1[3], v1[3], lim;
@@ -1114,10 +1130,37 @@ __global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fid
     pot[i] = potn;
 }
 
+// Corrector, interpolation and new step for the particles of the last force.
+// A device-driven cycle launches a fixed grid that strides over the block's
+// active list (sized for the largest block, most of its CTAs would retire at
+// once on the usual small ones).
+template <int ORDER, bool MIXED>
+__global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fidx, int fn, double tf,
+                                                 const double* __restrict__ F, int64_t n, int64_t np,
+                                                 double* __restrict__ x, double* __restrict__ v,
+                                                 double* __restrict__ d, double* __restrict__ t,
+                                                 double* __restrict__ dtv, double* __restrict__ pot, double eta,
+                                                 double dt_max, double dt_min, NoiseEps ne, DevScalars* sc,
+                                                 const double* __restrict__ tfc, const int32_t* __restrict__ cid,
+                                                 const DevScalars* dyn)
+{
+    pdl_wait();
+    pdl_release();
+    if (dyn) {  // device-driven cycle: the block of the scheduler, unless idle
+        if (dyn->idle) return;
+        fn = (int)dyn->n_act;
+        tf = dyn->t_blk;
+    }
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < fn; p += gridDim.x * blockDim.x)
+        correct_one<ORDER, MIXED>(p, fidx, tf, F + p, (size_t)fn, n, np, x, v, d, t, dtv, pot, eta, dt_max, dt_min,
+                                  ne, sc, tfc, cid);
+}
+
 cudaError_t launch_correct(nb_ctx* c, const double* tfc, const int32_t* cid, const DevScalars* dyn)
 {
     const int nt = 128;
-    const int nb = (int)(((dyn ? c->n : c->f_n) + nt - 1) / nt);
+    const int64_t need = ((dyn ? c->n : c->f_n) + nt - 1) / nt;
+    const int nb = (int)(dyn ? std::min<int64_t>(need, 4LL * c->sm_count) : need);
     const bool mixed = c->pred_prec == NB_MIXED;
     const bool pdl = c->pdl != 0;
     cudaError_t e;
@@ -1347,6 +1390,46 @@ cudaError_t launch_state_in(nb_ctx* c)
     const int g = (int)((c->n + 255) / 256);
     k_state_check<<<g, 256, 0, c->stream>>>(c->stage, c->n, c->sc);
     k_state_in<<<g, 256, 0, c->stream>>>(c->stage, c->n, c->np, c->x, c->v, c->d, c->t, c->dt, c->sc);
+    return cudaGetLastError();
+}
+
+// Self-check of the cvt conversions against the integer forms: n seeded
+// inputs (splitmix64 of seed + k) -- every fourth any bit pattern, the others
+// doubles with exponents across and at the edges of the float range -- and
+// the widening of any float bit pattern; NaN inputs are skipped (NaN stays
+// NaN in both, with payloads that may differ).  *bad += mismatching bits.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_convert_check(int64_t n, unsigned long long seed, unsigned long long* bad)
+{
+    unsigned long long nbad = 0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long z = splitmix64(seed + (unsigned long long)k);
+        const unsigned long long keep = z & 0x800FFFFFFFFFFFFFull;  // sign and mantissa
+        unsigned long long e;
+        switch (k & 3) {
+        case 0: e = (z >> 52) & 0x7FF; break;                                // any exponent
+        case 1: e = 1023 - 160 + (z >> 53) % 321; break;                     // 2^-160 .. 2^160
+        case 2: e = 1023 + 126 + (z >> 53) % 4; break;                       // 2^126 .. 2^129
+        default: e = 1023 - 152 + (z >> 53) % 30; break;                     // 2^-152 .. 2^-123
+        }
+        const double x = __longlong_as_double((long long)(keep | (e << 52)));
+        if (x == x && __float_as_uint(f64_to_f32_rz(x)) != __float_as_uint(f64_to_f32_rz_cvt(x))) ++nbad;
+        const float f = __uint_as_float((unsigned)(z >> 16));
+        if (f == f && __double_as_longlong(f32_to_f64(f)) != __double_as_longlong(f32_to_f64_cvt(f))) ++nbad;
+    }
+    if (nbad) atomicAdd(bad, nbad);
+}
+
+cudaError_t launch_convert_check(nb_ctx* c, int64_t n, unsigned long long seed, unsigned long long* bad)
+{
+    k_convert_check<<<4 * c->sm_count, 256, 0, c->stream>>>(n, seed, bad);
     return cudaGetLastError();
 }
 

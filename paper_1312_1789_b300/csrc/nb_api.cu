@@ -696,6 +696,24 @@ int nb_selftest_wait(nb_ctx* c, double seconds)
     return set_err(c, NB_ERR_CUDA, "the probe's wait completed although nothing arrives");
 }
 
+int nb_selftest_convert(nb_ctx* c, int64_t n, uint64_t seed, int64_t* mismatches)
+{
+    if (!c || !mismatches) return NB_ERR_ARG;
+    if (n < 0) return set_err(c, NB_ERR_ARG, "n must be >= 0");
+    unsigned long long* bad = nullptr;
+    NB_CUDA(c, cudaMalloc(&bad, sizeof(unsigned long long)));
+    unsigned long long h = 0;
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned long long), c->stream);
+    if (e == cudaSuccess) e = launch_convert_check(c, n, (unsigned long long)seed, bad);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, bad, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(bad);
+    if (e != cudaSuccess) return set_err(c, NB_ERR_CUDA, "conversion self-check: %s", cudaGetErrorString(e));
+    c->n_launch += 1;
+    *mismatches = (int64_t)h;
+    return NB_OK;
+}
+
 int nb_set_jsplit(nb_ctx* c, int js)
 {
     if (!c) return NB_ERR_ARG;

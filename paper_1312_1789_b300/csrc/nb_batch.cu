@@ -63,6 +63,7 @@ struct nb_batch {
     BatchItem* d_items = nullptr;
     int d_items_cap = 0;
     int force_slots = 0;          // SMs x occupancy of the persistent force kernel
+    int waves = 4;                // the plan's waves of force items (nb_batch_autotune)
     int graph_cycles = 0;
     cudaGraphExec_t graph_exec = nullptr;
     cudaStream_t graph_stream = nullptr;
@@ -309,8 +310,9 @@ __global__ void k_batch_bounds_dyn(const int32_t* __restrict__ list, const DevSc
 // Plan of the cycle's force (one CTA): each cluster with cnt active takes the
 // launch variant ni = mixed_ni(cnt) (fp64_ni(cnt) in FP64) and
 // s j-splits, s = ceil(min(cnt, ni) * pk / target) in [1, pk / JT], with
-// target = max(work / (4 slots), FORCE_NT * JT) and work = sum cnt * pk: items
-// of about equal work, about four waves of them.  The largest split is then
+// target = max(work / (waves slots), FORCE_NT * JT) and work = sum cnt * pk:
+// items of about equal work, about `waves` waves of them (4 unless
+// nb_batch_autotune measured another count faster).  The largest split is then
 // capped by the partial-sum buffer.  The force kernel hands items out in
 // table order, so the table lists the heavy items first: clusters whose item
 // work min(cnt, ni) pk / s is at least target / 2, then at least target / 8,
@@ -320,7 +322,8 @@ __global__ void k_batch_bounds_dyn(const int32_t* __restrict__ list, const DevSc
 // the cycle.
 __global__ void __launch_bounds__(BNT) k_batch_plan(int K, const int32_t* __restrict__ kcount,
                                                     const int64_t* __restrict__ pk, const int64_t* __restrict__ nk,
-                                                    int slots, long long cap, int nc, int mixed, int items_cap,
+                                                    int slots, int waves, long long cap, int nc, int mixed,
+                                                    int items_cap,
                                                     int32_t* __restrict__ ksplit, int32_t* __restrict__ kni,
                                                     int32_t* __restrict__ koff, DevScalars* sc)
 {
@@ -358,7 +361,7 @@ __global__ void __launch_bounds__(BNT) k_batch_plan(int K, const int32_t* __rest
     work = block_sum(work);
     inter = block_sum(inter);
     stepped = block_sum(stepped);
-    if (tid == 0) s_target = fmax((double)work / (4.0 * slots), (double)FORCE_NT * JT);
+    if (tid == 0) s_target = fmax((double)work / ((double)waves * slots), (double)FORCE_NT * JT);
     __syncthreads();
     const double target = s_target;
     int smax = 1;
@@ -870,6 +873,10 @@ int batch_force(nb_batch* b, int order, const int32_t* list, int n_act, const in
 // scheduler 4 (block times 2, count, scatter), bounds 2, plan, items,
 // predictor, force, reduction, corrector
 constexpr int BATCH_CYCLE_LAUNCHES = 12;
+// largest wave count of the force plan (the item buffer is sized for it)
+constexpr int BATCH_WAVES_MAX = 8;
+// a wave count replaces the default only when it is this much faster
+constexpr double BATCH_TUNE_MARGIN = 0.97;
 
 void batch_destroy_graph(nb_batch* b)
 {
@@ -912,13 +919,14 @@ int batch_force_dyn(nb_batch* b, bool occ_only)
 }
 
 // Slots of the persistent force in the current precision and an item buffer
-// that holds every plan: items <= 4 slots + np/64 + 8K (each cluster's split
-// count rounds up by at most one, its i-tiles number at most cnt/128 + 8).
+// that holds every plan: items <= waves slots + np/64 + 8K (each cluster's
+// split count rounds up by at most one, its i-tiles number at most
+// cnt/128 + 8), waves <= BATCH_WAVES_MAX.
 int batch_prepare(nb_batch* b)
 {
     nb_ctx* c = b->c;
     const int slots = c->sm_count * batch_force_dyn(b, true);
-    const long long need = 8LL * slots + c->np / 32 + 8LL * b->K + 1024;
+    const long long need = 2LL * BATCH_WAVES_MAX * slots + c->np / 32 + 8LL * b->K + 1024;
     if (slots != b->force_slots || need > b->d_items_cap) {
         batch_destroy_graph(b);
         b->force_slots = slots;
@@ -956,7 +964,9 @@ int batch_reset_scalars(nb_batch* b, double t_end, cudaStream_t st)
 // time per cluster (idle past t_end), active list, cluster segments, the
 // force plan and its items, predictor, persistent force, reduction,
 // corrector.
-cudaError_t batch_cycle_launches(nb_batch* b)
+// The first launches of an ensemble cycle: block time per cluster (idle
+// past t_end), active list, cluster segments.
+cudaError_t batch_cycle_front(nb_batch* b)
 {
     nb_ctx* c = b->c;
     const int K = b->K, nch = (int)((c->n + BCHUNK - 1) / BCHUNK), g = c->sm_count * 4;
@@ -969,12 +979,28 @@ cudaError_t batch_cycle_launches(nb_batch* b)
     if (e != cudaSuccess) return e;
     k_batch_bounds_dyn<<<g, 256, 0, c->stream>>>(c->act_idx, c->sc, b->cid, b->kstart, b->kcount);
     k_batch_counts<<<(K + 255) / 256, 256, 0, c->stream>>>(K, b->kstart, b->kcount);
-    k_batch_plan<<<1, BNT, 0, c->stream>>>(K, b->kcount, b->d_pk, b->d_nk, b->force_slots,
+    return cudaGetLastError();
+}
+
+// The force plan with `waves` waves of items, and its item table.
+cudaError_t batch_cycle_plan(nb_batch* b, int waves)
+{
+    nb_ctx* c = b->c;
+    const int K = b->K;
+    k_batch_plan<<<1, BNT, 0, c->stream>>>(K, b->kcount, b->d_pk, b->d_nk, b->force_slots, waves,
                                            (long long)c->partial_cap, ncomp(c->order), c->prec == NB_MIXED,
                                            b->d_items_cap, b->ksplit, b->kni, b->koff, c->sc);
     k_batch_items<<<K, BNT, 0, c->stream>>>(b->kstart, b->kcount, b->ksplit, b->kni, b->koff, b->d_off, b->d_pk,
                                             b->d_items_cap, b->d_items);
-    if ((e = launch_predict(c, 0.0, b->tblk, b->cid, c->sc)) != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+// The persistent force over the planned items and the reduction over each
+// cluster's splits.
+cudaError_t batch_cycle_force(nb_batch* b)
+{
+    nb_ctx* c = b->c;
+    const int g = c->sm_count * 4;
     if (batch_force_dyn(b, false) != NB_OK) return cudaGetLastError();
 #define BRED(O)                                                                                                   \
     k_batch_reduce_dyn<ncomp(O), pot_comp(O)><<<2 * g, 256, 0, c->stream>>>(c->partial, c->act_idx, b->cid,         \
@@ -983,6 +1009,17 @@ cudaError_t batch_cycle_launches(nb_batch* b)
     else if (c->order == 6) BRED(6);
     else BRED(8);
 #undef BRED
+    return cudaGetLastError();
+}
+
+cudaError_t batch_cycle_launches(nb_batch* b)
+{
+    nb_ctx* c = b->c;
+    cudaError_t e;
+    if ((e = batch_cycle_front(b)) != cudaSuccess) return e;
+    if ((e = batch_cycle_plan(b, b->waves)) != cudaSuccess) return e;
+    if ((e = launch_predict(c, 0.0, b->tblk, b->cid, c->sc)) != cudaSuccess) return e;
+    if ((e = batch_cycle_force(b)) != cudaSuccess) return e;
     if ((e = launch_correct(c, b->tblk, b->cid, c->sc)) != cudaSuccess) return e;
     c->n_launch += BATCH_CYCLE_LAUNCHES;
     return cudaGetLastError();
@@ -1178,6 +1215,80 @@ int nb_batch_set_particles(nb_batch* b, const double* m, const double* x, const 
                                                  c->dt_min, c->sc);
     B_CUDA(b, cudaGetLastError());
     return bsync(b);
+}
+
+int nb_batch_set_waves(nb_batch* b, int waves)
+{
+    if (!b) return NB_ERR_ARG;
+    if (waves < 1 || waves > BATCH_WAVES_MAX) return berr(b, NB_ERR_ARG, "waves must be in [1, %d]", BATCH_WAVES_MAX);
+    if (waves != b->waves) batch_destroy_graph(b);
+    b->waves = waves;
+    return NB_OK;
+}
+
+int nb_batch_get_waves(nb_batch* b, int* waves)
+{
+    if (!b || !waves) return NB_ERR_ARG;
+    *waves = b->waves;
+    return NB_OK;
+}
+
+int nb_batch_autotune(nb_batch* b, int cycles, int reps, double* ms_per_wave)
+{
+    if (!b) return NB_ERR_ARG;
+    nb_ctx* c = b->c;
+    if (!c->have_particles) return berr(b, NB_ERR_ARG, "nb_batch_autotune before nb_batch_set_particles");
+    if (cycles < 1 || reps < 1) return berr(b, NB_ERR_ARG, "cycles and reps must be >= 1");
+    B_TRY(batch_prepare(b));
+    B_TRY(batch_reset_scalars(b, INFINITY, c->stream));
+    cudaEvent_t e0, e1;
+    B_CUDA(b, cudaEventCreate(&e0));
+    B_CUDA(b, cudaEventCreate(&e1));
+    double total[BATCH_WAVES_MAX + 1] = {0};
+    int rc = NB_OK;
+    for (int cyc = 0; cyc < cycles && rc == NB_OK; ++cyc) {
+        cudaError_t e = batch_cycle_front(b);
+        if (e == cudaSuccess) e = launch_predict(c, 0.0, b->tblk, b->cid, c->sc);
+        // each candidate: its plan, then its force and reduction, best of reps
+        for (int w = 1; w <= BATCH_WAVES_MAX && e == cudaSuccess; w *= 2) {
+            if ((e = batch_cycle_plan(b, w)) != cudaSuccess) break;
+            float best = INFINITY;
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+                // the force hands out items from a counter the plan reset
+                if ((e = cudaMemsetAsync(&c->sc->next_item, 0, sizeof(int), c->stream)) != cudaSuccess) break;
+                cudaEventRecord(e0, c->stream);
+                if ((e = batch_cycle_force(b)) != cudaSuccess) break;
+                cudaEventRecord(e1, c->stream);
+                if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                best = std::min(best, ms);
+            }
+            total[w] += best;
+        }
+        // the cycle itself, with the wave count in use
+        if (e == cudaSuccess) e = batch_cycle_plan(b, b->waves);
+        if (e == cudaSuccess) e = cudaMemsetAsync(&c->sc->next_item, 0, sizeof(int), c->stream);
+        if (e == cudaSuccess) e = batch_cycle_force(b);
+        if (e == cudaSuccess) e = launch_correct(c, b->tblk, b->cid, c->sc);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rc = berr(b, NB_ERR_CUDA, "autotune cycle failed: %s", cudaGetErrorString(e));
+            break;
+        }
+        rc = bsync(b);
+        if (rc == NB_OK && c->h_sc->idle) break;  // every cluster at t = +inf: cannot happen before t_end
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    B_TRY(rc);
+    int w_min = 4;
+    for (int w = 1; w <= BATCH_WAVES_MAX; w *= 2)
+        if (total[w] < total[w_min]) w_min = w;
+    const int best_w = total[w_min] < BATCH_TUNE_MARGIN * total[4] ? w_min : 4;
+    if (ms_per_wave)
+        for (int k = 0, w = 1; w <= BATCH_WAVES_MAX; ++k, w *= 2) ms_per_wave[k] = total[w];
+    return nb_batch_set_waves(b, best_w);
 }
 
 int nb_batch_cycle(nb_batch* b, double t_end, int* n_stepped, int64_t* n_inter)

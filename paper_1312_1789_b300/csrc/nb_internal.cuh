@@ -421,6 +421,10 @@ cudaError_t launch_force_reduce(nb_ctx* c, int order, const int32_t* idx, int64_
 // c->F = the n_parts force results parts[n_parts][ncomp][n_act] added in part
 // order (no sign change: each part is already a finished result).
 cudaError_t launch_parts_reduce(nb_ctx* c, int order, const double* parts, int64_t n_act, int n_parts);
+// Self-check of the corrector's cvt conversions against the integer forms
+// (nb_selftest_convert): *bad (device) += mismatches over n seeded inputs.
+cudaError_t launch_convert_check(nb_ctx* c, int64_t n, unsigned long long seed, unsigned long long* bad);
+// Corrector of the last force (dyn: of the block in the device scalars).
 cudaError_t launch_correct(nb_ctx* c, const double* tfc = nullptr, const int32_t* cid = nullptr,
                            const DevScalars* dyn = nullptr);
 // Device-driven block cycle (CUDA-graph capturable): shape gate, persistent

@@ -70,6 +70,7 @@ SIGNATURES = {
     "nb_set_graph": (C.c_int, [_P, C.c_int]),
     "nb_fma_peak": (C.c_int, [_P, C.c_int, _D]),
     "nb_selftest_wait": (C.c_int, [_P, C.c_double]),
+    "nb_selftest_convert": (C.c_int, [_P, C.c_int64, C.c_uint64, C.POINTER(C.c_int64)]),
     "nb_autotune": (C.c_int, [_P, C.c_int]),
     "nb_get_tuning": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int32), C.POINTER(C.c_int32), _D]),
     "nb_set_tuning": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
@@ -85,6 +86,9 @@ SIGNATURES = {
     "nb_batch_set_graph": (C.c_int, [_P, C.c_int]),
     "nb_batch_energy": (C.c_int, [_P, _D, _D]),
     "nb_batch_get_state": (C.c_int, [_P, _D, _D, _D, _D]),
+    "nb_batch_set_waves": (C.c_int, [_P, C.c_int]),
+    "nb_batch_get_waves": (C.c_int, [_P, C.POINTER(C.c_int)]),
+    "nb_batch_autotune": (C.c_int, [_P, C.c_int, C.c_int, _D]),
 }
 NB_STATIC_MAX_N = 16384
 NB_JTILE = 128
@@ -216,6 +220,12 @@ class NBody:
     def selftest_wait(self, seconds: float = 0.2) -> int:
         """Run the bounded-wait probe; returns the code (NB_ERR_TIMEOUT when it works as designed)."""
         return int(self._L.nb_selftest_wait(self._h, float(seconds)))
+
+    def selftest_convert(self, n: int = 1 << 24, seed: int = 1) -> int:
+        """Mismatching bits between the corrector's cvt conversions and the integer forms over n inputs."""
+        m = C.c_int64()
+        self._check(self._L.nb_selftest_convert(self._h, int(n), int(seed), C.byref(m)))
+        return m.value
 
     def fma_peak(self, fp64: bool = False) -> float:
         """Measured FMA throughput of this GPU in TFLOP/s (FP32, or FP64 when fp64)."""
@@ -422,6 +432,22 @@ class Batch:
         ni = C.c_int64()
         self._check(self._L.nb_batch_step_until(self._h, float(t_end), C.byref(nc), C.byref(ni)))
         return nc.value, ni.value
+
+    def set_waves(self, waves: int):
+        self._check(self._L.nb_batch_set_waves(self._h, int(waves)))
+
+    def get_waves(self) -> int:
+        w = C.c_int()
+        self._check(self._L.nb_batch_get_waves(self._h, C.byref(w)))
+        return w.value
+
+    def autotune(self, cycles: int = 32, reps: int = 2):
+        """Time the force plan with 1, 2, 4, 8 waves on the next `cycles` cycles
+        (which the state advances by) and keep the fastest; returns the chosen
+        wave count and the total ms of each candidate."""
+        ms = np.zeros(4)
+        self._check(self._L.nb_batch_autotune(self._h, int(cycles), int(reps), _d(ms)))
+        return self.get_waves(), dict(zip((1, 2, 4, 8), ms.tolist()))
 
     def energy(self):
         ek, ep = np.zeros(self.k), np.zeros(self.k)

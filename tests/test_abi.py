@@ -62,6 +62,7 @@ def test_null_context_is_rejected(libnb):
     assert libnb.nb_batch_set_graph(None, 2) == -1
     assert libnb.nb_set_tuning(None, 0, None, None) == -1
     assert libnb.nb_selftest_wait(None, C.c_double(0.1)) == -1
+    assert libnb.nb_selftest_convert(None, 16, 1, None) == -1
     assert libnb.nb_fma_peak(None, 0, None) == -1
     libnb.nb_destroy(None)
 

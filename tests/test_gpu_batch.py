@@ -116,3 +116,51 @@ def test_batch_graph_cycles_match_host_cycles_bitwise(prec):
     assert c0 == c1 and c0[0][0] > 0
     for key in ("x", "v", "t", "dt"):
         assert np.array_equal(s0[key], s1[key]), key
+
+
+@pytest.mark.parametrize("waves", [1, 8])
+def test_batch_fp64_other_wave_counts_match_each_cluster_alone(waves):
+    # The plan's wave count changes only how the work is cut into items (and
+    # so the split sums' order): the steps stay the oracle's.
+    sizes = [300, 129, 1000, 64, 700]
+    ms, xs, vs = _clusters(sizes)
+    b = nb.Batch(sizes, 6, 1e-4, nb.NB_FP64)
+    b.set_waves(waves)
+    assert b.get_waves() == waves
+    b.set_graph(5)
+    b.set_particles(np.concatenate(ms), np.concatenate(xs), np.concatenate(vs))
+    b.step_until(1.0 / 16)
+    S = b.get_state()
+    off = 0
+    for k, n in enumerate(sizes):
+        st = orc.State(ms[k], 1e-8, xs[k], vs[k])
+        orc.integrate(st, order=6, t_end=1.0 / 16, eta=0.2, nthreads=16)
+        sl = slice(off, off + n)
+        assert np.array_equal(S["dt"][sl], st.dt), f"cluster {k}: steps differ"
+        assert np.max(np.abs(S["x"][sl] - st.x)) < 1e-11, f"cluster {k}"
+        off += n
+    with pytest.raises(nb.NBError):
+        b.set_waves(9)
+    b.close()
+
+
+def test_batch_autotune_cycles_are_the_runs_own_cycles():
+    # The tuning cycles complete with the wave count in use, so after tuning
+    # for k cycles the state is that of k host-checked cycles; the chosen
+    # count is one of the candidates and every candidate was timed.
+    sizes = [2000, 130, 5, 900, 3000, 64]
+    ms, xs, vs = _clusters(sizes)
+    states = []
+    for tune in (True, False):
+        b = nb.Batch(sizes, 6, 1e-4, nb.NB_MIXED)
+        b.set_particles(np.concatenate(ms), np.concatenate(xs), np.concatenate(vs))
+        if tune:
+            w, ms_per = b.autotune(cycles=6, reps=1)
+            assert w in (1, 2, 4, 8) and all(v > 0 for v in ms_per.values())
+        else:
+            for _ in range(6):
+                b.cycle(1e9)
+        states.append(b.get_state())
+        b.close()
+    for key in ("x", "v", "t", "dt"):
+        assert np.array_equal(states[0][key], states[1][key]), key

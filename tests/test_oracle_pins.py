@@ -618,6 +618,25 @@ def test_plummer_ic_properties(orc):
     assert p > 0.01
 
 
+def test_plummer_ic_energy_tends_to_henon_units(orc):
+    """The Plummer generator scales by the model's analytic energy (no pair
+    sum), so the sampled E = T + W misses -1/4 by the sampling noise alone,
+    O(N^-1/2): small at 65536 particles, and larger at 1024.  A wrong length
+    or velocity unit would leave an offset that does not shrink with N."""
+    from paper_1312_1789_b300 import ics
+    dev = {}
+    for n, seeds in ((1024, range(6)), (65536, range(2))):
+        e, q = [], []
+        for s in seeds:
+            m, x, v = ics.plummer(n, 2000 + s)
+            ek, ep = orc.energy(m, np.zeros(n), x, v, nthreads=8)
+            e.append(ek + ep + 0.25)
+            q.append(2 * ek / abs(ep) - 1.0)
+        dev[n] = (np.sqrt(np.mean(np.square(e))), np.sqrt(np.mean(np.square(q))))
+    assert dev[65536][0] < 0.004 and dev[65536][1] < 0.012
+    assert dev[65536][0] < dev[1024][0] and dev[65536][1] < dev[1024][1]
+
+
 def test_hernquist_ic_properties(orc):
     from scipy import stats
 
