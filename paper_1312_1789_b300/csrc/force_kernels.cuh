@@ -128,6 +128,9 @@ __device__ __forceinline__ void reduce_warp(const double* __restrict__ partial, 
 {
     const int p = q / NC, c = q - p * NC;
     double s = 0.0;
+    // unrolled so that the loads of several splits are in flight at once
+    // (the adds keep their order: the same bits)
+#pragma unroll 8
     for (int sp = lane; sp < jsplit; sp += 32) s += partial[((size_t)sp * NC + c) * n_act + p];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
