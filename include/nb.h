@@ -167,7 +167,9 @@ int nb_get_force(nb_ctx* ctx, double* acc, double* jerk, double* snap, double* c
 
 /* The predicted j-particle store of the last nb_predict, converted to double
  * exactly as the force kernel sees it (mixed: hi + lo positions, FP32
- * velocity/acc/jerk): xp, vp, ap, jp [n][3] (NULL to skip).  Synchronises. */
+ * velocity/acc/jerk): xp, vp, ap, jp [n][3] (NULL to skip).  After a
+ * prediction restricted by a j range (nb_set_jrange) the records outside the
+ * range and the block hold earlier predictions.  Synchronises.             */
 int nb_get_predicted(nb_ctx* ctx, double* xp, double* vp, double* ap, double* jp);
 
 /* Kernel launch shape of the last nb_force: CTAs along i, j-splits and
@@ -262,10 +264,14 @@ int nb_set_jsplit(nb_ctx* ctx, int j_splits);
  * also be n).  (0, 0) or (0, n) restores the whole range.  The start-up
  * passes and nb_energy always use every particle.  While a range is set,
  * nb_block_step, nb_step_until and graph cycles fail with NB_ERR_ARG: step
- * with nb_next_block, nb_predict, nb_force, the exchange, nb_reduce_force and
- * nb_correct.  With the ranges [r T / G, (r + 1) T / G) tiles (T = tiles of
- * the store, G ranks) and one j-split per rank, the reduced force is bit for
- * bit the single-rank force with G j-splits.                                */
+ * with nb_next_block, nb_predict, nb_force(NULL), the exchange,
+ * nb_reduce_force and nb_correct.  nb_predict after nb_next_block then
+ * predicts only the range's particles and the block's active ones (each rank
+ * predicts its own share of the j particles), and nb_force takes the
+ * scheduled list only (an explicit list fails with NB_ERR_ARG); a changed
+ * range asks for a new nb_predict.  With the ranges [r T / G, (r + 1) T / G)
+ * tiles (T = tiles of the store, G ranks) and one j-split per rank, the
+ * reduced force is bit for bit the single-rank force with G j-splits.      */
 #define NB_JTILE 128
 int nb_set_jrange(nb_ctx* ctx, int64_t j_begin, int64_t j_end);
 

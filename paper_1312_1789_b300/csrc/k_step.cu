@@ -655,6 +655,50 @@ cudaError_t launch_sched_predict(nb_ctx* c, bool use_t_end, const int* shape_slo
     return e;
 }
 
+// Prediction of a rank's share of the j particles (records [r0, r1)) and of
+// the block's active particles outside it (list[0..nl)): what a j-restricted
+// force reads.  Threads [0, r1 - r0) take the range, the next nl the list.
+template <int ORDER, bool MIXED>
+__global__ void __launch_bounds__(256) k_predict_ranged(const double* __restrict__ m,
+                                                        const double* __restrict__ eps2,
+                                                        const double* __restrict__ x, const double* __restrict__ v,
+                                                        const double* __restrict__ d, const double* __restrict__ t,
+                                                        int64_t n, int64_t np, double tp, void* __restrict__ jstore,
+                                                        int64_t r0, int64_t r1, const int32_t* __restrict__ list,
+                                                        int64_t nl)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t i;
+    if (g < r1 - r0) {
+        i = r0 + g;
+    } else if (g < r1 - r0 + nl) {
+        i = list[g - (r1 - r0)];
+        if ((uint64_t)i >= (uint64_t)n || (i >= r0 && i < r1)) return;  // in the range: predicted above
+    } else {
+        return;
+    }
+    predict_one<ORDER, MIXED>(i, tp, m, eps2, x, v, d, t, n, np, jstore, nullptr, nullptr);
+}
+
+cudaError_t launch_predict_ranged(nb_ctx* c, double t, int64_t r0, int64_t r1, const int32_t* list, int64_t nl)
+{
+    const int nt = 256;
+    const int64_t work = (r1 - r0) + nl;
+    if (work <= 0) return cudaSuccess;
+    const int nb = (int)((work + nt - 1) / nt);
+    const bool mixed = c->prec == NB_MIXED;
+#define NB_PR(O, MX)                                                                                                 k_predict_ranged<O, MX><<<nb, nt, 0, c->stream>>>(c->m, c->eps2, c->x, c->v, c->d, c->t, c->n, c->np, t,                                                           c->jstore, r0, r1, list, nl)
+    if (c->order == 4) {
+        if (mixed) NB_PR(4, true); else NB_PR(4, false);
+    } else if (c->order == 6) {
+        if (mixed) NB_PR(6, true); else NB_PR(6, false);
+    } else {
+        if (mixed) NB_PR(8, true); else NB_PR(8, false);
+    }
+#undef NB_PR
+    return cudaGetLastError();
+}
+
 cudaError_t launch_predict(nb_ctx* c, double t, const double* tpc, const int32_t* cid, const DevScalars* dyn)
 {
     const int nt = 256;

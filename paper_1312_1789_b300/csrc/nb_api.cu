@@ -316,7 +316,18 @@ int step_until_graph(nb_ctx* c, double t_end, int64_t* n_blocks, int64_t* n_inte
 
 int do_predict(nb_ctx* c, double t)
 {
-    NB_CUDA(c, timed(c, NB_PHASE_PREDICT, 1, [&] { return launch_predict(c, t); }));
+    // a j range with a scheduled block: the rank's records and the block's
+    // active particles, which is all its force reads
+    const bool ranged = c->jr_end > 0 && c->have_sched;
+    if (ranged) {
+        const int64_t r1 = std::min<int64_t>(c->np, (c->jr_end + JT - 1) / JT * JT);  // padding of the last tile
+        NB_CUDA(c, timed(c, NB_PHASE_PREDICT, 1, [&] {
+            return launch_predict_ranged(c, t, c->jr_begin, r1, c->act_idx, c->sched_n);
+        }));
+    } else {
+        NB_CUDA(c, timed(c, NB_PHASE_PREDICT, 1, [&] { return launch_predict(c, t); }));
+    }
+    c->pred_ranged = ranged ? 1 : 0;
     c->pred_prec = c->prec;
     c->have_pred = 1;
     c->t_pred = t;
@@ -727,6 +738,7 @@ int nb_set_jrange(nb_ctx* c, int64_t j_begin, int64_t j_end)
 {
     if (!c) return NB_ERR_ARG;
     if (j_begin == 0 && (j_end == 0 || j_end == c->n)) {
+        if (c->pred_ranged) c->have_pred = 0;  // the store holds only the old share
         c->jr_begin = c->jr_end = 0;
         return NB_OK;
     }
@@ -734,6 +746,7 @@ int nb_set_jrange(nb_ctx* c, int64_t j_begin, int64_t j_end)
         return set_err(c, NB_ERR_ARG, "j range [%lld, %lld) must lie in [0, %lld) and start and end on multiples of %d "
                        "(or end at n)", (long long)j_begin, (long long)j_end, (long long)c->n, JT);
     if (c->graph_cycles > 0) return set_err(c, NB_ERR_ARG, "a j range cannot be combined with graph cycles");
+    if (j_begin != c->jr_begin || j_end != c->jr_end) c->have_pred = 0;  // a new share: predict again
     c->jr_begin = j_begin;
     c->jr_end = j_end;
     return NB_OK;
@@ -855,6 +868,8 @@ int nb_force(nb_ctx* c, const int32_t* idx, int64_t n_act)
                                    c->stream));
     } else {
         if (n_act < 1 || n_act > c->n) return set_err(c, NB_ERR_ARG, "n_act = %lld outside [1, n]", (long long)n_act);
+        if (c->pred_ranged)
+            return set_err(c, NB_ERR_ARG, "after a j-range prediction nb_force takes the scheduled list (NULL)");
         cudaPointerAttributes pa;
         bool on_device = false;
         if (cudaPointerGetAttributes(&pa, idx) == cudaSuccess)

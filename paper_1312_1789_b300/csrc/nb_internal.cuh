@@ -365,6 +365,8 @@ struct nb_ctx {
     double* F = nullptr;        // [ncomp][n] reduced force, list order
     // j range of nb_force (nb_set_jrange): particles [jr_begin, jr_end); jr_end = 0: all
     int64_t jr_begin = 0, jr_end = 0;
+    // the last prediction covered the j range and the scheduled block only
+    int pred_ranged = 0;
     // j tiles of the force launch in progress: [lt0, lt0 + ltn) (run_force sets them)
     int lt0 = 0, ltn = 0;
     int have_particles = 0, have_pred = 0, have_force = 0;
@@ -421,6 +423,9 @@ cudaError_t launch_force_reduce(nb_ctx* c, int order, const int32_t* idx, int64_
 // c->F = the n_parts force results parts[n_parts][ncomp][n_act] added in part
 // order (no sign change: each part is already a finished result).
 cudaError_t launch_parts_reduce(nb_ctx* c, int order, const double* parts, int64_t n_act, int n_parts);
+// Prediction of the records [r0, r1) and of the listed particles outside
+// them (nl entries of a device list): a rank's j share and the block's active set.
+cudaError_t launch_predict_ranged(nb_ctx* c, double t, int64_t r0, int64_t r1, const int32_t* list, int64_t nl);
 // Self-check of the corrector's cvt conversions against the integer forms
 // (nb_selftest_convert): *bad (device) += mismatches over n seeded inputs.
 cudaError_t launch_convert_check(nb_ctx* c, int64_t n, unsigned long long seed, unsigned long long* bad);

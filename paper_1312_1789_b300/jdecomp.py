@@ -8,10 +8,11 @@ GPUs once per block, and the corrector runs on the summed force.  Here:
 
   rank r owns the j tiles [r T / G, (r + 1) T / G) of the store (T tiles of
   NB_JTILE particles, G ranks), via nb_set_jrange;
-  every rank schedules, predicts and forces the same active set (replicated
-  state, identical arithmetic), copies its partial result (nb_copy_force),
-  takes part in ONE all-gather of the G partial results, adds them in rank
-  order on the device (nb_reduce_force) and corrects.
+  every rank schedules the same active set (replicated state, identical
+  arithmetic), predicts its own j particles and the active ones, forces the
+  active set from its own j particles, copies its partial result
+  (nb_copy_force), takes part in ONE all-gather of the G partial results,
+  adds them in rank order on the device (nb_reduce_force) and corrects.
 
 Every rank adds the same parts in the same order, so the ranks' states stay
 bit for bit identical; with one j-split per rank the summed force is also bit

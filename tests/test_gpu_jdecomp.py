@@ -63,6 +63,41 @@ def test_lockstep_ranks_equal_one_context_with_world_splits(prec, world):
     single.close()
 
 
+def test_ranged_prediction_covers_the_share_and_the_block_only():
+    # each rank predicts its own j tiles and the block's active particles;
+    # the other records keep the previous prediction, which the restricted
+    # force never reads
+    n = 4 * 128 + 33
+    m, x, v, eps2 = _system(n)
+    c = make_ctx(m, x, v, eps2, 6, nb.NB_MIXED, pair=True)
+    c.predict(0.0)
+    before = c.get_predicted()[0]
+    jb, je = 128, 384
+    c.set_jrange(jb, je)
+    tb, idx = c.next_block(want_idx=True)
+    c.predict(tb)
+    after = c.get_predicted()[0]
+    full = make_ctx(m, x, v, eps2, 6, nb.NB_MIXED, pair=True)
+    full.predict(tb)
+    ref = full.get_predicted()[0]
+    covered = np.zeros(n, bool)
+    covered[jb:je] = True
+    covered[idx] = True
+    assert (~covered).any() and len(idx) < n
+    assert np.array_equal(after[covered], ref[covered])
+    assert np.array_equal(after[~covered], before[~covered])
+    with pytest.raises(nb.NBError) as e:
+        c.force(idx.astype(np.int32))
+    assert e.value.code == nb.NB_ERR_ARG
+    c.force()
+    # a new share needs a new prediction
+    c.set_jrange(0, 128)
+    with pytest.raises(nb.NBError):
+        c.force()
+    c.close()
+    full.close()
+
+
 def test_jrange_rules():
     n = 3 * 128 + 5
     m, x, v, eps2 = _system(n)

@@ -576,11 +576,14 @@ def test_unsoftened_kepler_pair_matches_oracle(order):
     assert np.array_equal(S["dt"], st.dt)
 
 
-def test_ragged_sizes_force():
+@pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
+def test_ragged_sizes_force(prec):
+    # stores of one particle, of less than one tile, of a tile and one more;
+    # an empty active list is an argument error, not a launch
     for n in (1, 2, 127, 128, 129, 255):
         m, x, v, eps2 = _system(max(n, 3), 77, "plummer")
         m, x, v, eps2 = m[:n], x[:n], v[:n], eps2[:n]
-        ctx = make_ctx(m, x, v, eps2, 6, nb.NB_FP64)
+        ctx = make_ctx(m, x, v, eps2, 6, prec)
         ctx.predict(1.0 / 1024)
         idx = np.arange(n, dtype=np.int32)
         ctx.force(idx)
@@ -589,7 +592,11 @@ def test_ragged_sizes_force():
         if n == 1:
             assert np.all(G["acc"] == 0) and G["pot"][0] == 0.0
         else:
-            assert_force_close(G, O, 6, nb.NB_FP64, f"n={n}")
+            assert_force_close(G, O, 6, prec, f"n={n}")
+        with pytest.raises(nb.NBError) as e:
+            ctx.force(np.zeros(0, dtype=np.int32))
+        assert e.value.code == nb.NB_ERR_ARG
+        ctx.close()
 
 
 # --------------------------------------------------------------- error paths
