@@ -352,15 +352,12 @@ __device__ __forceinline__ void pair_mixed_x2(const float4 w0, const float4 w1, 
 // One j tile for NP lane-pairs (2 NP i-particles) of a thread: every record
 // is read once from shared memory and applied to each pair.
 // j-loop unroll of the packed tile: 4 records in flight at orders 4 and 6
-// (+1-6 % measured), none at order 8 (its larger body is 3 % slower
-// unrolled).
-#ifndef NB_XN_UNROLL6
-#define NB_XN_UNROLL6 4
-#endif
+// (+1-6 % measured), none at order 8 (its larger body unrolled by 2 is 1.5 %
+// slower at 4 CTAs per SM).
 template <int ORDER>
 __host__ __device__ constexpr int xn_unroll()
 {
-    return ORDER >= 8 ? 1 : NB_XN_UNROLL6;
+    return ORDER >= 8 ? 1 : 4;
 }
 template <int ORDER, int RW, bool PAIR, bool SELF, int NP>
 __device__ __forceinline__ void tile_mixed_xn(const float4* __restrict__ b, const IMixed2 (&I)[NP],
@@ -402,14 +399,14 @@ __device__ __forceinline__ IMixed2 pack_pair(const IMixed& a, const IMixed& z, f
 }
 
 // Resident CTAs per SM that the persistent kernels holding several mixed
-// variants are compiled for: 4 at orders <= 6, 3 at order 8 -- the CTAs that
-// the shared memory of the two-per-thread variant admits.
+// variants are compiled for: 4 at orders <= 6, 3 at order 8 (where the
+// 4-particle variant's chain needs more than the 128 registers of 4 CTAs).
 __host__ __device__ constexpr int dyn_min_ctas(int order) { return order >= 8 ? 3 : 4; }
-// The per-launch two-per-thread kernel: at orders <= 6 the same hint lets
-// ptxas use the registers that occupancy leaves free (116 instead of 96 at
-// order 6: 3 % faster); at order 8 it is left to ptxas (compiled for 3 CTAs
-// it ran 0.6 % slower).
-__host__ __device__ constexpr int xs_min_ctas(int order) { return order >= 8 ? 1 : dyn_min_ctas(order); }
+// The per-launch two-per-thread kernel is compiled for the 4 CTAs per SM
+// that its shared memory admits (at order 8 with the 2-stage ring), so that
+// ptxas may use the registers occupancy leaves free: 116 instead of 96 at
+// order 6 (3 % faster); at order 8, 3.2 % faster than ptxas's own target.
+__host__ __device__ constexpr int xs_min_ctas(int order) { return 4; }
 
 // Stages of the two-per-thread variant's ring: 2 at order 8, where 3 stages of
 // 80-byte records and the sums of 13 components (57 KB per CTA) left room
