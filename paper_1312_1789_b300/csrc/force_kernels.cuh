@@ -1081,7 +1081,7 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_fp64(const double2* __restri
 // device-chosen shape.  SMALL: the variants of up to FORCE_NT i-particles per
 // CTA (4, 32, FORCE_NT), compiled for dyn_min_ctas resident CTAs; otherwise
 // the two-per-thread variant (2 FORCE_NT), whose block is an out-of-line
-// call (xs_item).  The kernel not matching the chosen variant returns at
+// call (xs_item), compiled for the CTAs of its per-launch kernel.  The kernel not matching the chosen variant returns at
 // once.
 // The two-per-thread block as a call of its own: compiled apart from a
 // persistent caller's item loop it keeps the code of its per-launch kernel
@@ -1096,7 +1096,7 @@ __device__ __noinline__ void xs_item(const float4* __restrict__ js, const int32_
 }
 
 template <int ORDER, int RW, bool PAIR, bool SMALL>
-__global__ void __launch_bounds__(FORCE_NT, dyn_min_ctas(ORDER))
+__global__ void __launch_bounds__(FORCE_NT, SMALL ? dyn_min_ctas(ORDER) : xs_min_ctas(ORDER))
     k_force_mixed_dyn(const float4* __restrict__ js, const int32_t* __restrict__ idx, int n, int ntiles, float eps2u,
                       float eps2max, double* __restrict__ partial, DevScalars* sc, double* F)
 {
