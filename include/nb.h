@@ -111,7 +111,9 @@ int nb_next_block(nb_ctx* ctx, double* t_blk, int32_t* idx_out, int64_t* n_act);
 /* Predictor: advance every particle's position and velocity (and, for orders
  * 6 and 8, acceleration; for 8, jerk) from its own time t_i to t by the
  * Taylor series in the derivatives it holds, and write the j-particle store
- * the force kernel reads.  t must be >= every t_i.                        */
+ * the force kernel reads.  t must be >= every t_i.  With a j range set
+ * after nb_next_block: only the range's and the block's particles
+ * (nb_set_jrange).                                                         */
 int nb_predict(nb_ctx* ctx, double t);
 
 /* Force: for each listed particle i, sum over all j != i of the Plummer-
