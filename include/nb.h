@@ -214,7 +214,8 @@ int nb_set_graph(nb_ctx* ctx, int cycles);
  * the split count scaled to keep the tuned number of CTAs.  reps <= 0 drops
  * the current precision's table (back to the analytic makespan rule).  The
  * particle state is untouched (predicted store and force result are
- * scratch); needs nb_set_particles.  Synchronises.                         */
+ * scratch); needs nb_set_particles and the whole j range (NB_ERR_ARG while
+ * nb_set_jrange holds one).  Synchronises.                                 */
 #define NB_TUNE_MAX 32
 int nb_autotune(nb_ctx* ctx, int reps);
 
@@ -265,7 +266,8 @@ int nb_set_jsplit(nb_ctx* ctx, int j_splits);
  * [j_begin, j_end) only; j_begin and j_end multiples of NB_JTILE (j_end may
  * also be n).  (0, 0) or (0, n) restores the whole range.  The start-up
  * passes and nb_energy always use every particle.  While a range is set,
- * nb_block_step, nb_step_until and graph cycles fail with NB_ERR_ARG: step
+ * nb_block_step, nb_step_until, graph cycles and nb_autotune fail with
+ * NB_ERR_ARG: step
  * with nb_next_block, nb_predict, nb_force(NULL), the exchange,
  * nb_reduce_force and nb_correct.  nb_predict after nb_next_block then
  * predicts only the range's particles and the block's active ones (each rank

@@ -569,6 +569,7 @@ int nb_autotune(nb_ctx* c, int reps)
 {
     if (!c) return NB_ERR_ARG;
     if (!c->have_particles) return set_err(c, NB_ERR_ARG, "nb_autotune before nb_set_particles");
+    if (c->jr_end > 0) return set_err(c, NB_ERR_ARG, "nb_autotune needs the whole j range (nb_set_jrange(0, 0))");
     const int pi = c->prec == NB_MIXED ? 1 : 0;
     destroy_graph(c);
     c->tune_n[pi] = 0;

@@ -112,6 +112,8 @@ def test_jrange_rules():
         c.step_until(1.0 / 16)
     with pytest.raises(nb.NBError):
         c.set_graph(8)
+    with pytest.raises(nb.NBError):
+        c.autotune(1)
     # the range restricts the force only: the energy still sums every pair
     ek, ep = c.energy()
     c.set_jrange(0, 0)
