@@ -509,11 +509,14 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
                 t0 = time.perf_counter()
                 c2.autotune(tune)
                 rec["autotune_seconds"] = time.perf_counter() - t0
+            c2.get_nact_histogram(reset=True)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             nblk, ni = c2.step_until(t_end)
             torch.cuda.synchronize()
             el = time.perf_counter() - t0
+            hist = c2.get_nact_histogram()
+            rec["nact_histogram"] = {f"{1 << k}-{(2 << k) - 1}": int(hist[k]) for k in np.nonzero(hist)[0]}
             xf = c2.get_state()["x"]
             c2.set_precision(nb.NB_FP64)
             e1 = sum(c2.energy())

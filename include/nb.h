@@ -332,6 +332,17 @@ int nb_set_profiling(nb_ctx* ctx, int enable);
  * kernel launches since nb_create (NULL to skip).  Synchronises.           */
 int nb_get_profile(nb_ctx* ctx, double* ms, int64_t* launches, int64_t* total_launches);
 
+/* Histogram of block sizes: counts[k] = corrector passes (block steps; for
+ * an ensemble, cycles) whose active set had 2^k .. 2^(k+1) - 1 particles,
+ * k < NB_NACT_CLASSES, counted on the device since nb_create or the last
+ * reset (host- and device-driven cycles alike).  counts may be NULL; reset
+ * != 0 zeroes the counts after reading them.  Synchronises.  The profiling
+ * phases also open NVTX ranges ("nb:force", ...) around their launches, and
+ * nb_block_step, nb_step_until and the graph replays around their calls,
+ * for profilers that filter by range.                                      */
+#define NB_NACT_CLASSES 48
+int nb_get_nact_histogram(nb_ctx* ctx, int64_t* counts, int reset);
+
 /* FMA-throughput microbenchmark on the context's GPU (a measurement aid for
  * roofline fractions, not part of the method): every SM runs independent
  * multiply-add chains in FP32 (fp64 = 0) or FP64 (fp64 != 0); *tflops = the

@@ -1186,7 +1186,7 @@ __global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fid
                                                  double* __restrict__ dtv, double* __restrict__ pot, double eta,
                                                  double dt_max, double dt_min, NoiseEps ne, DevScalars* sc,
                                                  const double* __restrict__ tfc, const int32_t* __restrict__ cid,
-                                                 const DevScalars* dyn)
+                                                 const DevScalars* dyn, unsigned long long* hist)
 {
     pdl_wait();
     pdl_release();
@@ -1195,6 +1195,7 @@ __global__ void __launch_bounds__(128) k_correct(const int32_t* __restrict__ fid
         fn = (int)dyn->n_act;
         tf = dyn->t_blk;
     }
+    if (hist && blockIdx.x == 0 && threadIdx.x == 0 && fn > 0) atomicAdd(&hist[31 - __clz(fn)], 1ull);
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < fn; p += gridDim.x * blockDim.x)
         correct_one<ORDER, MIXED>(p, fidx, tf, F + p, (size_t)fn, n, np, x, v, d, t, dtv, pot, eta, dt_max, dt_min,
                                   ne, sc, tfc, cid);
@@ -1211,7 +1212,7 @@ cudaError_t launch_correct(nb_ctx* c, const double* tfc, const int32_t* cid, con
 #define NB_CORR(O, MX)                                                                                           \
     e = launch_k(k_correct<O, MX>, dim3(nb), dim3(nt), 0, c->stream, pdl, dyn ? c->act_idx : c->f_idx,         \
                  (int)c->f_n, c->f_t, c->F, c->n, c->np, c->x, c->v, c->d, c->t, c->dt, c->pot, c->eta,         \
-                 c->dt_max, c->dt_min, c->noise[mixed ? 1 : 0], c->sc, tfc, cid, dyn)
+                 c->dt_max, c->dt_min, c->noise[mixed ? 1 : 0], c->sc, tfc, cid, dyn, c->nact_hist)
     if (c->order == 4) {
         if (mixed) NB_CORR(4, true); else NB_CORR(4, false);
     } else if (c->order == 6) {

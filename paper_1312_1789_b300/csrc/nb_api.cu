@@ -11,6 +11,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "nb_internal.cuh"
 
 using namespace nb;
@@ -134,10 +136,22 @@ void prof_fold(nb_ctx* c)
 
 // Run one launcher (nk kernels) as phase `phase`, counting and, when profiling
 // is on, bracketing it with events on the context's stream.
+// NVTX range of a scope (a no-op unless a profiler is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+const char* const PHASE_RANGE[NB_NPHASES] = {"nb:sched", "nb:predict", "nb:force",
+                                             "nb:reduce", "nb:correct", "nb:other"};
+
 template <typename F>
 cudaError_t timed(nb_ctx* c, int phase, int nk, F&& launch)
 {
     c->n_launch += nk;
+    NvtxRange range(PHASE_RANGE[phase]);
     if (!c->prof_on) return launch();
     cudaEvent_t a = prof_event(c), b = prof_event(c);
     if (a) cudaEventRecord(a, c->stream);
@@ -296,6 +310,7 @@ int step_until_graph(nb_ctx* c, double t_end, int64_t* n_blocks, int64_t* n_inte
     // force (two kernels on the mixed path), reduction, corrector
     const long long per_cycle = 2 + (c->prec == NB_MIXED ? 2 : 1) + 1 + 1;
     for (;;) {
+        NvtxRange range("nb:graph replay");
         NB_CUDA(c, cudaGraphLaunch(c->graph_exec, c->graph_stream));
         c->n_launch += per_cycle * c->graph_cycles;
         NB_CUDA(c, cudaMemcpyAsync(h, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->graph_stream));
@@ -358,7 +373,8 @@ void nb_destroy(nb_ctx* c)
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     void* ptrs[] = {c->m, c->eps2, c->x, c->v, c->d, c->t, c->dt, c->pot, c->jstore, c->act_idx, c->all_idx,
-                    c->chunk_cnt, c->chunk_min, c->chunk_off, c->d_tune, c->stage, c->sc, c->red, c->f_idx, c->partial, c->F};
+                    c->chunk_cnt, c->chunk_min, c->chunk_off, c->d_tune, c->stage, c->sc, c->nact_hist, c->red,
+                    c->f_idx, c->partial, c->F};
     for (void* p : ptrs) dfree(c, p);
     if (c->h_sc) cudaFreeHost(c->h_sc);
     if (c->h_red) cudaFreeHost(c->h_red);
@@ -417,7 +433,8 @@ int nb_create(nb_ctx** out, int64_t n, int order, double eps)
         (rc = dalloc(c, &c->f_idx, (size_t)n)) || (rc = dalloc(c, &c->chunk_cnt, (size_t)c->n_chunks)) ||
         (rc = dalloc(c, &c->chunk_min, (size_t)c->n_chunks)) || (rc = dalloc(c, &c->chunk_off, (size_t)c->n_chunks)) ||
         (rc = dalloc(c, &c->d_tune, (size_t)2 * TUNE_MAX)) ||
-        (rc = dalloc(c, &c->sc, 1)) || (rc = dalloc(c, &c->red, (size_t)c->red_len)) ||
+        (rc = dalloc(c, &c->sc, 1)) || (rc = dalloc(c, &c->nact_hist, (size_t)NB_NACT_CLASSES)) ||
+        (rc = dalloc(c, &c->red, (size_t)c->red_len)) ||
         (rc = dalloc(c, &c->partial, c->partial_cap)) || (rc = dalloc(c, &c->F, (size_t)nc * (size_t)n)))
         return fail(rc);
     if (cudaMallocHost(&c->h_sc, sizeof(DevScalars)) != cudaSuccess ||
@@ -429,7 +446,9 @@ int nb_create(nb_ctx** out, int64_t n, int order, double eps)
     std::vector<int32_t> iota((size_t)n);
     for (int64_t k = 0; k < n; ++k) iota[(size_t)k] = (int32_t)k;
     if (cudaMemcpy(c->all_idx, iota.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(c->sc, 0, sizeof(DevScalars)) != cudaSuccess || cudaMemset(c->m, 0, np * 8) != cudaSuccess ||
+        cudaMemset(c->sc, 0, sizeof(DevScalars)) != cudaSuccess ||
+        cudaMemset(c->nact_hist, 0, NB_NACT_CLASSES * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(c->m, 0, np * 8) != cudaSuccess ||
         cudaMemset(c->d_tune, 0, sizeof(TuneEntry) * 2 * TUNE_MAX) != cudaSuccess ||
         cudaMemset(c->x, 0, 3 * np * 8) != cudaSuccess || cudaMemset(c->v, 0, 3 * np * 8) != cudaSuccess ||
         cudaMemset(c->d, 0, 18 * np * 8) != cudaSuccess || cudaMemset(c->t, 0, np * 8) != cudaSuccess ||
@@ -795,6 +814,7 @@ static int upload_vec(nb_ctx* c, double* dst, const double* src)
 
 int nb_set_particles(nb_ctx* c, const double* m, const double* x, const double* v)
 {
+    NvtxRange range("nb_set_particles");
     if (!c || !m || !x || !v) return c ? set_err(c, NB_ERR_ARG, "m, x and v are required") : NB_ERR_ARG;
     const size_t n = (size_t)c->n, np = (size_t)c->np;
     for (size_t k = 0; k < n; ++k)
@@ -940,6 +960,7 @@ static int need_whole_range(nb_ctx* c)
 
 int nb_block_step(nb_ctx* c, double* t_blk, int64_t* n_act)
 {
+    NvtxRange range("nb_block_step");
     if (!c) return NB_ERR_ARG;
     NB_TRY(need_whole_range(c));
     double tb = 0.0;
@@ -954,6 +975,7 @@ int nb_block_step(nb_ctx* c, double* t_blk, int64_t* n_act)
 
 int nb_step_until(nb_ctx* c, double t_end, int64_t* n_blocks, int64_t* n_inter)
 {
+    NvtxRange range("nb_step_until");
     if (!c) return NB_ERR_ARG;
     NB_TRY(need_whole_range(c));
     if (!std::isfinite(t_end)) return set_err(c, NB_ERR_ARG, "t_end must be finite");
@@ -977,6 +999,7 @@ int nb_step_until(nb_ctx* c, double t_end, int64_t* n_blocks, int64_t* n_inter)
 
 int nb_energy(nb_ctx* c, double* ekin, double* epot)
 {
+    NvtxRange range("nb_energy");
     if (!c) return NB_ERR_ARG;
     if (!c->have_particles) return set_err(c, NB_ERR_ARG, "nb_energy before nb_set_particles");
     const int g = energy_grid(c);
@@ -1152,6 +1175,18 @@ int nb_set_profiling(nb_ctx* c, int enable)
         c->prof_n[k] = 0;
     }
     c->prof_on = enable != 0;
+    return NB_OK;
+}
+
+int nb_get_nact_histogram(nb_ctx* c, int64_t* counts, int reset)
+{
+    if (!c) return NB_ERR_ARG;
+    unsigned long long h[NB_NACT_CLASSES];
+    NB_CUDA(c, cudaMemcpyAsync(h, c->nact_hist, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    if (reset) NB_CUDA(c, cudaMemsetAsync(c->nact_hist, 0, sizeof h, c->stream));
+    NB_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (counts)
+        for (int k = 0; k < NB_NACT_CLASSES; ++k) counts[k] = (int64_t)h[k];
     return NB_OK;
 }
 

@@ -351,6 +351,7 @@ struct nb_ctx {
     double* stage = nullptr;      // state I/O staging, 26 n doubles (allocated on first use)
     int n_chunks = 0;
     nb::DevScalars* sc = nullptr;
+    unsigned long long* nact_hist = nullptr;  // [NB_NACT_CLASSES] corrector passes by floor(log2(n_act))
     nb::DevScalars* h_sc = nullptr;  // pinned
     double* red = nullptr;           // reduction scratch [red_len]
     int red_len = 0;

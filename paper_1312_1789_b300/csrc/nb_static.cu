@@ -34,6 +34,7 @@ constexpr size_t PARTIAL_REGION = PARTIAL_DOUBLES * sizeof(double);
 constexpr size_t SCALAR_REGION = 256;
 constexpr size_t SCRATCH_BYTES = REC_REGION + PARTIAL_REGION + SCALAR_REGION;
 static_assert(SCRATCH_BYTES == NB_STATIC_SCRATCH_BYTES, "scratch size must match nb.h");
+static_assert(sizeof(DevScalars) <= SCALAR_REGION, "the device scalars must fit their scratch region");
 static_assert(STATIC_MAX_N % JT == 0, "the scratch capacity must be whole j tiles");
 
 static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];

@@ -64,6 +64,7 @@ SIGNATURES = {
     "nb_set_block_step": (C.c_int, [_P, C.c_double]),
     "nb_set_profiling": (C.c_int, [_P, C.c_int]),
     "nb_get_profile": (C.c_int, [_P, _D, _I64, _I64]),
+    "nb_get_nact_histogram": (C.c_int, [_P, _I64, C.c_int]),
     "nb_set_noise_floor": (C.c_int, [_P, C.c_int, _D]),
     "nb_get_noise_floor": (C.c_int, [_P, C.c_int, _D]),
     "nb_force_static": (C.c_int, [C.c_int, C.c_int, C.c_int64, _P, _P, _P, _P, _P, _P, _P, C.c_int64, _P, _P]),
@@ -94,6 +95,7 @@ NB_STATIC_MAX_N = 16384
 NB_JTILE = 128
 NB_NPHASES = 6
 NB_TUNE_MAX = 32
+NB_NACT_CLASSES = 48
 PHASES = ("sched", "predict", "force", "reduce", "correct", "other")
 
 _lib = None
@@ -360,6 +362,12 @@ class NBody:
         tot = C.c_int64()
         self._check(self._L.nb_get_profile(self._h, _d(ms), nl.ctypes.data_as(_I64), C.byref(tot)))
         return {p: (float(ms[k]), int(nl[k])) for k, p in enumerate(PHASES)}, tot.value
+
+    def get_nact_histogram(self, reset: bool = False):
+        """Corrector passes by active-set size class: counts[k] for 2^k .. 2^(k+1) - 1 particles."""
+        h = np.zeros(NB_NACT_CLASSES, dtype=np.int64)
+        self._check(self._L.nb_get_nact_histogram(self._h, h.ctypes.data_as(_I64), 1 if reset else 0))
+        return h
 
     def get_pair_warps(self) -> int:
         """Warps of the mixed force that took the per-pair softening form since the last call."""

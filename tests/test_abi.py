@@ -63,6 +63,7 @@ def test_null_context_is_rejected(libnb):
     assert libnb.nb_set_tuning(None, 0, None, None) == -1
     assert libnb.nb_selftest_wait(None, C.c_double(0.1)) == -1
     assert libnb.nb_selftest_convert(None, 16, 1, None) == -1
+    assert libnb.nb_get_nact_histogram(None, None, 0) == -1
     assert libnb.nb_fma_peak(None, 0, None) == -1
     libnb.nb_destroy(None)
 
@@ -76,3 +77,13 @@ def test_missing_library_fails_loudly(tmp_path):
             nb.lib(str(tmp_path / "libnb.so"))
     finally:
         nb._lib = saved
+
+
+def test_binding_constants_match_the_header():
+    from paper_1312_1789_b300 import nb
+    src = open(os.path.join(ROOT, "include", "nb.h")).read()
+    defs = dict(re.findall(r"#define\s+(NB_[A-Z_0-9]+)\s+\(?(-?\d+)\)?", src))
+    shared = [k for k in defs if hasattr(nb, k)]
+    assert {"NB_NACT_CLASSES", "NB_TUNE_MAX", "NB_NPHASES", "NB_JTILE", "NB_MIXED", "NB_ERR_TIMEOUT"} <= set(shared)
+    for k in shared:
+        assert getattr(nb, k) == int(defs[k]), k

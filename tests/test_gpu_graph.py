@@ -100,3 +100,34 @@ def test_graph_no_block_before_t_end_and_bad_argument():
     nblk, _ = ctx.step_until(1.0 / 128)
     assert nblk > 0
     ctx.close()
+
+
+def test_nact_histogram_counts_every_block_in_both_modes():
+    # host-driven block steps, n_act read per step, against the device count;
+    # then graph replays: the same blocks, so the same histogram
+    n = 1531
+    m, x, v = ics.plummer(n, 29)
+    t_end = 1.0 / 32
+    hists = []
+    for cycles in (0, 7):
+        ctx = make_ctx(m, x, v, 1e-4, 6, nb.NB_MIXED)
+        ctx.get_nact_histogram(reset=True)
+        expect = np.zeros(nb.NB_NACT_CLASSES, dtype=np.int64)
+        if cycles == 0:
+            while True:
+                tb, na = ctx.next_block()
+                if tb > t_end:
+                    break
+                ctx.block_step()
+                expect[int(na).bit_length() - 1] += 1
+            h = ctx.get_nact_histogram()
+            assert np.array_equal(h, expect)
+        else:
+            ctx.set_graph(cycles)
+            blocks, _ = ctx.step_until(t_end)
+            h = ctx.get_nact_histogram(reset=True)
+            assert h.sum() == blocks
+            assert ctx.get_nact_histogram().sum() == 0
+        hists.append(h)
+        ctx.close()
+    assert np.array_equal(hists[0], hists[1]) and hists[0].sum() > 20
