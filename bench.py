@@ -312,6 +312,13 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def momentum_drift(S0, S1, m):
+    """|P1 - P0| / sum_i m_i |v_i| (at the start) of the total momentum."""
+    p0 = (m[:, None] * S0["v"]).sum(axis=0)
+    p1 = (m[:, None] * S1["v"]).sum(axis=0)
+    return float(np.linalg.norm(p1 - p0) / (m * np.linalg.norm(S0["v"], axis=1)).sum())
+
+
 def binary_elements(S, m):
     """Two-body semi-major axis and eccentricity of the last two particles."""
     r = S["x"][-2] - S["x"][-1]
@@ -330,7 +337,8 @@ def cusp_run(nb, w, p, stream, torch, t_end, dt_max=None):
     c.set_particles(w.m, w.x, w.v)
     c.set_precision(nb.NB_FP64)
     e0 = sum(c.energy())
-    a0, ec0 = binary_elements(c.get_state(), w.m)
+    S0 = c.get_state()
+    a0, ec0 = binary_elements(S0, w.m)
     c.set_precision(p)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -339,9 +347,11 @@ def cusp_run(nb, w, p, stream, torch, t_end, dt_max=None):
     el = time.perf_counter() - t0
     c.set_precision(nb.NB_FP64)
     e1 = sum(c.energy())
-    a1, ec1 = binary_elements(c.get_state(), w.m)
+    S1 = c.get_state()
+    a1, ec1 = binary_elements(S1, w.m)
     c.close()
-    return {"dE_E": (e1 - e0) / abs(e0), "binary_a": [a0, a1], "binary_e": [ec0, ec1], "blocks": nblk,
+    return {"dE_E": (e1 - e0) / abs(e0), "dP_rel": momentum_drift(S0, S1, w.m), "binary_a": [a0, a1],
+            "binary_e": [ec0, ec1], "blocks": nblk,
             "interactions": ni, "seconds": el, "whole_run_interactions_per_s": ni / el}
 
 
@@ -353,6 +363,7 @@ def nucleus_run(nb, w, p, stream, torch, t_end, graph=0, dt_max=None):
     c.set_particles(w.m, w.x, w.v)
     c.set_precision(nb.NB_FP64)
     e0 = sum(c.energy())
+    S0 = c.get_state()
     c.set_precision(p)
     c.set_graph(graph)
     torch.cuda.synchronize()
@@ -362,8 +373,9 @@ def nucleus_run(nb, w, p, stream, torch, t_end, graph=0, dt_max=None):
     el = time.perf_counter() - t0
     c.set_precision(nb.NB_FP64)
     e1 = sum(c.energy())
+    dp = momentum_drift(S0, c.get_state(), w.m)
     c.close()
-    return {"dE_E": (e1 - e0) / abs(e0), "blocks": nblk, "interactions": ni, "seconds": el,
+    return {"dE_E": (e1 - e0) / abs(e0), "dP_rel": dp, "blocks": nblk, "interactions": ni, "seconds": el,
             "whole_run_interactions_per_s": ni / el}
 
 
@@ -501,6 +513,7 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
             c2.set_particles(w.m, w.x, w.v)
             c2.set_precision(nb.NB_FP64)
             e0 = sum(c2.energy())
+            S0 = c2.get_state()
             c2.set_precision(p)
             c2.set_graph(cyc)
             rec = {}
@@ -517,11 +530,13 @@ def extras(args, nb, ics, wl, ctx, stream, out, prec):
             el = time.perf_counter() - t0
             hist = c2.get_nact_histogram()
             rec["nact_histogram"] = {f"{1 << k}-{(2 << k) - 1}": int(hist[k]) for k in np.nonzero(hist)[0]}
-            xf = c2.get_state()["x"]
+            S1 = c2.get_state()
+            xf = S1["x"]
             c2.set_precision(nb.NB_FP64)
             e1 = sum(c2.energy())
             c2.close()
-            rec.update({"dE_E": (e1 - e0) / abs(e0), "blocks": nblk, "interactions": ni,
+            rec.update({"dE_E": (e1 - e0) / abs(e0), "dP_rel": momentum_drift(S0, S1, w.m), "blocks": nblk,
+                        "interactions": ni,
                         "whole_run_interactions_per_s": ni / el, "seconds": el})
             return rec, xf
 

@@ -149,6 +149,7 @@ class NBody:
             raise NBError(rc, self._L.nb_last_error(None).decode())
         self.n = int(n)
         self.order = int(order)
+        self.precision = NB_MIXED
         self.set_precision(precision)
 
     # -------------------------------------------------------------- plumbing
@@ -186,6 +187,7 @@ class NBody:
 
     def set_precision(self, mode: int):
         self._check(self._L.nb_set_precision(self._h, int(mode)))
+        self.precision = int(mode)
 
     def set_softening(self, eps_i=None):
         e = None if eps_i is None else np.ascontiguousarray(eps_i, dtype=np.float64)
@@ -218,6 +220,32 @@ class NBody:
         js = np.array([e[2] for e in table] or [0], dtype=np.int32)
         self._check(self._L.nb_set_tuning(self._h, len(table), ni.ctypes.data_as(C.POINTER(C.c_int32)),
                                           js.ctypes.data_as(C.POINTER(C.c_int32))))
+
+    def save_tuning(self, path: str):
+        """Write the current precision's autotuned table as JSON, keyed by the
+        store it was measured on (n, order, precision) and the device."""
+        import json
+        import torch
+        doc = {"n": self.n, "order": self.order, "precision": "mixed" if self.precision == NB_MIXED else "fp64",
+               "device": torch.cuda.get_device_name() if torch.cuda.is_available() else None,
+               "classes": [{"log2_n_act": k, "ni": ni, "js": js, "ms": ms} for k, ni, js, ms in self.get_tuning()]}
+        with open(path, "w") as f:
+            json.dump(doc, f, indent=1)
+
+    def load_tuning(self, path: str):
+        """Install a table that save_tuning wrote for the same n, order and
+        precision (ValueError otherwise)."""
+        import json
+        with open(path) as f:
+            doc = json.load(f)
+        want = {"n": self.n, "order": self.order, "precision": "mixed" if self.precision == NB_MIXED else "fp64"}
+        got = {k: doc.get(k) for k in want}
+        if got != want:
+            raise ValueError(f"tuning table for {got}, context is {want}")
+        table = [(c["log2_n_act"], int(c["ni"]), int(c["js"])) for c in doc["classes"]]
+        if [t[0] for t in table] != list(range(len(table))):
+            raise ValueError("tuning classes must be 0, 1, ... in order")
+        self.set_tuning(table)
 
     def selftest_wait(self, seconds: float = 0.2) -> int:
         """Run the bounded-wait probe; returns the code (NB_ERR_TIMEOUT when it works as designed)."""

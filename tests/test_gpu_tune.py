@@ -60,6 +60,26 @@ def test_autotune_table_shapes_and_parity():
             assert js == min(e_js, n // 128 + 1)  # the split is also capped by the j tiles
         O = oracle_force_on_predicted(ctx, m, eps2, idx, 6)
         assert_force_close(ctx.get_force(na), O, 6, nb.NB_MIXED, f"tuned shape n_act {na}")
+    # the table as a JSON file, restored into another context of the same store
+    import json
+    import os
+    import tempfile
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "tune.json")
+        ctx.save_tuning(path)
+        other = make_ctx(m, x, v, eps2, 6, nb.NB_MIXED)
+        other.load_tuning(path)
+        assert [e[:3] for e in other.get_tuning()] == [e[:3] for e in table]
+        other.set_precision(nb.NB_FP64)
+        with pytest.raises(ValueError):
+            other.load_tuning(path)  # measured in the other precision
+        doc = json.load(open(path))
+        doc["n"] = n + 1
+        json.dump(doc, open(path, "w"))
+        other.set_precision(nb.NB_MIXED)
+        with pytest.raises(ValueError):
+            other.load_tuning(path)  # measured on another store
+        other.close()
     ctx.autotune(0)
     assert ctx.get_tuning() == []
     with pytest.raises(nb.NBError):
