@@ -117,11 +117,12 @@ def _rank(rank, world, port, q, steps):
     dist.destroy_process_group()
 
 
-def test_two_gloo_ranks_equal_one_rank_with_two_splits():
-    steps, world = 5, 2
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_ranks_equal_one_rank_with_world_splits(world):
+    steps = 5
     mpc = mp.get_context("spawn")
     q = mpc.Queue()
-    port = 29500 + os.getpid() % 1000
+    port = 29500 + (os.getpid() * 7 + world) % 1000
     procs = [mpc.Process(target=_rank, args=(r, world, port, q, steps)) for r in range(world)]
     for p in procs:
         p.start()
@@ -129,15 +130,15 @@ def test_two_gloo_ranks_equal_one_rank_with_two_splits():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    (r0, x0, jr0, calls), (r1, x1, jr1, _) = res
-    assert jr0 == (0, 512) and jr1 == (512, 1000)
-    assert calls == ["predict", "force", "reduce", "correct"]
-    assert np.array_equal(x0, x1)
-    # one rank, the same tiles as two j-splits: the same bits
+    assert [r[2] for r in res] == jdecomp.jranges(1000, world)
+    assert res[0][3] == ["predict", "force", "reduce", "correct"]
+    for r in res[1:]:
+        assert np.array_equal(r[1], res[0][1])
+    # one rank, the same tiles as `world` j-splits: the same bits
     ref = StandIn(1000)
     ref.set_jsplit(world)
     for _ in range(steps):
         ref.predict(0.0)
         ref.force()
         ref.correct()
-    assert np.array_equal(x0, ref.x)
+    assert np.array_equal(res[0][1], ref.x)
