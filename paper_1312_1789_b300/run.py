@@ -8,8 +8,11 @@ libnb's kernels through nb.NBody; this module only sequences the calls.
 
 Configuration keys (DEFAULTS below fills the rest):
   workload      "plummer1k", "plummer65k", "nucleus", "cusp" (the standard
-                problems of ics.standard_workload), or a dict
-                {"model": "plummer", "n": N, "seed": S, "eps": E}
+                problems of ics.standard_workload), a dict
+                {"model": "plummer", "n": N, "seed": S, "eps": E}, or
+                {"model": "ensemble", "clusters": K, "lo": N0, "hi": N1}
+                (independent Plummer clusters stepped together, order 6;
+                outputs give the per-cluster energy errors; no checkpoints)
   order         4, 6 or 8 (default: the workload's)
   precision     "mixed" or "fp64"
   eta, eta_s, dt_max, dt_min   time-step parameters (default: the workload's)
@@ -59,8 +62,14 @@ def load_config(cfg: dict) -> dict:
     wl = c["workload"]
     if isinstance(wl, str) and wl not in STANDARD:
         raise ValueError(f"workload must be one of {sorted(STANDARD)} or a dict")
-    if isinstance(wl, dict) and wl.get("model") != "plummer":
-        raise ValueError("a custom workload is {'model': 'plummer', 'n': N, 'seed': S, 'eps': E}")
+    if isinstance(wl, dict) and wl.get("model") not in ("plummer", "ensemble"):
+        raise ValueError("a custom workload is {'model': 'plummer', 'n': N, 'seed': S, 'eps': E} or "
+                         "{'model': 'ensemble', 'clusters': K, 'lo': N0, 'hi': N1}")
+    if isinstance(wl, dict) and wl.get("model") == "ensemble":
+        if c["checkpoint"] or c["resume"] or c["tuning"] or c["autotune"]:
+            raise ValueError("an ensemble run takes no checkpoint, resume or launch tuning")
+        if c["order"] not in (None, 6):
+            raise ValueError("ensembles run at order 6")
     if c["precision"] not in ("mixed", "fp64"):
         raise ValueError("precision must be 'mixed' or 'fp64'")
     if c["order"] is not None and c["order"] not in (4, 6, 8):
@@ -122,10 +131,53 @@ def save_checkpoint(path: str, ctx, w, cfg, t, e0, p0, pscale, blocks, inter, fp
                               "fingerprint": fp}))
 
 
+def _run_ensemble(c: dict, log, stream):
+    wl = c["workload"]
+    clusters = ics.ensemble(int(wl.get("clusters", 256)), int(wl.get("lo", 1024)), int(wl.get("hi", 32768)))
+    w0 = clusters[0]
+    dt_max = c["dt_max"] if c["dt_max"] is not None else w0.dt_max
+    t_end = c["t_end"] if c["t_end"] is not None else w0.t_end
+    probe = ics.Workload("ensemble", w0.m, w0.x, w0.v, w0.eps2, dt_max=dt_max, t_end=t_end)
+    outs = _steps(c, probe)
+    prec = nb.NB_MIXED if c["precision"] == "mixed" else nb.NB_FP64
+    sizes = [w.n for w in clusters]
+    b = nb.Batch(sizes, 6, math.sqrt(w0.eps2[0]), prec)
+    try:
+        if stream is not None:
+            b.set_stream(stream)
+        b.set_params(c["eta"] if c["eta"] is not None else w0.eta, c["eta_s"] if c["eta_s"] is not None else w0.eta_s,
+                     dt_max, c["dt_min"])
+        b.set_particles(np.concatenate([w.m for w in clusters]), np.concatenate([w.x for w in clusters]),
+                        np.concatenate([w.v for w in clusters]))
+        b.set_graph(int(c["graph_cycles"]))
+        ek, ep = b.energy()
+        e0 = ek + ep
+        cycles, inter, records = 0, 0, []
+        for t_out in outs:
+            t0 = time.perf_counter()
+            nc, ni = b.step_until(t_out)
+            el = time.perf_counter() - t0
+            cycles, inter = cycles + nc, inter + ni
+            ek, ep = b.energy()
+            de = np.abs((ek + ep - e0) / np.abs(e0))
+            rec = {"workload": f"ensemble_{len(sizes)}_clusters", "t": t_out, "cycles": cycles,
+                   "interactions": inter, "seconds": el, "interactions_per_s": ni / el if el > 0 else None,
+                   "dE_E_median": float(np.median(de)), "dE_E_worst": float(de.max())}
+            records.append(rec)
+            if log is not None:
+                log.write(json.dumps(rec) + "\n")
+                log.flush()
+        return records
+    finally:
+        b.close()
+
+
 def run(cfg: dict, log=None, stream=None):
     """Integrate as the configuration says; returns the list of output records
     (also written, one JSON line each, to the file object `log`)."""
     c = load_config(cfg)
+    if isinstance(c["workload"], dict) and c["workload"]["model"] == "ensemble":
+        return _run_ensemble(c, log, stream)
     w = build_workload(c)
     prec = nb.NB_MIXED if c["precision"] == "mixed" else nb.NB_FP64
     outs = _steps(c, w)

@@ -40,3 +40,12 @@ def test_run_outputs_checkpoints_and_bitwise_resume(tmp_path, precision, cycles)
     with pytest.raises(ValueError):
         run.run(dict(cfg, workload={"model": "plummer", "n": 700, "seed": 13, "eps": 1e-3},
                      resume=str(tmp_path / "a_last.npz"), checkpoint=None))
+
+
+def test_ensemble_run_reports_per_cluster_energy_errors():
+    cfg = {"workload": {"model": "ensemble", "clusters": 6, "lo": 256, "hi": 1024}, "t_end": 0.125,
+           "dt_out": 0.0625, "graph_cycles": 8}
+    recs = run.run(cfg)
+    assert [r["t"] for r in recs] == [0.0625, 0.125]
+    assert recs[-1]["cycles"] > recs[0]["cycles"] > 0
+    assert 0 <= recs[-1]["dE_E_median"] <= recs[-1]["dE_E_worst"] < 1e-3

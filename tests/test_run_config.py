@@ -30,3 +30,11 @@ def test_output_times_must_synchronise_every_particle(t_end, dt_out):
     w = run.build_workload(c)
     with pytest.raises(ValueError):
         run._steps(c, w)
+
+
+def test_ensemble_configuration_rules():
+    ens = {"model": "ensemble", "clusters": 4, "lo": 256, "hi": 512}
+    run.load_config({"workload": ens})
+    for extra in ({"checkpoint": "x"}, {"resume": "x"}, {"autotune": 2}, {"order": 8}):
+        with pytest.raises(ValueError):
+            run.load_config(dict({"workload": ens}, **extra))
