@@ -240,14 +240,15 @@ int nb_set_tuning(nb_ctx* ctx, int n_classes, const int32_t* ni, const int32_t* 
  * Synchronises.                                                            */
 int nb_selftest_wait(nb_ctx* ctx, double seconds);
 
-/* Self-check of the format conversions of the mixed corrector (the reading
- * of the mixed precision: FP32 values truncated toward zero from FP64, with
+/* Self-check of the format conversions of the mixed path (the reading of
+ * the mixed precision: FP32 values truncated toward zero from FP64, with
  * results below the normal float range flushed to zero and those from
  * |x| >= 2^128 taken to inf; FP32 widened exactly, subnormals flushed): the
- * corrector converts with the cvt instruction, the predictor with integer
- * arithmetic.  Compares the two forms bit for bit on n seeded inputs (any
- * bit pattern, and exponents across and at the edges of the float range;
- * NaN skipped); *mismatches = the count (0 when they agree).  Synchronises. */
+ * predictor and the corrector convert in integer arithmetic; this compares
+ * that form bit for bit with the hardware's cvt instruction on n seeded
+ * inputs (any bit pattern, and exponents across and at the edges of the
+ * float range; NaN skipped); *mismatches = the count (0 when they agree).
+ * Synchronises.                                                            */
 int nb_selftest_convert(nb_ctx* ctx, int64_t n, uint64_t seed, int64_t* mismatches);
 
 /* Force the j-split count of later nb_force calls (0 = automatic).         */

@@ -325,13 +325,11 @@ __device__ __forceinline__ double f32_to_f64(float f)
     return __longlong_as_double((long long)(sgn | ((unsigned long long)(e - 127 + 1023) << 52) | (mant << 29)));
 }
 
-// The same two conversions by the cvt instruction, for code that runs once
-// per particle on small blocks (the corrector), where the dozen integer
-// instructions of the forms above cost more in instruction fetch than one
-// conversion on the FP64 pipe: round toward zero with subnormal results and
-// inputs flushed, and |x| >= 2^128 -- which the rounding mode would clamp to
-// the largest float -- taken to inf as above, so both give the same bits
-// for every non-NaN input.
+// The same two conversions by the cvt instruction (on the FP64 pipe), the
+// reference that nb_selftest_convert checks the integer forms against: round
+// toward zero with subnormal results and inputs flushed, and |x| >= 2^128 --
+// which the rounding mode would clamp to the largest float -- taken to inf as
+// above, so both give the same bits for every non-NaN input.
 __device__ __forceinline__ float f64_to_f32_rz_cvt(double x)
 {
     float r;
@@ -959,9 +957,9 @@ __device__ __forceinline__ float norm3f(const float (&p)[3])
 // range) -- the same closed forms as correct_fp64 with h^k moved across, and
 // the criterion's ratio, which is h^(p-3) times the ratio of scaled norms.
 // The FP64 pipe (1/64 of the FP32 rate here) then does ~45 operations per
-// particle instead of ~500, plus the format conversions (cvt: one
-// instruction each; this code runs once per active particle, where
-// instruction fetch, not the pipe, sets the time of small blocks).  Returns false, with nothing usable written, if a
+// particle instead of ~500; the format conversions run on the integer pipe
+// (with cvt on the FP64 pipe a full block of 2^20 took 235 instead of 201 us,
+// and small blocks in graph replays were no faster).  Returns false, with nothing usable written, if a
 // float value is not finite (a derivative beyond the float range); the
 // caller then takes correct_fp64.
 template <int ORDER>
@@ -971,19 +969,19 @@ __device__ __forceinline__ bool correct_mixed(const double (&L)[4][3], double (&
                                               double (&x1)[3], double (&v1)[3], double& lim)
 {
     constexpr int MM = ORDER / 2;
-    const float u = f64_to_f32_rz_cvt(h);
+    const float u = f64_to_f32_rz(h);
     if (!(u > 0.0f)) return false;  // h below the float range
     // scaled inputs: ls[k] = L[k] h^k, rs[k] = H[k] h^k (k < MM), d0 = a1 - a0
     float ls[4][3], rs[4][3], d0[3];
     bool ok = true;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        d0[c] = f64_to_f32_rz_cvt(H[0][c] - L[0][c]);
+        d0[c] = f64_to_f32_rz(H[0][c] - L[0][c]);
         float uk = 1.0f;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            ls[k][c] = f64_to_f32_rz_cvt(L[k][c]) * uk;
-            rs[k][c] = k < MM ? f64_to_f32_rz_cvt(H[k][c]) * uk : 0.0f;
+            ls[k][c] = f64_to_f32_rz(L[k][c]) * uk;
+            rs[k][c] = k < MM ? f64_to_f32_rz(H[k][c]) * uk : 0.0f;
             ok = ok && isfinite(ls[k][c]) && isfinite(rs[k][c]);
             uk *= u;
         }
@@ -1041,10 +1039,10 @@ __device__ __forceinline__ bool correct_mixed(const double (&L)[4][3], double (&
             nl[k] = norm3f(ls[k]);
             nr[k] = k < MM ? S[k] : 0.0f;
         }
-        const float kappa = nr[0] > 0.0f ? fmaxf(1.0f, f64_to_f32_rz_cvt(bacc) / nr[0]) : 1.0f;
+        const float kappa = nr[0] > 0.0f ? fmaxf(1.0f, f64_to_f32_rz(bacc) / nr[0]) : 1.0f;
         float e[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) e[k] = f64_to_f32_rz_cvt(ne.e[k]) * kappa;
+        for (int k = 0; k < 4; ++k) e[k] = f64_to_f32_rz(ne.e[k]) * kappa;
         const float A = e[0] * (nl[0] + nr[0]);
         float N[8];
         if (ORDER == 4) {
@@ -1070,7 +1068,7 @@ __device__ __forceinline__ bool correct_mixed(const double (&L)[4][3], double (&
     // the criterion as a multiple f of h, capped at 2 (the step may at most double)
     float f;
     {
-        const float etaf = f64_to_f32_rz_cvt(eta);
+        const float etaf = f64_to_f32_rz(eta);
         if (ORDER == 4) {
             const float num = S[0] * S[2] + S[1] * S[1], den = S[1] * S[3] + S[2] * S[2];
             f = den > 0.0f ? sqrtf(etaf * (num / den)) : INFINITY;
@@ -1083,7 +1081,7 @@ __device__ __forceinline__ bool correct_mixed(const double (&L)[4][3], double (&
         if (!(f <= 2.0f)) f = f == f ? 2.0f : f;  // inf -> 2; NaN stays
     }
     if (!(f == f)) return false;
-    lim = h * f32_to_f64_cvt(f);
+    lim = h * f32_to_f64(f);
     // H[k] = T[k] / h^k, and the corrected state
     double ihk = 1.0;
 #pragma unroll
@@ -1091,13 +1089,13 @@ __device__ __forceinline__ bool correct_mixed(const double (&L)[4][3], double (&
         ihk *= ih;
         if (k >= MM)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) H[k][c] = f32_to_f64_cvt(T[k][c]) * ihk;
+            for (int c = 0; c < 3; ++c) H[k][c] = f32_to_f64(T[k][c]) * ihk;
     }
     const double hh = 0.5 * h;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        v1[c] = fma(hh, L[0][c] + H[0][c], v0[c]) + f32_to_f64_cvt(tv[c]);
-        x1[c] = fma(hh, v0[c] + v1[c], x0[c]) + f32_to_f64_cvt(tx[c]);
+        v1[c] = fma(hh, L[0][c] + H[0][c], v0[c]) + f32_to_f64(tv[c]);
+        x1[c] = fma(hh, v0[c] + v1[c], x0[c]) + f32_to_f64(tx[c]);
     }
     return true;
 }
@@ -1438,7 +1436,7 @@ cudaError_t launch_state_in(nb_ctx* c)
     return cudaGetLastError();
 }
 
-// Self-check of the cvt conversions against the integer forms: n seeded
+// Self-check of the integer conversions against cvt: n seeded
 // inputs (splitmix64 of seed + k) -- every fourth any bit pattern, the others
 // doubles with exponents across and at the edges of the float range -- and
 // the widening of any float bit pattern; NaN inputs are skipped (NaN stays

@@ -252,7 +252,7 @@ class NBody:
         return int(self._L.nb_selftest_wait(self._h, float(seconds)))
 
     def selftest_convert(self, n: int = 1 << 24, seed: int = 1) -> int:
-        """Mismatching bits between the corrector's cvt conversions and the integer forms over n inputs."""
+        """Mismatching bits between the integer f64 <-> f32 conversions and the hardware's cvt over n inputs."""
         m = C.c_int64()
         self._check(self._L.nb_selftest_convert(self._h, int(n), int(seed), C.byref(m)))
         return m.value

@@ -664,9 +664,9 @@ def test_bounded_wait_runs_out_and_reports_a_timeout():
     ctx.close()
 
 
-def test_corrector_conversions_match_the_integer_forms():
-    # The mixed corrector converts with cvt (rz, ftz, inf beyond 2^128), the
-    # predictor with integer arithmetic; both must give the same bits.
+def test_integer_conversions_match_the_hardware_cvt():
+    # The mixed predictor and corrector convert f64 <-> f32 in integer
+    # arithmetic; it must give the bits of cvt (rz, ftz, inf beyond 2^128).
     m, x, v, eps2 = _system(256, 8, "plummer")
     ctx = make_ctx(m, x, v, eps2, 6, nb.NB_MIXED)
     assert ctx.selftest_convert(1 << 24, 12345) == 0
