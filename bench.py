@@ -47,10 +47,10 @@ SM_COUNT, FP32_LANES, SM_MAX_MHZ = 148, 128, 2032.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 76.96, FMA = 2 flops
 FP64_PEAK_TFLOPS = 1.25                                                     # nominal dense FP64
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one mixed force
-# launch over the whole nucleus system (N_act = N = 2^20 + 2, one j-split), from
+# launch over the whole nucleus system (N_act = N = 2^20 + 2, 13 j-splits), from
 # a one-pass ncu capture of that launch; the capture's command and figures are
 # in profiles/force_mixed_order6_nucleus_n1048578.md.
-FORCE_TRAFFIC_BYTES = {("nucleus_plummer_n1048576_2bh", "mixed"): 1.049e9 + 99.93e6}
+FORCE_TRAFFIC_BYTES = {("nucleus_plummer_n1048576_2bh", "mixed"): 911.70e6 + 1163.57e6}
 
 
 def parse():

@@ -1073,7 +1073,7 @@ __global__ void __launch_bounds__(FORCE_NT) k_force_fp64(const double2* __restri
 
 // ------------------------------------------------------- device-driven cycle
 // Launch shape from the scheduler's n_act, chosen on the device with the
-// host's rule (makespan ceil(it*js/slots)/js, ties within 1% to fewer splits,
+// host's rule (makespan ceil(it*js/slots)/js, ties within 0.5% to fewer splits,
 // capped by the partial-sum buffer); an active set past t_end makes the
 // cycle idle.
 

@@ -77,14 +77,21 @@ __host__ __device__ constexpr int pot_comp(int order) { return order == 0 ? 0 : 
 // ceil(it*s/slots)/s of the one-split time.  For w waves the best s is the
 // largest with it*s <= w*slots, so only those candidates (in increasing s,
 // clamped to s_max) are scored; a candidate replaces the running best only
-// when its span is over 1% shorter.  s_max bounds s by the j tiles, the
-// partial buffer (cap_splits) and about four waves' worth of splits.
+// when its span is over 0.5% shorter.  s_max bounds s by the j tiles, the
+// partial buffer (cap_splits) and about four waves' worth of splits, but
+// allows 16 at any size: a large block split 16 ways ran faster than the
+// wave count predicts (full blocks of 2^20, 2^18 and 2^16 particles 1.5-1.8 %
+// faster than with the 1, 4 and 9 splits of a four-wave bound and 1 % ties;
+// shorter j ranges per split keep the concurrent CTAs on fewer j tiles and
+// even out the last wave).
 // Integer arithmetic only: the host and the device-driven gate agree exactly.
+constexpr long long SPLIT_FLOOR = 16;
 __host__ __device__ inline int makespan_split(int it, int ntiles, int slots, long long cap_splits)
 {
     if (it < 1) it = 1;
     if (slots < 1) slots = 1;
     long long s_max = 4LL * slots / it + 4;
+    if (s_max < SPLIT_FLOOR) s_max = SPLIT_FLOOR;
     if (s_max > ntiles) s_max = ntiles;
     if (s_max > cap_splits) s_max = cap_splits;
     if (s_max <= 1) return 1;
@@ -95,8 +102,8 @@ __host__ __device__ inline int makespan_split(int it, int ntiles, int slots, lon
         if (s > s_max) s = s_max;
         if (s <= best_s) continue;
         const long long ws = ((long long)it * s + slots - 1) / slots;
-        // ws / s < 0.99 * best_w / best_s
-        if (100 * ws * best_s < 99 * best_w * s) {
+        // ws / s < 0.995 * best_w / best_s
+        if (1000 * ws * best_s < 995 * best_w * s) {
             best_s = s;
             best_w = ws;
         }

@@ -67,10 +67,10 @@ def harness(tmp_path_factory):
 
 
 def _s_max(it, ntiles, slots, cap):
-    return max(1, min(4 * slots // it + 4, ntiles, cap))
+    return max(1, min(max(4 * slots // it + 4, 16), ntiles, cap))
 
 
-def test_makespan_split_within_one_percent_of_brute_force(harness):
+def test_makespan_split_within_half_a_percent_of_brute_force(harness):
     rng = np.random.default_rng(11)
     cases = []
     for slots in (148, 444, 592):            # SMs x resident CTAs of the force variants
@@ -86,7 +86,7 @@ def test_makespan_split_within_one_percent_of_brute_force(harness):
         assert 1 <= s <= smax, (it, nt, sl, cap, s)
         span = lambda k: -(-it * k // sl) / k  # noqa: E731  waves x (1/k) of the one-split time
         best = min(span(k) for k in range(1, smax + 1))
-        assert span(s) <= best / 0.99 * (1 + 1e-12), (it, nt, sl, cap, s, span(s), best)
+        assert span(s) <= best / 0.995 * (1 + 1e-12), (it, nt, sl, cap, s, span(s), best)
 
 
 def test_eps2_threshold_rounds_toward_zero(harness):
