@@ -424,10 +424,11 @@ int nb_create(nb_ctx** out, int64_t n, int order, double eps)
     c->red_len = 4 * c->sm_count + 8;
     if (c->red_len < 2 * c->sm_count) c->red_len = 2 * c->sm_count;
     // j-split partial sums: room for the 16 splits the split rule allows a
-    // full block (SPLIT_FLOOR; 1.5 GB at 2^20, order 6), and for the many
-    // splits of small blocks
+    // full block (SPLIT_FLOOR; 1.5 GB at 2^20, order 6) up to 2^21 particles,
+    // for a full block of any size, and for the many splits of small blocks
     const size_t span = (size_t)2 * 16 * c->sm_count * FORCE_NT;
-    c->partial_cap = (size_t)nc * std::max((size_t)SPLIT_FLOOR * (size_t)n, span);
+    const size_t floor_rows = std::min((size_t)SPLIT_FLOOR * (size_t)n, (size_t)SPLIT_FLOOR << 21);
+    c->partial_cap = (size_t)nc * std::max({floor_rows, (size_t)n, span});
     if ((rc = dalloc(c, &c->m, np)) || (rc = dalloc(c, &c->eps2, np)) || (rc = dalloc(c, &c->x, 3 * np)) ||
         (rc = dalloc(c, &c->v, 3 * np)) || (rc = dalloc(c, &c->d, 18 * np)) || (rc = dalloc(c, &c->t, np)) ||
         (rc = dalloc(c, &c->dt, np)) || (rc = dalloc(c, &c->pot, np)) ||
