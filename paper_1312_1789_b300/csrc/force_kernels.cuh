@@ -203,12 +203,12 @@ __device__ __forceinline__ void pair_mixed(const float4 w0, const float4 w1, con
         acc[8] = fmaf(q, fmaf(c3, dz, fmaf(c2, dvz, daz)), acc[8]);
         if (ORDER >= 8) {
             const float dkx = w4.x - I.i4.x, dky = w4.y - I.i4.y, dkz = w4.z - I.i4.z;
-            // u3 = -3 u; crackle: c4 = -9 alpha, c5 = 45 alpha^2 - 9 w,
+            // u3 = -3 u; crackle: c4 = -9 alpha, c5 = 45 alpha^2 - 9 w = 3 c3,
             // c6 = -105 alpha^3 + 45 alpha w - 3 u
             const float u3 =
                 fmaf(3.0f, fmaf(dvx, dax, fmaf(dvy, day, dvz * daz)), fmaf(dx, dkx, fmaf(dy, dky, dz * dkz))) * r3;
             const float c4 = 3.0f * a3;
-            const float c5 = fmaf(5.0f * a3, a3, 3.0f * ww3);
+            const float c5 = 3.0f * c3;  // 5 a3^2 + 3 ww3
             const float c6 = fmaf(a3, fmaf((35.0f / 9.0f) * a3, a3, 5.0f * ww3), u3);
             acc[9] = fmaf(q, fmaf(c6, dx, fmaf(c5, dvx, fmaf(c4, dax, dkx))), acc[9]);
             acc[10] = fmaf(q, fmaf(c6, dy, fmaf(c5, dvy, fmaf(c4, day, dky))), acc[10]);
@@ -325,7 +325,7 @@ __device__ __forceinline__ void pair_mixed_x2j(const JMixed2& J, const IMixed2& 
                            __ffma2_rn(dx, dkx, __ffma2_rn(dy, dky, __fmul2_rn(dz, dkz)))),
                 r3);
             const float2 c4 = __fmul2_rn(bc2(3.0f), a3);
-            const float2 c5 = __ffma2_rn(__fmul2_rn(bc2(5.0f), a3), a3, __fmul2_rn(bc2(3.0f), ww3));
+            const float2 c5 = __fmul2_rn(bc2(3.0f), c3);  // 5 a3^2 + 3 ww3
             const float2 c6 =
                 __ffma2_rn(a3, __ffma2_rn(__fmul2_rn(bc2(35.0f / 9.0f), a3), a3, __fmul2_rn(bc2(5.0f), ww3)), u3);
             acc[9] = __ffma2_rn(q, __ffma2_rn(c6, dx, __ffma2_rn(c5, dvx, __ffma2_rn(c4, dax, dkx))), acc[9]);
