@@ -402,8 +402,8 @@ int nb_batch_set_graph(nb_batch* b, int cycles);
 int nb_batch_set_waves(nb_batch* b, int waves);
 int nb_batch_get_waves(nb_batch* b, int* waves);
 
-/* Autotuner of the force plan (the benchmark spec: autotuned tiles for the
- * ensemble): for each of the next `cycles` cycles, the force and split
+/* Autotuner of the ensemble's force plan (how its work is cut into items):
+ * for each of the next `cycles` cycles, the force and split
  * reduction are timed (CUDA events, best of reps) with the plans of 1, 2, 4
  * and 8 waves, then the cycle is completed with the wave count in use; the
  * count with the least total time is kept if it beats 4 by 3 %.  The tuning
