@@ -48,8 +48,8 @@ FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 76.96
 FP64_PEAK_TFLOPS = 1.25                                                     # nominal dense FP64
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one mixed force
 # launch over the whole nucleus system (N_act = N = 2^20 + 2, 13 j-splits), from
-# a one-pass ncu capture of that launch; the capture's command and figures are
-# in profiles/force_mixed_order6_nucleus_n1048578.md.
+# a one-pass ncu capture of that launch (the command is the profiling case
+# `bench.py --profile-force --n-act 1048578 --repeat 1`).
 FORCE_TRAFFIC_BYTES = {("nucleus_plummer_n1048576_2bh", "mixed"): 911.70e6 + 1163.57e6}
 
 
