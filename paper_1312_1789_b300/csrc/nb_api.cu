@@ -946,6 +946,7 @@ static int next_block_predicted(nb_ctx* c, double* tb, int64_t* na)
     c->have_sched = 1;
     c->pred_prec = c->prec;
     c->have_pred = 1;
+    c->pred_ranged = 0;  // the fused predictor covers every particle
     c->t_pred = c->sched_t;
     c->have_force = 0;
     *tb = c->sched_t;
