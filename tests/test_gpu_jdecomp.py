@@ -94,6 +94,12 @@ def test_ranged_prediction_covers_the_share_and_the_block_only():
     c.set_jrange(0, 128)
     with pytest.raises(nb.NBError):
         c.force()
+    # back to the whole range: a block step predicts every particle again, and
+    # an explicit list is accepted afterwards
+    c.set_jrange(0, 0)
+    c.block_step()
+    c.predict(c.next_block()[0])
+    c.force(np.arange(n, dtype=np.int32))
     c.close()
     full.close()
 
