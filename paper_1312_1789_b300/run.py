@@ -124,6 +124,9 @@ def fingerprint(w: ics.Workload) -> str:
 
 
 def save_checkpoint(path: str, ctx, w, cfg, t, e0, p0, pscale, blocks, inter, fp):
+    d = os.path.dirname(path)
+    if d:
+        os.makedirs(d, exist_ok=True)
     S = ctx.get_state()
     np.savez(path, x=S["x"], v=S["v"], d=S["d"], t=S["t"], dt=S["dt"],
              meta=json.dumps({"config": cfg, "time": t, "e0": e0, "p0": [float(q) for q in p0], "pscale": pscale,

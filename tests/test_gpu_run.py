@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 @pytest.mark.parametrize("precision,cycles", [("mixed", 8), ("fp64", 0)])
 def test_run_outputs_checkpoints_and_bitwise_resume(tmp_path, precision, cycles):
     cfg = {"workload": {"model": "plummer", "n": 700, "seed": 12, "eps": 1e-3}, "precision": precision,
-           "t_end": 0.25, "dt_out": 0.0625, "graph_cycles": cycles, "checkpoint": str(tmp_path / "a")}
+           "t_end": 0.25, "dt_out": 0.0625, "graph_cycles": cycles, "checkpoint": str(tmp_path / "ck" / "a")}
     log = io.StringIO()
     recs = run.run(cfg, log)
     assert [r["t"] for r in recs] == [0.0625, 0.125, 0.1875, 0.25]
@@ -26,9 +26,9 @@ def test_run_outputs_checkpoints_and_bitwise_resume(tmp_path, precision, cycles)
         assert abs(r["dE_E"]) < 1e-4 and r["dP_rel"] < 1e-5
         assert sum(r["nact_histogram"].values()) > 0
     assert recs[-1]["blocks"] == sum(sum(r["nact_histogram"].values()) for r in recs)
-    full = np.load(tmp_path / "a_last.npz")
+    full = np.load(tmp_path / "ck" / "a_last.npz")
     # resume from the second output: the same end state and counts
-    cfg2 = dict(cfg, checkpoint=str(tmp_path / "b"), resume=str(tmp_path / "a_t0.125.npz"))
+    cfg2 = dict(cfg, checkpoint=str(tmp_path / "b"), resume=str(tmp_path / "ck" / "a_t0.125.npz"))
     recs2 = run.run(cfg2)
     assert [r["t"] for r in recs2] == [0.1875, 0.25]
     assert recs2[-1]["blocks"] == recs[-1]["blocks"] and recs2[-1]["interactions"] == recs[-1]["interactions"]
@@ -39,7 +39,7 @@ def test_run_outputs_checkpoints_and_bitwise_resume(tmp_path, precision, cycles)
     # a checkpoint of another workload is refused
     with pytest.raises(ValueError):
         run.run(dict(cfg, workload={"model": "plummer", "n": 700, "seed": 13, "eps": 1e-3},
-                     resume=str(tmp_path / "a_last.npz"), checkpoint=None))
+                     resume=str(tmp_path / "ck" / "a_last.npz"), checkpoint=None))
 
 
 def test_ensemble_run_reports_per_cluster_energy_errors():
