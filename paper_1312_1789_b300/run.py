@@ -123,11 +123,11 @@ def fingerprint(w: ics.Workload) -> str:
     return h.hexdigest()
 
 
-def save_checkpoint(path: str, ctx, w, cfg, t, e0, p0, pscale, blocks, inter, fp):
+def save_checkpoint(path: str, S, w, cfg, t, e0, p0, pscale, blocks, inter, fp):
+    """Write the state S (NBody.get_state) and the run's bookkeeping to path."""
     d = os.path.dirname(path)
     if d:
         os.makedirs(d, exist_ok=True)
-    S = ctx.get_state()
     np.savez(path, x=S["x"], v=S["v"], d=S["d"], t=S["t"], dt=S["dt"],
              meta=json.dumps({"config": cfg, "time": t, "e0": e0, "p0": [float(q) for q in p0], "pscale": pscale,
                               "blocks": blocks, "interactions": inter, "workload": w.name,
@@ -229,7 +229,7 @@ def run(cfg: dict, log=None, stream=None):
                    "nact_histogram": {f"{1 << k}-{(2 << k) - 1}": int(h[k]) for k in np.nonzero(h)[0]}}
             if c["checkpoint"]:
                 for path in (f"{c['checkpoint']}_t{t_out:.10g}.npz", f"{c['checkpoint']}_last.npz"):
-                    save_checkpoint(path, ctx, w, cfg, t_out, e0, p0, pscale, blocks, inter, fp)
+                    save_checkpoint(path, S, w, cfg, t_out, e0, p0, pscale, blocks, inter, fp)
                 rec["checkpoint"] = f"{c['checkpoint']}_last.npz"
             records.append(rec)
             if log is not None:
